@@ -1,0 +1,357 @@
+"""Gauge-invariant PEPS in gauge canonical form and its contraction (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Ansatz (main text, "Gauge-invariant TNS", Eqs. 6-7): every vertex carries a
+matter tensor A^p_{l r d u}; virtual index j on a leg has charge q(j) in Z_N,
+and A is non-zero only where p + q(l) + q(d) - q(r) - q(u) = Q_x (mod N).
+Gauge tensors B^n_{l r} on the links are non-zero only for n = q(l) = q(r).
+Bond dimension D = sum_k D_k; here every sector has the same degeneracy D_k.
+
+Gauge canonical form (Eqs. 8-9): after A -> A X, B -> X^{-1} B with
+X = (+)_k B^[k], every B becomes delta_{lr} delta_{n,q(l)} delta_{n,q(r)}; only
+the A tensors carry parameters.
+
+Sampled network (Sec. S-2, Eq. S5): a physical configuration s = (n, p)
+selects, at every vertex, the single block of A whose leg charges are the
+electric fields on the four adjacent links; B is absent, and every bond of the
+resulting single-layer network has dimension D_k.  Open-boundary legs have
+dimension 1 and charge 0.
+
+Parameter layout (interface shared with the CUDA library; float64/complex128
+here).  Vertices in row-major order v = y*Lx + x.  At a vertex the existing
+legs, in the order (l, r, d, u), are legs[0..k-1].  The block index is the
+mixed-radix number (p, n_legs[0], ..., n_legs[k-2]) with p most significant
+and radix N for charges (P = 2 for matter, 1 without); the last existing leg's
+charge is fixed by Eq. (1).  A block holds D_k^k entries ordered
+[i_l][i_r][i_d][i_u] over existing legs (row-major).  Blocks of a vertex are
+contiguous; vertices follow one another.
+
+Boundary-MPS contraction (Sec. S-2: "SVD or variational compression"; main
+text, cost paragraph: cutoff chi).  Reading used here (the paper gives no more
+detail): rows are absorbed bottom-up into an MPS; after each row the MPS is
+left-canonicalised by QR (left to right), then swept right to left with an SVD
+on every bond keeping the chi largest singular values, and normalised with the
+norm accumulated in a log-scale.  Top environments are built the same way
+from the top row downward.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from .lattice import Lattice
+
+LEG_SIGN = (+1, -1, +1, -1)  # l, r, d, u in Eq. (1)
+
+
+@dataclass
+class VertexLayout:
+    legs: tuple          # indices into (l, r, d, u) of the existing legs
+    dims: tuple          # (Dl, Dr, Dd, Du) with 1 for missing legs
+    n_blocks: int
+    block_size: int
+    offset: int
+
+
+def layout(lat: Lattice, Dk: int):
+    """Per-vertex block layout and the total parameter count."""
+    P = 2 if lat.matter else 1
+    verts = []
+    off = 0
+    for y in range(lat.Ly):
+        for x in range(lat.Lx):
+            has = lat.has_legs(x, y)
+            legs = tuple(i for i in range(4) if has[i])
+            k = len(legs)
+            dims = tuple(Dk if has[i] else 1 for i in range(4))
+            nb = P * lat.N ** (k - 1)
+            bs = Dk ** k
+            verts.append(VertexLayout(legs, dims, nb, bs, off))
+            off += nb * bs
+    return verts, off
+
+
+def block_id(lat: Lattice, vl: VertexLayout, x, y, p, charges):
+    """Block index for matter value p and leg charges (n_l, n_r, n_d, n_u).
+
+    Returns -1 when the charges violate Eq. (1) at this vertex (or a missing
+    leg carries a non-zero charge), i.e. when A has no such block.
+    """
+    for i in range(4):
+        if i not in vl.legs and charges[i] != 0:
+            return -1
+    tot = p + sum(LEG_SIGN[i] * charges[i] for i in range(4))
+    if (tot - lat.Q[y, x]) % lat.N:
+        return -1
+    bid = p
+    for i in vl.legs[:-1]:
+        bid = bid * lat.N + charges[i] % lat.N
+    return bid
+
+
+class GIPEPS:
+    """A GCF gauge-invariant PEPS: the flat parameter vector plus its layout."""
+
+    def __init__(self, lat: Lattice, Dk: int, params: np.ndarray):
+        self.lat = lat
+        self.Dk = Dk
+        self.verts, self.n_params = layout(lat, Dk)
+        params = np.asarray(params)
+        if params.shape != (self.n_params,):
+            raise ValueError(f"expected {self.n_params} parameters, got {params.shape}")
+        self.params = params.astype(np.complex128 if np.iscomplexobj(params) else np.float64)
+
+    def vertex(self, x, y) -> VertexLayout:
+        return self.verts[y * self.lat.Lx + x]
+
+    def block(self, x, y, bid):
+        vl = self.vertex(x, y)
+        a = vl.offset + bid * vl.block_size
+        return self.params[a:a + vl.block_size].reshape(vl.dims)
+
+    def selected_block(self, cfg, x, y):
+        """(block id, tensor A~_x) selected by configuration cfg (Eq. S5).
+
+        Returns (-1, None) if the configuration violates Eq. (1) at (x, y).
+        """
+        lat = self.lat
+        p = int(cfg[lat.pi(x, y)])
+        if p not in ((0, 1) if lat.matter else (0,)):
+            return -1, None
+        ch = lat.leg_values(cfg, x, y)
+        bid = block_id(lat, self.vertex(x, y), x, y, p, ch)
+        if bid < 0:
+            return -1, None
+        return bid, self.block(x, y, bid)
+
+    def sampled_network(self, cfg):
+        """tensors[y][x] = A~_x with shape (Dl, Dr, Dd, Du), or None if unphysical."""
+        rows = []
+        for y in range(self.lat.Ly):
+            row = []
+            for x in range(self.lat.Lx):
+                bid, t = self.selected_block(cfg, x, y)
+                if bid < 0:
+                    return None
+                row.append(t)
+            rows.append(row)
+        return rows
+
+    # ---- dense (non-sampled) tensors for definition-level checks --------
+    def dense_A(self, x, y):
+        """Full A^p_{lrdu}: shape (P, Dl', Dr', Dd', Du') with D' = N*D_k on
+        existing legs (index j has charge j // D_k) and 1 on missing legs."""
+        lat, Dk = self.lat, self.Dk
+        vl = self.vertex(x, y)
+        P = 2 if lat.matter else 1
+        full = tuple(lat.N * Dk if i in vl.legs else 1 for i in range(4))
+        A = np.zeros((P,) + full, dtype=self.params.dtype)
+        ranges = [range(lat.N) if i in vl.legs else range(1) for i in range(4)]
+        for p in range(P):
+            for ch in np.ndindex(*[len(r) for r in ranges]):
+                bid = block_id(lat, vl, x, y, p, ch)
+                if bid < 0:
+                    continue
+                sl = tuple(slice(ch[i] * Dk, (ch[i] + 1) * Dk) if i in vl.legs else slice(0, 1)
+                           for i in range(4))
+                A[(p,) + sl] = self.block(x, y, bid)
+        return A
+
+
+# ---------------------------------------------------------------------------
+# Full (double-index) network with explicit B tensors: the definition of the
+# amplitude <s|Psi> before the GCF / sampling simplifications.
+# ---------------------------------------------------------------------------
+
+def gcf_link_tensor(N, Dk):
+    """B^n_{lr} in gauge canonical form, Eq. (9): shape (N, N*Dk, N*Dk)."""
+    D = N * Dk
+    B = np.zeros((N, D, D))
+    for n in range(N):
+        for i in range(Dk):
+            B[n, n * Dk + i, n * Dk + i] = 1.0
+    return B
+
+
+def general_link_tensor(blocks, N, Dk):
+    """B^n_{lr} = calB^n_{lr} delta_{n,q(l)} delta_{n,q(r)}, Eq. (7), from
+    blocks[n] of shape (Dk, Dk)."""
+    D = N * Dk
+    B = np.zeros((N, D, D), dtype=np.result_type(*blocks))
+    for n in range(N):
+        B[n, n * Dk:(n + 1) * Dk, n * Dk:(n + 1) * Dk] = blocks[n]
+    return B
+
+
+def full_amplitude(lat: Lattice, A, Bh, Bv, cfg):
+    """<s|Psi> of the GI-PEPS with matter tensors A[y][x] (dense, shape
+    (P, l, r, d, u)) and link tensors Bh[y][x], Bv[y][x] (shape (N, D, D)),
+    by direct contraction of every virtual index.  Defined for any integer
+    configuration, physical or not."""
+    Lx, Ly = lat.Lx, lat.Ly
+    # Build the projected single-layer network with double-size bonds: link
+    # tensor matrices are absorbed into the tensor on their left / below.
+    T = []
+    for y in range(Ly):
+        row = []
+        for x in range(Lx):
+            p = int(cfg[lat.pi(x, y)])
+            t = A[y][x][p]
+            if x < Lx - 1:
+                n = int(cfg[lat.hi(x, y)])
+                t = np.einsum("lrdu,rs->lsdu", t, Bh[y][x][n])
+            if y < Ly - 1:
+                n = int(cfg[lat.vi(x, y)])
+                t = np.einsum("lrdu,uv->lrdv", t, Bv[y][x][n])
+            row.append(t)
+        T.append(row)
+    return contract_exact(T)
+
+
+# ---------------------------------------------------------------------------
+# Exact contraction of a single-layer network (the plain definition).
+# ---------------------------------------------------------------------------
+
+def contract_exact(T):
+    """Sum over all virtual indices of prod_x T[y][x][l, r, d, u].
+
+    Row by row on the full vector over the up-legs of the rows absorbed so far
+    (no truncation).  Exponential in Lx: small lattices only.
+    """
+    Ly, Lx = len(T), len(T[0])
+    vec = np.ones((1,) * Lx)  # down-legs of row 0 all have dimension 1
+    for y in range(Ly):
+        # carry t with axes (h, u_0..u_{x-1}, d_x..d_{Lx-1})
+        t = vec[None, ...]
+        for x in range(Lx):
+            W = T[y][x]
+            # contract h (axis 0) and d_x (axis 1 + x) with W[l, r, d, u]
+            t = np.tensordot(t, W, axes=([0, 1 + x], [0, 2]))
+            # now axes: (u_0..u_{x-1}, d_{x+1}..d_{Lx-1}, r, u_x)
+            nd = t.ndim
+            order = [nd - 2] + list(range(x)) + [nd - 1] + list(range(x, nd - 2))
+            t = np.transpose(t, order)
+        vec = t[0]  # right-most horizontal leg has dimension 1
+    return complex(vec.reshape(-1)[0]) if np.iscomplexobj(vec) else float(vec.reshape(-1)[0])
+
+
+# ---------------------------------------------------------------------------
+# Boundary MPS (Sec. S-2; cutoff chi from the main-text cost paragraph).
+# MPS site tensors have shape (left bond, physical, right bond).
+# ---------------------------------------------------------------------------
+
+def trivial_mps(Lx, dtype=np.float64):
+    return [np.ones((1, 1, 1), dtype=dtype) for _ in range(Lx)]
+
+
+def absorb(mps, row):
+    """Apply one PEPS row (tensors W[l, r, d, u]) to an MPS whose physical legs
+    are the d legs: M'[(a,l), u, (b,r)] = sum_d M[a, d, b] W[l, r, d, u]."""
+    out = []
+    for M, W in zip(mps, row):
+        a, _, b = M.shape
+        l, r, _, u = W.shape
+        X = np.einsum("adb,lrdu->alubr", M, W)
+        out.append(X.reshape(a * l, u, b * r))
+    return out
+
+
+def flip_row(row):
+    """Swap the d and u legs so a row can be absorbed from above."""
+    return [np.transpose(W, (0, 1, 3, 2)) for W in row]
+
+
+def compress(mps, chi):
+    """SVD compression of an MPS to bond dimension <= chi, normalised.
+
+    1. QR left to right (left-canonical sites 0..L-2);
+    2. right to left: SVD of each site as (left bond) x (phys, right bond),
+       keep the chi largest singular values, push U S into the left
+       neighbour;
+    3. divide the first site by the state norm.
+    Returns (mps, log_norm); the input state equals exp(log_norm) * output
+    (up to the discarded weight).
+    """
+    mps = [m.copy() for m in mps]
+    L = len(mps)
+    for i in range(L - 1):
+        a, d, b = mps[i].shape
+        Qm, R = np.linalg.qr(mps[i].reshape(a * d, b))
+        k = Qm.shape[1]
+        mps[i] = Qm.reshape(a, d, k)
+        mps[i + 1] = np.tensordot(R, mps[i + 1], axes=(1, 0))
+    for i in range(L - 1, 0, -1):
+        a, d, b = mps[i].shape
+        U, S, Vh = np.linalg.svd(mps[i].reshape(a, d * b), full_matrices=False)
+        k = min(chi, len(S))
+        mps[i] = Vh[:k].reshape(k, d, b)
+        mps[i - 1] = np.tensordot(mps[i - 1], U[:, :k] * S[:k], axes=(2, 0))
+    nrm = np.linalg.norm(mps[0])
+    if nrm == 0.0:
+        return mps, -np.inf
+    mps[0] = mps[0] / nrm
+    return mps, float(np.log(nrm))
+
+
+def bottom_envs(rows, chi):
+    """B[r] (r = -1 .. Ly-1) as (mps, log_scale): rows 0..r absorbed bottom-up.
+
+    Returned as a dict keyed by r; B[-1] is the trivial MPS with log-scale 0.
+    """
+    Lx = len(rows[0])
+    dt = np.result_type(*[w.dtype for w in rows[0]])
+    env = {-1: (trivial_mps(Lx, dt), 0.0)}
+    for r in range(len(rows)):
+        m, s = env[r - 1]
+        m2, ds = compress(absorb(m, rows[r]), chi)
+        env[r] = (m2, s + ds)
+    return env
+
+
+def top_envs(rows, chi):
+    """T[r] (r = Ly .. 0): rows r..Ly-1 absorbed top-down; physical legs are
+    the down legs of row r.  T[Ly] is trivial."""
+    Ly, Lx = len(rows), len(rows[0])
+    dt = np.result_type(*[w.dtype for w in rows[0]])
+    env = {Ly: (trivial_mps(Lx, dt), 0.0)}
+    for r in range(Ly - 1, -1, -1):
+        m, s = env[r + 1]
+        m2, ds = compress(absorb(m, flip_row(rows[r])), chi)
+        env[r] = (m2, s + ds)
+    return env
+
+
+def contract_row(Bm, row, Tm):
+    """<B| row |T> for one PEPS row between two MPS (3 layers), exact."""
+    E = np.ones((1, 1, 1))
+    for Bs, W, Ts in zip(Bm, row, Tm):
+        # E[a, l, b] Bs[a, d, a'] W[l, r, d, u] Ts[b, u, b']
+        E = np.einsum("alb,adA,lrdu,buB->ArB", E, Bs, W, Ts)
+    return E.reshape(-1)[0]
+
+
+def contract_strip(Bm, row1, row2, Tm):
+    """<B| row1 row2 |T> for two adjacent rows between two MPS (4 layers), exact."""
+    E = np.ones((1, 1, 1, 1))
+    for Bs, W1, W2, Ts in zip(Bm, row1, row2, Tm):
+        # E[a,i,j,b] Bs[a,d,A] W1[i,I,d,m] W2[j,J,m,u] Ts[b,u,B] -> E[A,I,J,B]
+        E = np.einsum("aijb,adA,iIdm,jJmu,buB->AIJB", E, Bs, W1, W2, Ts)
+    return E.reshape(-1)[0]
+
+
+def row_site_environment(Bm, row, Tm, x):
+    """d<B|row|T>/dW_x: the open tensor of shape W_x.shape (Dl, Dr, Dd, Du)."""
+    L = np.ones((1, 1, 1))
+    for c in range(x):
+        L = np.einsum("alb,adA,lrdu,buB->ArB", L, Bm[c], row[c], Tm[c])
+    R = np.ones((1, 1, 1))
+    for c in range(len(row) - 1, x, -1):
+        R = np.einsum("adA,lrdu,buB,ArB->alb", Bm[c], row[c], Tm[c], R)
+    return np.einsum("alb,adA,buB,ArB->lrdu", L, Bm[x], Tm[x], R)
+
+
+def mps_bond_dims(mps):
+    return [m.shape[2] for m in mps[:-1]]
