@@ -1,0 +1,209 @@
+/*
+ * gcfvmc.h - C ABI of the GB300 library for variational Monte Carlo of
+ * gauge-canonical-form (GCF) gauge-invariant PEPS for Z_N lattice gauge
+ * theories in (2+1)D, following Wu & Liu, "Accurate gauge-invariant tensor
+ * network simulations for Abelian lattice gauge theory in (2+1)D".
+ *
+ * Library: libgcfvmc.so (hand-written CUDA for sm_103a).  No torch types
+ * appear here; the Python binding passes raw pointers.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Lattice: open Lx x Ly square lattice, vertex (x, y), x to the right,
+ *   y up.  Horizontal link (x,1) joins (x,y)-(x+1,y); vertical link (x,2)
+ *   joins (x,y)-(x,y+1).
+ * - Configuration (int8, cfg_len = Ly*(Lx-1) + (Ly-1)*Lx + Lx*Ly bytes per
+ *   chain): [h: Ly x (Lx-1), row-major][v: (Ly-1) x Lx][p: Ly x Lx], link
+ *   values in [0, N), occupations in {0,1} (0 without matter).  A
+ *   configuration is physical iff every vertex satisfies the Gauss law
+ *   p + n_l + n_d - n_r - n_u = Q_x (mod N)   (paper Eq. 1 and Eq. S4).
+ * - Parameters: the GCF matter tensors A^p_{lrdu} (Eqs. 6 and 9), stored
+ *   block-sparse.  Vertex v = y*Lx + x in order.  At a vertex the existing
+ *   legs in the order (l, r, d, u) are legs[0..k-1]; block index =
+ *   mixed radix (p, n_legs[0], ..., n_legs[k-2]) with p most significant and
+ *   radix N for the charges; the last leg's charge follows from the Gauss
+ *   law.  P = 2 occupation values with matter, 1 without.  A block holds
+ *   D_k^k entries [i_l][i_r][i_d][i_u] over the existing legs, row-major.
+ *   D_k = D / N (every charge sector has the same degeneracy).
+ * - Pointers documented "device" are CUDA device pointers, read/written in
+ *   order on the context's stream; "host" pointers are ordinary memory.
+ *   The caller owns every buffer it passes; the context owns its own
+ *   parameter store and scratch.
+ * - Every entry point returns a gcf_status and never aborts; on failure the
+ *   reason is available from gcf_last_error().  Calls on one context are not
+ *   thread-safe.
+ */
+#ifndef GCFVMC_H
+#define GCFVMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GCF_API_VERSION 1
+
+typedef struct gcf_ctx gcf_ctx;
+
+typedef enum {
+  GCF_OK = 0,
+  GCF_EINVAL = 1,    /* invalid argument (sizes, null pointers, bad enum)   */
+  GCF_ENOMEM = 2,    /* device or host allocation failed                    */
+  GCF_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed         */
+  GCF_EGAUSS = 4,    /* an input configuration violates the Gauss law       */
+  GCF_ENUMERIC = 5,  /* non-finite value met (NaN/Inf tensors, zero psi)    */
+  GCF_ETIMEOUT = 6   /* a bounded iterative routine did not converge        */
+} gcf_status;
+
+/* tensor element type */
+enum { GCF_REAL = 0, GCF_COMPLEX = 1 };
+/* contraction precision: FP64 (reference form), FP32 (plain CUDA-core form),
+ * TF32 / BF16 (tensor-core operand rounding with FP32 accumulation). */
+enum { GCF_FP64 = 0, GCF_FP32 = 1, GCF_TF32 = 2, GCF_BF16 = 3 };
+/* parameter update of gcf_sr_step */
+enum { GCF_SR = 0, GCF_TDVP_STAGE1 = 1, GCF_TDVP_STAGE2 = 2 };
+
+/* Model and ansatz.  Couplings are in the paper's form, Eqs. (2)-(5):
+ *   H = m sum_x p_x + J sum (c^dag U c + h.c.) - h sum_x (P_x + P_x^dag)
+ *       + g sum_links (2 - 2 cos(2 pi n / N));
+ * for N = 2, P_x = P_x^dag so the magnetic term is -2h P_x.  J is real. */
+typedef struct {
+  int N;            /* gauge group Z_N, 2 <= N <= 8                          */
+  int Lx, Ly;       /* 2 <= Lx, Ly <= 64                                     */
+  int D;            /* total bond dimension, multiple of N; D_k = D/N <= 4   */
+  int chi;          /* boundary-MPS cutoff, >= 1                              */
+  int has_matter;   /* 1: hard-core bosons on the vertices                   */
+  const int32_t* Q; /* host, Lx*Ly background charges (row-major) or NULL=0  */
+  double h, g, J, m;
+  int dtype;        /* GCF_REAL | GCF_COMPLEX                                */
+  int precision;    /* GCF_FP64 | GCF_FP32 | GCF_TF32 | GCF_BF16             */
+} gcf_model;
+
+/* Measurement outputs of gcf_sample_batch (all device pointers, chain-major:
+ * sample s = chain * n_sweeps + sweep).  Any member may be NULL to skip it. */
+typedef struct {
+  double* log_abs;    /* [n_samples]   log|psi(s)|                           */
+  double* phase;      /* [n_samples]   arg psi(s) (0 or pi for real tensors) */
+  double* e_loc;      /* [2*n_samples] (re, im) of E_loc(s), Eq. S2          */
+  int32_t* block_ids; /* [n_samples*Lx*Ly] block selected at each vertex     */
+  void* O;            /* [n_samples*Lx*Ly*D_k^4] d ln psi / d A~_x, Eq. S3;
+                         storage scalar (see gcf_scalar_bytes); the first
+                         D_k^k entries of each vertex slot are the block,
+                         in the parameter block order                      */
+  int32_t* accepted;  /* [n_chains] accepted moves in this call              */
+  int32_t* proposed;  /* [n_chains] proposed moves in this call              */
+} gcf_samples;
+
+/* Create a context: validates the model, builds the layout, allocates the
+ * parameter store and fills it with i.i.d. N(0,1) entries from the
+ * counter-based SplitMix64 / Box-Muller generator (stream 0 of `seed`;
+ * complex: real part = normal 2k, imaginary part = normal 2k+1).
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Paper: "Gauge-invariant TNS" and "Gauge canonical form" (Eqs. 6-9). */
+gcf_status gcf_init_peps(const gcf_model* model, uint64_t seed, void* cuda_stream,
+                         gcf_ctx** out);
+void gcf_destroy(gcf_ctx* ctx);
+const char* gcf_last_error(const gcf_ctx* ctx);
+
+/* Sizes of the context's layout. */
+int64_t gcf_num_params(const gcf_ctx* ctx);   /* number of scalars in A      */
+int gcf_config_len(const gcf_ctx* ctx);        /* bytes per configuration     */
+int gcf_scalar_bytes(const gcf_ctx* ctx);      /* 4, 8 (f32/c64... see below) */
+/* gcf_scalar_bytes: FP64 real 8, FP64 complex 16, other real 4, other complex 8 */
+
+/* Copy parameters in/out.  host_params: host, gcf_num_params values of
+ * float64 (real) or complex128 (complex, interleaved re/im); bytes must equal
+ * that size.  Values are rounded to the storage type (float for FP32, TF32,
+ * BF16; double for FP64).  Returns GCF_ENUMERIC if a value is not finite. */
+gcf_status gcf_set_tensors(gcf_ctx* ctx, const void* host_params, size_t bytes);
+gcf_status gcf_get_tensors(gcf_ctx* ctx, void* host_params, size_t bytes);
+
+/* Build physical starting configurations (Sec. S-2, "Configuration
+ * sampling"): for chain c, links are first fixed on the comb tree (all
+ * horizontal links and the vertical links of column 0, other links 0) so that
+ * every vertex satisfies the Gauss law for the occupations of that chain,
+ * then P_j^{t_j} is applied for every plaquette j = y*(Lx-1)+x.
+ * occupations: device, n_chains*Lx*Ly int8 in {0,1}, or NULL (all empty);
+ * plaquette_powers: device, n_chains*(Lx-1)*(Ly-1) int8 in [0, N) or NULL;
+ * configs: device output, n_chains*cfg_len.
+ * GCF_EGAUSS if some chain's occupations violate sum(p) = sum(Q) mod N. */
+gcf_status gcf_init_configs(gcf_ctx* ctx, int n_chains, const int8_t* occupations,
+                            const int8_t* plaquette_powers, int8_t* configs);
+
+/* Amplitude psi(s) = <B[Ly-2] | row Ly-1> where B[r] is the boundary MPS of
+ * rows 0..r absorbed bottom-up, each compressed to chi by QR left-to-right
+ * and LQ / truncated SVD right-to-left (Sec. S-2, Eq. S5; cost paragraph of
+ * the main text).  configs: device n*cfg_len; log_abs, phase: device [n].
+ * An unphysical configuration gives log_abs = -inf, phase = 0 (its amplitude
+ * is exactly zero in a GI-PEPS, Sec. S-2) and GCF_OK. */
+gcf_status gcf_amplitude(gcf_ctx* ctx, int n, const int8_t* configs, double* log_abs,
+                         double* phase);
+
+/* Local energy E_loc(s) = sum_s' <s|H|s'> psi(s')/psi(s), Eq. (S2); the
+ * plaquette ratios of row pair (r, r+1) use the strip <B[r-1]|W_r W_{r+1}|T[r+2]>
+ * and the hop ratios the row <B[r-1]|W_r|T[r+1]> (horizontal) or the strip
+ * (vertical), with the environments of s in numerator and denominator.
+ * e_loc: device [2n] (re, im).  GCF_EGAUSS if any configuration is unphysical. */
+gcf_status gcf_local_energy(gcf_ctx* ctx, int n, const int8_t* configs, double* e_loc);
+
+/* Log-derivatives O_x = (d psi_r / d A~_x) / psi_r with psi_r the row value
+ * <B[r-1]|W_r|T[r+1]> (Eq. S3).  block_ids: device [n*Lx*Ly]; O: device
+ * [n*Lx*Ly*D_k^4] storage scalars (first D_k^k entries per vertex are used).
+ * GCF_EGAUSS if any configuration is unphysical. */
+gcf_status gcf_log_grad(gcf_ctx* ctx, int n, const int8_t* configs, int32_t* block_ids,
+                        void* O);
+
+/* Markov-chain sampling (Sec. S-1 Metropolis rule, Sec. S-2 moves and
+ * sequential order): n_sweeps sweeps of every chain in one persistent launch;
+ * each sweep visits the plaquettes (row pairs bottom to top, left to right,
+ * power t uniform in [1, N-1]) and, with matter, the horizontal links (rows
+ * top to bottom) then the vertical links (row pairs bottom to top) with the
+ * gauge-dressed hop; after each sweep the sample is measured (amplitude,
+ * E_loc, O) into `out`.  A proposal s1 from s0 is accepted iff
+ * u * |psi(s0)|^2 < |psi(s1)|^2, u uniform in [0,1) from the counter-based
+ * SplitMix64 stream of (seed, chain): word k = mix64(key + (k+1)*GAMMA),
+ * key = mix64(seed + (chain+1)*GAMMA), GAMMA = 0x9E3779B97F4A7C15,
+ * u = (word >> 11) * 2^-53.  Counter of sweep w: k = w*n_slots + slot with
+ * slot 2j (power t = 1 + word % (N-1)) and 2j+1 (u) for plaquette
+ * j = y*(Lx-1)+x; with matter, slot 2*Np + j for horizontal link j and
+ * 2*Np + n_h + j for vertical link j; n_slots = 2*Np (+ n_h + n_v).
+ * configs: device n_chains*cfg_len, in/out (must be physical).
+ * GCF_EGAUSS if a starting configuration is unphysical. */
+gcf_status gcf_sample_batch(gcf_ctx* ctx, int n_chains, int n_sweeps, uint64_t seed,
+                            int8_t* configs, const gcf_samples* out);
+
+/* FP64 reductions and parameter update (Sec. S-1 Eq. S3; Sec. S-3 Eqs. S6-S8):
+ *   F = <O^* E_loc> - <O^*><E_loc>,  S = <O^* O> - <O^*><O>   (Eq. S7)
+ *   x = (S + diag_shift I)^{-1} F by conjugate gradient (S never formed).
+ *   mode GCF_SR:          A <- A - lr * x
+ *   mode GCF_TDVP_STAGE1: A <- A + c1 * dt * (-i x),  c1 = (1+i)/2
+ *   mode GCF_TDVP_STAGE2: A <- A + c2 * dt * (-i x),  c2 = (1-i)/2
+ * (TDVP modes need GCF_COMPLEX.)  e_loc, block_ids, O: device, as written by
+ * gcf_sample_batch for n_samples samples, all with equal weight.
+ * stats: host double[8] = {Re<E>, Im<E>, std error of Re<E> over chains
+ * (n_chains > 1, else over samples), CG iterations, relative residual,
+ * |F|, 0, 0}; n_chains is the number of chains the samples came from
+ * (chain-major order).  GCF_ETIMEOUT if CG hits max_iter before tol (the
+ * update is still applied). */
+gcf_status gcf_sr_step(gcf_ctx* ctx, int n_samples, int n_chains, const double* e_loc,
+                       const int32_t* block_ids, const void* O, double diag_shift, double lr,
+                       int mode, double dt, int max_iter, double tol, double* stats);
+
+/* One VMC iteration end to end from host memory: copies configs (host,
+ * n_chains*cfg_len, in/out) to the device, runs gcf_sample_batch into
+ * context-owned sample buffers, then gcf_sr_step, and copies the configs and
+ * stats (host double[8], as gcf_sr_step) back. */
+gcf_status gcf_vmc_step_host(gcf_ctx* ctx, int n_chains, int n_sweeps, uint64_t seed,
+                             int8_t* host_configs, double diag_shift, double lr, int mode,
+                             double dt, int max_iter, double tol, double* stats);
+
+/* Number of kernel launches this context issued since creation (for
+ * accounting in benchmarks). */
+int64_t gcf_launch_count(const gcf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GCFVMC_H */

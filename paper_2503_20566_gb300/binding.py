@@ -1,0 +1,260 @@
+"""ctypes binding of libgcfvmc (the C ABI in include/gcfvmc.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  PyTorch provides device memory and the stream.  If the shared
+library has not been built, loading fails with an error: there is no
+fallback implementation.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgcfvmc.so")
+
+GCF_OK, GCF_EINVAL, GCF_ENOMEM, GCF_ECUDA, GCF_EGAUSS, GCF_ENUMERIC, GCF_ETIMEOUT = range(7)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EGAUSS", "ENUMERIC", "ETIMEOUT"]
+REAL, COMPLEX = 0, 1
+FP64, FP32, TF32, BF16 = 0, 1, 2, 3
+SR, TDVP_STAGE1, TDVP_STAGE2 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
+
+
+class GcfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"gcf status {STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+class _Model(C.Structure):
+    _fields_ = [("N", C.c_int), ("Lx", C.c_int), ("Ly", C.c_int), ("D", C.c_int), ("chi", C.c_int),
+                ("has_matter", C.c_int), ("Q", C.POINTER(C.c_int32)), ("h", C.c_double),
+                ("g", C.c_double), ("J", C.c_double), ("m", C.c_double), ("dtype", C.c_int),
+                ("precision", C.c_int)]
+
+
+class _Samples(C.Structure):
+    _fields_ = [("log_abs", C.c_void_p), ("phase", C.c_void_p), ("e_loc", C.c_void_p),
+                ("block_ids", C.c_void_p), ("O", C.c_void_p), ("accepted", C.c_void_p),
+                ("proposed", C.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgcfvmc.so (built by ``paper_2503_20566_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgcfvmc.so not built at {path}; run paper_2503_20566_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, i, i64, d, u64 = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_uint64
+    sigs = {
+        "gcf_init_peps": (i, [C.POINTER(_Model), u64, vp, C.POINTER(vp)]),
+        "gcf_destroy": (None, [vp]),
+        "gcf_last_error": (C.c_char_p, [vp]),
+        "gcf_num_params": (i64, [vp]),
+        "gcf_config_len": (i, [vp]),
+        "gcf_scalar_bytes": (i, [vp]),
+        "gcf_launch_count": (i64, [vp]),
+        "gcf_set_tensors": (i, [vp, vp, C.c_size_t]),
+        "gcf_get_tensors": (i, [vp, vp, C.c_size_t]),
+        "gcf_init_configs": (i, [vp, i, vp, vp, vp]),
+        "gcf_amplitude": (i, [vp, i, vp, vp, vp]),
+        "gcf_local_energy": (i, [vp, i, vp, vp]),
+        "gcf_log_grad": (i, [vp, i, vp, vp, vp]),
+        "gcf_sample_batch": (i, [vp, i, i, u64, vp, C.POINTER(_Samples)]),
+        "gcf_sr_step": (i, [vp, i, i, vp, vp, vp, d, d, i, d, i, d, C.POINTER(C.c_double)]),
+        "gcf_vmc_step_host": (i, [vp, i, i, u64, vp, d, d, i, d, i, d, C.POINTER(C.c_double)]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names the binding expects the library to export."""
+    return ["gcf_init_peps", "gcf_destroy", "gcf_last_error", "gcf_num_params", "gcf_config_len",
+            "gcf_scalar_bytes", "gcf_launch_count", "gcf_set_tensors", "gcf_get_tensors",
+            "gcf_init_configs", "gcf_amplitude", "gcf_local_energy", "gcf_log_grad",
+            "gcf_sample_batch", "gcf_sr_step", "gcf_vmc_step_host"]
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One GCF-PEPS ansatz on one lattice (a ``gcf_ctx``)."""
+
+    def __init__(self, N, Lx, Ly, D, chi, matter=False, Q=None, h=1.0, g=0.0, J=0.0, m=0.0,
+                 complex_=False, precision="fp32", seed=0, stream=None):
+        import torch
+
+        self._torch = torch
+        self.lib = load_library()
+        self.N, self.Lx, self.Ly, self.D, self.chi = N, Lx, Ly, D, chi
+        self.Dk = D // N
+        self.matter = bool(matter)
+        self.complex = bool(complex_)
+        self.precision = precision
+        self.n_s = Lx * Ly
+        self.n_plaq = (Lx - 1) * (Ly - 1)
+        q = None
+        if Q is not None:
+            self._Q = np.ascontiguousarray(np.asarray(Q, dtype=np.int32).reshape(-1))
+            q = self._Q.ctypes.data_as(C.POINTER(C.c_int32))
+        mdl = _Model(N, Lx, Ly, D, chi, int(matter), q, h, g, J, m, COMPLEX if complex_ else REAL,
+                     PRECISIONS[precision])
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h_ctx = C.c_void_p()
+        st = self.lib.gcf_init_peps(C.byref(mdl), C.c_uint64(seed), C.c_void_p(stream.cuda_stream),
+                                    C.byref(h_ctx))
+        if st != GCF_OK:
+            raise GcfError(st, "gcf_init_peps failed")
+        self.ctx = h_ctx
+        self.n_params = int(self.lib.gcf_num_params(self.ctx))
+        self.cfg_len = int(self.lib.gcf_config_len(self.ctx))
+        self.scalar_bytes = int(self.lib.gcf_scalar_bytes(self.ctx))
+        if precision == "fp64":
+            self.o_dtype = torch.complex128 if complex_ else torch.float64
+        else:
+            self.o_dtype = torch.complex64 if complex_ else torch.float32
+
+    # ---- lifecycle ------------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.gcf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what, allow=()):
+        if st != GCF_OK and st not in allow:
+            msg = self.lib.gcf_last_error(self.ctx)
+            raise GcfError(st, f"{what}: {msg.decode() if msg else ''}")
+        return st
+
+    @property
+    def launch_count(self):
+        return int(self.lib.gcf_launch_count(self.ctx))
+
+    # ---- parameters -------------------------------------------------------
+    def set_tensors(self, values):
+        v = np.ascontiguousarray(np.asarray(values, dtype=np.complex128 if self.complex else np.float64))
+        if v.shape != (self.n_params,):
+            raise ValueError(f"expected {self.n_params} parameters")
+        self._check(self.lib.gcf_set_tensors(self.ctx, v.ctypes.data_as(C.c_void_p), v.nbytes), "set_tensors")
+
+    def get_tensors(self):
+        v = np.zeros(self.n_params, dtype=np.complex128 if self.complex else np.float64)
+        self._check(self.lib.gcf_get_tensors(self.ctx, v.ctypes.data_as(C.c_void_p), v.nbytes), "get_tensors")
+        return v
+
+    # ---- configurations ----------------------------------------------------
+    def init_configs(self, n_chains, occupations=None, powers=None):
+        torch = self._torch
+        dev = torch.device("cuda")
+        occ = None if occupations is None else torch.as_tensor(occupations, dtype=torch.int8).to(dev).contiguous()
+        pw = None if powers is None else torch.as_tensor(powers, dtype=torch.int8).to(dev).contiguous()
+        cfg = torch.empty((n_chains, self.cfg_len), dtype=torch.int8, device=dev)
+        self._check(self.lib.gcf_init_configs(self.ctx, n_chains, _ptr(occ), _ptr(pw), _ptr(cfg)), "init_configs")
+        return cfg
+
+    def _configs(self, configs):
+        torch = self._torch
+        c = torch.as_tensor(configs, dtype=torch.int8)
+        if c.dim() == 1:
+            c = c.unsqueeze(0)
+        return c.to("cuda").contiguous()
+
+    # ---- fixed-configuration evaluations ---------------------------------------
+    def amplitude(self, configs):
+        torch = self._torch
+        c = self._configs(configs)
+        n = c.shape[0]
+        la = torch.empty(n, dtype=torch.float64, device="cuda")
+        ph = torch.empty(n, dtype=torch.float64, device="cuda")
+        self._check(self.lib.gcf_amplitude(self.ctx, n, _ptr(c), _ptr(la), _ptr(ph)), "amplitude")
+        return la, ph
+
+    def local_energy(self, configs):
+        torch = self._torch
+        c = self._configs(configs)
+        n = c.shape[0]
+        e = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+        self._check(self.lib.gcf_local_energy(self.ctx, n, _ptr(c), _ptr(e)), "local_energy")
+        return torch.view_as_complex(e.view(n, 2))
+
+    def log_grad(self, configs):
+        torch = self._torch
+        c = self._configs(configs)
+        n = c.shape[0]
+        D4 = self.Dk ** 4
+        bid = torch.empty((n, self.n_s), dtype=torch.int32, device="cuda")
+        O = torch.zeros((n, self.n_s, D4), dtype=self.o_dtype, device="cuda")
+        self._check(self.lib.gcf_log_grad(self.ctx, n, _ptr(c), _ptr(bid), _ptr(O)), "log_grad")
+        return bid, O
+
+    # ---- sampling and SR ---------------------------------------------------------
+    def alloc_samples(self, n_chains, n_sweeps, grad=True):
+        torch = self._torch
+        ns = n_chains * n_sweeps
+        out = {
+            "log_abs": torch.empty(ns, dtype=torch.float64, device="cuda"),
+            "phase": torch.empty(ns, dtype=torch.float64, device="cuda"),
+            "e_loc": torch.empty(2 * ns, dtype=torch.float64, device="cuda"),
+            "accepted": torch.zeros(n_chains, dtype=torch.int32, device="cuda"),
+            "proposed": torch.zeros(n_chains, dtype=torch.int32, device="cuda"),
+        }
+        if grad:
+            out["block_ids"] = torch.empty((ns, self.n_s), dtype=torch.int32, device="cuda")
+            out["O"] = torch.zeros((ns, self.n_s, self.Dk ** 4), dtype=self.o_dtype, device="cuda")
+        return out
+
+    def sample_batch(self, configs, n_sweeps, seed, out=None, grad=True):
+        """configs: device int8 tensor (n_chains, cfg_len), updated in place."""
+        n = configs.shape[0]
+        if out is None:
+            out = self.alloc_samples(n, n_sweeps, grad)
+        s = _Samples(*[C.c_void_p(out[k].data_ptr()) if k in out else None
+                       for k in ("log_abs", "phase", "e_loc", "block_ids", "O", "accepted", "proposed")])
+        self._check(self.lib.gcf_sample_batch(self.ctx, n, n_sweeps, C.c_uint64(seed), _ptr(configs),
+                                              C.byref(s)), "sample_batch")
+        return out
+
+    def sr_step(self, samples, n_chains, diag_shift=1e-4, lr=0.01, mode=SR, dt=0.0, max_iter=100,
+                tol=1e-10):
+        ns = samples["e_loc"].shape[0] // 2
+        stats = (C.c_double * 8)()
+        st = self.lib.gcf_sr_step(self.ctx, ns, n_chains, _ptr(samples["e_loc"]), _ptr(samples["block_ids"]),
+                                  _ptr(samples["O"]), diag_shift, lr, mode, dt, max_iter, tol, stats)
+        self._check(st, "sr_step", allow=(GCF_ETIMEOUT,))
+        return list(stats)
+
+    def vmc_step_host(self, host_configs, n_sweeps, seed, diag_shift=1e-4, lr=0.01, mode=SR, dt=0.0,
+                      max_iter=100, tol=1e-10):
+        """One VMC iteration from host memory (configs: numpy int8, in/out)."""
+        assert host_configs.dtype == np.int8 and host_configs.flags["C_CONTIGUOUS"]
+        n = host_configs.shape[0]
+        stats = (C.c_double * 8)()
+        st = self.lib.gcf_vmc_step_host(self.ctx, n, n_sweeps, C.c_uint64(seed),
+                                        host_configs.ctypes.data_as(C.c_void_p), diag_shift, lr, mode, dt,
+                                        max_iter, tol, stats)
+        self._check(st, "vmc_step_host", allow=(GCF_ETIMEOUT,))
+        return list(stats)

@@ -1,0 +1,659 @@
+// C ABI of libgcfvmc: context management, the host planner (layout, bond
+// dimension tables, scratch plan) and the entry points declared in
+// include/gcfvmc.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gcfvmc.h"
+#include "launch.h"
+#include "peps_dev.cuh"
+#include "sr.cuh"
+
+using namespace gcf;
+
+namespace {
+
+enum ScalarKind { S_F32 = 0, S_F64 = 1, S_C64 = 2, S_C128 = 3 };
+
+struct Plan {
+  std::vector<int> bondB, bondT, qrB, svdB, qrT, svdT;  // (Ly+1) x (Lx+1) each
+  long long mps_stride = 0, qsite_stride = 0, mat_max = 0, tau_max = 0, tmp_max = 0;
+  int env_stride = 0, env3_stride = 0;
+  long long ws_stride = 0;
+  long long o_net, o_prop, o_B, o_T, o_Q, o_M1, o_M2, o_M3, o_tau, o_J, o_envR, o_envL, o_envX,
+      o_envY, o_t1, o_t2, o_t3, o_env3R, o_env3L, o_env3X, o_env3Y, o_G;
+};
+
+}  // namespace
+
+struct gcf_ctx {
+  gcf_model m{};
+  std::vector<int> Q;
+  int Dk = 0, P = 1, n_h = 0, n_v = 0, n_s = 0, cfg_len = 0, n_plaq = 0, n_slots = 0;
+  long long n_params = 0;
+  std::vector<long long> voff;
+  std::vector<int> vbs, vnb;
+  int kind = S_F32;
+  size_t sbytes = 4;
+  cudaStream_t stream = nullptr;
+  int device = 0, sms = 0;
+  Plan plan;
+  // device
+  void* d_params = nullptr;
+  int* d_Q = nullptr;
+  long long* d_voff = nullptr;
+  int* d_vbs = nullptr;
+  int* d_vnb = nullptr;
+  int* d_tables = nullptr;
+  int* d_status = nullptr;
+  void* d_scratch = nullptr;
+  long long scratch_ctas = 0;
+  // SR work
+  SrWork sr{};
+  long long sr_ns_cap = 0;
+  int sr_chain_cap = 0;
+  // e2e sample buffers
+  int8_t* d_cfg = nullptr;
+  double* d_e = nullptr;
+  double* d_la = nullptr;
+  double* d_ph = nullptr;
+  int* d_bid = nullptr;
+  void* d_O = nullptr;
+  int* d_acc = nullptr;
+  long long e2e_cap = 0;
+  int e2e_chains = 0;
+  long long launches = 0;
+  std::string err;
+};
+
+namespace {
+
+gcf_status fail(gcf_ctx* c, gcf_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+gcf_status cuda_fail(gcf_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, GCF_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(ctx, expr)                                      \
+  do {                                                           \
+    cudaError_t _e = (expr);                                     \
+    if (_e != cudaSuccess) return cuda_fail((ctx), _e, #expr);   \
+  } while (0)
+
+inline long long al32(long long n) { return (n + 31) / 32 * 32; }
+
+// One absorption step: input bond table bin (Lx+1), output bout, qr, svd.
+void plan_step(int Lx, int Dk, int chi, int pout, const int* bin, int* qr, int* svd, int* bout) {
+  std::vector<int> ab(Lx + 1);
+  ab[0] = 1;
+  for (int c = 1; c < Lx; ++c) ab[c] = bin[c] * Dk;
+  ab[Lx] = 1;
+  qr[0] = 1;
+  for (int c = 0; c < Lx - 1; ++c) qr[c + 1] = std::min(qr[c] * pout, ab[c + 1]);
+  qr[Lx] = 1;
+  bout[Lx] = 1;
+  for (int c = Lx - 1; c >= 1; --c) {
+    const int k0 = std::min(qr[c], pout * bout[c + 1]);
+    svd[c] = k0 > chi ? 1 : 0;
+    bout[c] = std::min(chi, k0);
+  }
+  bout[0] = 1;
+  svd[0] = 0;
+  svd[Lx] = 0;
+}
+
+void build_plan(gcf_ctx* c) {
+  const int Lx = c->m.Lx, Ly = c->m.Ly, Dk = c->Dk, chi = c->m.chi;
+  const int W = Lx + 1;
+  Plan& p = c->plan;
+  p.bondB.assign((Ly + 1) * W, 1);
+  p.bondT.assign((Ly + 1) * W, 1);
+  p.qrB.assign((Ly + 1) * W, 1);
+  p.svdB.assign((Ly + 1) * W, 0);
+  p.qrT.assign((Ly + 1) * W, 1);
+  p.svdT.assign((Ly + 1) * W, 0);
+  // B: slot j holds B[j-1]; step r absorbs row r: slot r -> slot r+1
+  for (int r = 0; r <= Ly - 2; ++r)
+    plan_step(Lx, Dk, chi, Dk, &p.bondB[r * W], &p.qrB[r * W], &p.svdB[r * W], &p.bondB[(r + 1) * W]);
+  // T: slot r holds T[r]; step r: slot r+1 -> slot r
+  for (int r = Ly - 1; r >= 1; --r)
+    plan_step(Lx, Dk, chi, Dk, &p.bondT[(r + 1) * W], &p.qrT[r * W], &p.svdT[r * W], &p.bondT[r * W]);
+  auto mps_size = [&](const int* bd, int phys) {
+    long long s = 0;
+    for (int cc = 0; cc < Lx; ++cc) s += (long long)bd[cc] * phys * bd[cc + 1];
+    return s;
+  };
+  long long ms = Lx;
+  for (int j = 0; j <= Ly; ++j) {
+    ms = std::max(ms, mps_size(&p.bondB[j * W], j == 0 ? 1 : Dk));
+    ms = std::max(ms, mps_size(&p.bondT[j * W], j == Ly ? 1 : Dk));
+  }
+  p.mps_stride = al32(ms);
+  // QR-pass sites, matrices, taus
+  long long qs = 1, mat = 1, tau = 1;
+  auto step_sizes = [&](const int* bin, const int* qr, const int* svd, const int* bout, int pin,
+                        int pout) {
+    std::vector<int> ab(Lx + 1);
+    ab[0] = 1;
+    for (int cc = 1; cc < Lx; ++cc) ab[cc] = bin[cc] * Dk;
+    ab[Lx] = 1;
+    for (int cc = 0; cc < Lx; ++cc) {
+      const long long rows = (long long)qr[cc] * pout, cols = ab[cc + 1];
+      qs = std::max(qs, rows * std::min(rows, cols));
+      mat = std::max(mat, (long long)ab[cc] * pout * ab[cc + 1]);  // Z
+      mat = std::max(mat, rows * cols);                             // X
+      mat = std::max(mat, (long long)std::max(rows, cols) * std::max(rows, cols));
+      tau = std::max(tau, std::max(rows, cols));
+    }
+    for (int cc = Lx - 1; cc >= 1; --cc) {
+      const long long yr = qr[cc], yc = (long long)pout * bout[cc + 1];
+      const long long k0 = std::min(yr, yc);
+      mat = std::max(mat, std::max(yr, yc) * std::max(yr, yc));
+      mat = std::max(mat, k0 * k0);
+      mat = std::max(mat, (long long)qr[cc - 1] * pout * bout[cc]);
+      tau = std::max(tau, std::max(yr, yc));
+    }
+    (void)pin;
+    (void)svd;
+  };
+  for (int r = 0; r <= Ly - 2; ++r)
+    step_sizes(&p.bondB[r * W], &p.qrB[r * W], &p.svdB[r * W], &p.bondB[(r + 1) * W], r == 0 ? 1 : Dk, Dk);
+  for (int r = Ly - 1; r >= 1; --r)
+    step_sizes(&p.bondT[(r + 1) * W], &p.qrT[r * W], &p.svdT[r * W], &p.bondT[r * W], r == Ly - 1 ? 1 : Dk, Dk);
+  p.qsite_stride = al32(qs);
+  p.mat_max = al32(mat);
+  p.tau_max = al32(tau);
+  // strip / row environments and intermediates
+  long long env = 1, env3 = 1, tmp = 1;
+  for (int r = 0; r <= Ly - 2; ++r) {
+    const int* bb = &p.bondB[r * W];
+    const int* bt = &p.bondT[(r + 2) * W];
+    const int pB = r == 0 ? 1 : Dk, pT = (r + 2 == Ly) ? 1 : Dk;
+    for (int cc = 0; cc <= Lx; ++cc) {
+      const int h = (cc == 0 || cc == Lx) ? 1 : Dk;
+      env = std::max(env, (long long)bb[cc] * h * h * bt[cc]);
+    }
+    for (int cc = 0; cc < Lx; ++cc) {
+      const long long nA = bb[cc], nB = bt[cc], nA2 = bb[cc + 1], nB2 = bt[cc + 1];
+      const long long hI = cc == 0 ? 1 : Dk, hO = cc == Lx - 1 ? 1 : Dk;
+      tmp = std::max(tmp, hI * hI * nB * pB * nA2);
+      tmp = std::max(tmp, hI * nB * nA2 * hO * Dk);
+      tmp = std::max(tmp, nA2 * hO * hO * nB * pT);
+      tmp = std::max(tmp, nA2 * hO * hI * Dk * nB);
+      tmp = std::max(tmp, nA2 * hI * hI * pB * nB);
+      (void)nA;
+      (void)nB2;
+    }
+  }
+  for (int r = 0; r <= Ly - 1; ++r) {
+    const int* bb = &p.bondB[r * W];
+    const int* bt = &p.bondT[(r + 1) * W];
+    const int pB = r == 0 ? 1 : Dk, pT = (r + 1 == Ly) ? 1 : Dk;
+    for (int cc = 0; cc <= Lx; ++cc) {
+      const int h = (cc == 0 || cc == Lx) ? 1 : Dk;
+      env3 = std::max(env3, (long long)bb[cc] * h * bt[cc]);
+    }
+    for (int cc = 0; cc < Lx; ++cc) {
+      const long long nB = bt[cc], nA2 = bb[cc + 1];
+      const long long hI = cc == 0 ? 1 : Dk, hO = cc == Lx - 1 ? 1 : Dk;
+      tmp = std::max(tmp, hI * nB * pB * nA2);
+      tmp = std::max(tmp, nB * nA2 * hO * pT);
+      tmp = std::max(tmp, nA2 * hO * nB * pT);
+      tmp = std::max(tmp, nA2 * hI * pB * nB);
+    }
+  }
+  p.env_stride = (int)al32(env);
+  p.env3_stride = (int)al32(env3);
+  p.tmp_max = al32(tmp);
+  const long long D4 = (long long)Dk * Dk * Dk * Dk;
+  long long o = 0;
+  auto take = [&](long long n) { long long r = o; o += al32(n); return r; };
+  p.o_net = take((long long)Lx * Ly * D4);
+  p.o_prop = take(4 * D4);
+  p.o_B = take((Ly + 1) * p.mps_stride);
+  p.o_T = take((Ly + 1) * p.mps_stride);
+  p.o_Q = take((long long)Lx * p.qsite_stride);
+  p.o_M1 = take(p.mat_max);
+  p.o_M2 = take(p.mat_max);
+  p.o_M3 = take(p.mat_max);
+  p.o_tau = take(p.tau_max);
+  p.o_J = take(p.mat_max);
+  p.o_envR = take((long long)(Lx + 1) * p.env_stride);
+  p.o_envL = take(p.env_stride);
+  p.o_envX = take(p.env_stride);
+  p.o_envY = take(p.env_stride);
+  p.o_t1 = take(p.tmp_max);
+  p.o_t2 = take(p.tmp_max);
+  p.o_t3 = take(p.tmp_max);
+  p.o_env3R = take((long long)(Lx + 1) * p.env3_stride);
+  p.o_env3L = take(p.env3_stride);
+  p.o_env3X = take(p.env3_stride);
+  p.o_env3Y = take(p.env3_stride);
+  p.o_G = take(D4);
+  p.ws_stride = o;
+}
+
+template <class T>
+KParams<T> make_params(gcf_ctx* c) {
+  KParams<T> k{};
+  const Plan& p = c->plan;
+  k.N = c->m.N; k.Lx = c->m.Lx; k.Ly = c->m.Ly; k.Dk = c->Dk; k.chi = c->m.chi;
+  k.matter = c->m.has_matter; k.P = c->P;
+  k.n_h = c->n_h; k.n_v = c->n_v; k.n_s = c->n_s; k.cfg_len = c->cfg_len;
+  k.n_plaq = c->n_plaq; k.n_slots = c->n_slots;
+  k.h = c->m.h; k.g = c->m.g; k.J = c->m.J; k.m = c->m.m;
+  k.Q = c->d_Q; k.voff = c->d_voff; k.vbs = c->d_vbs; k.params = (const T*)c->d_params;
+  const int W = c->m.Lx + 1, R = c->m.Ly + 1;
+  k.bondB = c->d_tables;
+  k.bondT = c->d_tables + R * W;
+  k.qrB = c->d_tables + 2 * R * W;
+  k.svdB = c->d_tables + 3 * R * W;
+  k.qrT = c->d_tables + 4 * R * W;
+  k.svdT = c->d_tables + 5 * R * W;
+  k.scratch = (T*)c->d_scratch;
+  k.ws_stride = p.ws_stride;
+  k.o_net = p.o_net; k.o_prop = p.o_prop; k.o_B = p.o_B; k.o_T = p.o_T; k.o_Q = p.o_Q;
+  k.o_M1 = p.o_M1; k.o_M2 = p.o_M2; k.o_M3 = p.o_M3; k.o_tau = p.o_tau; k.o_J = p.o_J;
+  k.o_envR = p.o_envR; k.o_envL = p.o_envL; k.o_envX = p.o_envX; k.o_envY = p.o_envY;
+  k.o_t1 = p.o_t1; k.o_t2 = p.o_t2; k.o_t3 = p.o_t3;
+  k.o_env3R = p.o_env3R; k.o_env3L = p.o_env3L; k.o_env3X = p.o_env3X; k.o_env3Y = p.o_env3Y;
+  k.o_G = p.o_G;
+  k.mps_stride = p.mps_stride; k.qsite_stride = p.qsite_stride;
+  k.env_stride = p.env_stride; k.env3_stride = p.env3_stride;
+  k.max_sweeps_svd = 40;
+  k.status = c->d_status;
+  return k;
+}
+
+int grid_for(gcf_ctx* c, int n_chains) {
+  const long long want = std::min<long long>(n_chains, (long long)c->sms * 4);
+  return (int)std::max<long long>(1, want);
+}
+
+gcf_status ensure_scratch(gcf_ctx* c, int ctas) {
+  if (ctas <= c->scratch_ctas) return GCF_OK;
+  if (c->d_scratch) cudaFree(c->d_scratch);
+  c->d_scratch = nullptr;
+  c->scratch_ctas = 0;
+  const size_t bytes = (size_t)ctas * c->plan.ws_stride * c->sbytes;
+  cudaError_t e = cudaMalloc(&c->d_scratch, bytes);
+  if (e != cudaSuccess) return fail(c, GCF_ENOMEM, "scratch allocation failed");
+  c->scratch_ctas = ctas;
+  return GCF_OK;
+}
+
+template <class T>
+gcf_status run_vmc(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t seed,
+                   int8_t* configs, const gcf_samples* out, int* gauss_count) {
+  const int grid = grid_for(c, n);
+  gcf_status st = ensure_scratch(c, grid);
+  if (st != GCF_OK) return st;
+  KParams<T> k = make_params<T>(c);
+  k.n_chains = n; k.n_sweeps = n_sweeps; k.mode = mode; k.want = want; k.seed = seed;
+  k.configs = configs;
+  if (out) {
+    k.log_abs = out->log_abs; k.phase = out->phase; k.e_loc = out->e_loc;
+    k.block_ids = out->block_ids; k.O = (T*)out->O;
+    k.accepted = out->accepted; k.proposed = out->proposed;
+  }
+  CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), c->stream));
+  CUDA_TRY(c, launch_vmc<T>(k, grid, 256, (size_t)c->cfg_len, c->stream));
+  c->launches += 1;
+  int h_status[4];
+  CUDA_TRY(c, cudaMemcpyAsync(h_status, c->d_status, sizeof(h_status), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (gauss_count) *gauss_count = h_status[ST_GAUSS];
+  return GCF_OK;
+}
+
+gcf_status dispatch(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t seed, int8_t* cfg,
+                    const gcf_samples* out, int* gauss) {
+  switch (c->kind) {
+    case S_F32: return run_vmc<float>(c, mode, want, n, n_sweeps, seed, cfg, out, gauss);
+    case S_F64: return run_vmc<double>(c, mode, want, n, n_sweeps, seed, cfg, out, gauss);
+    case S_C64: return run_vmc<cfloat>(c, mode, want, n, n_sweeps, seed, cfg, out, gauss);
+    default: return run_vmc<cdouble>(c, mode, want, n, n_sweeps, seed, cfg, out, gauss);
+  }
+}
+
+// host SplitMix64 / Box-Muller normals (stream 0), same definition as the
+// documented generator
+double host_normal(uint64_t seed, uint64_t j) {
+  const uint64_t key = stream_key(seed, 0);
+  const double u0 = word_to_uniform(stream_word(key, 2 * j));
+  const double u1 = word_to_uniform(stream_word(key, 2 * j + 1));
+  return std::sqrt(-2.0 * std::log1p(-u0)) * std::cos(2.0 * 3.14159265358979323846 * u1);
+}
+
+gcf_status upload_params(gcf_ctx* c, const double* vals /* n_params or 2*n_params */) {
+  const long long n = c->n_params;
+  const bool cplx = c->m.dtype == GCF_COMPLEX;
+  const long long nv = cplx ? 2 * n : n;
+  for (long long i = 0; i < nv; ++i)
+    if (!std::isfinite(vals[i])) return fail(c, GCF_ENUMERIC, "non-finite tensor entry");
+  std::vector<char> buf(n * c->sbytes);
+  if (c->kind == S_F32 || c->kind == S_C64) {
+    float* f = (float*)buf.data();
+    for (long long i = 0; i < nv; ++i) f[i] = (float)vals[i];
+  } else {
+    std::memcpy(buf.data(), vals, nv * sizeof(double));
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_params, buf.data(), buf.size(), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return GCF_OK;
+}
+
+gcf_status ensure_sr(gcf_ctx* c, long long Ns, int n_chains) {
+  if (!c->sr.obar) {
+    const long long Np = c->n_params;
+    cdouble** vecs[6] = {&c->sr.obar, &c->sr.F, &c->sr.x, &c->sr.r, &c->sr.p, &c->sr.Ap};
+    for (auto v : vecs)
+      if (cudaMalloc(v, sizeof(cdouble) * Np) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR vectors");
+    if (cudaMalloc(&c->sr.tbar, sizeof(cdouble)) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR");
+    if (cudaMalloc(&c->sr.scal, 32 * sizeof(double)) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR");
+  }
+  if (Ns > c->sr_ns_cap) {
+    if (c->sr.t) cudaFree(c->sr.t);
+    if (c->sr.coef) cudaFree(c->sr.coef);
+    c->sr.t = c->sr.coef = nullptr;
+    if (cudaMalloc(&c->sr.t, sizeof(cdouble) * Ns) != cudaSuccess ||
+        cudaMalloc(&c->sr.coef, sizeof(cdouble) * Ns) != cudaSuccess)
+      return fail(c, GCF_ENOMEM, "SR sample vectors");
+    c->sr_ns_cap = Ns;
+  }
+  if (n_chains > c->sr_chain_cap) {
+    if (c->sr.chain_mean) cudaFree(c->sr.chain_mean);
+    if (cudaMalloc(&c->sr.chain_mean, sizeof(cdouble) * n_chains) != cudaSuccess)
+      return fail(c, GCF_ENOMEM, "SR chain means");
+    c->sr_chain_cap = n_chains;
+  }
+  return GCF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gcf_status gcf_init_peps(const gcf_model* model, uint64_t seed, void* cuda_stream, gcf_ctx** out) {
+  if (!model || !out) return GCF_EINVAL;
+  *out = nullptr;
+  const gcf_model& m = *model;
+  if (m.N < 2 || m.N > 8 || m.Lx < 2 || m.Ly < 2 || m.Lx > MAX_L || m.Ly > MAX_L || m.D < m.N ||
+      m.D % m.N != 0 || m.D / m.N > 4 || m.chi < 1 || (m.dtype != GCF_REAL && m.dtype != GCF_COMPLEX) ||
+      m.precision < GCF_FP64 || m.precision > GCF_BF16 || (m.has_matter != 0 && m.has_matter != 1))
+    return GCF_EINVAL;
+  gcf_ctx* c = new gcf_ctx();
+  c->m = m;
+  c->m.Q = nullptr;
+  c->Dk = m.D / m.N;
+  c->P = m.has_matter ? 2 : 1;
+  c->n_h = m.Ly * (m.Lx - 1);
+  c->n_v = (m.Ly - 1) * m.Lx;
+  c->n_s = m.Lx * m.Ly;
+  c->cfg_len = c->n_h + c->n_v + c->n_s;
+  c->n_plaq = (m.Lx - 1) * (m.Ly - 1);
+  c->n_slots = 2 * c->n_plaq + (m.has_matter ? c->n_h + c->n_v : 0);
+  c->Q.assign(c->n_s, 0);
+  if (m.Q)
+    for (int i = 0; i < c->n_s; ++i) c->Q[i] = ((m.Q[i] % m.N) + m.N) % m.N;
+  const bool cplx = m.dtype == GCF_COMPLEX;
+  if (m.precision == GCF_FP64) { c->kind = cplx ? S_C128 : S_F64; c->sbytes = cplx ? 16 : 8; }
+  else { c->kind = cplx ? S_C64 : S_F32; c->sbytes = cplx ? 8 : 4; }
+  c->stream = (cudaStream_t)cuda_stream;
+  // layout (Eqs. 6, 9): per vertex P * N^(k-1) blocks of D_k^k
+  long long off = 0;
+  for (int y = 0; y < m.Ly; ++y)
+    for (int x = 0; x < m.Lx; ++x) {
+      const int k = (x > 0) + (x < m.Lx - 1) + (y > 0) + (y < m.Ly - 1);
+      int nb = c->P, bs = 1;
+      for (int i = 0; i < k - 1; ++i) nb *= m.N;
+      for (int i = 0; i < k; ++i) bs *= c->Dk;
+      c->voff.push_back(off);
+      c->vbs.push_back(bs);
+      c->vnb.push_back(nb);
+      off += (long long)nb * bs;
+    }
+  c->n_params = off;
+  build_plan(c);
+  cudaError_t e;
+  if ((e = cudaGetDevice(&c->device)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess) {
+    delete c;
+    return GCF_ECUDA;
+  }
+  const int W = m.Lx + 1, R = m.Ly + 1;
+  std::vector<int> tables;
+  for (auto* v : {&c->plan.bondB, &c->plan.bondT, &c->plan.qrB, &c->plan.svdB, &c->plan.qrT, &c->plan.svdT})
+    tables.insert(tables.end(), v->begin(), v->end());
+  bool ok = cudaMalloc(&c->d_params, c->n_params * c->sbytes) == cudaSuccess &&
+            cudaMalloc(&c->d_Q, sizeof(int) * c->n_s) == cudaSuccess &&
+            cudaMalloc(&c->d_voff, sizeof(long long) * c->n_s) == cudaSuccess &&
+            cudaMalloc(&c->d_vbs, sizeof(int) * c->n_s) == cudaSuccess &&
+            cudaMalloc(&c->d_vnb, sizeof(int) * c->n_s) == cudaSuccess &&
+            cudaMalloc(&c->d_tables, sizeof(int) * tables.size()) == cudaSuccess &&
+            cudaMalloc(&c->d_status, sizeof(int) * 4) == cudaSuccess;
+  (void)W; (void)R;
+  if (!ok) { gcf_destroy(c); return GCF_ENOMEM; }
+  if (cudaMemcpy(c->d_Q, c->Q.data(), sizeof(int) * c->n_s, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_voff, c->voff.data(), sizeof(long long) * c->n_s, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_vbs, c->vbs.data(), sizeof(int) * c->n_s, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_vnb, c->vnb.data(), sizeof(int) * c->n_s, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_tables, tables.data(), sizeof(int) * tables.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    gcf_destroy(c);
+    return GCF_ECUDA;
+  }
+  // N(0,1) initial tensors from the documented counter-based generator
+  const long long nv = cplx ? 2 * c->n_params : c->n_params;
+  std::vector<double> vals(nv);
+  for (long long i = 0; i < nv; ++i) vals[i] = host_normal(seed, (uint64_t)i);
+  if (upload_params(c, vals.data()) != GCF_OK) { gcf_destroy(c); return GCF_ECUDA; }
+  *out = c;
+  return GCF_OK;
+}
+
+void gcf_destroy(gcf_ctx* c) {
+  if (!c) return;
+  void* ptrs[] = {c->d_params, c->d_Q, c->d_voff, c->d_vbs, c->d_vnb, c->d_tables, c->d_status,
+                  c->d_scratch, c->sr.obar, c->sr.F, c->sr.x, c->sr.r, c->sr.p, c->sr.Ap,
+                  c->sr.t, c->sr.coef, c->sr.chain_mean, c->sr.tbar, c->sr.scal, c->d_cfg, c->d_e,
+                  c->d_la, c->d_ph, c->d_bid, c->d_O, c->d_acc};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+const char* gcf_last_error(const gcf_ctx* c) { return c ? c->err.c_str() : "null context"; }
+int64_t gcf_num_params(const gcf_ctx* c) { return c ? c->n_params : -1; }
+int gcf_config_len(const gcf_ctx* c) { return c ? c->cfg_len : -1; }
+int gcf_scalar_bytes(const gcf_ctx* c) { return c ? (int)c->sbytes : -1; }
+int64_t gcf_launch_count(const gcf_ctx* c) { return c ? c->launches : -1; }
+
+gcf_status gcf_set_tensors(gcf_ctx* c, const void* host, size_t bytes) {
+  if (!c || !host) return GCF_EINVAL;
+  const bool cplx = c->m.dtype == GCF_COMPLEX;
+  if (bytes != (size_t)c->n_params * (cplx ? 16 : 8))
+    return fail(c, GCF_EINVAL, "gcf_set_tensors: byte count does not match the layout");
+  return upload_params(c, (const double*)host);
+}
+
+gcf_status gcf_get_tensors(gcf_ctx* c, void* host, size_t bytes) {
+  if (!c || !host) return GCF_EINVAL;
+  const bool cplx = c->m.dtype == GCF_COMPLEX;
+  const long long nv = cplx ? 2 * c->n_params : c->n_params;
+  if (bytes != (size_t)nv * 8) return fail(c, GCF_EINVAL, "gcf_get_tensors: byte count mismatch");
+  std::vector<char> buf(c->n_params * c->sbytes);
+  CUDA_TRY(c, cudaMemcpyAsync(buf.data(), c->d_params, buf.size(), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  double* d = (double*)host;
+  if (c->kind == S_F32 || c->kind == S_C64) {
+    const float* f = (const float*)buf.data();
+    for (long long i = 0; i < nv; ++i) d[i] = f[i];
+  } else {
+    std::memcpy(d, buf.data(), nv * sizeof(double));
+  }
+  return GCF_OK;
+}
+
+gcf_status gcf_init_configs(gcf_ctx* c, int n_chains, const int8_t* occ, const int8_t* powers,
+                            int8_t* configs) {
+  if (!c || n_chains < 0 || (n_chains > 0 && !configs)) return GCF_EINVAL;
+  if (n_chains == 0) return GCF_OK;
+  CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), c->stream));
+  CUDA_TRY(c, launch_init_configs(c->m.N, c->m.Lx, c->m.Ly, c->m.has_matter, c->d_Q, n_chains, occ,
+                                  powers, configs, c->d_status, c->stream));
+  c->launches += 1;
+  int st[4];
+  CUDA_TRY(c, cudaMemcpyAsync(st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (st[0]) return fail(c, GCF_EGAUSS, "occupations violate sum(p) = sum(Q) mod N");
+  return GCF_OK;
+}
+
+gcf_status gcf_amplitude(gcf_ctx* c, int n, const int8_t* configs, double* log_abs, double* phase) {
+  if (!c || n < 0 || (n > 0 && (!configs || !log_abs || !phase))) return GCF_EINVAL;
+  if (n == 0) return GCF_OK;
+  gcf_samples out{};
+  out.log_abs = log_abs;
+  out.phase = phase;
+  return dispatch(c, 0, WANT_AMP, n, 1, 0, (int8_t*)configs, &out, nullptr);
+}
+
+gcf_status gcf_local_energy(gcf_ctx* c, int n, const int8_t* configs, double* e_loc) {
+  if (!c || n < 0 || (n > 0 && (!configs || !e_loc))) return GCF_EINVAL;
+  if (n == 0) return GCF_OK;
+  gcf_samples out{};
+  out.e_loc = e_loc;
+  int gauss = 0;
+  gcf_status st = dispatch(c, 0, WANT_ELOC, n, 1, 0, (int8_t*)configs, &out, &gauss);
+  if (st != GCF_OK) return st;
+  if (gauss) return fail(c, GCF_EGAUSS, "configuration violates the Gauss law");
+  return GCF_OK;
+}
+
+gcf_status gcf_log_grad(gcf_ctx* c, int n, const int8_t* configs, int32_t* block_ids, void* O) {
+  if (!c || n < 0 || (n > 0 && (!configs || !block_ids || !O))) return GCF_EINVAL;
+  if (n == 0) return GCF_OK;
+  gcf_samples out{};
+  out.block_ids = block_ids;
+  out.O = O;
+  int gauss = 0;
+  gcf_status st = dispatch(c, 0, WANT_GRAD, n, 1, 0, (int8_t*)configs, &out, &gauss);
+  if (st != GCF_OK) return st;
+  if (gauss) return fail(c, GCF_EGAUSS, "configuration violates the Gauss law");
+  return GCF_OK;
+}
+
+gcf_status gcf_sample_batch(gcf_ctx* c, int n_chains, int n_sweeps, uint64_t seed, int8_t* configs,
+                            const gcf_samples* out) {
+  if (!c || n_chains < 0 || n_sweeps < 1 || (n_chains > 0 && !configs)) return GCF_EINVAL;
+  if (n_chains == 0) return GCF_OK;
+  gcf_samples o{};
+  if (out) o = *out;
+  int want = (o.log_abs || o.phase ? WANT_AMP : 0) | (o.e_loc ? WANT_ELOC : 0) |
+             (o.O || o.block_ids ? WANT_GRAD : 0);
+  int gauss = 0;
+  gcf_status st = dispatch(c, 1, want, n_chains, n_sweeps, seed, configs, &o, &gauss);
+  if (st != GCF_OK) return st;
+  if (gauss) return fail(c, GCF_EGAUSS, "starting configuration violates the Gauss law");
+  return GCF_OK;
+}
+
+gcf_status gcf_sr_step(gcf_ctx* c, int n_samples, int n_chains, const double* e_loc,
+                       const int32_t* block_ids, const void* O, double diag_shift, double lr,
+                       int mode, double dt, int max_iter, double tol, double* stats) {
+  if (!c || n_samples < 1 || n_chains < 1 || n_samples % n_chains != 0 || !e_loc || !block_ids ||
+      !O || !stats || max_iter < 0 || !(diag_shift >= 0.0))
+    return GCF_EINVAL;
+  if (mode != GCF_SR && mode != GCF_TDVP_STAGE1 && mode != GCF_TDVP_STAGE2) return GCF_EINVAL;
+  if (mode != GCF_SR && c->m.dtype != GCF_COMPLEX)
+    return fail(c, GCF_EINVAL, "TDVP modes need complex tensors");
+  gcf_status st = ensure_sr(c, n_samples, n_chains);
+  if (st != GCF_OK) return st;
+  double cr = -lr, ci = 0.0;
+  if (mode != GCF_SR) {
+    // A += c_k dt (-i x), c_{1,2} = (1 +- i)/2  ->  coefficient c_k * dt * (-i)
+    const double sgn = mode == GCF_TDVP_STAGE1 ? 1.0 : -1.0;
+    const double kr = 0.5 * dt, ki = 0.5 * sgn * dt;  // c_k dt
+    cr = ki;    // (kr + i ki)(-i) = ki - i kr
+    ci = -kr;
+  }
+  SrGeom g{};
+  g.Np = c->n_params; g.Ns = n_samples; g.n_s = c->n_s;
+  g.D4 = c->Dk * c->Dk * c->Dk * c->Dk;
+  g.voff = c->d_voff; g.vbs = c->d_vbs; g.vnb = c->d_vnb;
+  int mx = 1;
+  for (int v = 0; v < c->n_s; ++v) mx = std::max(mx, c->vbs[v] * c->vnb[v]);
+  g.max_nb_bs = mx;
+  cudaError_t e;
+  switch (c->kind) {
+    case S_F32:
+      e = sr_solve_update<float>(g, c->sr, e_loc, block_ids, O, c->d_params, n_chains, diag_shift, cr, ci,
+                                 max_iter, tol, stats, c->stream, &c->launches);
+      break;
+    case S_F64:
+      e = sr_solve_update<double>(g, c->sr, e_loc, block_ids, O, c->d_params, n_chains, diag_shift, cr, ci,
+                                  max_iter, tol, stats, c->stream, &c->launches);
+      break;
+    case S_C64:
+      e = sr_solve_update<cfloat>(g, c->sr, e_loc, block_ids, O, c->d_params, n_chains, diag_shift, cr, ci,
+                                  max_iter, tol, stats, c->stream, &c->launches);
+      break;
+    default:
+      e = sr_solve_update<cdouble>(g, c->sr, e_loc, block_ids, O, c->d_params, n_chains, diag_shift, cr, ci,
+                                   max_iter, tol, stats, c->stream, &c->launches);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "gcf_sr_step");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (stats[6] == 0.0 && max_iter > 0) return fail(c, GCF_ETIMEOUT, "CG reached max_iter before tol");
+  return GCF_OK;
+}
+
+gcf_status gcf_vmc_step_host(gcf_ctx* c, int n_chains, int n_sweeps, uint64_t seed, int8_t* host_configs,
+                             double diag_shift, double lr, int mode, double dt, int max_iter, double tol,
+                             double* stats) {
+  if (!c || n_chains < 1 || n_sweeps < 1 || !host_configs || !stats) return GCF_EINVAL;
+  const long long ns = (long long)n_chains * n_sweeps;
+  const int D4 = c->Dk * c->Dk * c->Dk * c->Dk;
+  if (ns > c->e2e_cap || n_chains > c->e2e_chains) {
+    void* ptrs[] = {c->d_cfg, c->d_e, c->d_la, c->d_ph, c->d_bid, c->d_O, c->d_acc};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    c->d_cfg = nullptr; c->d_e = c->d_la = c->d_ph = nullptr; c->d_bid = c->d_acc = nullptr;
+    c->d_O = nullptr;
+    bool ok = cudaMalloc(&c->d_cfg, (size_t)n_chains * c->cfg_len) == cudaSuccess &&
+              cudaMalloc(&c->d_e, sizeof(double) * 2 * ns) == cudaSuccess &&
+              cudaMalloc(&c->d_la, sizeof(double) * ns) == cudaSuccess &&
+              cudaMalloc(&c->d_ph, sizeof(double) * ns) == cudaSuccess &&
+              cudaMalloc(&c->d_bid, sizeof(int) * ns * c->n_s) == cudaSuccess &&
+              cudaMalloc(&c->d_O, c->sbytes * ns * c->n_s * D4) == cudaSuccess &&
+              cudaMalloc(&c->d_acc, sizeof(int) * 2 * n_chains) == cudaSuccess;
+    if (!ok) return fail(c, GCF_ENOMEM, "e2e sample buffers");
+    c->e2e_cap = ns;
+    c->e2e_chains = n_chains;
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_cfg, host_configs, (size_t)n_chains * c->cfg_len,
+                              cudaMemcpyHostToDevice, c->stream));
+  gcf_samples o{};
+  o.log_abs = c->d_la; o.phase = c->d_ph; o.e_loc = c->d_e; o.block_ids = c->d_bid; o.O = c->d_O;
+  o.accepted = c->d_acc; o.proposed = c->d_acc + n_chains;
+  gcf_status st = gcf_sample_batch(c, n_chains, n_sweeps, seed, c->d_cfg, &o);
+  if (st != GCF_OK) return st;
+  st = gcf_sr_step(c, (int)ns, n_chains, c->d_e, c->d_bid, c->d_O, diag_shift, lr, mode, dt, max_iter,
+                   tol, stats);
+  if (st != GCF_OK && st != GCF_ETIMEOUT) return st;
+  CUDA_TRY(c, cudaMemcpyAsync(host_configs, c->d_cfg, (size_t)n_chains * c->cfg_len,
+                              cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Scalar types, complex arithmetic and CTA-wide helpers shared by the
+// GB300 kernels of the GCF-PEPS VMC library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+namespace gcf {
+
+struct cfloat { float x, y; };
+struct cdouble { double x, y; };
+
+// ---- scalar traits -----------------------------------------------------
+template <class T> struct Traits;
+template <> struct Traits<float> {
+  using R = float; static constexpr bool cplx = false;
+  __host__ __device__ static constexpr float eps() { return 1.1920929e-07f; }
+};
+template <> struct Traits<double> {
+  using R = double; static constexpr bool cplx = false;
+  __host__ __device__ static constexpr double eps() { return 2.220446049250313e-16; }
+};
+template <> struct Traits<cfloat> {
+  using R = float; static constexpr bool cplx = true;
+  __host__ __device__ static constexpr float eps() { return 1.1920929e-07f; }
+};
+template <> struct Traits<cdouble> {
+  using R = double; static constexpr bool cplx = true;
+  __host__ __device__ static constexpr double eps() { return 2.220446049250313e-16; }
+};
+
+// ---- arithmetic (real overloads are the identity where appropriate) ------
+__host__ __device__ inline float zero_of(float) { return 0.f; }
+__host__ __device__ inline double zero_of(double) { return 0.0; }
+__host__ __device__ inline cfloat zero_of(cfloat) { return {0.f, 0.f}; }
+__host__ __device__ inline cdouble zero_of(cdouble) { return {0.0, 0.0}; }
+template <class T> __host__ __device__ inline T zero() { return zero_of(T()); }
+
+__host__ __device__ inline float one_of(float) { return 1.f; }
+__host__ __device__ inline double one_of(double) { return 1.0; }
+__host__ __device__ inline cfloat one_of(cfloat) { return {1.f, 0.f}; }
+__host__ __device__ inline cdouble one_of(cdouble) { return {1.0, 0.0}; }
+template <class T> __host__ __device__ inline T one() { return one_of(T()); }
+
+__host__ __device__ inline float conjg(float a) { return a; }
+__host__ __device__ inline double conjg(double a) { return a; }
+__host__ __device__ inline cfloat conjg(cfloat a) { return {a.x, -a.y}; }
+__host__ __device__ inline cdouble conjg(cdouble a) { return {a.x, -a.y}; }
+
+__host__ __device__ inline float re(float a) { return a; }
+__host__ __device__ inline double re(double a) { return a; }
+__host__ __device__ inline float re(cfloat a) { return a.x; }
+__host__ __device__ inline double re(cdouble a) { return a.x; }
+__host__ __device__ inline float im(float) { return 0.f; }
+__host__ __device__ inline double im(double) { return 0.0; }
+__host__ __device__ inline float im(cfloat a) { return a.y; }
+__host__ __device__ inline double im(cdouble a) { return a.y; }
+
+__host__ __device__ inline float abs2(float a) { return a * a; }
+__host__ __device__ inline double abs2(double a) { return a * a; }
+__host__ __device__ inline float abs2(cfloat a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ inline double abs2(cdouble a) { return a.x * a.x + a.y * a.y; }
+
+__host__ __device__ inline float absmax1(float a) { return fabsf(a); }
+__host__ __device__ inline double absmax1(double a) { return fabs(a); }
+__host__ __device__ inline float absmax1(cfloat a) { return fmaxf(fabsf(a.x), fabsf(a.y)); }
+__host__ __device__ inline double absmax1(cdouble a) { return fmax(fabs(a.x), fabs(a.y)); }
+
+__host__ __device__ inline cfloat operator+(cfloat a, cfloat b) { return {a.x + b.x, a.y + b.y}; }
+__host__ __device__ inline cdouble operator+(cdouble a, cdouble b) { return {a.x + b.x, a.y + b.y}; }
+__host__ __device__ inline cfloat operator-(cfloat a, cfloat b) { return {a.x - b.x, a.y - b.y}; }
+__host__ __device__ inline cdouble operator-(cdouble a, cdouble b) { return {a.x - b.x, a.y - b.y}; }
+__host__ __device__ inline cfloat operator-(cfloat a) { return {-a.x, -a.y}; }
+__host__ __device__ inline cdouble operator-(cdouble a) { return {-a.x, -a.y}; }
+__host__ __device__ inline cfloat operator*(cfloat a, cfloat b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+__host__ __device__ inline cdouble operator*(cdouble a, cdouble b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+__host__ __device__ inline cfloat operator*(cfloat a, float s) { return {a.x * s, a.y * s}; }
+__host__ __device__ inline cdouble operator*(cdouble a, double s) { return {a.x * s, a.y * s}; }
+__host__ __device__ inline cfloat& operator+=(cfloat& a, cfloat b) { a.x += b.x; a.y += b.y; return a; }
+__host__ __device__ inline cdouble& operator+=(cdouble& a, cdouble b) { a.x += b.x; a.y += b.y; return a; }
+__host__ __device__ inline cfloat& operator-=(cfloat& a, cfloat b) { a.x -= b.x; a.y -= b.y; return a; }
+__host__ __device__ inline cdouble& operator-=(cdouble& a, cdouble b) { a.x -= b.x; a.y -= b.y; return a; }
+
+// fused multiply-add acc + a*b
+__device__ inline float fmac(float acc, float a, float b) { return fmaf(a, b, acc); }
+__device__ inline double fmac(double acc, double a, double b) { return fma(a, b, acc); }
+__device__ inline cfloat fmac(cfloat acc, cfloat a, cfloat b) {
+  acc.x = fmaf(a.x, b.x, acc.x); acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y); acc.y = fmaf(a.y, b.x, acc.y);
+  return acc;
+}
+__device__ inline cdouble fmac(cdouble acc, cdouble a, cdouble b) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+
+__host__ __device__ inline float scale(float a, float s) { return a * s; }
+__host__ __device__ inline double scale(double a, double s) { return a * s; }
+__host__ __device__ inline cfloat scale(cfloat a, float s) { return {a.x * s, a.y * s}; }
+__host__ __device__ inline cdouble scale(cdouble a, double s) { return {a.x * s, a.y * s}; }
+
+template <class T> __host__ __device__ inline T make_scalar(double r, double i);
+template <> __host__ __device__ inline float make_scalar<float>(double r, double) { return (float)r; }
+template <> __host__ __device__ inline double make_scalar<double>(double r, double) { return r; }
+template <> __host__ __device__ inline cfloat make_scalar<cfloat>(double r, double i) { return {(float)r, (float)i}; }
+template <> __host__ __device__ inline cdouble make_scalar<cdouble>(double r, double i) { return {r, i}; }
+
+// complex division a / b (b != 0)
+__device__ inline float cdiv(float a, float b) { return a / b; }
+__device__ inline double cdiv(double a, double b) { return a / b; }
+__device__ inline cfloat cdiv(cfloat a, cfloat b) {
+  float d = b.x * b.x + b.y * b.y;
+  return {(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
+}
+__device__ inline cdouble cdiv(cdouble a, cdouble b) {
+  double d = b.x * b.x + b.y * b.y;
+  return {(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
+}
+
+// ---- CTA reductions (all threads must call; result broadcast) -----------
+// `red` is shared scratch of at least 32 doubles.
+template <class R>
+__device__ inline R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <class R>
+__device__ inline R warp_max(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ inline double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ inline double block_max(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? red[threadIdx.x] : -1.0;
+  if (wid == 0) t = warp_max(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// complex sum: two doubles
+__device__ inline void block_sum2(double& a, double& b, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  a = warp_sum(a); b = warp_sum(b);
+  __syncthreads();
+  if (lane == 0) { red[wid] = a; red[32 + wid] = b; }
+  __syncthreads();
+  double ta = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  double tb = (threadIdx.x < nw) ? red[32 + threadIdx.x] : 0.0;
+  if (wid == 0) { ta = warp_sum(ta); tb = warp_sum(tb); }
+  if (threadIdx.x == 0) { red[0] = ta; red[32] = tb; }
+  __syncthreads();
+  a = red[0]; b = red[32];
+  __syncthreads();
+}
+
+// ---- SplitMix64 counter generator (Steele, Lea & Flood 2014) -------------
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+static constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+__host__ __device__ inline uint64_t stream_key(uint64_t seed, uint64_t stream) {
+  return mix64(seed + (stream + 1) * kGamma);
+}
+__host__ __device__ inline uint64_t stream_word(uint64_t key, uint64_t counter) {
+  return mix64(key + (counter + 1) * kGamma);
+}
+__host__ __device__ inline double word_to_uniform(uint64_t w) {
+  return (double)(w >> 11) * (1.0 / 9007199254740992.0);
+}
+
+}  // namespace gcf

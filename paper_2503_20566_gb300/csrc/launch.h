@@ -1,0 +1,15 @@
+// Launch entry points of the per-type VMC kernels (one translation unit each).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace gcf {
+template <class T> struct KParams;
+template <class T>
+cudaError_t launch_vmc(const KParams<T>& k, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_init_configs(int N, int Lx, int Ly, int matter, const int* Q, int n_chains,
+                                const int8_t* occ, const int8_t* powers, int8_t* configs,
+                                int* status, cudaStream_t st);
+}  // namespace gcf

@@ -1,0 +1,218 @@
+// CTA-cooperative dense linear algebra on small matrices (one chain per CTA):
+// strided GEMM, Householder QR / LQ and one-sided Jacobi SVD.
+//
+// Every routine is called by all threads of the CTA with identical arguments;
+// matrices live in global scratch or shared memory and are addressed through
+// (row stride, column stride), so transposed views cost nothing.  Routines
+// end with __syncthreads() so their results are visible on return.
+//
+// The algorithms are the textbook ones: Householder QR (Golub & Van Loan,
+// "Matrix Computations", Alg. 5.1.1 / 5.2.1, with the complex reflector that
+// maps x to -sign(Re x_1) |x| e_1) and the one-sided (Hestenes) Jacobi SVD
+// with the round-robin pair schedule.
+#pragma once
+
+#include "common.cuh"
+
+namespace gcf {
+
+// C(i,j) = [C(i,j) +] sum_k op(A)(i,k) op(B)(k,j); op = optional conjugation.
+template <class T, bool CA = false, bool CB = false>
+__device__ __noinline__ void cta_gemm(int M, int N, int K, const T* A, int sAm, int sAk, const T* B,
+                         int sBk, int sBn, T* C, int sCm, int sCn, bool accumulate) {
+  const int MN = M * N;
+  for (int idx = threadIdx.x; idx < MN; idx += blockDim.x) {
+    const int i = idx / N, j = idx - (idx / N) * N;
+    T s = accumulate ? C[i * sCm + j * sCn] : zero<T>();
+    const T* a = A + i * sAm;
+    const T* b = B + j * sBn;
+    for (int k = 0; k < K; ++k) {
+      T av = a[k * sAk], bv = b[k * sBk];
+      if (CA) av = conjg(av);
+      if (CB) bv = conjg(bv);
+      s = fmac(s, av, bv);
+    }
+    C[i * sCm + j * sCn] = s;
+  }
+  __syncthreads();
+}
+
+template <class T>
+__device__ inline T warp_sum_scalar(T v);
+template <>
+__device__ inline float warp_sum_scalar<float>(float v) { return warp_sum(v); }
+template <>
+__device__ inline double warp_sum_scalar<double>(double v) { return warp_sum(v); }
+template <>
+__device__ inline cfloat warp_sum_scalar<cfloat>(cfloat v) { return {warp_sum(v.x), warp_sum(v.y)}; }
+template <>
+__device__ inline cdouble warp_sum_scalar<cdouble>(cdouble v) { return {warp_sum(v.x), warp_sum(v.y)}; }
+
+// Householder reflector for column (alpha; x) with |x|^2 = xn2:
+// H = I - tau v v^H, v = (1; x * scal), H^H (alpha; x) = (beta; 0), beta real.
+template <class T>
+__device__ inline void householder(T alpha, double xn2, T& tau, T& scal, T& beta) {
+  using R = typename Traits<T>::R;
+  const double ar = (double)re(alpha), ai = (double)im(alpha);
+  if (xn2 == 0.0 && ai == 0.0) {
+    tau = zero<T>(); scal = zero<T>(); beta = alpha;
+    return;
+  }
+  double b = sqrt(ar * ar + ai * ai + xn2);
+  if (ar >= 0.0) b = -b;
+  tau = make_scalar<T>((b - ar) / b, -ai / b);
+  // scal = 1 / (alpha - beta)
+  const double dr = ar - b, di = ai;
+  const double d2 = dr * dr + di * di;
+  scal = make_scalar<T>(dr / d2, -di / d2);
+  beta = make_scalar<T>(b, 0.0);
+  (void)sizeof(R);
+}
+
+// In-place Householder QR of A (m x n): on return the upper triangle of the
+// leading k = min(m,n) rows holds R, the part below the diagonal holds the
+// reflector vectors, tau[0..k) their factors.  `red` is shared scratch (64 doubles).
+template <class T>
+__device__ __noinline__ void cta_qr(int m, int n, T* A, int sm, int sn, T* tau, double* red) {
+  const int k = min(m, n);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < k; ++j) {
+    double part = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) part += (double)abs2(A[i * sm + j * sn]);
+    const double xn2 = block_sum(part, red);
+    const T alpha = A[j * sm + j * sn];
+    T t, sc, beta;
+    householder(alpha, xn2, t, sc, beta);
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[i * sm + j * sn] = A[i * sm + j * sn] * sc;
+    if (threadIdx.x == 0) { A[j * sm + j * sn] = beta; tau[j] = t; }
+    __syncthreads();
+    const T ct = conjg(t);
+    for (int c = j + 1 + wid; c < n; c += nw) {
+      T w = zero<T>();
+      for (int i = j + lane; i < m; i += 32) {
+        const T v = (i == j) ? one<T>() : A[i * sm + j * sn];
+        w = fmac(w, conjg(v), A[i * sm + c * sn]);
+      }
+      w = warp_sum_scalar(w);
+      const T f = ct * w;
+      for (int i = j + lane; i < m; i += 32) {
+        const T v = (i == j) ? one<T>() : A[i * sm + j * sn];
+        A[i * sm + c * sn] -= v * f;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Q = H_0 H_1 ... H_{k-1} restricted to its first k columns (m x k), from
+// the reflectors stored by cta_qr in A.
+template <class T>
+__device__ __noinline__ void cta_form_q(int m, int k, const T* A, int sm, int sn, const T* tau, T* Q, int sQm,
+                           int sQn) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x) {
+    const int i = idx / k, c = idx - (idx / k) * k;
+    Q[i * sQm + c * sQn] = (i == c) ? one<T>() : zero<T>();
+  }
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {
+    const T t = tau[j];
+    for (int c = j + wid; c < k; c += nw) {
+      T w = zero<T>();
+      for (int i = j + lane; i < m; i += 32) {
+        const T v = (i == j) ? one<T>() : A[i * sm + j * sn];
+        w = fmac(w, conjg(v), Q[i * sQm + c * sQn]);
+      }
+      w = warp_sum_scalar(w);
+      const T f = t * w;
+      for (int i = j + lane; i < m; i += 32) {
+        const T v = (i == j) ? one<T>() : A[i * sm + j * sn];
+        Q[i * sQm + c * sQn] -= v * f;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Copy with optional conjugate-transpose: dst(i,j) = src(j,i)^* for i<rows, j<cols.
+template <class T>
+__device__ __noinline__ void cta_adjoint(int rows, int cols, const T* src, int sSm, int sSn, T* dst, int sDm,
+                            int sDn) {
+  for (int idx = threadIdx.x; idx < rows * cols; idx += blockDim.x) {
+    const int i = idx / cols, j = idx - (idx / cols) * cols;
+    dst[i * sDm + j * sDn] = conjg(src[j * sSm + i * sSn]);
+  }
+  __syncthreads();
+}
+
+// One-sided Jacobi on the columns of W (p x q), accumulating J (q x q, reset
+// to the identity here) so that on return W = W_in J has mutually orthogonal
+// columns.  Returns the number of sweeps used; *converged set to 0 if the
+// sweep limit was hit.  sflag: shared int scratch.
+template <class T>
+__device__ __noinline__ int cta_jacobi_svd(int p, int q, T* W, int sWm, int sWn, T* J, int sJm, int sJn,
+                              int* sflag, int max_sweeps, int* converged) {
+  using R = typename Traits<T>::R;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int idx = threadIdx.x; idx < q * q; idx += blockDim.x) {
+    const int i = idx / q, c = idx - (idx / q) * q;
+    J[i * sJm + c * sJn] = (i == c) ? one<T>() : zero<T>();
+  }
+  const int n = q + (q & 1);
+  const double tol = 8.0 * (double)Traits<T>::eps();
+  int sweep = 0;
+  if (converged) *converged = 1;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) *sflag = 0;
+    __syncthreads();
+    for (int r = 0; r < n - 1; ++r) {
+      for (int kp = wid; kp < n / 2; kp += nw) {
+        int a, b;
+        if (kp == 0) { a = r % (n - 1); b = n - 1; }
+        else { a = (r + kp) % (n - 1); b = (r - kp + n - 1) % (n - 1); }
+        if (a >= q || b >= q) continue;
+        if (a > b) { int t = a; a = b; b = t; }
+        double al = 0.0, be = 0.0;
+        T g = zero<T>();
+        for (int i = lane; i < p; i += 32) {
+          const T wa = W[i * sWm + a * sWn], wb = W[i * sWm + b * sWn];
+          al += (double)abs2(wa);
+          be += (double)abs2(wb);
+          g = fmac(g, conjg(wa), wb);
+        }
+        al = warp_sum(al); be = warp_sum(be); g = warp_sum_scalar(g);
+        const double gr = (double)re(g), gi = (double)im(g);
+        const double ga = sqrt(gr * gr + gi * gi);
+        if (ga == 0.0 || !(ga > tol * sqrt(al * be))) continue;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        // G = [[c, s e^{i phi}], [-s e^{-i phi}, c]], e^{i phi} = g / |g|
+        const T eph = make_scalar<T>(gr / ga, gi / ga);
+        const T s_e = scale(eph, (R)s);                 // s e^{i phi}
+        const T s_ec = scale(conjg(eph), (R)s);         // s e^{-i phi}
+        for (int i = lane; i < p; i += 32) {
+          const T wa = W[i * sWm + a * sWn], wb = W[i * sWm + b * sWn];
+          W[i * sWm + a * sWn] = scale(wa, (R)c) - wb * s_ec;
+          W[i * sWm + b * sWn] = wa * s_e + scale(wb, (R)c);
+        }
+        for (int i = lane; i < q; i += 32) {
+          const T ja = J[i * sJm + a * sJn], jb = J[i * sJm + b * sJn];
+          J[i * sJm + a * sJn] = scale(ja, (R)c) - jb * s_ec;
+          J[i * sJm + b * sJn] = ja * s_e + scale(jb, (R)c);
+        }
+        if (lane == 0) *sflag = 1;
+      }
+      __syncthreads();
+    }
+    const int any = *sflag;
+    __syncthreads();
+    if (!any) break;
+  }
+  if (sweep >= max_sweeps && converged) *converged = 0;
+  __syncthreads();
+  return sweep;
+}
+
+}  // namespace gcf

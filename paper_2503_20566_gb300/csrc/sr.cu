@@ -1,0 +1,331 @@
+// FP64 reductions and the stochastic-reconfiguration / tVMC solve.
+//
+// Paper, Sec. S-1 (Eq. S3, read as F = <O^* E> - <O^*><E>) and Sec. S-3
+// (Eqs. S6-S8): S_mn = <O_m^* O_n> - <O_m^*><O_n>; (S + lambda) x = F is
+// solved by conjugate gradient without forming S, using the sparsity of O:
+// sample s touches exactly one block per vertex.
+//   S v = (1/Ns) sum_s O_s^* (t_s - tbar),  t_s = O_s . v,  tbar = mean_s t_s.
+// Everything here runs in FP64 (complex FP64 for complex tensors).
+#include "sr.cuh"
+
+namespace gcf {
+
+__device__ inline void atomic_add_c(cdouble* a, double r, double i) {
+  atomicAdd(&a->x, r);
+  atomicAdd(&a->y, i);
+}
+
+template <class T>
+__device__ inline cdouble to_cd(T v) {
+  return {(double)re(v), (double)im(v)};
+}
+
+// t_s = sum_v sum_e O[s][v][e] * x[off(v, bid) + e]; one warp per sample.
+template <class T>
+__global__ void k_gather_dot(SrGeom g, const int* bids, const T* O, const cdouble* x, cdouble* t) {
+  const int lane = threadIdx.x & 31;
+  const long long s = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (s >= g.Ns) return;
+  double ar = 0.0, ai = 0.0;
+  for (int v = 0; v < g.n_s; ++v) {
+    const int bid = bids[s * g.n_s + v];
+    const int bs = g.vbs[v];
+    const long long base = g.voff[v] + (long long)bid * bs;
+    const T* o = O + (s * g.n_s + v) * (long long)g.D4;
+    for (int e = lane; e < bs; e += 32) {
+      const cdouble a = to_cd(o[e]);
+      const cdouble b = x[base + e];
+      ar += a.x * b.x - a.y * b.y;
+      ai += a.x * b.y + a.y * b.x;
+    }
+  }
+  ar = warp_sum(ar);
+  ai = warp_sum(ai);
+  if (lane == 0) t[s] = {ar, ai};
+}
+
+// out[off(v,bid)+e] += sum_s coef_s * conj?(O[s][v][e]) for one vertex per
+// blockIdx.y and a chunk of samples per blockIdx.x; block-local accumulation
+// in shared memory (all blocks of the vertex), flushed with global atomics.
+template <class T, bool CONJ>
+__global__ void k_scatter(SrGeom g, const int* bids, const T* O, const cdouble* coef, cdouble* out,
+                          int chunk) {
+  extern __shared__ double acc[];  // 2 * nb_v * bs_v
+  const int v = blockIdx.y;
+  const int bs = g.vbs[v];
+  const int nb = g.vnb[v];
+  const int n = nb * bs;
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) acc[i] = 0.0;
+  __syncthreads();
+  const long long s0 = (long long)blockIdx.x * chunk;
+  const long long s1 = min((long long)g.Ns, s0 + chunk);
+  const long long tot = (s1 - s0) * bs;
+  for (long long q = threadIdx.x; q < tot; q += blockDim.x) {
+    const long long s = s0 + q / bs;
+    const int e = (int)(q % bs);
+    const int bid = bids[s * g.n_s + v];
+    cdouble o = to_cd(O[(s * g.n_s + v) * (long long)g.D4 + e]);
+    if (CONJ) o.y = -o.y;
+    const cdouble c = coef[s];
+    const double pr = c.x * o.x - c.y * o.y, pi = c.x * o.y + c.y * o.x;
+    atomicAdd(&acc[2 * (bid * bs + e)], pr);
+    atomicAdd(&acc[2 * (bid * bs + e) + 1], pi);
+  }
+  __syncthreads();
+  cdouble* dst = out + g.voff[v];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double r = acc[2 * i], im_ = acc[2 * i + 1];
+    if (r != 0.0 || im_ != 0.0) atomic_add_c(&dst[i], r, im_);
+  }
+}
+
+// per-chain means of E_loc and the global mean (one block per chain)
+__global__ void k_chain_means(const double* e, int n_per_chain, cdouble* chain_mean) {
+  __shared__ double red[64];
+  const int c = blockIdx.x;
+  double r = 0.0, i = 0.0;
+  for (int s = threadIdx.x; s < n_per_chain; s += blockDim.x) {
+    r += e[2 * ((long long)c * n_per_chain + s)];
+    i += e[2 * ((long long)c * n_per_chain + s) + 1];
+  }
+  block_sum2(r, i, red);
+  if (threadIdx.x == 0) chain_mean[c] = {r / n_per_chain, i / n_per_chain};
+}
+
+// mean and std error over m values (single block); out[0..2] = Re, Im, err
+__global__ void k_mean_err(const cdouble* v, int m, double* out) {
+  __shared__ double red[64];
+  double r = 0.0, i = 0.0;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) { r += v[k].x; i += v[k].y; }
+  block_sum2(r, i, red);
+  const double mr = r / m, mi = i / m;
+  double q = 0.0;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) q += (v[k].x - mr) * (v[k].x - mr);
+  q = block_sum(q, red);
+  if (threadIdx.x == 0) {
+    out[0] = mr;
+    out[1] = mi;
+    out[2] = m > 1 ? sqrt(q / (m - 1) / m) : 0.0;
+  }
+}
+
+// E_loc as complex per sample; coefficient for F: (E_s - Ebar) / Ns
+__global__ void k_f_coef(const double* e, long long Ns, const double* emean, cdouble* coef) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= Ns) return;
+  coef[s] = {(e[2 * s] - emean[0]) / (double)Ns, (e[2 * s + 1] - emean[1]) / (double)Ns};
+}
+
+// coef_s = (t_s - tbar) / Ns where tbar = mean t
+__global__ void k_center(cdouble* t, long long Ns, const cdouble* tbar) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= Ns) return;
+  t[s] = {(t[s].x - tbar->x) / (double)Ns, (t[s].y - tbar->y) / (double)Ns};
+}
+
+__global__ void k_sum_c(const cdouble* v, long long n, cdouble* out, double scale_) {
+  __shared__ double red[64];
+  double r = 0.0, i = 0.0;
+  for (long long k = threadIdx.x; k < n; k += blockDim.x) { r += v[k].x; i += v[k].y; }
+  block_sum2(r, i, red);
+  if (threadIdx.x == 0) *out = {r * scale_, i * scale_};
+}
+
+// dot products <a, b> = sum conj(a) b (single block, grid-stride)
+__global__ void k_dot(const cdouble* a, const cdouble* b, long long n, double* out) {
+  __shared__ double red[64];
+  double r = 0.0, i = 0.0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    r += a[k].x * b[k].x + a[k].y * b[k].y;
+    i += a[k].x * b[k].y - a[k].y * b[k].x;
+  }
+  block_sum2(r, i, red);
+  if (threadIdx.x == 0) { atomicAdd(&out[0], r); atomicAdd(&out[1], i); }
+}
+
+// y = y + lambda x (the diagonal shift)
+__global__ void k_axpy_real(cdouble* y, const cdouble* x, double a, long long n) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) { y[k].x += a * x[k].x; y[k].y += a * x[k].y; }
+}
+
+// CG vector update: x += alpha p; r -= alpha Ap; alpha = rr / pAp (real)
+__global__ void k_cg_xr(cdouble* x, cdouble* r, const cdouble* p, const cdouble* Ap,
+                        const double* sc, long long n) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double alpha = sc[0] / sc[2];
+  x[k].x += alpha * p[k].x; x[k].y += alpha * p[k].y;
+  r[k].x -= alpha * Ap[k].x; r[k].y -= alpha * Ap[k].y;
+}
+
+// p = r + beta p, beta = rr_new / rr_old
+__global__ void k_cg_p(cdouble* p, const cdouble* r, const double* sc, long long n) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double beta = sc[4] / sc[0];
+  p[k].x = r[k].x + beta * p[k].x;
+  p[k].y = r[k].y + beta * p[k].y;
+}
+
+// params += c * x  (c complex); real storage takes the real part
+template <class T>
+__global__ void k_update(T* params, const cdouble* x, double cr, double ci, long long n) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double dr = cr * x[k].x - ci * x[k].y;
+  const double di = cr * x[k].y + ci * x[k].x;
+  T v = params[k];
+  params[k] = make_scalar<T>((double)re(v) + dr, (double)im(v) + di);
+}
+
+__global__ void k_fill_c(cdouble* v, long long n, double r, double i) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) v[k] = {r, i};
+}
+
+__global__ void k_e_to_c(const double* e, long long n, cdouble* v) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) v[k] = {e[2 * k], e[2 * k + 1]};
+}
+
+__global__ void k_copy_scalar(double* sc) { sc[0] = sc[4]; sc[1] = sc[5]; }
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+template <class T>
+static cudaError_t scatter(const SrGeom& g, const int* bids, const T* O, const cdouble* coef,
+                           cdouble* out, bool conj, cudaStream_t st, long long* launches) {
+  const int chunk = 4096;
+  dim3 grid((unsigned)((g.Ns + chunk - 1) / chunk), (unsigned)g.n_s);
+  const size_t smem = 2 * sizeof(double) * (size_t)g.max_nb_bs;
+  if (conj)
+    k_scatter<T, true><<<grid, 256, smem, st>>>(g, bids, O, coef, out, chunk);
+  else
+    k_scatter<T, false><<<grid, 256, smem, st>>>(g, bids, O, coef, out, chunk);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+template <class T>
+static cudaError_t dot(const cdouble* a, const cdouble* b, long long n, double* out, cudaStream_t st,
+                       long long* launches) {
+  cudaError_t err = cudaMemsetAsync(out, 0, 2 * sizeof(double), st);
+  if (err != cudaSuccess) return err;
+  const int grid = (int)std::min<long long>(nblk(n, 256), 1024);
+  k_dot<<<grid, 256, 0, st>>>(a, b, n, out);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t sr_solve_update(const SrGeom& g, SrWork& w, const double* e_loc, const int* bids,
+                            const void* Ov, void* params, int n_chains, double shift, double cr,
+                            double ci, int max_iter, double tol, double* stats, cudaStream_t st,
+                            long long* launches) {
+  const T* O = (const T*)Ov;
+  const long long Np = g.Np, Ns = g.Ns;
+  cudaError_t err;
+#define CK(x)                                   \
+  do {                                          \
+    if ((err = (x)) != cudaSuccess) return err; \
+  } while (0)
+  // energy mean and error bar (over chain means, or over samples for one chain)
+  if (n_chains > 1) {
+    k_chain_means<<<n_chains, 256, 0, st>>>(e_loc, (int)(Ns / n_chains), w.chain_mean);
+    ++*launches;
+    k_mean_err<<<1, 1024, 0, st>>>(w.chain_mean, n_chains, w.scal);
+  } else {
+    k_e_to_c<<<nblk(Ns, 256), 256, 0, st>>>(e_loc, Ns, w.coef);
+    ++*launches;
+    k_mean_err<<<1, 1024, 0, st>>>(w.coef, (int)Ns, w.scal);
+  }
+  ++*launches;
+  CK(cudaGetLastError());
+  // Obar = (1/Ns) sum_s O_s
+  CK(cudaMemsetAsync(w.obar, 0, sizeof(cdouble) * Np, st));
+  k_fill_c<<<nblk(Ns, 256), 256, 0, st>>>(w.coef, Ns, 1.0 / (double)Ns, 0.0);
+  ++*launches;
+  CK(scatter<T>(g, bids, O, w.coef, w.obar, false, st, launches));
+  // F = (1/Ns) sum_s conj(O_s) (E_s - Ebar)
+  k_f_coef<<<nblk(Ns, 256), 256, 0, st>>>(e_loc, Ns, w.scal, w.coef);
+  ++*launches;
+  CK(cudaMemsetAsync(w.F, 0, sizeof(cdouble) * Np, st));
+  CK(scatter<T>(g, bids, O, w.coef, w.F, true, st, launches));
+  // CG: x = 0, r = p = F
+  CK(cudaMemsetAsync(w.x, 0, sizeof(cdouble) * Np, st));
+  CK(cudaMemcpyAsync(w.r, w.F, sizeof(cdouble) * Np, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(w.p, w.F, sizeof(cdouble) * Np, cudaMemcpyDeviceToDevice, st));
+  CK(dot<T>(w.r, w.r, Np, w.scal + 8, st, launches));   // sc[0] = rr
+  double h_sc[8];
+  CK(cudaMemcpyAsync(h_sc, w.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double e_re = h_sc[0], e_im = h_sc[1], e_err = h_sc[2];
+  double rr0;
+  CK(cudaMemcpy(&rr0, w.scal + 8, sizeof(double), cudaMemcpyDeviceToHost));
+  const double fnorm = sqrt(rr0);
+  double rr = rr0;
+  int it = 0;
+  double* sc = w.scal + 8;  // sc[0..1] rr, sc[2..3] pAp, sc[4..5] rr_new
+  bool converged = !(fnorm > 0.0);
+  while (!converged && it < max_iter) {
+    // Ap = S p + shift p
+    k_gather_dot<T><<<nblk(Ns * 32, 256), 256, 0, st>>>(g, bids, O, w.p, w.t);
+    ++*launches;
+    k_sum_c<<<1, 1024, 0, st>>>(w.t, Ns, w.tbar, 1.0 / (double)Ns);
+    ++*launches;
+    k_center<<<nblk(Ns, 256), 256, 0, st>>>(w.t, Ns, w.tbar);
+    ++*launches;
+    CK(cudaMemsetAsync(w.Ap, 0, sizeof(cdouble) * Np, st));
+    CK(scatter<T>(g, bids, O, w.t, w.Ap, true, st, launches));
+    k_axpy_real<<<nblk(Np, 256), 256, 0, st>>>(w.Ap, w.p, shift, Np);
+    ++*launches;
+    CK(dot<T>(w.p, w.Ap, Np, sc + 2, st, launches));
+    k_cg_xr<<<nblk(Np, 256), 256, 0, st>>>(w.x, w.r, w.p, w.Ap, sc, Np);
+    ++*launches;
+    CK(dot<T>(w.r, w.r, Np, sc + 4, st, launches));
+    k_cg_p<<<nblk(Np, 256), 256, 0, st>>>(w.p, w.r, sc, Np);
+    ++*launches;
+    k_copy_scalar<<<1, 1, 0, st>>>(sc);
+    ++*launches;
+    double rn;
+    CK(cudaMemcpyAsync(&rn, sc + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    rr = rn;
+    ++it;
+    if (sqrt(rr) <= tol * fnorm) converged = true;
+  }
+  CK(cudaGetLastError());
+  k_update<T><<<nblk(Np, 256), 256, 0, st>>>((T*)params, w.x, cr, ci, Np);
+  ++*launches;
+  CK(cudaGetLastError());
+  stats[0] = e_re;
+  stats[1] = e_im;
+  stats[2] = e_err;
+  stats[3] = (double)it;
+  stats[4] = fnorm > 0.0 ? sqrt(rr) / fnorm : 0.0;
+  stats[5] = fnorm;
+  stats[6] = converged ? 1.0 : 0.0;
+  stats[7] = 0.0;
+  return cudaSuccess;
+#undef CK
+}
+
+template cudaError_t sr_solve_update<float>(const SrGeom&, SrWork&, const double*, const int*,
+                                            const void*, void*, int, double, double, double, int,
+                                            double, double*, cudaStream_t, long long*);
+template cudaError_t sr_solve_update<double>(const SrGeom&, SrWork&, const double*, const int*,
+                                             const void*, void*, int, double, double, double, int,
+                                             double, double*, cudaStream_t, long long*);
+template cudaError_t sr_solve_update<cfloat>(const SrGeom&, SrWork&, const double*, const int*,
+                                             const void*, void*, int, double, double, double, int,
+                                             double, double*, cudaStream_t, long long*);
+template cudaError_t sr_solve_update<cdouble>(const SrGeom&, SrWork&, const double*, const int*,
+                                              const void*, void*, int, double, double, double, int,
+                                              double, double*, cudaStream_t, long long*);
+
+}  // namespace gcf

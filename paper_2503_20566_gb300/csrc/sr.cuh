@@ -1,0 +1,37 @@
+// FP64 stochastic-reconfiguration / tVMC solve (declarations).
+#pragma once
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace gcf {
+
+struct SrGeom {
+  long long Np;        // number of parameters
+  long long Ns;        // number of samples
+  int n_s;             // vertices
+  int D4;              // O slot per vertex (D_k^4)
+  const long long* voff;  // device [n_s]
+  const int* vbs;         // device [n_s] block size
+  const int* vnb;         // device [n_s] number of blocks
+  int max_nb_bs;          // max_v nb*bs
+};
+
+struct SrWork {
+  cdouble *obar, *F, *x, *r, *p, *Ap;  // [Np]
+  cdouble *t, *coef;                   // [Ns]
+  cdouble *chain_mean;                 // [n_chains]
+  cdouble *tbar;                       // [1]
+  double* scal;                        // [16] device scalars
+};
+
+// Computes <E>, F, solves (S + shift) x = F by CG, then params += (cr + i ci) x.
+// stats[8] as documented for gcf_sr_step.
+template <class T>
+cudaError_t sr_solve_update(const SrGeom& g, SrWork& w, const double* e_loc, const int* bids,
+                            const void* O, void* params, int n_chains, double shift, double cr,
+                            double ci, int max_iter, double tol, double* stats, cudaStream_t st,
+                            long long* launches);
+
+}  // namespace gcf

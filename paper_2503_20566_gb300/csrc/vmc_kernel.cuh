@@ -1,0 +1,633 @@
+// The persistent VMC kernel: one CTA per Markov chain at a time.
+//
+// mode 0 (measure): for each given configuration, absorb rows bottom-up into
+//   B[r], then run the measurement pass.
+// mode 1 (sample): for each chain, build T[r] top-down once, then per sweep
+//   the plaquette pass (bottom-up, Metropolis, Sec. S-1/S-2), with matter the
+//   horizontal-hop pass (top-down) and vertical-hop pass (bottom-up), then the
+//   measurement pass, whose T[r] serve the next sweep.
+// Measurement pass (top-down over rows r): 3-layer row environments of row r
+//   give O (Eq. S3), horizontal-hop ratios and, for r = Ly-1, the amplitude;
+//   the 4-layer strip (r, r+1) gives plaquette and vertical-hop ratios for
+//   E_loc (Eq. S2); then T[r] = absorb(T[r+1], row r).
+#pragma once
+
+#include "peps_dev.cuh"
+
+namespace gcf {
+
+struct SharedV {
+  Shared base;
+  int offB[MAX_L + 1];
+  int offT[MAX_L + 1];
+  double logB[MAX_L + 2];
+  double logT[MAX_L + 2];
+  double logR[MAX_L + 2];
+  double eacc[2];
+  int bid_tmp[8];
+  int n_acc, n_prop;
+};
+
+template <class T>
+struct Chain {
+  const KParams<T>& k;
+  T* ws;
+  SharedV& sv;
+  int8_t* cfg;  // shared copy of the configuration
+  int chain;
+  unsigned long long key;
+
+  __device__ Chain(const KParams<T>& kk, T* w, SharedV& s, int8_t* c, int ch)
+      : k(kk), ws(w), sv(s), cfg(c), chain(ch) {
+    key = stream_key(k.seed, (unsigned long long)ch);
+  }
+
+  __device__ T* Bslot(int j) const { return ws + k.o_B + (long long)j * k.mps_stride; }
+  __device__ T* Tslot(int r) const { return ws + k.o_T + (long long)r * k.mps_stride; }
+  __device__ const int* bdB(int j) const { return k.bondB + j * (k.Lx + 1); }
+  __device__ const int* bdT(int r) const { return k.bondT + r * (k.Lx + 1); }
+  __device__ int physB(int j) const { return j == 0 ? 1 : k.Dk; }   // B[j-1] phys = up dim of row j-1
+  __device__ int physT(int r) const { return r == k.Ly ? 1 : k.Dk; } // T[r] phys = down dim of row r
+  __device__ T* box(int x, int y) const { return net_box(k, ws, x, y); }
+  __device__ T* prop(int i) const { return ws + k.o_prop + i * (k.Dk * k.Dk * k.Dk * k.Dk); }
+
+  // ---- configuration moves on the shared copy (thread 0 writes) ---------
+  __device__ void plaq_apply(int x, int y, int t) {
+    if (threadIdx.x == 0) {
+      const int N = k.N;
+      int8_t* h = cfg;
+      int8_t* v = cfg + k.n_h;
+      h[y * (k.Lx - 1) + x] = (int8_t)((h[y * (k.Lx - 1) + x] + t) % N);
+      v[y * k.Lx + x + 1] = (int8_t)((v[y * k.Lx + x + 1] + t) % N);
+      h[(y + 1) * (k.Lx - 1) + x] = (int8_t)((h[(y + 1) * (k.Lx - 1) + x] - t + N) % N);
+      v[y * k.Lx + x] = (int8_t)((v[y * k.Lx + x] - t + N) % N);
+    }
+    __syncthreads();
+  }
+  // Hop across link (x,a): returns 1 if a move exists (and applies it).
+  // On a hard-core lattice the hop available after a hop is its inverse, so
+  // calling this again reverts the move.
+  __device__ int hop_apply(int x, int y, int a) {
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+      const int N = k.N;
+      const int x2 = a == 1 ? x + 1 : x, y2 = a == 1 ? y : y + 1;
+      int8_t* p = cfg + k.n_h + k.n_v;
+      int8_t* lk = a == 1 ? &cfg[y * (k.Lx - 1) + x] : &cfg[k.n_h + y * k.Lx + x];
+      const int s1 = y * k.Lx + x, s2 = y2 * k.Lx + x2;
+      ok = 0;
+      // forward: boson from x+e to x raises the link; conjugate lowers it
+      int dir = 0;
+      if (p[s1] == 0 && p[s2] == 1) dir = +1;
+      else if (p[s1] == 1 && p[s2] == 0) dir = -1;
+      if (dir != 0) {
+        p[s1] = (int8_t)(1 - p[s1]);
+        p[s2] = (int8_t)(1 - p[s2]);
+        *lk = (int8_t)(((int)*lk + dir + N) % N);
+        ok = 1;
+      }
+    }
+    __syncthreads();
+    const int r = ok;
+    __syncthreads();
+    return r;
+  }
+
+  __device__ __noinline__ void gather_into(int x, int y, T* dst) {
+    const int bid = block_of(k, cfg, x, y);
+    if (bid < 0) {
+      if (threadIdx.x == 0) atomicAdd(&k.status[ST_GAUSS], 1);
+      return;
+    }
+    gather_box(k, x, y, bid, dst);
+  }
+
+  __device__ __noinline__ bool check_and_gather_all() {
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int v = threadIdx.x; v < k.n_s; v += blockDim.x) {
+      if (block_of(k, cfg, v % k.Lx, v / k.Lx) < 0) bad = 1;
+    }
+    __syncthreads();
+    const bool ok = bad == 0;
+    __syncthreads();
+    if (!ok) return false;
+    for (int y = 0; y < k.Ly; ++y)
+      for (int x = 0; x < k.Lx; ++x) gather_box(k, x, y, block_of(k, cfg, x, y), box(x, y));
+    __syncthreads();
+    return true;
+  }
+
+  // ---- boundary MPS --------------------------------------------------------
+  __device__ __noinline__ void absorb_B(int r) {  // B[r] = absorb(B[r-1], row r)
+    const double ls = absorb_compress(k, ws, sv.base, Bslot(r), bdB(r), physB(r), r, 0, Bslot(r + 1),
+                                      bdB(r + 1), physB(r + 1), k.qrB + r * (k.Lx + 1),
+                                      k.svdB + r * (k.Lx + 1));
+    if (threadIdx.x == 0) sv.logB[r + 1] = sv.logB[r] + ls;
+    __syncthreads();
+  }
+  __device__ __noinline__ void absorb_T(int r) {  // T[r] = absorb(T[r+1], row r flipped)
+    const double ls = absorb_compress(k, ws, sv.base, Tslot(r + 1), bdT(r + 1), physT(r + 1), r, 1,
+                                      Tslot(r), bdT(r), physT(r), k.qrT + r * (k.Lx + 1),
+                                      k.svdT + r * (k.Lx + 1));
+    if (threadIdx.x == 0) sv.logT[r] = sv.logT[r + 1] + ls;
+    __syncthreads();
+  }
+
+  // ---- strip (rows r, r+1) between B[r-1] (slot r) and T[r+2] -------------
+  __device__ StripDims sdims(int r, int c) const {
+    StripDims d;
+    const int* bb = bdB(r);
+    const int* bt = bdT(r + 2);
+    d.nA = bb[c]; d.nB = bt[c];
+    d.nI = d.nJ = hl_dim(c, k.Dk);
+    d.nA2 = bb[c + 1]; d.nB2 = bt[c + 1];
+    d.nI2 = d.nJ2 = hr_dim(c, k.Lx, k.Dk);
+    d.pB = physB(r); d.pM = k.Dk; d.pT = physT(r + 2);
+    return d;
+  }
+  __device__ int env_size(const StripDims& d, bool right) const {
+    return right ? d.nA2 * d.nI2 * d.nJ2 * d.nB2 : d.nA * d.nI * d.nJ * d.nB;
+  }
+  __device__ T* envR(int c) const { return ws + k.o_envR + (long long)c * k.env_stride; }
+
+  // builds R_c for c = Lx..0 (logs in sv.logR), returns strip value (re, im) and log
+  __device__ __noinline__ void strip_right_envs(int r, double& vr, double& vi, double& vlog) {
+    const int Lx = k.Lx;
+    mps_offsets(bdB(r), physB(r), Lx, sv.offB);
+    mps_offsets(bdT(r + 2), physT(r + 2), Lx, sv.offT);
+    if (threadIdx.x == 0) { envR(Lx)[0] = one<T>(); sv.logR[Lx] = 0.0; }
+    __syncthreads();
+    for (int c = Lx - 1; c >= 0; --c) {
+      const StripDims d = sdims(r, c);
+      strip_right_step<T>(k.Dk, d, envR(c + 1), Bslot(r) + sv.offB[c], box(c, r), box(c, r + 1),
+                          Tslot(r + 2) + sv.offT[c], envR(c), ws + k.o_t1, ws + k.o_t2, ws + k.o_t3);
+      const double ls = rescale(envR(c), env_size(d, false), sv.base.red);
+      if (threadIdx.x == 0) sv.logR[c] = sv.logR[c + 1] + ls;
+      __syncthreads();
+    }
+    vr = (double)re(envR(0)[0]);
+    vi = (double)im(envR(0)[0]);
+    vlog = sv.logR[0];
+    __syncthreads();
+  }
+
+  __device__ __noinline__ double strip_step_left(int r, int c, const T* Lin, const T* W1, const T* W2, T* out) {
+    const StripDims d = sdims(r, c);
+    strip_left_step<T>(k.Dk, d, Lin, Bslot(r) + sv.offB[c], W1, W2, Tslot(r + 2) + sv.offT[c], out,
+                       ws + k.o_t1, ws + k.o_t2, ws + k.o_t3);
+    return rescale(out, env_size(d, true), sv.base.red);
+  }
+
+  // ---- row r between B[r-1] (slot r) and T[r+1] ---------------------------
+  __device__ RowDims rdims(int r, int c) const {
+    RowDims d;
+    const int* bb = bdB(r);
+    const int* bt = bdT(r + 1);
+    d.nA = bb[c]; d.nB = bt[c]; d.nH = hl_dim(c, k.Dk);
+    d.nA2 = bb[c + 1]; d.nB2 = bt[c + 1]; d.nH2 = hr_dim(c, k.Lx, k.Dk);
+    d.pB = physB(r); d.pT = physT(r + 1);
+    return d;
+  }
+  __device__ T* env3R(int c) const { return ws + k.o_env3R + (long long)c * k.env3_stride; }
+
+  __device__ __noinline__ void row_right_envs(int r, double& vr, double& vi, double& vlog) {
+    const int Lx = k.Lx;
+    mps_offsets(bdB(r), physB(r), Lx, sv.offB);
+    mps_offsets(bdT(r + 1), physT(r + 1), Lx, sv.offT);
+    if (threadIdx.x == 0) { env3R(Lx)[0] = one<T>(); sv.logR[Lx] = 0.0; }
+    __syncthreads();
+    for (int c = Lx - 1; c >= 0; --c) {
+      const RowDims d = rdims(r, c);
+      row_right_step<T>(k.Dk, d, env3R(c + 1), Bslot(r) + sv.offB[c], box(c, r),
+                        Tslot(r + 1) + sv.offT[c], env3R(c), ws + k.o_t1, ws + k.o_t2);
+      const double ls = rescale(env3R(c), d.nA * d.nH * d.nB, sv.base.red);
+      if (threadIdx.x == 0) sv.logR[c] = sv.logR[c + 1] + ls;
+      __syncthreads();
+    }
+    vr = (double)re(env3R(0)[0]);
+    vi = (double)im(env3R(0)[0]);
+    vlog = sv.logR[0];
+    __syncthreads();
+  }
+
+  __device__ __noinline__ double row_step_left(int r, int c, const T* Lin, const T* W, T* out) {
+    const RowDims d = rdims(r, c);
+    row_left_step<T>(k.Dk, d, Lin, Bslot(r) + sv.offB[c], W, Tslot(r + 1) + sv.offT[c], out,
+                     ws + k.o_t1, ws + k.o_t2);
+    return rescale(out, d.nA2 * d.nH2 * d.nB2, sv.base.red);
+  }
+
+  // ---- RNG -------------------------------------------------------------------
+  __device__ double uniform_at(unsigned long long ctr) const {
+    return word_to_uniform(stream_word(key, ctr));
+  }
+  __device__ int power_at(unsigned long long ctr) const {
+    if (k.N == 2) return 1;
+    return 1 + (int)(stream_word(key, ctr) % (unsigned long long)(k.N - 1));
+  }
+};
+
+// log|z|^2 helper with z = (vr, vi) * exp(vlog); -inf for z = 0
+__device__ inline double log_abs2(double vr, double vi, double vlog) {
+  const double a2 = vr * vr + vi * vi;
+  if (!(a2 > 0.0)) return -INFINITY;
+  return log(a2) + 2.0 * vlog;
+}
+
+// ratio (nr + i ni) e^{nl} / ((dr + i di) e^{dl})
+__device__ inline void ratio_of(double nr, double ni, double nl, double dr, double di, double dl,
+                                double& rr, double& ri) {
+  const double d2 = dr * dr + di * di;
+  const double f = exp(nl - dl) / d2;
+  rr = (nr * dr + ni * di) * f;
+  ri = (ni * dr - nr * di) * f;
+}
+
+template <class T>
+__device__ void copy_box(T* dst, const T* src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// ---------------------------------------------------------------------------
+// Passes
+// ---------------------------------------------------------------------------
+
+// plaquette pass, bottom-up, Metropolis
+template <class T>
+__device__ __noinline__ void plaquette_pass(Chain<T>& ch, int w) {
+  const KParams<T>& k = ch.k;
+  const int Lx = k.Lx, Ly = k.Ly, D4 = k.Dk * k.Dk * k.Dk * k.Dk;
+  T* Lc = ch.ws + k.o_envL;
+  T* X1 = ch.ws + k.o_envX;
+  T* X2 = ch.ws + k.o_envY;
+  for (int r = 0; r < Ly - 1; ++r) {
+    double dr, di, dl;
+    ch.strip_right_envs(r, dr, di, dl);
+    if (threadIdx.x == 0) Lc[0] = one<T>();
+    __syncthreads();
+    double logL = 0.0;
+    for (int c = 0; c < Lx - 1; ++c) {
+      const int j = r * (Lx - 1) + c;
+      const unsigned long long base = (unsigned long long)w * k.n_slots;
+      const int t = ch.power_at(base + 2 * j);
+      const double u = ch.uniform_at(base + 2 * j + 1);
+      ch.plaq_apply(c, r, t);
+      ch.gather_into(c, r, ch.prop(0));
+      ch.gather_into(c + 1, r, ch.prop(1));
+      ch.gather_into(c, r + 1, ch.prop(2));
+      ch.gather_into(c + 1, r + 1, ch.prop(3));
+      __syncthreads();
+      const double l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
+      const double l2 = ch.strip_step_left(r, c + 1, X1, ch.prop(1), ch.prop(3), X2);
+      double nr, ni;
+      const StripDims d2 = ch.sdims(r, c + 1);
+      cta_dot(X2, ch.envR(c + 2), ch.env_size(d2, true), ch.sv.base.red, nr, ni);
+      const double nl = logL + l1 + l2 + ch.sv.logR[c + 2];
+      const bool acc = (log(u) + log_abs2(dr, di, dl)) < log_abs2(nr, ni, nl) ||
+                       (u == 0.0 && (nr != 0.0 || ni != 0.0));
+      if (threadIdx.x == 0) { ch.sv.n_prop += 1; if (acc) ch.sv.n_acc += 1; }
+      if (acc) {
+        copy_box(ch.box(c, r), ch.prop(0), D4);
+        copy_box(ch.box(c + 1, r), ch.prop(1), D4);
+        copy_box(ch.box(c, r + 1), ch.prop(2), D4);
+        copy_box(ch.box(c + 1, r + 1), ch.prop(3), D4);
+        dr = nr; di = ni; dl = nl;
+        // L_{c+1} is X1 (built from the accepted column c)
+        const StripDims d1 = ch.sdims(r, c);
+        const int n1 = ch.env_size(d1, true);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
+        logL += l1;
+      } else {
+        ch.plaq_apply(c, r, k.N - t);  // revert
+        logL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), X1);
+        const StripDims d1 = ch.sdims(r, c);
+        const int n1 = ch.env_size(d1, true);
+        for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
+      }
+      __syncthreads();
+    }
+    ch.absorb_B(r);
+  }
+}
+
+// horizontal-hop pass (matter), top-down with row environments
+template <class T>
+__device__ __noinline__ void hhop_pass(Chain<T>& ch, int w) {
+  const KParams<T>& k = ch.k;
+  const int Lx = k.Lx, Ly = k.Ly, D4 = k.Dk * k.Dk * k.Dk * k.Dk;
+  T* Lc = ch.ws + k.o_env3L;
+  T* X1 = ch.ws + k.o_env3X;
+  T* X2 = ch.ws + k.o_env3Y;
+  for (int r = Ly - 1; r >= 0; --r) {
+    double dr, di, dl;
+    ch.row_right_envs(r, dr, di, dl);
+    if (threadIdx.x == 0) Lc[0] = one<T>();
+    __syncthreads();
+    double logL = 0.0;
+    for (int c = 0; c < Lx - 1; ++c) {
+      const unsigned long long ctr =
+          (unsigned long long)w * k.n_slots + 2 * k.n_plaq + r * (Lx - 1) + c;
+      const double u = ch.uniform_at(ctr);
+      bool acc = false;
+      double l1 = 0.0;
+      if (ch.hop_apply(c, r, 1)) {
+        ch.gather_into(c, r, ch.prop(0));
+        ch.gather_into(c + 1, r, ch.prop(1));
+        __syncthreads();
+        l1 = ch.row_step_left(r, c, Lc, ch.prop(0), X1);
+        const double l2 = ch.row_step_left(r, c + 1, X1, ch.prop(1), X2);
+        double nr, ni;
+        const RowDims d2 = ch.rdims(r, c + 1);
+        cta_dot(X2, ch.env3R(c + 2), d2.nA2 * d2.nH2 * d2.nB2, ch.sv.base.red, nr, ni);
+        const double nl = logL + l1 + l2 + ch.sv.logR[c + 2];
+        acc = (log(u) + log_abs2(dr, di, dl)) < log_abs2(nr, ni, nl) ||
+              (u == 0.0 && (nr != 0.0 || ni != 0.0));
+        if (threadIdx.x == 0) { ch.sv.n_prop += 1; if (acc) ch.sv.n_acc += 1; }
+        if (acc) {
+          copy_box(ch.box(c, r), ch.prop(0), D4);
+          copy_box(ch.box(c + 1, r), ch.prop(1), D4);
+          dr = nr; di = ni; dl = nl;
+        } else {
+          ch.hop_apply(c, r, 1);
+        }
+      }
+      __syncthreads();
+      const RowDims d1 = ch.rdims(r, c);
+      const int n1 = d1.nA2 * d1.nH2 * d1.nB2;
+      if (acc) {
+        for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
+        logL += l1;
+      } else {
+        logL += ch.row_step_left(r, c, Lc, ch.box(c, r), X1);
+        for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
+      }
+      __syncthreads();
+    }
+    if (r >= 1) ch.absorb_T(r);
+  }
+}
+
+// vertical-hop pass (matter), bottom-up with strip environments
+template <class T>
+__device__ __noinline__ void vhop_pass(Chain<T>& ch, int w) {
+  const KParams<T>& k = ch.k;
+  const int Lx = k.Lx, Ly = k.Ly, D4 = k.Dk * k.Dk * k.Dk * k.Dk;
+  T* Lc = ch.ws + k.o_envL;
+  T* X1 = ch.ws + k.o_envX;
+  for (int r = 0; r < Ly - 1; ++r) {
+    double dr, di, dl;
+    ch.strip_right_envs(r, dr, di, dl);
+    if (threadIdx.x == 0) Lc[0] = one<T>();
+    __syncthreads();
+    double logL = 0.0;
+    for (int c = 0; c < Lx; ++c) {
+      const unsigned long long ctr =
+          (unsigned long long)w * k.n_slots + 2 * k.n_plaq + k.n_h + r * Lx + c;
+      const double u = ch.uniform_at(ctr);
+      bool acc = false;
+      double l1 = 0.0;
+      if (ch.hop_apply(c, r, 2)) {
+        ch.gather_into(c, r, ch.prop(0));
+        ch.gather_into(c, r + 1, ch.prop(2));
+        __syncthreads();
+        l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
+        double nr, ni;
+        const StripDims d1 = ch.sdims(r, c);
+        cta_dot(X1, ch.envR(c + 1), ch.env_size(d1, true), ch.sv.base.red, nr, ni);
+        const double nl = logL + l1 + ch.sv.logR[c + 1];
+        acc = (log(u) + log_abs2(dr, di, dl)) < log_abs2(nr, ni, nl) ||
+              (u == 0.0 && (nr != 0.0 || ni != 0.0));
+        if (threadIdx.x == 0) { ch.sv.n_prop += 1; if (acc) ch.sv.n_acc += 1; }
+        if (acc) {
+          copy_box(ch.box(c, r), ch.prop(0), D4);
+          copy_box(ch.box(c, r + 1), ch.prop(2), D4);
+          dr = nr; di = ni; dl = nl;
+        } else {
+          ch.hop_apply(c, r, 2);
+        }
+      }
+      __syncthreads();
+      const StripDims d1 = ch.sdims(r, c);
+      const int n1 = ch.env_size(d1, true);
+      T* Lnext = ch.ws + k.o_envY;
+      if (acc) {
+        for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
+        logL += l1;
+      } else {
+        logL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), Lnext);
+        for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = Lnext[i];
+      }
+      __syncthreads();
+    }
+    ch.absorb_B(r);
+  }
+}
+
+// measurement pass, top-down; writes sample s
+template <class T>
+__device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
+  const KParams<T>& k = ch.k;
+  const int Lx = k.Lx, Ly = k.Ly, Dk = k.Dk, D4 = Dk * Dk * Dk * Dk;
+  const bool want_e = (k.want & WANT_ELOC) && k.e_loc;
+  const bool want_g = (k.want & WANT_GRAD) && (k.O || k.block_ids);
+  const bool want_a = (k.want & WANT_AMP) && (k.log_abs || k.phase);
+  if (threadIdx.x == 0) { ch.sv.eacc[0] = 0.0; ch.sv.eacc[1] = 0.0; }
+  __syncthreads();
+  for (int r = Ly - 1; r >= 0; --r) {
+    // ---- row r: gradient, horizontal hops, amplitude
+    const bool need_row = want_g || (r == Ly - 1 && want_a) || (want_e && k.matter && k.J != 0.0);
+    if (need_row) {
+      double dr, di, dl;
+      ch.row_right_envs(r, dr, di, dl);
+      if (r == Ly - 1 && want_a && threadIdx.x == 0) {
+        const double a2 = dr * dr + di * di;
+        const double la = (a2 > 0.0) ? ch.sv.logB[Ly - 1] + dl + 0.5 * log(a2) : -INFINITY;
+        if (k.log_abs) k.log_abs[s] = la;
+        if (k.phase) k.phase[s] = (a2 > 0.0) ? atan2(di, dr) : 0.0;
+      }
+      T* Lc = ch.ws + k.o_env3L;
+      T* X1 = ch.ws + k.o_env3X;
+      T* X2 = ch.ws + k.o_env3Y;
+      if (threadIdx.x == 0) Lc[0] = one<T>();
+      __syncthreads();
+      double logL = 0.0;
+      const double den2 = dr * dr + di * di;
+      for (int c = 0; c < Lx; ++c) {
+        const RowDims d = ch.rdims(r, c);
+        if (want_g) {
+          T* G = ch.ws + k.o_G;
+          row_site_open<T>(Dk, d, Lc, ch.Bslot(r) + ch.sv.offB[c], ch.Tslot(r + 1) + ch.sv.offT[c],
+                           ch.env3R(c + 1), G, ch.ws + k.o_t1, ch.ws + k.o_t2);
+          // O = G * exp(logL + logR[c+1] - dl) / (dr + i di)
+          const double f = exp(logL + ch.sv.logR[c + 1] - dl) / den2;
+          const T fac = make_scalar<T>(dr * f, -di * f);
+          const int v = r * Lx + c;
+          const int n = d.nH * d.nH2 * d.pB * d.pT;
+          if (k.O) {
+            T* dst = k.O + (s * k.n_s + v) * (long long)D4;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = G[i] * fac;
+          }
+          if (k.block_ids && threadIdx.x == 0) k.block_ids[s * k.n_s + v] = block_of(k, ch.cfg, c, r);
+        }
+        if (want_e && k.matter && k.J != 0.0 && c < Lx - 1) {
+          if (ch.hop_apply(c, r, 1)) {
+            ch.gather_into(c, r, ch.prop(0));
+            ch.gather_into(c + 1, r, ch.prop(1));
+            __syncthreads();
+            const double l1 = ch.row_step_left(r, c, Lc, ch.prop(0), X1);
+            const double l2 = ch.row_step_left(r, c + 1, X1, ch.prop(1), X2);
+            double nr, ni;
+            const RowDims d2 = ch.rdims(r, c + 1);
+            cta_dot(X2, ch.env3R(c + 2), d2.nA2 * d2.nH2 * d2.nB2, ch.sv.base.red, nr, ni);
+            double rr, ri;
+            ratio_of(nr, ni, logL + l1 + l2 + ch.sv.logR[c + 2], dr, di, dl, rr, ri);
+            if (threadIdx.x == 0) { ch.sv.eacc[0] += k.J * rr; ch.sv.eacc[1] += k.J * ri; }
+            ch.hop_apply(c, r, 1);
+          }
+        }
+        if (c < Lx - 1) {
+          logL += ch.row_step_left(r, c, Lc, ch.box(c, r), X1);
+          const int n1 = d.nA2 * d.nH2 * d.nB2;
+          for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
+          __syncthreads();
+        }
+      }
+    }
+    // ---- strip (r, r+1): plaquettes and vertical hops
+    if (want_e && r <= Ly - 2) {
+      double dr, di, dl;
+      ch.strip_right_envs(r, dr, di, dl);
+      T* Lc = ch.ws + k.o_envL;
+      T* X1 = ch.ws + k.o_envX;
+      T* X2 = ch.ws + k.o_envY;
+      if (threadIdx.x == 0) Lc[0] = one<T>();
+      __syncthreads();
+      double logL = 0.0;
+      const int npow = k.N == 2 ? 1 : 2;
+      const double amp = k.N == 2 ? -2.0 * k.h : -k.h;
+      for (int c = 0; c < Lx; ++c) {
+        if (c < Lx - 1 && k.h != 0.0) {
+          for (int q = 0; q < npow; ++q) {
+            const int t = q == 0 ? 1 : k.N - 1;
+            ch.plaq_apply(c, r, t);
+            ch.gather_into(c, r, ch.prop(0));
+            ch.gather_into(c + 1, r, ch.prop(1));
+            ch.gather_into(c, r + 1, ch.prop(2));
+            ch.gather_into(c + 1, r + 1, ch.prop(3));
+            __syncthreads();
+            const double l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
+            const double l2 = ch.strip_step_left(r, c + 1, X1, ch.prop(1), ch.prop(3), X2);
+            double nr, ni;
+            const StripDims d2 = ch.sdims(r, c + 1);
+            cta_dot(X2, ch.envR(c + 2), ch.env_size(d2, true), ch.sv.base.red, nr, ni);
+            double rr, ri;
+            ratio_of(nr, ni, logL + l1 + l2 + ch.sv.logR[c + 2], dr, di, dl, rr, ri);
+            if (threadIdx.x == 0) { ch.sv.eacc[0] += amp * rr; ch.sv.eacc[1] += amp * ri; }
+            ch.plaq_apply(c, r, k.N - t);
+          }
+        }
+        if (k.matter && k.J != 0.0) {
+          if (ch.hop_apply(c, r, 2)) {
+            ch.gather_into(c, r, ch.prop(0));
+            ch.gather_into(c, r + 1, ch.prop(2));
+            __syncthreads();
+            const double l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
+            double nr, ni;
+            const StripDims d1 = ch.sdims(r, c);
+            cta_dot(X1, ch.envR(c + 1), ch.env_size(d1, true), ch.sv.base.red, nr, ni);
+            double rr, ri;
+            ratio_of(nr, ni, logL + l1 + ch.sv.logR[c + 1], dr, di, dl, rr, ri);
+            if (threadIdx.x == 0) { ch.sv.eacc[0] += k.J * rr; ch.sv.eacc[1] += k.J * ri; }
+            ch.hop_apply(c, r, 2);
+          }
+        }
+        if (c < Lx - 1) {
+          const StripDims d1 = ch.sdims(r, c);
+          logL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), X1);
+          const int n1 = ch.env_size(d1, true);
+          for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
+          __syncthreads();
+        }
+      }
+    }
+    // ---- T[r]
+    if (r >= 1 && (k.mode == 1 || want_e || want_g)) ch.absorb_T(r);
+  }
+  if (want_e && threadIdx.x == 0) {
+    // diagonal part: g sum_links (2 - 2 cos(2 pi n / N)) + m sum_x p_x
+    double e = 0.0;
+    const double w0 = 2.0 * 3.14159265358979323846 / k.N;
+    for (int i = 0; i < k.n_h + k.n_v; ++i) e += k.g * (2.0 - 2.0 * cos(w0 * ch.cfg[i]));
+    if (k.matter)
+      for (int i = 0; i < k.n_s; ++i) e += k.m * ch.cfg[k.n_h + k.n_v + i];
+    k.e_loc[2 * s] = e + ch.sv.eacc[0];
+    k.e_loc[2 * s + 1] = ch.sv.eacc[1];
+  }
+  __syncthreads();
+}
+
+template <class T>
+__device__ void init_trivial_slots(const KParams<T>& k, T* ws) {
+  for (int c = threadIdx.x; c < k.Lx; c += blockDim.x) {
+    (ws + k.o_B)[c] = one<T>();                                     // B[-1]
+    (ws + k.o_T + (long long)k.Ly * k.mps_stride)[c] = one<T>();    // T[Ly]
+  }
+  __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) vmc_kernel(KParams<T> k) {
+  extern __shared__ int8_t dyn_cfg[];
+  __shared__ SharedV sv;
+  T* ws = ws_of(k);
+  init_trivial_slots(k, ws);
+  for (int chain = blockIdx.x; chain < k.n_chains; chain += gridDim.x) {
+    int8_t* gcfg = k.configs + (long long)chain * k.cfg_len;
+    for (int i = threadIdx.x; i < k.cfg_len; i += blockDim.x) dyn_cfg[i] = gcfg[i];
+    if (threadIdx.x == 0) {
+      sv.logB[0] = 0.0; sv.logT[k.Ly] = 0.0; sv.n_acc = 0; sv.n_prop = 0;
+    }
+    __syncthreads();
+    Chain<T> ch(k, ws, sv, dyn_cfg, chain);
+    const bool ok = ch.check_and_gather_all();
+    if (!ok) {
+      if (threadIdx.x == 0) {
+        atomicAdd(&k.status[ST_GAUSS], 1);
+        const int ns = k.mode == 1 ? k.n_sweeps : 1;
+        for (int w = 0; w < ns; ++w) {
+          const long long s = (long long)chain * ns + w;
+          if (k.log_abs) k.log_abs[s] = -INFINITY;
+          if (k.phase) k.phase[s] = 0.0;
+          if (k.e_loc) { k.e_loc[2 * s] = NAN; k.e_loc[2 * s + 1] = NAN; }
+        }
+      }
+      __syncthreads();
+      continue;
+    }
+    if (k.mode == 0) {
+      for (int r = 0; r < k.Ly - 1; ++r) ch.absorb_B(r);
+      measure_pass(ch, (long long)chain);
+    } else {
+      for (int r = k.Ly - 1; r >= 2; --r) ch.absorb_T(r);
+      for (int w = 0; w < k.n_sweeps; ++w) {
+        plaquette_pass(ch, w);
+        if (k.matter) {
+          hhop_pass(ch, w);
+          vhop_pass(ch, w);
+        }
+        measure_pass(ch, (long long)chain * k.n_sweeps + w);
+      }
+      for (int i = threadIdx.x; i < k.cfg_len; i += blockDim.x) gcfg[i] = dyn_cfg[i];
+      if (threadIdx.x == 0) {
+        if (k.accepted) k.accepted[chain] = sv.n_acc;
+        if (k.proposed) k.proposed[chain] = sv.n_prop;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace gcf
