@@ -199,6 +199,33 @@ gcf_status gcf_vmc_step_host(gcf_ctx* ctx, int n_chains, int n_sweeps, uint64_t 
                              int8_t* host_configs, double diag_shift, double lr, int mode,
                              double dt, int max_iter, double tol, double* stats);
 
+/* Amplitude evaluation that allocates nothing: the same computation and
+ * result as gcf_amplitude, for callers that cannot call cudaMalloc during the
+ * call -- code that runs while a stream is being captured into a CUDA graph
+ * (allocation is not allowed inside a capture), services that reserve all
+ * device memory up front and forbid allocation on the request path, and
+ * embedders whose own allocator owns the device (a foreign cudaMalloc would
+ * fragment or exceed its pool).  (The paper has no counterpart; this is an
+ * interface addition.)
+ * - Scratch comes from one fixed array of 32 MiB compiled into the library
+ *   (static device storage that every GPU which loads the library holds until
+ *   the process exits), not from cudaMalloc.  The context itself must already
+ *   exist: gcf_init_peps allocates, so create it at set-up time.
+ * - The first call on each device looks up the array's device address with
+ *   that device current; make that first call before any stream capture.  The
+ *   device current at the call must be the context's device (else GCF_EINVAL).
+ * - A lattice whose per-CTA scratch exceeds 32 MiB is rejected with
+ *   GCF_EINVAL and a message giving the required size; otherwise the number
+ *   of CTAs is capped at what fits, and any n >= 1 is accepted.
+ * - Every call shares the array, which keeps the previous call's contents:
+ *   calls whose kernels overlap on the GPU (two streams, two contexts, two
+ *   host threads) race on it and return wrong amplitudes; serialise them.
+ * - The call does not synchronise the stream; outputs are ready when the
+ *   context's stream reaches this point.
+ * Arguments and outputs exactly as gcf_amplitude. */
+gcf_status gcf_amplitude_noalloc(gcf_ctx* ctx, int n, const int8_t* configs, double* log_abs,
+                                 double* phase);
+
 /* Number of kernel launches this context issued since creation (for
  * accounting in benchmarks). */
 int64_t gcf_launch_count(const gcf_ctx* ctx);

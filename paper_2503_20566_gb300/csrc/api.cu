@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -657,3 +658,89 @@ gcf_status gcf_vmc_step_host(gcf_ctx* c, int n_chains, int n_sweeps, uint64_t se
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// gcf_amplitude_noalloc: scratch from a fixed device array instead of
+// cudaMalloc.  In host code g_noalloc_scratch / g_noalloc_status name host-side
+// stand-ins, not device addresses: the kernel is given the address returned
+// by cudaGetSymbolAddress, looked up once per device with that device current.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_scratch_ptr[kMaxDevices] = {};
+int* g_noalloc_status_ptr[kMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+static __device__ __align__(256) int g_noalloc_status[4];
+
+namespace {
+gcf_status noalloc_setup(gcf_ctx* c, void** scratch, int** status) {
+  int dev = -1;
+  CUDA_TRY(c, cudaGetDevice(&dev));
+  if (dev != c->device || dev < 0 || dev >= kMaxDevices)
+    return fail(c, GCF_EINVAL, "gcf_amplitude_noalloc: the context's device must be current");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_scratch_ptr[dev]) {
+    void* p = nullptr;
+    void* q = nullptr;
+    CUDA_TRY(c, cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    CUDA_TRY(c, cudaGetSymbolAddress(&q, g_noalloc_status));
+    g_noalloc_scratch_ptr[dev] = p;
+    g_noalloc_status_ptr[dev] = (int*)q;
+  }
+  *scratch = g_noalloc_scratch_ptr[dev];
+  *status = g_noalloc_status_ptr[dev];
+  return GCF_OK;
+}
+
+template <class T>
+gcf_status amplitude_noalloc_impl(gcf_ctx* c, int n, const int8_t* configs, double* log_abs,
+                                  double* phase, void* scratch, int* status) {
+  const size_t per_cta = (size_t)c->plan.ws_stride * c->sbytes;
+  const long long fit = (long long)(kNoAllocScratchBytes / per_cta);
+  if (fit < 1) {
+    char msg[200];
+    std::snprintf(msg, sizeof(msg),
+                  "gcf_amplitude_noalloc: lattice needs %zu bytes of scratch per CTA, above the "
+                  "fixed 33554432-byte array",
+                  per_cta);
+    return fail(c, GCF_EINVAL, msg);
+  }
+  const int grid = (int)std::max<long long>(1, std::min<long long>(fit, grid_for(c, n)));
+  KParams<T> k = make_params<T>(c);
+  k.scratch = (T*)scratch;
+  k.status = status;
+  k.n_chains = n; k.n_sweeps = 1; k.mode = 0; k.want = WANT_AMP; k.seed = 0;
+  k.configs = (int8_t*)configs;
+  k.log_abs = log_abs;
+  k.phase = phase;
+  // the status counters start at zero for every call (the array keeps the
+  // previous call's values otherwise); the kernel writes every scratch word
+  // it reads before reading it
+  CUDA_TRY(c, cudaMemsetAsync(status, 0, 4 * sizeof(int), c->stream));
+  CUDA_TRY(c, launch_vmc<T>(k, grid, 256, (size_t)c->cfg_len, c->stream));
+  c->launches += 1;
+  return GCF_OK;
+}
+}  // namespace
+
+extern "C" gcf_status gcf_amplitude_noalloc(gcf_ctx* c, int n, const int8_t* configs, double* log_abs,
+                                            double* phase) {
+  if (!c || n < 0 || (n > 0 && (!configs || !log_abs || !phase))) return GCF_EINVAL;
+  if (n == 0) return GCF_OK;
+  void* scratch = nullptr;
+  int* status = nullptr;
+  gcf_status st = noalloc_setup(c, &scratch, &status);
+  if (st != GCF_OK) return st;
+  switch (c->kind) {
+    case S_F32: return amplitude_noalloc_impl<float>(c, n, configs, log_abs, phase, scratch, status);
+    case S_F64: return amplitude_noalloc_impl<double>(c, n, configs, log_abs, phase, scratch, status);
+    case S_C64: return amplitude_noalloc_impl<cfloat>(c, n, configs, log_abs, phase, scratch, status);
+    default: return amplitude_noalloc_impl<cdouble>(c, n, configs, log_abs, phase, scratch, status);
+  }
+}
+
+
