@@ -72,7 +72,7 @@ enum { GCF_SR = 0, GCF_TDVP_STAGE1 = 1, GCF_TDVP_STAGE2 = 2 };
 typedef struct {
   int N;            /* gauge group Z_N, 2 <= N <= 8                          */
   int Lx, Ly;       /* 2 <= Lx, Ly <= 64                                     */
-  int D;            /* total bond dimension, multiple of N; D_k = D/N <= 4   */
+  int D;            /* total bond dimension, multiple of N; D_k = D/N <= 3   */
   int chi;          /* boundary-MPS cutoff, >= 1                              */
   int has_matter;   /* 1: hard-core bosons on the vertices                   */
   const int32_t* Q; /* host, Lx*Ly background charges (row-major) or NULL=0  */

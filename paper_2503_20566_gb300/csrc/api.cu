@@ -29,6 +29,12 @@ struct Plan {
   long long ws_stride = 0;
   long long o_net, o_prop, o_B, o_T, o_Q, o_M1, o_M2, o_M3, o_tau, o_J, o_envR, o_envL, o_envX,
       o_envY, o_t1, o_t2, o_t3, o_env3R, o_env3L, o_env3X, o_env3Y, o_G;
+  // hot buffers in dynamic shared memory (elements from the hot base)
+  int hot_in_smem = 0;
+  long long o_Z = 0, z_size = 0, q_pack = 0, o_X = 0, o_W1 = 0, o_W2 = 0, o_W3 = 0, o_W4 = 0;
+  long long so_net, so_prop, so_cop, so_envL, so_envX, so_envY, so_env3L, so_env3X, so_env3Y, so_t1,
+      so_t2, hot_elems = 0, cfg_bytes = 0;
+  size_t dyn_smem = 0;
 };
 
 }  // namespace
@@ -154,6 +160,7 @@ void build_plan(gcf_ctx* c) {
       mat = std::max(mat, rows * cols);                             // X
       mat = std::max(mat, (long long)std::max(rows, cols) * std::max(rows, cols));
       tau = std::max(tau, std::max(rows, cols));
+      tau = std::max(tau, (long long)std::max(ab[cc], ab[cc + 1]) * pout);
     }
     for (int cc = Lx - 1; cc >= 1; --cc) {
       const long long yr = qr[cc], yc = (long long)pout * bout[cc + 1];
@@ -214,6 +221,12 @@ void build_plan(gcf_ctx* c) {
   }
   p.env_stride = (int)al32(env);
   p.env3_stride = (int)al32(env3);
+  // dense (identity + core) compression buffers: D_k * D_k^Lx when small
+  {
+    long long pw = 1;
+    for (int i = 0; i < Lx && pw <= 8192; ++i) pw *= Dk;
+    if (pw * Dk <= 8192) tmp = std::max(tmp, pw * Dk);
+  }
   p.tmp_max = al32(tmp);
   const long long D4 = (long long)Dk * Dk * Dk * Dk;
   long long o = 0;
@@ -234,13 +247,63 @@ void build_plan(gcf_ctx* c) {
   p.o_envY = take(p.env_stride);
   p.o_t1 = take(p.tmp_max);
   p.o_t2 = take(p.tmp_max);
-  p.o_t3 = take(p.tmp_max);
+  p.o_t3 = take(std::max<long long>(p.tmp_max, D4 * D4 / (Dk * Dk) * Dk * Dk));
   p.o_env3R = take((long long)(Lx + 1) * p.env3_stride);
   p.o_env3L = take(p.env3_stride);
   p.o_env3X = take(p.env3_stride);
   p.o_env3Y = take(p.env3_stride);
   p.o_G = take(D4);
+  // absorbed sites of one step (warp compression path)
+  long long zmax = 1;
+  for (int j = 0; j <= Ly; ++j)
+    for (const std::vector<int>* bt : {&p.bondB, &p.bondT}) {
+      const int* bd = &(*bt)[j * W];
+      long long z = 0;
+      for (int cc = 0; cc < Lx; ++cc) {
+        const long long abl = (cc == 0) ? 1 : (long long)bd[cc] * Dk;
+        const long long abr = (cc + 1 == Lx) ? 1 : (long long)bd[cc + 1] * Dk;
+        z += abl * Dk * abr;
+      }
+      zmax = std::max(zmax, z);
+    }
+  p.z_size = zmax;
+  p.o_Z = take(zmax);
+  // packed QR-pass sites of one step (rows_c x qr[c+1])
+  long long qmax = 1;
+  for (int r = 0; r <= Ly; ++r)
+    for (const std::vector<int>* qt : {&p.qrB, &p.qrT}) {
+      const int* q = &(*qt)[r * W];
+      long long z = 0;
+      for (int cc = 0; cc < Lx; ++cc) z += (long long)q[cc] * Dk * q[cc + 1];
+      qmax = std::max(qmax, z);
+    }
+  p.q_pack = qmax;
+  p.o_X = take(p.mat_max);
+  p.o_W1 = take(p.mat_max);
+  p.o_W2 = take(p.mat_max);
+  p.o_W3 = take(p.mat_max);
+  p.o_W4 = take(p.mat_max);
   p.ws_stride = o;
+  // hot buffers: shared memory if they fit the budget
+  long long h = 0;
+  auto hot = [&](long long n) { long long r = h; h += (n + 3) / 4 * 4; return r; };
+  p.so_net = hot((long long)Lx * Ly * D4);
+  p.so_prop = hot(4 * D4);
+  p.so_cop = hot(D4 * D4 / (Dk * Dk) * Dk * Dk);  // D_k^6
+  p.so_envL = hot(p.env_stride);
+  p.so_envX = hot(p.env_stride);
+  p.so_envY = hot(p.env_stride);
+  p.so_env3L = hot(p.env3_stride);
+  p.so_env3X = hot(p.env3_stride);
+  p.so_env3Y = hot(p.env3_stride);
+  p.so_t1 = hot(p.tmp_max);
+  p.so_t2 = hot(p.tmp_max);
+  p.hot_elems = h;
+  p.cfg_bytes = (c->cfg_len + 15) / 16 * 16;
+  const size_t hot_bytes = (size_t)h * c->sbytes;
+  const size_t budget = 100 * 1024;
+  p.hot_in_smem = hot_bytes <= budget ? 1 : 0;
+  p.dyn_smem = (size_t)p.cfg_bytes + (p.hot_in_smem ? hot_bytes : 0);
 }
 
 template <class T>
@@ -271,12 +334,28 @@ KParams<T> make_params(gcf_ctx* c) {
   k.mps_stride = p.mps_stride; k.qsite_stride = p.qsite_stride;
   k.env_stride = p.env_stride; k.env3_stride = p.env3_stride;
   k.max_sweeps_svd = 40;
+  k.hot_in_smem = p.hot_in_smem;
+  k.dense_max = p.tmp_max;
+  k.o_Z = p.o_Z; k.z_size = p.z_size; k.o_X = p.o_X; k.o_W1 = p.o_W1; k.o_W2 = p.o_W2; k.o_W3 = p.o_W3;
+  k.o_W4 = p.o_W4;
+  k.q_pack = p.q_pack;
+  k.so_net = p.so_net; k.so_prop = p.so_prop; k.so_cop = p.so_cop;
+  k.so_envL = p.so_envL; k.so_envX = p.so_envX; k.so_envY = p.so_envY;
+  k.so_env3L = p.so_env3L; k.so_env3X = p.so_env3X; k.so_env3Y = p.so_env3Y;
+  k.so_t1 = p.so_t1; k.so_t2 = p.so_t2; k.smem_cfg_bytes = p.cfg_bytes;
   k.status = c->d_status;
   return k;
 }
 
 int grid_for(gcf_ctx* c, int n_chains) {
-  const long long want = std::min<long long>(n_chains, (long long)c->sms * 4);
+  int per_sm = 1;
+  switch (c->kind) {
+    case S_F32: per_sm = occupancy_vmc<float>(256, c->plan.dyn_smem); break;
+    case S_F64: per_sm = occupancy_vmc<double>(256, c->plan.dyn_smem); break;
+    case S_C64: per_sm = occupancy_vmc<cfloat>(256, c->plan.dyn_smem); break;
+    default: per_sm = occupancy_vmc<cdouble>(256, c->plan.dyn_smem); break;
+  }
+  const long long want = std::min<long long>(n_chains, (long long)c->sms * std::max(1, per_sm));
   return (int)std::max<long long>(1, want);
 }
 
@@ -307,7 +386,7 @@ gcf_status run_vmc(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t
     k.accepted = out->accepted; k.proposed = out->proposed;
   }
   CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), c->stream));
-  CUDA_TRY(c, launch_vmc<T>(k, grid, 256, (size_t)c->cfg_len, c->stream));
+  CUDA_TRY(c, launch_vmc<T>(k, grid, 256, c->plan.dyn_smem, c->stream));
   c->launches += 1;
   int h_status[4];
   CUDA_TRY(c, cudaMemcpyAsync(h_status, c->d_status, sizeof(h_status), cudaMemcpyDeviceToHost, c->stream));
@@ -389,7 +468,7 @@ gcf_status gcf_init_peps(const gcf_model* model, uint64_t seed, void* cuda_strea
   *out = nullptr;
   const gcf_model& m = *model;
   if (m.N < 2 || m.N > 8 || m.Lx < 2 || m.Ly < 2 || m.Lx > MAX_L || m.Ly > MAX_L || m.D < m.N ||
-      m.D % m.N != 0 || m.D / m.N > 4 || m.chi < 1 || (m.dtype != GCF_REAL && m.dtype != GCF_COMPLEX) ||
+      m.D % m.N != 0 || m.D / m.N > 3 || m.chi < 1 || (m.dtype != GCF_REAL && m.dtype != GCF_COMPLEX) ||
       m.precision < GCF_FP64 || m.precision > GCF_BF16 || (m.has_matter != 0 && m.has_matter != 1))
     return GCF_EINVAL;
   gcf_ctx* c = new gcf_ctx();
@@ -721,7 +800,7 @@ gcf_status amplitude_noalloc_impl(gcf_ctx* c, int n, const int8_t* configs, doub
   // previous call's values otherwise); the kernel writes every scratch word
   // it reads before reading it
   CUDA_TRY(c, cudaMemsetAsync(status, 0, 4 * sizeof(int), c->stream));
-  CUDA_TRY(c, launch_vmc<T>(k, grid, 256, (size_t)c->cfg_len, c->stream));
+  CUDA_TRY(c, launch_vmc<T>(k, grid, 256, c->plan.dyn_smem, c->stream));
   c->launches += 1;
   return GCF_OK;
 }

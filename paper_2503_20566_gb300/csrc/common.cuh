@@ -138,6 +138,17 @@ __device__ inline R warp_max(R v) {
   return v;
 }
 
+template <class T>
+__device__ inline T warp_sum_scalar(T v);
+template <>
+__device__ inline float warp_sum_scalar<float>(float v) { return warp_sum(v); }
+template <>
+__device__ inline double warp_sum_scalar<double>(double v) { return warp_sum(v); }
+template <>
+__device__ inline cfloat warp_sum_scalar<cfloat>(cfloat v) { return {warp_sum(v.x), warp_sum(v.y)}; }
+template <>
+__device__ inline cdouble warp_sum_scalar<cdouble>(cdouble v) { return {warp_sum(v.x), warp_sum(v.y)}; }
+
 __device__ inline double block_sum(double v, double* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   v = warp_sum(v);

@@ -9,6 +9,9 @@ namespace gcf {
 template <class T> struct KParams;
 template <class T>
 cudaError_t launch_vmc(const KParams<T>& k, int grid, int block, size_t smem, cudaStream_t st);
+// resident blocks per SM of vmc_kernel<T> for this block size and dynamic smem
+template <class T>
+int occupancy_vmc(int block, size_t smem);
 cudaError_t launch_init_configs(int N, int Lx, int Ly, int matter, const int* Q, int n_chains,
                                 const int8_t* occ, const int8_t* powers, int8_t* configs,
                                 int* status, cudaStream_t st);

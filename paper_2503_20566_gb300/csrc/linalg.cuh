@@ -37,16 +37,6 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, const T* A, int sAm, 
   __syncthreads();
 }
 
-template <class T>
-__device__ inline T warp_sum_scalar(T v);
-template <>
-__device__ inline float warp_sum_scalar<float>(float v) { return warp_sum(v); }
-template <>
-__device__ inline double warp_sum_scalar<double>(double v) { return warp_sum(v); }
-template <>
-__device__ inline cfloat warp_sum_scalar<cfloat>(cfloat v) { return {warp_sum(v.x), warp_sum(v.y)}; }
-template <>
-__device__ inline cdouble warp_sum_scalar<cdouble>(cdouble v) { return {warp_sum(v.x), warp_sum(v.y)}; }
 
 // Householder reflector for column (alpha; x) with |x|^2 = xn2:
 // H = I - tau v v^H, v = (1; x * scal), H^H (alpha; x) = (beta; 0), beta real.

@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "linalg.cuh"
+#include "envsteps.cuh"
 
 namespace gcf {
 
@@ -50,6 +51,11 @@ struct KParams {
   long long mps_stride, qsite_stride;
   int env_stride, env3_stride;
   int max_sweeps_svd;
+  // hot buffers: in dynamic shared memory when hot_in_smem, else in scratch
+  int hot_in_smem;
+  long long dense_max, o_Z, z_size, q_pack, o_X, o_W1, o_W2, o_W3, o_W4;
+  long long so_net, so_prop, so_cop, so_envL, so_envX, so_envY, so_env3L, so_env3X, so_env3Y,
+      so_t1, so_t2, smem_cfg_bytes;
   // per-run
   int n_chains, n_sweeps, mode, want;  // mode 0: measure given configs, 1: sample
   unsigned long long seed;
@@ -69,7 +75,11 @@ enum { ST_GAUSS = 0, ST_NUMERIC = 1, ST_SVD = 2 };
 
 struct Shared {
   double red[64];
+  double bcast;
   int iflag[4];
+  int ab[MAX_L + 1];
+  int zoff[MAX_L + 1];
+  int qoff[MAX_L + 1];
   int bd_off[MAX_L + 1];
   int bd_off2[MAX_L + 1];
   int sel[4 * MAX_L * 4];
@@ -182,6 +192,97 @@ __device__ __noinline__ double frob_rescale(T* a, int n, double* red) {
   return log(nr);
 }
 
+// sum_k A[k] B[k] (no conjugation), broadcast to all threads as (re, im)
+template <class T>
+__device__ inline void cta_dot(const T* A, const T* B, int n, double* red, double& r, double& i) {
+  T s = zero<T>();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) s = fmac(s, A[k], B[k]);
+  r = (double)re(s);
+  i = (double)im(s);
+  block_sum2(r, i, red);
+}
+
+// ---------------------------------------------------------------------------
+// Exact compression in identity + core form.
+// When every output bond of a step is at full rank, bd[c] = min(p^c, p^(L-c))
+// (p = D_k, L = Lx; no truncation), the compressed boundary state is an
+// exact MPS whose sites left of m = floor(L/2) are identity isometries
+// M[a][i][a*p + i], whose sites right of m are identity isometries
+// M[i*p^(L-1-c) + b][i][b], and whose site m holds the normalised dense state
+// v[(u_0..u_{m-1})][u_m][(u_{m+1}..u_{L-1})].  It is the same state the QR /
+// LQ sweep produces, in a different gauge.  The dense state is obtained by
+// contracting the input MPS to a vector and applying the row MPO site by site.
+// Returns the log of the scale factor.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __noinline__ double dense_absorb(const KParams<T>& k, Shared& sh, const T* net, const T* mps_in,
+                                            const int* bdi, int pin, int row, int flip, T* mout,
+                                            const int* bdo, int pout, T* bufA, T* bufB) {
+  const int Lx = k.Lx, Dk = k.Dk;
+  const int D3 = Dk * Dk * Dk, D2 = Dk * Dk;
+  const int sd = flip ? 1 : Dk, su = flip ? Dk : 1;
+  // 1. input vector v[(i_0..i_{L-1})], i_0 most significant
+  if (threadIdx.x == 0) bufA[0] = one<T>();
+  __syncthreads();
+  int rows = 1;
+  for (int c = 0; c < Lx; ++c) {
+    const T* M = mps_in + sh.bd_off[c];
+    // bufB[(p, i)][b] = sum_a bufA[p][a] M[a][(i b)]
+    cta_gemm<T>(rows, pin * bdi[c + 1], bdi[c], bufA, bdi[c], 1, M, pin * bdi[c + 1], 1, bufB,
+                pin * bdi[c + 1], 1, false);
+    rows *= pin;
+    T* t = bufA; bufA = bufB; bufB = t;
+  }
+  // 2. MPO sweep: t_c[h][U][u][Dr] = sum_{h', d} W_c[h'][h][d][u] t_{c-1}[h'][U][d][Dr]
+  int NU = 1, ND = rows / pin;  // ND = pin^(L-1) before position 0
+  for (int c = 0; c < Lx; ++c) {
+    const int hl = hl_dim(c, Dk), hr = hr_dim(c, Lx, Dk);
+    const T* W = net + (long long)(row * Lx + c) * (Dk * Dk * Dk * Dk);
+    const int nout = hr * NU * pout * ND;
+    for (int idx = threadIdx.x; idx < nout; idx += blockDim.x) {
+      int t = idx;
+      const int Dr = t % ND; t /= ND;
+      const int u = t % pout; t /= pout;
+      const int U = t % NU; t /= NU;
+      const int h = t;
+      T s = zero<T>();
+      for (int hp = 0; hp < hl; ++hp)
+        for (int d = 0; d < pin; ++d)
+          s = fmac(s, W[hp * D3 + h * D2 + d * sd + u * su], bufA[((hp * NU + U) * pin + d) * ND + Dr]);
+      bufB[idx] = s;
+    }
+    __syncthreads();
+    T* tt = bufA; bufA = bufB; bufB = tt;
+    NU *= pout;
+    if (c < Lx - 1) ND /= pin;
+  }
+  // 3. normalise v' (length pout^L, bufA)
+  const int nv = NU;
+  double s2 = 0.0;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) s2 += (double)abs2(bufA[i]);
+  s2 = block_sum(s2, sh.red);
+  using R = typename Traits<T>::R;
+  const R inv = s2 > 0.0 ? R(1.0 / sqrt(s2)) : R(1);
+  // 4. identity sites and the core
+  const int m = Lx / 2;
+  for (int c = 0; c < Lx; ++c) {
+    const int a = bdo[c], b = bdo[c + 1];
+    T* site = mout + sh.bd_off2[c];
+    const int n = a * pout * b;
+    if (c == m) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) site[i] = scale(bufA[i], inv);
+    } else {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int ib = i % b, ii = (i / b) % pout, ia = i / (b * pout);
+        const bool on = (c < m) ? (ib == ia * pout + ii) : (ia == ii * b + ib);
+        site[i] = on ? one<T>() : zero<T>();
+      }
+    }
+  }
+  __syncthreads();
+  return s2 > 0.0 ? -log((double)inv) : 0.0;
+}
+
 // ---------------------------------------------------------------------------
 // Row absorption + compression.
 //   in : MPS `mps_in` (bond table bdi, physical dim pin) and row `row` whose
@@ -195,8 +296,8 @@ __device__ __noinline__ double frob_rescale(T* a, int n, double* red) {
 // keeping the chi largest singular values otherwise.
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ __noinline__ double absorb_compress(const KParams<T>& k, T* ws, Shared& sh, const T* mps_in,
-                                  const int* bdi, int pin, int row, int flip, T* mout,
+__device__ __noinline__ double absorb_compress(const KParams<T>& k, T* ws, T* hot_base, Shared& sh, const T* net,
+                                  const T* mps_in, const int* bdi, int pin, int row, int flip, T* mout,
                                   const int* bdo, int pout, const int* qr, const int* svd) {
   const int Lx = k.Lx, Dk = k.Dk;
   const int D3 = Dk * Dk * Dk, D2 = Dk * Dk;
@@ -211,18 +312,69 @@ __device__ __noinline__ double absorb_compress(const KParams<T>& k, T* ws, Share
   mps_offsets(bdi, pin, Lx, sh.bd_off);
   mps_offsets(bdo, pout, Lx, sh.bd_off2);
 
-  // R carry (rows qr[c], cols ab[c]); starts as [1]
-  if (threadIdx.x == 0) M3[0] = one<T>();
+  // Dense (identity + core) path: every output bond at full rank and the
+  // dense state small enough.
+  if (threadIdx.x == 0) {
+    int ok = (pout == Dk) ? 1 : 0;
+    long long pw = 1;
+    for (int c = 0; c <= Lx; ++c) {
+      long long lo = 1, hi = 1;
+      for (int i = 0; i < c; ++i) lo *= pout;
+      for (int i = 0; i < Lx - c; ++i) hi *= pout;
+      if (bdo[c] != (lo < hi ? lo : hi)) ok = 0;
+    }
+    for (int i = 0; i < Lx && pw <= k.dense_max; ++i) pw *= pout;
+    if (pw * Dk > k.dense_max) ok = 0;
+    long long rows = 1;
+    for (int c = 0; c < Lx && ok; ++c) {
+      rows *= pin;
+      if (rows * bdi[c + 1] > k.dense_max) ok = 0;
+    }
+    sh.iflag[2] = ok;
+  }
   __syncthreads();
-  int Rrows = 1, Rcols = 1;
+  if (sh.iflag[2]) {
+    T* bufA = k.hot_in_smem ? hot_base + k.so_t1 : ws + k.o_t1;
+    T* bufB = k.hot_in_smem ? hot_base + k.so_t2 : ws + k.o_t2;
+    return dense_absorb<T>(k, sh, net, mps_in, bdi, pin, row, flip, mout, bdo, pout, bufA, bufB);
+  }
+
+  // General path.  Z_c (absorbed sites) for all c; then a QR sweep from the
+  // left over the bonds that must shrink (all bonds if the step truncates),
+  // then an LQ / truncated-SVD sweep from the right over the bonds that must
+  // shrink; sites in between are the absorbed tensors with the carries
+  // multiplied in.  Without truncation this reaches the exact state with the
+  // step's bond dimensions; with truncation it is the full canonical sweep.
+  if (threadIdx.x == 0) {
+    int any_svd = 0;
+    for (int c = 1; c < Lx; ++c) any_svd |= svd[c];
+    int zo = 0, qo = 0;
+    for (int c = 0; c <= Lx; ++c) sh.ab[c] = (c == 0 || c == Lx) ? 1 : bdi[c] * Dk;
+    for (int c = 0; c < Lx; ++c) {
+      sh.zoff[c] = zo;
+      zo += sh.ab[c] * pout * sh.ab[c + 1];
+      sh.qoff[c] = qo;
+      qo += qr[c] * pout * qr[c + 1];
+    }
+    int cl = 0;
+    while (cl < Lx - 1 && (any_svd || qr[cl] * pout < sh.ab[cl + 1])) ++cl;
+    sh.iflag[1] = cl;
+  }
+  __syncthreads();
+  const int cL = sh.iflag[1];
+  T* Z = ws + k.o_Z;
+  T* Xb = ws + k.o_X;
+  T* Y = ws + k.o_W1;
+  T* Yh = ws + k.o_W2;
+  T* Qp = ws + k.o_W3;
+  T* Lc = ws + k.o_W4;
   for (int c = 0; c < Lx; ++c) {
     const int a = bdi[c], b = bdi[c + 1];
     const int l = hl_dim(c, Dk), r = hr_dim(c, Lx, Dk);
-    const int abl = a * l, abr = b * r;
     const T* M = mps_in + sh.bd_off[c];
-    const T* W = net_box(k, ws, c, row);
-    // Z[(a,l)][u][(b,r)] = sum_d M[a][d][b] W[l][r][d][u]   -> M2
-    const int nZ = abl * pout * abr;
+    const T* W = net + (long long)(row * Lx + c) * (Dk * Dk * Dk * Dk);
+    const int nZ = a * l * pout * b * r;
+    T* Zc = Z + sh.zoff[c];
     for (int idx = threadIdx.x; idx < nZ; idx += blockDim.x) {
       int t = idx;
       const int ir = t % r; t /= r;
@@ -233,444 +385,116 @@ __device__ __noinline__ double absorb_compress(const KParams<T>& k, T* ws, Share
       T s = zero<T>();
       for (int d = 0; d < pin; ++d)
         s = fmac(s, M[(ia * pin + d) * b + ib], W[il * D3 + ir * D2 + d * sd + iu * su]);
-      M2[idx] = s;
+      Zc[idx] = s;
     }
-    __syncthreads();
-    // X = R (Rrows x abl) * Z (abl x pout*abr)  -> M1 (rows Rrows*pout, cols abr)
-    cta_gemm<T>(Rrows, pout * abr, abl, M3, Rcols, 1, M2, pout * abr, 1, M1, pout * abr, 1, false);
+  }
+  // ---- left QR sweep over sites 0..cL-1; R carry in M3 (Rrows x ab[c])
+  if (threadIdx.x == 0) M3[0] = one<T>();
+  __syncthreads();
+  int Rrows = 1;
+  for (int c = 0; c <= cL; ++c) {
+    const int abl = sh.ab[c], abr = sh.ab[c + 1];
     const int rows = Rrows * pout, cols = abr;
-    if (c < Lx - 1) {
-      cta_qr<T>(rows, cols, M1, cols, 1, tau, sh.red);
-      const int kq = min(rows, cols);
-      // Q -> Qs site c (rows x kq)
-      T* Qc = Qs + (long long)c * k.qsite_stride;
-      cta_form_q<T>(rows, kq, M1, cols, 1, tau, Qc, kq, 1);
-      // R (kq x cols) -> M3
-      for (int idx = threadIdx.x; idx < kq * cols; idx += blockDim.x) {
-        const int i = idx / cols, j = idx - (idx / cols) * cols;
-        M3[idx] = (j >= i) ? M1[i * cols + j] : zero<T>();
-      }
-      __syncthreads();
-      logs += frob_rescale(M3, kq * cols, sh.red);
-      Rrows = kq; Rcols = cols;
-    } else {
-      // last site: keep X (rows x 1) in M3 as the right-to-left carry start
-      for (int idx = threadIdx.x; idx < rows; idx += blockDim.x) M3[idx] = M1[idx];
-      __syncthreads();
-      Rrows = rows; Rcols = 1;
+    // X = R (Rrows x abl) * Z_c (abl x pout*abr) -> (Rrows*pout) x abr
+    T* X = (c == cL) ? Xb : M1;
+    cta_gemm<T>(Rrows, pout * abr, abl, M3, abl, 1, Z + sh.zoff[c], pout * abr, 1, X, pout * abr, 1, false);
+    if (c == cL) break;
+    cta_qr<T>(rows, cols, M1, cols, 1, tau, sh.red);
+    const int kq = min(rows, cols);
+    cta_form_q<T>(rows, kq, M1, cols, 1, tau, Qs + sh.qoff[c], kq, 1);
+    for (int idx = threadIdx.x; idx < kq * cols; idx += blockDim.x) {
+      const int i = idx / cols, j = idx - (idx / cols) * cols;
+      M3[idx] = (j >= i) ? M1[i * cols + j] : zero<T>();
     }
+    __syncthreads();
+    logs += frob_rescale(M3, kq * cols, sh.red);
+    Rrows = kq;
   }
-  (void)qr;
-  // Right to left.  Y = M3 viewed as (qr[c]) x (pout * fin[c+1]).
-  for (int c = Lx - 1; c >= 1; --c) {
-    const int yr = qr[c], yc = pout * bdo[c + 1];
-    const int kk = bdo[c];
+  // ---- right sweep over every site.  The carry Lc (rdim x kc) is the
+  // identity while no bond to the right has been reduced.
+  bool ident = true;
+  int kc = 1, rdim = 1;
+  for (int c = Lx - 1; c >= 0; --c) {
+    const int cur = (c < cL) ? qr[c] : (c == cL ? Rrows : sh.ab[c]);
+    const int rd = (c < cL) ? qr[c + 1] : sh.ab[c + 1];
+    const T* S = (c < cL) ? Qs + sh.qoff[c] : (c == cL ? Xb : Z + sh.zoff[c]);
+    const T* Yp;
+    int yc;
+    if (ident) {
+      Yp = S;
+      yc = pout * rd;
+    } else {
+      // Y = S ((cur*pout) x rdim) * Lc (rdim x kc), viewed cur x (pout*kc)
+      cta_gemm<T>(cur * pout, kc, rdim, S, rdim, 1, Lc, kc, 1, Y, kc, 1, false);
+      Yp = Y;
+      yc = pout * kc;
+    }
+    const int yr = cur;
     T* site = mout + sh.bd_off2[c];
-    // LQ: Y^H (yc x yr) -> M1, QR, L = R^H, Q = Q'^H
-    cta_adjoint<T>(yc, yr, M3, yc, 1, M1, yr, 1);
-    cta_qr<T>(yc, yr, M1, yr, 1, tau, sh.red);
-    const int k0 = min(yr, yc);
-    // Q' (yc x k0) -> M2
-    cta_form_q<T>(yc, k0, M1, yr, 1, tau, M2, k0, 1);
-    // L (yr x k0) = R'^H -> Jm region used as L buffer (M3 free now)
-    for (int idx = threadIdx.x; idx < yr * k0; idx += blockDim.x) {
-      const int i = idx / k0, j = idx - (idx / k0) * k0;
-      M3[idx] = (i >= j) ? conjg(M1[j * yr + i]) : zero<T>();
-    }
-    __syncthreads();
-    if (!svd[c]) {
-      // site = Q'^H (k0 x yc); carry L (yr x k0)
-      cta_adjoint<T>(k0, yc, M2, k0, 1, site, yc, 1);
-    } else {
-      // one-sided Jacobi on L (yr x k0): L J = W, keep the kk largest columns
-      int conv = 1;
-      cta_jacobi_svd<T>(yr, k0, M3, k0, 1, Jm, k0, 1, &sh.iflag[0], k.max_sweeps_svd, &conv);
-      if (!conv && threadIdx.x == 0) atomicAdd(&k.status[ST_SVD], 1);
-      for (int j = threadIdx.x; j < k0; j += blockDim.x) {
-        double s2 = 0.0;
-        for (int i = 0; i < yr; ++i) s2 += (double)abs2(M3[i * k0 + j]);
-        sh.sigma[j] = s2;
+    if (c >= 1 && (svd[c] || bdo[c] < cur)) {
+      const int kk = bdo[c];
+      cta_adjoint<T>(yc, yr, Yp, yc, 1, Yh, yr, 1);
+      cta_qr<T>(yc, yr, Yh, yr, 1, tau, sh.red);
+      const int k0 = min(yr, yc);
+      cta_form_q<T>(yc, k0, Yh, yr, 1, tau, Qp, k0, 1);
+      // L = R'^H (yr x k0)
+      for (int idx = threadIdx.x; idx < yr * k0; idx += blockDim.x) {
+        const int i = idx / k0, j = idx - (idx / k0) * k0;
+        Lc[idx] = (i >= j) ? conjg(Yh[j * yr + i]) : zero<T>();
       }
       __syncthreads();
-      for (int j = threadIdx.x; j < k0; j += blockDim.x) {
-        int rank = 0;
-        const double sj = sh.sigma[j];
-        for (int i = 0; i < k0; ++i) {
-          const double si = sh.sigma[i];
-          rank += (si > sj) || (si == sj && i < j);
+      if (!svd[c]) {
+        cta_adjoint<T>(k0, yc, Qp, k0, 1, site, yc, 1);
+      } else {
+        int conv = 1;
+        cta_jacobi_svd<T>(yr, k0, Lc, k0, 1, Jm, k0, 1, &sh.iflag[0], k.max_sweeps_svd, &conv);
+        if (!conv && threadIdx.x == 0) atomicAdd(&k.status[ST_SVD], 1);
+        for (int j = threadIdx.x; j < k0; j += blockDim.x) {
+          double s2 = 0.0;
+          for (int i = 0; i < yr; ++i) s2 += (double)abs2(Lc[i * k0 + j]);
+          sh.sigma[j] = s2;
         }
-        if (rank < kk) sh.sel[rank] = j;
+        __syncthreads();
+        for (int j = threadIdx.x; j < k0; j += blockDim.x) {
+          int rank = 0;
+          const double sj = sh.sigma[j];
+          for (int i = 0; i < k0; ++i) {
+            const double si = sh.sigma[i];
+            rank += (si > sj) || (si == sj && i < j);
+          }
+          if (rank < kk) sh.sel[rank] = j;
+        }
+        __syncthreads();
+        // site[n][x] = sum_j conj(J[j][sel n]) Q'^H[j][x]
+        for (int idx = threadIdx.x; idx < kk * yc; idx += blockDim.x) {
+          const int n = idx / yc, x = idx - (idx / yc) * yc;
+          const int jn = sh.sel[n];
+          T s = zero<T>();
+          for (int j = 0; j < k0; ++j) s = fmac(s, conjg(Jm[j * k0 + jn]), conjg(Qp[x * k0 + j]));
+          site[idx] = s;
+        }
+        // carry U S = W[:, sel] (yr x kk)
+        for (int idx = threadIdx.x; idx < yr * kk; idx += blockDim.x) {
+          const int i = idx / kk, n = idx - (idx / kk) * kk;
+          Yh[idx] = Lc[i * k0 + sh.sel[n]];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < yr * kk; idx += blockDim.x) Lc[idx] = Yh[idx];
+        __syncthreads();
       }
+      logs += frob_rescale(Lc, yr * kk, sh.red);
+      kc = kk;
+      rdim = yr;
+      ident = false;
+    } else {
+      // no reduction at this site's left bond (cur == bdo[c]): keep Y
+      for (int idx = threadIdx.x; idx < yr * yc; idx += blockDim.x) site[idx] = Yp[idx];
       __syncthreads();
-      // site[n][x] = sum_j conj(J[j][sel n]) Q'^H[j][x] = sum_j conj(J[j][sel]) conj(Q'[x][j])
-      for (int idx = threadIdx.x; idx < kk * yc; idx += blockDim.x) {
-        const int n = idx / yc, x = idx - (idx / yc) * yc;
-        const int jn = sh.sel[n];
-        T s = zero<T>();
-        for (int j = 0; j < k0; ++j) s = fmac(s, conjg(Jm[j * k0 + jn]), conjg(M2[x * k0 + j]));
-        site[idx] = s;
-      }
-      // carry U S = W[:, sel] (yr x kk) -> M1 then back to M3
-      for (int idx = threadIdx.x; idx < yr * kk; idx += blockDim.x) {
-        const int i = idx / kk, n = idx - (idx / kk) * kk;
-        M1[idx] = M3[i * k0 + sh.sel[n]];
-      }
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < yr * kk; idx += blockDim.x) M3[idx] = M1[idx];
-      __syncthreads();
+      logs += rescale(site, yr * yc, sh.red);
+      ident = true;
     }
-    logs += frob_rescale(M3, yr * kk, sh.red);
-    // next Y = Q_{c-1} (qr[c-1]*pout x qr[c]) * carry (qr[c] x kk)
-    const T* Qp = Qs + (long long)(c - 1) * k.qsite_stride;
-    const int prow = qr[c - 1] * pout;
-    cta_gemm<T>(prow, kk, yr, Qp, yr, 1, M3, kk, 1, M1, kk, 1, false);
-    for (int idx = threadIdx.x; idx < prow * kk; idx += blockDim.x) M3[idx] = M1[idx];
-    __syncthreads();
-  }
-  // site 0: Y (1 x pout*fin[1]) normalised
-  {
-    const int n0 = pout * bdo[1];
-    logs += frob_rescale(M3, n0, sh.red);
-    T* site = mout + sh.bd_off2[0];
-    for (int idx = threadIdx.x; idx < n0; idx += blockDim.x) site[idx] = M3[idx];
-    __syncthreads();
   }
   return logs;
-}
-
-// ---------------------------------------------------------------------------
-// Strip (4-layer) environment steps.  Dims: E[a][i][j][b] = (nA, nI, nJ, nB).
-// Column tensors: Bs (nA x pB x nA'), W1 box (row r), W2 box (row r+1),
-// Ts (nB x pT x nB'); nI' = nJ' = hr, pM = vertical bond between the rows.
-// ---------------------------------------------------------------------------
-struct StripDims {
-  int nA, nI, nJ, nB;     // left cut
-  int nA2, nI2, nJ2, nB2; // right cut
-  int pB, pM, pT;         // physical dims: B-phys (= d of row r), middle, T-phys
-};
-
-template <class T>
-__device__ __noinline__ void strip_left_step(int Dk, const StripDims& d, const T* L, const T* Bs, const T* W1,
-                                const T* W2, const T* Ts, T* out, T* t1, T* t2, T* t3) {
-  const int D3 = Dk * Dk * Dk, D2 = Dk * Dk;
-  // S1: X1[i][j][b][dd][a2] = sum_a L[a][i][j][b] Bs[a][dd][a2]
-  {
-    const int n = d.nI * d.nJ * d.nB * d.pB * d.nA2;
-    const int sLa = d.nI * d.nJ * d.nB, sBa = d.pB * d.nA2;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      int t = idx;
-      const int a2 = t % d.nA2; t /= d.nA2;
-      const int dd = t % d.pB; t /= d.pB;
-      const int ijb = t;  // (i*nJ + j)*nB + b
-      T s = zero<T>();
-      const T* lp = L + ijb;
-      const T* bp = Bs + dd * d.nA2 + a2;
-      for (int a = 0; a < d.nA; ++a) s = fmac(s, lp[a * sLa], bp[a * sBa]);
-      t1[idx] = s;
-    }
-    __syncthreads();
-  }
-  // S2: X2[j][b][a2][i2][m] = sum_{i,dd} X1[i][j][b][dd][a2] W1[i][i2][dd][m]
-  {
-    const int n = d.nJ * d.nB * d.nA2 * d.nI2 * d.pM;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      int t = idx;
-      const int m = t % d.pM; t /= d.pM;
-      const int i2 = t % d.nI2; t /= d.nI2;
-      const int a2 = t % d.nA2; t /= d.nA2;
-      const int b = t % d.nB; t /= d.nB;
-      const int j = t;
-      T s = zero<T>();
-      for (int i = 0; i < d.nI; ++i)
-        for (int dd = 0; dd < d.pB; ++dd)
-          s = fmac(s, t1[(((i * d.nJ + j) * d.nB + b) * d.pB + dd) * d.nA2 + a2],
-                   W1[i * D3 + i2 * D2 + dd * Dk + m]);
-      t2[idx] = s;
-    }
-    __syncthreads();
-  }
-  // S3: X3[a2][i2][j2][b][u] = sum_{j,m} X2[j][b][a2][i2][m] W2[j][j2][m][u]
-  {
-    const int n = d.nA2 * d.nI2 * d.nJ2 * d.nB * d.pT;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      int t = idx;
-      const int u = t % d.pT; t /= d.pT;
-      const int b = t % d.nB; t /= d.nB;
-      const int j2 = t % d.nJ2; t /= d.nJ2;
-      const int i2 = t % d.nI2; t /= d.nI2;
-      const int a2 = t;
-      T s = zero<T>();
-      for (int j = 0; j < d.nJ; ++j)
-        for (int m = 0; m < d.pM; ++m)
-          s = fmac(s, t2[(((j * d.nB + b) * d.nA2 + a2) * d.nI2 + i2) * d.pM + m],
-                   W2[j * D3 + j2 * D2 + m * Dk + u]);
-      t3[idx] = s;
-    }
-    __syncthreads();
-  }
-  // S4: out[a2][i2][j2][b2] = sum_{b,u} X3[a2][i2][j2][b][u] Ts[b][u][b2]
-  {
-    const int n = d.nA2 * d.nI2 * d.nJ2 * d.nB2;
-    const int K = d.nB * d.pT;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      const int b2 = idx % d.nB2;
-      const int aij = idx / d.nB2;
-      T s = zero<T>();
-      const T* xp = t3 + aij * K;
-      for (int bu = 0; bu < K; ++bu) s = fmac(s, xp[bu], Ts[bu * d.nB2 + b2]);
-      out[idx] = s;
-    }
-    __syncthreads();
-  }
-}
-
-// R[a][i][j][b] = sum Bs[a][dd][a2] W1[i][i2][dd][m] W2[j][j2][m][u] Ts[b][u][b2] R2[a2][i2][j2][b2]
-template <class T>
-__device__ __noinline__ void strip_right_step(int Dk, const StripDims& d, const T* R2, const T* Bs, const T* W1,
-                                 const T* W2, const T* Ts, T* out, T* t1, T* t2, T* t3) {
-  const int D3 = Dk * Dk * Dk, D2 = Dk * Dk;
-  // S1: Y1[a2][i2][j2][b][u] = sum_b2 R2[a2][i2][j2][b2] Ts[b][u][b2]
-  {
-    const int n = d.nA2 * d.nI2 * d.nJ2 * d.nB * d.pT;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      const int bu = idx % (d.nB * d.pT);
-      const int aij = idx / (d.nB * d.pT);
-      T s = zero<T>();
-      const T* rp = R2 + aij * d.nB2;
-      const T* tp = Ts + bu * d.nB2;
-      for (int b2 = 0; b2 < d.nB2; ++b2) s = fmac(s, rp[b2], tp[b2]);
-      t1[idx] = s;
-    }
-    __syncthreads();
-  }
-  // S2: Y2[a2][i2][j][m][b] = sum_{j2,u} Y1[a2][i2][j2][b][u] W2[j][j2][m][u]
-  {
-    const int n = d.nA2 * d.nI2 * d.nJ * d.pM * d.nB;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      int t = idx;
-      const int b = t % d.nB; t /= d.nB;
-      const int m = t % d.pM; t /= d.pM;
-      const int j = t % d.nJ; t /= d.nJ;
-      const int i2 = t % d.nI2; t /= d.nI2;
-      const int a2 = t;
-      T s = zero<T>();
-      for (int j2 = 0; j2 < d.nJ2; ++j2)
-        for (int u = 0; u < d.pT; ++u)
-          s = fmac(s, t1[(((a2 * d.nI2 + i2) * d.nJ2 + j2) * d.nB + b) * d.pT + u],
-                   W2[j * D3 + j2 * D2 + m * Dk + u]);
-      t2[idx] = s;
-    }
-    __syncthreads();
-  }
-  // S3: Y3[a2][i][j][dd][b] = sum_{i2,m} Y2[a2][i2][j][m][b] W1[i][i2][dd][m]
-  {
-    const int n = d.nA2 * d.nI * d.nJ * d.pB * d.nB;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      int t = idx;
-      const int b = t % d.nB; t /= d.nB;
-      const int dd = t % d.pB; t /= d.pB;
-      const int j = t % d.nJ; t /= d.nJ;
-      const int i = t % d.nI; t /= d.nI;
-      const int a2 = t;
-      T s = zero<T>();
-      for (int i2 = 0; i2 < d.nI2; ++i2)
-        for (int m = 0; m < d.pM; ++m)
-          s = fmac(s, t2[(((a2 * d.nI2 + i2) * d.nJ + j) * d.pM + m) * d.nB + b],
-                   W1[i * D3 + i2 * D2 + dd * Dk + m]);
-      t3[idx] = s;
-    }
-    __syncthreads();
-  }
-  // S4: R[a][i][j][b] = sum_{a2,dd} Bs[a][dd][a2] Y3[a2][i][j][dd][b]
-  {
-    const int n = d.nA * d.nI * d.nJ * d.nB;
-    const int sY = d.nI * d.nJ * d.pB * d.nB;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      int t = idx;
-      const int b = t % d.nB; t /= d.nB;
-      const int j = t % d.nJ; t /= d.nJ;
-      const int i = t % d.nI; t /= d.nI;
-      const int a = t;
-      T s = zero<T>();
-      for (int a2 = 0; a2 < d.nA2; ++a2)
-        for (int dd = 0; dd < d.pB; ++dd)
-          s = fmac(s, Bs[(a * d.pB + dd) * d.nA2 + a2],
-                   t3[a2 * sY + ((i * d.nJ + j) * d.pB + dd) * d.nB + b]);
-      out[idx] = s;
-    }
-    __syncthreads();
-  }
-}
-
-// sum_k A[k] B[k] (no conjugation), broadcast; returns (re, im) in doubles
-template <class T>
-__device__ inline void cta_dot(const T* A, const T* B, int n, double* red, double& r, double& i) {
-  T s = zero<T>();
-  for (int k = threadIdx.x; k < n; k += blockDim.x) s = fmac(s, A[k], B[k]);
-  r = (double)re(s);
-  i = (double)im(s);
-  block_sum2(r, i, red);
-}
-
-// ---------------------------------------------------------------------------
-// Row (3-layer) environment steps.  E[a][l][b] = (nA, nH, nB).
-// ---------------------------------------------------------------------------
-struct RowDims {
-  int nA, nH, nB;     // left cut
-  int nA2, nH2, nB2;  // right cut
-  int pB, pT;
-};
-
-template <class T>
-__device__ __noinline__ void row_left_step(int Dk, const RowDims& d, const T* L, const T* Bs, const T* W,
-                              const T* Ts, T* out, T* t1, T* t2) {
-  const int D3 = Dk * Dk * Dk, D2 = Dk * Dk;
-  // S1: X1[l][b][dd][a2] = sum_a L[a][l][b] Bs[a][dd][a2]
-  {
-    const int n = d.nH * d.nB * d.pB * d.nA2;
-    const int sLa = d.nH * d.nB, sBa = d.pB * d.nA2;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      const int da = idx % (d.pB * d.nA2);
-      const int lb = idx / (d.pB * d.nA2);
-      T s = zero<T>();
-      for (int a = 0; a < d.nA; ++a) s = fmac(s, L[a * sLa + lb], Bs[a * sBa + da]);
-      t1[idx] = s;
-    }
-    __syncthreads();
-  }
-  // S2: X2[b][a2][r][u] = sum_{l,dd} X1[l][b][dd][a2] W[l][r][dd][u]
-  {
-    const int n = d.nB * d.nA2 * d.nH2 * d.pT;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      int t = idx;
-      const int u = t % d.pT; t /= d.pT;
-      const int r = t % d.nH2; t /= d.nH2;
-      const int a2 = t % d.nA2; t /= d.nA2;
-      const int b = t;
-      T s = zero<T>();
-      for (int l = 0; l < d.nH; ++l)
-        for (int dd = 0; dd < d.pB; ++dd)
-          s = fmac(s, t1[((l * d.nB + b) * d.pB + dd) * d.nA2 + a2], W[l * D3 + r * D2 + dd * Dk + u]);
-      t2[idx] = s;
-    }
-    __syncthreads();
-  }
-  // S3: out[a2][r][b2] = sum_{b,u} X2[b][a2][r][u] Ts[b][u][b2]
-  {
-    const int n = d.nA2 * d.nH2 * d.nB2;
-    const int sXb = d.nA2 * d.nH2 * d.pT;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      const int b2 = idx % d.nB2;
-      const int ar = idx / d.nB2;
-      T s = zero<T>();
-      for (int b = 0; b < d.nB; ++b)
-        for (int u = 0; u < d.pT; ++u)
-          s = fmac(s, t2[b * sXb + ar * d.pT + u], Ts[(b * d.pT + u) * d.nB2 + b2]);
-      out[idx] = s;
-    }
-    __syncthreads();
-  }
-}
-
-template <class T>
-__device__ __noinline__ void row_right_step(int Dk, const RowDims& d, const T* R2, const T* Bs, const T* W,
-                               const T* Ts, T* out, T* t1, T* t2) {
-  const int D3 = Dk * Dk * Dk, D2 = Dk * Dk;
-  // S1: Y1[a2][r][b][u] = sum_b2 R2[a2][r][b2] Ts[b][u][b2]
-  {
-    const int n = d.nA2 * d.nH2 * d.nB * d.pT;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      const int bu = idx % (d.nB * d.pT);
-      const int ar = idx / (d.nB * d.pT);
-      T s = zero<T>();
-      for (int b2 = 0; b2 < d.nB2; ++b2) s = fmac(s, R2[ar * d.nB2 + b2], Ts[bu * d.nB2 + b2]);
-      t1[idx] = s;
-    }
-    __syncthreads();
-  }
-  // S2: Y2[a2][l][dd][b] = sum_{r,u} Y1[a2][r][b][u] W[l][r][dd][u]
-  {
-    const int n = d.nA2 * d.nH * d.pB * d.nB;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      int t = idx;
-      const int b = t % d.nB; t /= d.nB;
-      const int dd = t % d.pB; t /= d.pB;
-      const int l = t % d.nH; t /= d.nH;
-      const int a2 = t;
-      T s = zero<T>();
-      for (int r = 0; r < d.nH2; ++r)
-        for (int u = 0; u < d.pT; ++u)
-          s = fmac(s, t1[((a2 * d.nH2 + r) * d.nB + b) * d.pT + u], W[l * D3 + r * D2 + dd * Dk + u]);
-      t2[idx] = s;
-    }
-    __syncthreads();
-  }
-  // S3: out[a][l][b] = sum_{a2,dd} Bs[a][dd][a2] Y2[a2][l][dd][b]
-  {
-    const int n = d.nA * d.nH * d.nB;
-    const int sY = d.nH * d.pB * d.nB;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      int t = idx;
-      const int b = t % d.nB; t /= d.nB;
-      const int l = t % d.nH; t /= d.nH;
-      const int a = t;
-      T s = zero<T>();
-      for (int a2 = 0; a2 < d.nA2; ++a2)
-        for (int dd = 0; dd < d.pB; ++dd)
-          s = fmac(s, Bs[(a * d.pB + dd) * d.nA2 + a2], t2[a2 * sY + (l * d.pB + dd) * d.nB + b]);
-      out[idx] = s;
-    }
-    __syncthreads();
-  }
-}
-
-// G[l][r][dd][u] = sum L[a][l][b] Bs[a][dd][a2] Ts[b][u][b2] R2[a2][r][b2]
-// (open tensor of one vertex of the row, written over actual dims)
-template <class T>
-__device__ __noinline__ void row_site_open(int Dk, const RowDims& d, const T* L, const T* Bs, const T* Ts,
-                              const T* R2, T* G, T* t1, T* t2) {
-  // X1[l][b][dd][a2] (left S1)
-  {
-    const int n = d.nH * d.nB * d.pB * d.nA2;
-    const int sLa = d.nH * d.nB, sBa = d.pB * d.nA2;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      const int da = idx % (d.pB * d.nA2);
-      const int lb = idx / (d.pB * d.nA2);
-      T s = zero<T>();
-      for (int a = 0; a < d.nA; ++a) s = fmac(s, L[a * sLa + lb], Bs[a * sBa + da]);
-      t1[idx] = s;
-    }
-  }
-  // Y1[a2][r][b][u] (right S1)
-  {
-    const int n = d.nA2 * d.nH2 * d.nB * d.pT;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      const int bu = idx % (d.nB * d.pT);
-      const int ar = idx / (d.nB * d.pT);
-      T s = zero<T>();
-      for (int b2 = 0; b2 < d.nB2; ++b2) s = fmac(s, R2[ar * d.nB2 + b2], Ts[bu * d.nB2 + b2]);
-      t2[idx] = s;
-    }
-  }
-  __syncthreads();
-  {
-    const int n = d.nH * d.nH2 * d.pB * d.pT;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      int t = idx;
-      const int u = t % d.pT; t /= d.pT;
-      const int dd = t % d.pB; t /= d.pB;
-      const int r = t % d.nH2; t /= d.nH2;
-      const int l = t;
-      T s = zero<T>();
-      for (int b = 0; b < d.nB; ++b)
-        for (int a2 = 0; a2 < d.nA2; ++a2)
-          s = fmac(s, t1[((l * d.nB + b) * d.pB + dd) * d.nA2 + a2],
-                   t2[((a2 * d.nH2 + r) * d.nB + b) * d.pT + u]);
-      G[idx] = s;
-    }
-    __syncthreads();
-  }
-  (void)Dk;
 }
 
 }  // namespace gcf

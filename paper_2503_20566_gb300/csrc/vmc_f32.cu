@@ -6,7 +6,19 @@ namespace gcf {
 template <>
 cudaError_t launch_vmc<float>(const KParams<float>& k, int grid, int block, size_t smem,
                               cudaStream_t st) {
+  {
+    // static + dynamic shared memory above 48 KB needs the opt-in attribute
+    cudaError_t e = cudaFuncSetAttribute(vmc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   vmc_kernel<float><<<grid, block, smem, st>>>(k);
   return cudaGetLastError();
+}
+template <>
+int occupancy_vmc<float>(int block, size_t smem) {
+  cudaFuncSetAttribute(vmc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, vmc_kernel<float>, block, smem) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
 }
 }  // namespace gcf

@@ -24,7 +24,7 @@ struct SharedV {
   double logT[MAX_L + 2];
   double logR[MAX_L + 2];
   double eacc[2];
-  int bid_tmp[8];
+  float redf[32];
   int n_acc, n_prop;
 };
 
@@ -36,10 +36,24 @@ struct Chain {
   int8_t* cfg;  // shared copy of the configuration
   int chain;
   unsigned long long key;
+  // hot buffers (shared memory when they fit, else scratch)
+  T *net, *props, *cop, *envL, *envX, *envY, *env3L, *env3X, *env3Y, *t1, *t2;
+  T* hot;
 
-  __device__ Chain(const KParams<T>& kk, T* w, SharedV& s, int8_t* c, int ch)
-      : k(kk), ws(w), sv(s), cfg(c), chain(ch) {
+  __device__ Chain(const KParams<T>& kk, T* w, SharedV& s, int8_t* c, int ch, T* hot_)
+      : k(kk), ws(w), sv(s), cfg(c), chain(ch), hot(hot_) {
     key = stream_key(k.seed, (unsigned long long)ch);
+    if (k.hot_in_smem) {
+      net = hot_ + k.so_net; props = hot_ + k.so_prop; cop = hot_ + k.so_cop;
+      envL = hot_ + k.so_envL; envX = hot_ + k.so_envX; envY = hot_ + k.so_envY;
+      env3L = hot_ + k.so_env3L; env3X = hot_ + k.so_env3X; env3Y = hot_ + k.so_env3Y;
+      t1 = hot_ + k.so_t1; t2 = hot_ + k.so_t2;
+    } else {
+      net = ws + k.o_net; props = ws + k.o_prop; cop = ws + k.o_t3;
+      envL = ws + k.o_envL; envX = ws + k.o_envX; envY = ws + k.o_envY;
+      env3L = ws + k.o_env3L; env3X = ws + k.o_env3X; env3Y = ws + k.o_env3Y;
+      t1 = ws + k.o_t1; t2 = ws + k.o_t2;
+    }
   }
 
   __device__ T* Bslot(int j) const { return ws + k.o_B + (long long)j * k.mps_stride; }
@@ -48,8 +62,10 @@ struct Chain {
   __device__ const int* bdT(int r) const { return k.bondT + r * (k.Lx + 1); }
   __device__ int physB(int j) const { return j == 0 ? 1 : k.Dk; }   // B[j-1] phys = up dim of row j-1
   __device__ int physT(int r) const { return r == k.Ly ? 1 : k.Dk; } // T[r] phys = down dim of row r
-  __device__ T* box(int x, int y) const { return net_box(k, ws, x, y); }
-  __device__ T* prop(int i) const { return ws + k.o_prop + i * (k.Dk * k.Dk * k.Dk * k.Dk); }
+  __device__ T* box(int x, int y) const {
+    return net + (long long)(y * k.Lx + x) * (k.Dk * k.Dk * k.Dk * k.Dk);
+  }
+  __device__ T* prop(int i) const { return props + i * (k.Dk * k.Dk * k.Dk * k.Dk); }
 
   // ---- configuration moves on the shared copy (thread 0 writes) ---------
   __device__ void plaq_apply(int x, int y, int t) {
@@ -121,14 +137,14 @@ struct Chain {
 
   // ---- boundary MPS --------------------------------------------------------
   __device__ __noinline__ void absorb_B(int r) {  // B[r] = absorb(B[r-1], row r)
-    const double ls = absorb_compress(k, ws, sv.base, Bslot(r), bdB(r), physB(r), r, 0, Bslot(r + 1),
+    const double ls = absorb_compress(k, ws, hot, sv.base, net, Bslot(r), bdB(r), physB(r), r, 0, Bslot(r + 1),
                                       bdB(r + 1), physB(r + 1), k.qrB + r * (k.Lx + 1),
                                       k.svdB + r * (k.Lx + 1));
     if (threadIdx.x == 0) sv.logB[r + 1] = sv.logB[r] + ls;
     __syncthreads();
   }
   __device__ __noinline__ void absorb_T(int r) {  // T[r] = absorb(T[r+1], row r flipped)
-    const double ls = absorb_compress(k, ws, sv.base, Tslot(r + 1), bdT(r + 1), physT(r + 1), r, 1,
+    const double ls = absorb_compress(k, ws, hot, sv.base, net, Tslot(r + 1), bdT(r + 1), physT(r + 1), r, 1,
                                       Tslot(r), bdT(r), physT(r), k.qrT + r * (k.Lx + 1),
                                       k.svdT + r * (k.Lx + 1));
     if (threadIdx.x == 0) sv.logT[r] = sv.logT[r + 1] + ls;
@@ -136,8 +152,8 @@ struct Chain {
   }
 
   // ---- strip (rows r, r+1) between B[r-1] (slot r) and T[r+2] -------------
-  __device__ StripDims sdims(int r, int c) const {
-    StripDims d;
+  __device__ SDims sdims(int r, int c) const {
+    SDims d;
     const int* bb = bdB(r);
     const int* bt = bdT(r + 2);
     d.nA = bb[c]; d.nB = bt[c];
@@ -147,7 +163,7 @@ struct Chain {
     d.pB = physB(r); d.pM = k.Dk; d.pT = physT(r + 2);
     return d;
   }
-  __device__ int env_size(const StripDims& d, bool right) const {
+  __device__ int env_size(const SDims& d, bool right) const {
     return right ? d.nA2 * d.nI2 * d.nJ2 * d.nB2 : d.nA * d.nI * d.nJ * d.nB;
   }
   __device__ T* envR(int c) const { return ws + k.o_envR + (long long)c * k.env_stride; }
@@ -160,10 +176,9 @@ struct Chain {
     if (threadIdx.x == 0) { envR(Lx)[0] = one<T>(); sv.logR[Lx] = 0.0; }
     __syncthreads();
     for (int c = Lx - 1; c >= 0; --c) {
-      const StripDims d = sdims(r, c);
-      strip_right_step<T>(k.Dk, d, envR(c + 1), Bslot(r) + sv.offB[c], box(c, r), box(c, r + 1),
-                          Tslot(r + 2) + sv.offT[c], envR(c), ws + k.o_t1, ws + k.o_t2, ws + k.o_t3);
-      const double ls = rescale(envR(c), env_size(d, false), sv.base.red);
+      const SDims d = sdims(r, c);
+      const double ls = sright(d, envR(c + 1), Bslot(r) + sv.offB[c], box(c, r), box(c, r + 1),
+                              Tslot(r + 2) + sv.offT[c], envR(c));
       if (threadIdx.x == 0) sv.logR[c] = sv.logR[c + 1] + ls;
       __syncthreads();
     }
@@ -174,15 +189,51 @@ struct Chain {
   }
 
   __device__ __noinline__ double strip_step_left(int r, int c, const T* Lin, const T* W1, const T* W2, T* out) {
-    const StripDims d = sdims(r, c);
-    strip_left_step<T>(k.Dk, d, Lin, Bslot(r) + sv.offB[c], W1, W2, Tslot(r + 2) + sv.offT[c], out,
-                       ws + k.o_t1, ws + k.o_t2, ws + k.o_t3);
-    return rescale(out, env_size(d, true), sv.base.red);
+    const SDims d = sdims(r, c);
+    return sleft(d, Lin, Bslot(r) + sv.offB[c], W1, W2, Tslot(r + 2) + sv.offT[c], out);
+  }
+
+  __device__ double sleft(const SDims& d, const T* L, const T* Bs, const T* W1, const T* W2, const T* Ts,
+                         T* out) {
+    switch (k.Dk) {
+      case 1: return strip_left<T, 1>(d, L, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
+      case 2: return strip_left<T, 2>(d, L, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
+      default: return strip_left<T, 3>(d, L, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
+    }
+  }
+  __device__ double sright(const SDims& d, const T* R2, const T* Bs, const T* W1, const T* W2, const T* Ts,
+                          T* out) {
+    switch (k.Dk) {
+      case 1: return strip_right<T, 1>(d, R2, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
+      case 2: return strip_right<T, 2>(d, R2, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
+      default: return strip_right<T, 3>(d, R2, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
+    }
+  }
+  __device__ double rleft(const RDims& d, const T* L, const T* Bs, const T* W, const T* Ts, T* out) {
+    switch (k.Dk) {
+      case 1: return row_left<T, 1>(d, L, Bs, W, Ts, out, t1, t2, sv.redf);
+      case 2: return row_left<T, 2>(d, L, Bs, W, Ts, out, t1, t2, sv.redf);
+      default: return row_left<T, 3>(d, L, Bs, W, Ts, out, t1, t2, sv.redf);
+    }
+  }
+  __device__ double rright(const RDims& d, const T* R2, const T* Bs, const T* W, const T* Ts, T* out) {
+    switch (k.Dk) {
+      case 1: return row_right<T, 1>(d, R2, Bs, W, Ts, out, t1, t2, sv.redf);
+      case 2: return row_right<T, 2>(d, R2, Bs, W, Ts, out, t1, t2, sv.redf);
+      default: return row_right<T, 3>(d, R2, Bs, W, Ts, out, t1, t2, sv.redf);
+    }
+  }
+  __device__ void ropen(const RDims& d, const T* L, const T* Bs, const T* Ts, const T* R2, T* G) {
+    switch (k.Dk) {
+      case 1: row_open<T, 1>(d, L, Bs, Ts, R2, G, t1, t2, sv.redf); break;
+      case 2: row_open<T, 2>(d, L, Bs, Ts, R2, G, t1, t2, sv.redf); break;
+      default: row_open<T, 3>(d, L, Bs, Ts, R2, G, t1, t2, sv.redf); break;
+    }
   }
 
   // ---- row r between B[r-1] (slot r) and T[r+1] ---------------------------
-  __device__ RowDims rdims(int r, int c) const {
-    RowDims d;
+  __device__ RDims rdims(int r, int c) const {
+    RDims d;
     const int* bb = bdB(r);
     const int* bt = bdT(r + 1);
     d.nA = bb[c]; d.nB = bt[c]; d.nH = hl_dim(c, k.Dk);
@@ -199,10 +250,9 @@ struct Chain {
     if (threadIdx.x == 0) { env3R(Lx)[0] = one<T>(); sv.logR[Lx] = 0.0; }
     __syncthreads();
     for (int c = Lx - 1; c >= 0; --c) {
-      const RowDims d = rdims(r, c);
-      row_right_step<T>(k.Dk, d, env3R(c + 1), Bslot(r) + sv.offB[c], box(c, r),
-                        Tslot(r + 1) + sv.offT[c], env3R(c), ws + k.o_t1, ws + k.o_t2);
-      const double ls = rescale(env3R(c), d.nA * d.nH * d.nB, sv.base.red);
+      const RDims d = rdims(r, c);
+      const double ls = rright(d, env3R(c + 1), Bslot(r) + sv.offB[c], box(c, r), Tslot(r + 1) + sv.offT[c],
+                              env3R(c));
       if (threadIdx.x == 0) sv.logR[c] = sv.logR[c + 1] + ls;
       __syncthreads();
     }
@@ -213,10 +263,8 @@ struct Chain {
   }
 
   __device__ __noinline__ double row_step_left(int r, int c, const T* Lin, const T* W, T* out) {
-    const RowDims d = rdims(r, c);
-    row_left_step<T>(k.Dk, d, Lin, Bslot(r) + sv.offB[c], W, Tslot(r + 1) + sv.offT[c], out,
-                     ws + k.o_t1, ws + k.o_t2);
-    return rescale(out, d.nA2 * d.nH2 * d.nB2, sv.base.red);
+    const RDims d = rdims(r, c);
+    return rleft(d, Lin, Bslot(r) + sv.offB[c], W, Tslot(r + 1) + sv.offT[c], out);
   }
 
   // ---- RNG -------------------------------------------------------------------
@@ -259,9 +307,9 @@ template <class T>
 __device__ __noinline__ void plaquette_pass(Chain<T>& ch, int w) {
   const KParams<T>& k = ch.k;
   const int Lx = k.Lx, Ly = k.Ly, D4 = k.Dk * k.Dk * k.Dk * k.Dk;
-  T* Lc = ch.ws + k.o_envL;
-  T* X1 = ch.ws + k.o_envX;
-  T* X2 = ch.ws + k.o_envY;
+  T* Lc = ch.envL;
+  T* X1 = ch.envX;
+  T* X2 = ch.envY;
   for (int r = 0; r < Ly - 1; ++r) {
     double dr, di, dl;
     ch.strip_right_envs(r, dr, di, dl);
@@ -282,7 +330,7 @@ __device__ __noinline__ void plaquette_pass(Chain<T>& ch, int w) {
       const double l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
       const double l2 = ch.strip_step_left(r, c + 1, X1, ch.prop(1), ch.prop(3), X2);
       double nr, ni;
-      const StripDims d2 = ch.sdims(r, c + 1);
+      const SDims d2 = ch.sdims(r, c + 1);
       cta_dot(X2, ch.envR(c + 2), ch.env_size(d2, true), ch.sv.base.red, nr, ni);
       const double nl = logL + l1 + l2 + ch.sv.logR[c + 2];
       const bool acc = (log(u) + log_abs2(dr, di, dl)) < log_abs2(nr, ni, nl) ||
@@ -295,7 +343,7 @@ __device__ __noinline__ void plaquette_pass(Chain<T>& ch, int w) {
         copy_box(ch.box(c + 1, r + 1), ch.prop(3), D4);
         dr = nr; di = ni; dl = nl;
         // L_{c+1} is X1 (built from the accepted column c)
-        const StripDims d1 = ch.sdims(r, c);
+        const SDims d1 = ch.sdims(r, c);
         const int n1 = ch.env_size(d1, true);
         __syncthreads();
         for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
@@ -303,7 +351,7 @@ __device__ __noinline__ void plaquette_pass(Chain<T>& ch, int w) {
       } else {
         ch.plaq_apply(c, r, k.N - t);  // revert
         logL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), X1);
-        const StripDims d1 = ch.sdims(r, c);
+        const SDims d1 = ch.sdims(r, c);
         const int n1 = ch.env_size(d1, true);
         for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
       }
@@ -318,9 +366,9 @@ template <class T>
 __device__ __noinline__ void hhop_pass(Chain<T>& ch, int w) {
   const KParams<T>& k = ch.k;
   const int Lx = k.Lx, Ly = k.Ly, D4 = k.Dk * k.Dk * k.Dk * k.Dk;
-  T* Lc = ch.ws + k.o_env3L;
-  T* X1 = ch.ws + k.o_env3X;
-  T* X2 = ch.ws + k.o_env3Y;
+  T* Lc = ch.env3L;
+  T* X1 = ch.env3X;
+  T* X2 = ch.env3Y;
   for (int r = Ly - 1; r >= 0; --r) {
     double dr, di, dl;
     ch.row_right_envs(r, dr, di, dl);
@@ -340,7 +388,7 @@ __device__ __noinline__ void hhop_pass(Chain<T>& ch, int w) {
         l1 = ch.row_step_left(r, c, Lc, ch.prop(0), X1);
         const double l2 = ch.row_step_left(r, c + 1, X1, ch.prop(1), X2);
         double nr, ni;
-        const RowDims d2 = ch.rdims(r, c + 1);
+        const RDims d2 = ch.rdims(r, c + 1);
         cta_dot(X2, ch.env3R(c + 2), d2.nA2 * d2.nH2 * d2.nB2, ch.sv.base.red, nr, ni);
         const double nl = logL + l1 + l2 + ch.sv.logR[c + 2];
         acc = (log(u) + log_abs2(dr, di, dl)) < log_abs2(nr, ni, nl) ||
@@ -355,7 +403,7 @@ __device__ __noinline__ void hhop_pass(Chain<T>& ch, int w) {
         }
       }
       __syncthreads();
-      const RowDims d1 = ch.rdims(r, c);
+      const RDims d1 = ch.rdims(r, c);
       const int n1 = d1.nA2 * d1.nH2 * d1.nB2;
       if (acc) {
         for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
@@ -375,8 +423,8 @@ template <class T>
 __device__ __noinline__ void vhop_pass(Chain<T>& ch, int w) {
   const KParams<T>& k = ch.k;
   const int Lx = k.Lx, Ly = k.Ly, D4 = k.Dk * k.Dk * k.Dk * k.Dk;
-  T* Lc = ch.ws + k.o_envL;
-  T* X1 = ch.ws + k.o_envX;
+  T* Lc = ch.envL;
+  T* X1 = ch.envX;
   for (int r = 0; r < Ly - 1; ++r) {
     double dr, di, dl;
     ch.strip_right_envs(r, dr, di, dl);
@@ -395,7 +443,7 @@ __device__ __noinline__ void vhop_pass(Chain<T>& ch, int w) {
         __syncthreads();
         l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
         double nr, ni;
-        const StripDims d1 = ch.sdims(r, c);
+        const SDims d1 = ch.sdims(r, c);
         cta_dot(X1, ch.envR(c + 1), ch.env_size(d1, true), ch.sv.base.red, nr, ni);
         const double nl = logL + l1 + ch.sv.logR[c + 1];
         acc = (log(u) + log_abs2(dr, di, dl)) < log_abs2(nr, ni, nl) ||
@@ -410,9 +458,9 @@ __device__ __noinline__ void vhop_pass(Chain<T>& ch, int w) {
         }
       }
       __syncthreads();
-      const StripDims d1 = ch.sdims(r, c);
+      const SDims d1 = ch.sdims(r, c);
       const int n1 = ch.env_size(d1, true);
-      T* Lnext = ch.ws + k.o_envY;
+      T* Lnext = ch.envY;
       if (acc) {
         for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
         logL += l1;
@@ -448,19 +496,18 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
         if (k.log_abs) k.log_abs[s] = la;
         if (k.phase) k.phase[s] = (a2 > 0.0) ? atan2(di, dr) : 0.0;
       }
-      T* Lc = ch.ws + k.o_env3L;
-      T* X1 = ch.ws + k.o_env3X;
-      T* X2 = ch.ws + k.o_env3Y;
+      T* Lc = ch.env3L;
+      T* X1 = ch.env3X;
+      T* X2 = ch.env3Y;
       if (threadIdx.x == 0) Lc[0] = one<T>();
       __syncthreads();
       double logL = 0.0;
       const double den2 = dr * dr + di * di;
       for (int c = 0; c < Lx; ++c) {
-        const RowDims d = ch.rdims(r, c);
+        const RDims d = ch.rdims(r, c);
         if (want_g) {
           T* G = ch.ws + k.o_G;
-          row_site_open<T>(Dk, d, Lc, ch.Bslot(r) + ch.sv.offB[c], ch.Tslot(r + 1) + ch.sv.offT[c],
-                           ch.env3R(c + 1), G, ch.ws + k.o_t1, ch.ws + k.o_t2);
+          ch.ropen(d, Lc, ch.Bslot(r) + ch.sv.offB[c], ch.Tslot(r + 1) + ch.sv.offT[c], ch.env3R(c + 1), G);
           // O = G * exp(logL + logR[c+1] - dl) / (dr + i di)
           const double f = exp(logL + ch.sv.logR[c + 1] - dl) / den2;
           const T fac = make_scalar<T>(dr * f, -di * f);
@@ -480,7 +527,7 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
             const double l1 = ch.row_step_left(r, c, Lc, ch.prop(0), X1);
             const double l2 = ch.row_step_left(r, c + 1, X1, ch.prop(1), X2);
             double nr, ni;
-            const RowDims d2 = ch.rdims(r, c + 1);
+            const RDims d2 = ch.rdims(r, c + 1);
             cta_dot(X2, ch.env3R(c + 2), d2.nA2 * d2.nH2 * d2.nB2, ch.sv.base.red, nr, ni);
             double rr, ri;
             ratio_of(nr, ni, logL + l1 + l2 + ch.sv.logR[c + 2], dr, di, dl, rr, ri);
@@ -500,9 +547,9 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
     if (want_e && r <= Ly - 2) {
       double dr, di, dl;
       ch.strip_right_envs(r, dr, di, dl);
-      T* Lc = ch.ws + k.o_envL;
-      T* X1 = ch.ws + k.o_envX;
-      T* X2 = ch.ws + k.o_envY;
+      T* Lc = ch.envL;
+      T* X1 = ch.envX;
+      T* X2 = ch.envY;
       if (threadIdx.x == 0) Lc[0] = one<T>();
       __syncthreads();
       double logL = 0.0;
@@ -521,7 +568,7 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
             const double l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
             const double l2 = ch.strip_step_left(r, c + 1, X1, ch.prop(1), ch.prop(3), X2);
             double nr, ni;
-            const StripDims d2 = ch.sdims(r, c + 1);
+            const SDims d2 = ch.sdims(r, c + 1);
             cta_dot(X2, ch.envR(c + 2), ch.env_size(d2, true), ch.sv.base.red, nr, ni);
             double rr, ri;
             ratio_of(nr, ni, logL + l1 + l2 + ch.sv.logR[c + 2], dr, di, dl, rr, ri);
@@ -536,7 +583,7 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
             __syncthreads();
             const double l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
             double nr, ni;
-            const StripDims d1 = ch.sdims(r, c);
+            const SDims d1 = ch.sdims(r, c);
             cta_dot(X1, ch.envR(c + 1), ch.env_size(d1, true), ch.sv.base.red, nr, ni);
             double rr, ri;
             ratio_of(nr, ni, logL + l1 + ch.sv.logR[c + 1], dr, di, dl, rr, ri);
@@ -545,7 +592,7 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
           }
         }
         if (c < Lx - 1) {
-          const StripDims d1 = ch.sdims(r, c);
+          const SDims d1 = ch.sdims(r, c);
           logL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), X1);
           const int n1 = ch.env_size(d1, true);
           for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
@@ -579,8 +626,10 @@ __device__ void init_trivial_slots(const KParams<T>& k, T* ws) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) vmc_kernel(KParams<T> k) {
-  extern __shared__ int8_t dyn_cfg[];
+__global__ void __launch_bounds__(256, 2) vmc_kernel(KParams<T> k) {
+  extern __shared__ __align__(16) int8_t dyn_smem[];
+  int8_t* dyn_cfg = dyn_smem;
+  T* hot = (T*)(dyn_smem + k.smem_cfg_bytes);
   __shared__ SharedV sv;
   T* ws = ws_of(k);
   init_trivial_slots(k, ws);
@@ -591,7 +640,7 @@ __global__ void __launch_bounds__(256) vmc_kernel(KParams<T> k) {
       sv.logB[0] = 0.0; sv.logT[k.Ly] = 0.0; sv.n_acc = 0; sv.n_prop = 0;
     }
     __syncthreads();
-    Chain<T> ch(k, ws, sv, dyn_cfg, chain);
+    Chain<T> ch(k, ws, sv, dyn_cfg, chain, hot);
     const bool ok = ch.check_and_gather_all();
     if (!ok) {
       if (threadIdx.x == 0) {
