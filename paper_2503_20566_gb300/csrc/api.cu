@@ -31,6 +31,9 @@ struct Plan {
       o_envY, o_t1, o_t2, o_t3, o_env3R, o_env3L, o_env3X, o_env3Y, o_G;
   // hot buffers in dynamic shared memory (elements from the hot base)
   int hot_in_smem = 0;
+  long long o_sigma = 0, o_sel = 0;
+  int env_in_smem = 0;
+  long long so_envR = 0, so_env3R = 0, so_sB = 0, so_sT = 0;
   long long o_Z = 0, z_size = 0, q_pack = 0, o_X = 0, o_W1 = 0, o_W2 = 0, o_W3 = 0, o_W4 = 0;
   long long so_net, so_prop, so_cop, so_envL, so_envX, so_envY, so_env3L, so_env3X, so_env3Y, so_t1,
       so_t2, hot_elems = 0, cfg_bytes = 0;
@@ -253,6 +256,8 @@ void build_plan(gcf_ctx* c) {
   p.o_env3X = take(p.env3_stride);
   p.o_env3Y = take(p.env3_stride);
   p.o_G = take(D4);
+  p.o_sigma = take(2 * p.tau_max + 32);  // SVD column norms (doubles)
+  p.o_sel = take(p.tau_max + 32);         // selected columns (ints)
   // absorbed sites of one step (warp compression path)
   long long zmax = 1;
   for (int j = 0; j <= Ly; ++j)
@@ -298,12 +303,23 @@ void build_plan(gcf_ctx* c) {
   p.so_env3Y = hot(p.env3_stride);
   p.so_t1 = hot(p.tmp_max);
   p.so_t2 = hot(p.tmp_max);
-  p.hot_elems = h;
   p.cfg_bytes = (c->cfg_len + 15) / 16 * 16;
-  const size_t hot_bytes = (size_t)h * c->sbytes;
   const size_t budget = 100 * 1024;
-  p.hot_in_smem = hot_bytes <= budget ? 1 : 0;
-  p.dyn_smem = (size_t)p.cfg_bytes + (p.hot_in_smem ? hot_bytes : 0);
+  const long long h_base = h;
+  p.so_envR = hot((long long)(Lx + 1) * p.env_stride);
+  p.so_env3R = hot((long long)(Lx + 1) * p.env3_stride);
+  p.so_sB = hot(p.mps_stride);
+  p.so_sT = hot(p.mps_stride);
+  if ((size_t)h * c->sbytes <= budget) {
+    p.hot_in_smem = 1;
+    p.env_in_smem = 1;
+  } else {
+    h = h_base;
+    p.hot_in_smem = (size_t)h * c->sbytes <= budget ? 1 : 0;
+    p.env_in_smem = 0;
+  }
+  p.hot_elems = h;
+  p.dyn_smem = (size_t)p.cfg_bytes + (p.hot_in_smem ? (size_t)h * c->sbytes : 0);
 }
 
 template <class T>
@@ -315,6 +331,8 @@ KParams<T> make_params(gcf_ctx* c) {
   k.n_h = c->n_h; k.n_v = c->n_v; k.n_s = c->n_s; k.cfg_len = c->cfg_len;
   k.n_plaq = c->n_plaq; k.n_slots = c->n_slots;
   k.h = c->m.h; k.g = c->m.g; k.J = c->m.J; k.m = c->m.m;
+  for (int n = 0; n < 8; ++n)
+    k.elink[n] = n < c->m.N ? c->m.g * (2.0 - 2.0 * std::cos(2.0 * 3.14159265358979323846 * n / c->m.N)) : 0.0;
   k.Q = c->d_Q; k.voff = c->d_voff; k.vbs = c->d_vbs; k.params = (const T*)c->d_params;
   const int W = c->m.Lx + 1, R = c->m.Ly + 1;
   k.bondB = c->d_tables;
@@ -335,6 +353,9 @@ KParams<T> make_params(gcf_ctx* c) {
   k.env_stride = p.env_stride; k.env3_stride = p.env3_stride;
   k.max_sweeps_svd = 40;
   k.hot_in_smem = p.hot_in_smem;
+  k.env_in_smem = p.env_in_smem;
+  k.so_envR = p.so_envR; k.so_env3R = p.so_env3R; k.so_sB = p.so_sB; k.so_sT = p.so_sT;
+  k.o_sigma = p.o_sigma; k.o_sel = p.o_sel;
   k.dense_max = p.tmp_max;
   k.o_Z = p.o_Z; k.z_size = p.z_size; k.o_X = p.o_X; k.o_W1 = p.o_W1; k.o_W2 = p.o_W2; k.o_W3 = p.o_W3;
   k.o_W4 = p.o_W4;

@@ -105,11 +105,23 @@ __host__ __device__ inline double scale(double a, double s) { return a * s; }
 __host__ __device__ inline cfloat scale(cfloat a, float s) { return {a.x * s, a.y * s}; }
 __host__ __device__ inline cdouble scale(cdouble a, double s) { return {a.x * s, a.y * s}; }
 
-template <class T> __host__ __device__ inline T make_scalar(double r, double i);
-template <> __host__ __device__ inline float make_scalar<float>(double r, double) { return (float)r; }
-template <> __host__ __device__ inline double make_scalar<double>(double r, double) { return r; }
-template <> __host__ __device__ inline cfloat make_scalar<cfloat>(double r, double i) { return {(float)r, (float)i}; }
-template <> __host__ __device__ inline cdouble make_scalar<cdouble>(double r, double i) { return {r, i}; }
+// make_scalar<T>(re, im): the argument type is deduced so that float
+// arguments never pass through double.
+template <class T> struct MakeS;
+template <> struct MakeS<float> {
+  template <class A> __host__ __device__ static float f(A r, A) { return (float)r; }
+};
+template <> struct MakeS<double> {
+  template <class A> __host__ __device__ static double f(A r, A) { return (double)r; }
+};
+template <> struct MakeS<cfloat> {
+  template <class A> __host__ __device__ static cfloat f(A r, A i) { return {(float)r, (float)i}; }
+};
+template <> struct MakeS<cdouble> {
+  template <class A> __host__ __device__ static cdouble f(A r, A i) { return {(double)r, (double)i}; }
+};
+template <class T, class A>
+__host__ __device__ inline T make_scalar(A r, A i) { return MakeS<T>::f(r, i); }
 
 // complex division a / b (b != 0)
 __device__ inline float cdiv(float a, float b) { return a / b; }
@@ -194,6 +206,49 @@ __device__ inline void block_sum2(double& a, double& b, double* red) {
   a = red[0]; b = red[32];
   __syncthreads();
 }
+
+// Block-wide sums in the real type R of the scalar (float for the FP32
+// forms: GB300's FP64 pipe is ~1/64 of FP32, so FP64 stays out of hot loops).
+// red: shared scratch of >= 64 R values.  All threads call; result broadcast.
+template <class R>
+__device__ inline R block_sum_r(R v, R* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  R t = (lane < nw) ? red[lane] : R(0);
+  t = warp_sum(t);
+  __syncthreads();
+  return t;
+}
+template <class R>
+__device__ inline void block_sum2_r(R& a, R& b, R* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __syncthreads();
+  if (lane == 0) { red[wid] = a; red[32 + wid] = b; }
+  __syncthreads();
+  R ta = (lane < nw) ? red[lane] : R(0);
+  R tb = (lane < nw) ? red[32 + lane] : R(0);
+  a = warp_sum(ta);
+  b = warp_sum(tb);
+  __syncthreads();
+}
+
+// Power-of-two scaling: the exponent e with m = f 2^e, f in [0.5, 1).
+// Scaling by 2^-e is exact, so log-scales are integers (units of ln 2).
+__device__ inline int exp2_of(float m) {
+  int e;
+  frexpf(m, &e);
+  return e;
+}
+__device__ inline float pow2f(int e) { return ldexpf(1.0f, e); }
+__device__ inline double pow2d(int e) { return ldexp(1.0, e); }
+template <class R> __device__ inline R pow2r(int e);
+template <> __device__ inline float pow2r<float>(int e) { return ldexpf(1.0f, e); }
+template <> __device__ inline double pow2r<double>(int e) { return ldexp(1.0, e); }
 
 // ---- SplitMix64 counter generator (Steele, Lea & Flood 2014) -------------
 __host__ __device__ inline uint64_t mix64(uint64_t z) {

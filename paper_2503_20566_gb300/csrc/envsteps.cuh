@@ -92,9 +92,11 @@ __device__ __forceinline__ float block_maxf(float v, float* red) {
   return t;
 }
 
-// Dispatch on the output size so that typically one tile per thread.
+// Dispatch on the output size so that typically one tile per thread.  With
+// rescale, the output is multiplied by 2^-e (exact) with e the binary
+// exponent of its largest |component|, and e is returned.
 template <class T>
-__device__ __noinline__ double cta_gemm_scaled(int M, int N, int K, const T* A, int sAm, int sAk,
+__device__ __noinline__ int cta_gemm_scaled(int M, int N, int K, const T* A, int sAm, int sAk,
                                               const T* B, int sBk, int sBn, T* C, int ldc,
                                               bool rescale, float* red) {
   float mx;
@@ -110,22 +112,22 @@ __device__ __noinline__ double cta_gemm_scaled(int M, int N, int K, const T* A, 
     mx = gemm_tiles<T, 1, 1>(M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc);
   if (!rescale) {
     __syncthreads();
-    return 0.0;
+    return 0;
   }
   mx = block_maxf(mx, red);
   if (mx > 0.f && isfinite(mx)) {
-    // the log returned is that of the factor actually applied
     using R = typename Traits<T>::R;
-    const R s = R(1) / R(mx);
+    const int e = exp2_of(mx);
+    const R s = pow2r<R>(-e);
     for (int i = threadIdx.x; i < MN; i += nt) {
       const int m = i / N, n = i - m * N;
       C[m * ldc + n] = scale(C[m * ldc + n], s);
     }
     __syncthreads();
-    return -log((double)s);
+    return e;
   }
   __syncthreads();
-  return 0.0;
+  return 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -159,7 +161,7 @@ __device__ __forceinline__ void build_column_op(const SDims& d, const T* W1, con
 
 // left step; returns log of the rescale factor of the output
 template <class T, int DK>
-__device__ __noinline__ double strip_left(const SDims& d, const T* L, const T* Bs, const T* W1,
+__device__ __noinline__ int strip_left(const SDims& d, const T* L, const T* Bs, const T* W1,
                                          const T* W2, const T* Ts, T* out, T* X1, T* X2, T* Cop,
                                          float* red) {
   build_column_op<T, DK>(d, W1, W2, Cop);
@@ -208,7 +210,7 @@ __device__ __noinline__ double strip_left(const SDims& d, const T* L, const T* B
 
 // right step: R[a][i][j][b] from R2[a2][i2][j2][b2]
 template <class T, int DK>
-__device__ __noinline__ double strip_right(const SDims& d, const T* R2, const T* Bs, const T* W1,
+__device__ __noinline__ int strip_right(const SDims& d, const T* R2, const T* Bs, const T* W1,
                                           const T* W2, const T* Ts, T* out, T* Y1, T* Y2, T* Cop,
                                           float* red) {
   build_column_op<T, DK>(d, W1, W2, Cop);
@@ -264,7 +266,7 @@ struct RDims {
 };
 
 template <class T, int DK>
-__device__ __noinline__ double row_left(const RDims& d, const T* L, const T* Bs, const T* W, const T* Ts,
+__device__ __noinline__ int row_left(const RDims& d, const T* L, const T* Bs, const T* W, const T* Ts,
                                        T* out, T* X1, T* X2, float* red, bool rescale = true) {
   // G1: X1[(l b)][(d a2)] = sum_a L[a][(l b)] Bs[a][(d a2)]
   const int Mlb = d.nH * d.nB, N1 = d.pB * d.nA2;
@@ -299,7 +301,7 @@ __device__ __noinline__ double row_left(const RDims& d, const T* L, const T* Bs,
 }
 
 template <class T, int DK>
-__device__ __noinline__ double row_right(const RDims& d, const T* R2, const T* Bs, const T* W, const T* Ts,
+__device__ __noinline__ int row_right(const RDims& d, const T* R2, const T* Bs, const T* W, const T* Ts,
                                         T* out, T* Y1, T* Y2, float* red) {
   // G1: Y1[(a2 r)][(b u)] = sum_b2 R2[(a2 r)][b2] Ts[(b u)][b2]
   const int M1 = d.nA2 * d.nH2, N1 = d.nB * d.pT;

@@ -38,38 +38,39 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, const T* A, int sAm, 
 }
 
 
-// Householder reflector for column (alpha; x) with |x|^2 = xn2:
-// H = I - tau v v^H, v = (1; x * scal), H^H (alpha; x) = (beta; 0), beta real.
+// Householder reflector for column (alpha; x) with |x|^2 = xn2, in the
+// scalar's own precision: H = I - tau v v^H, v = (1; x * scal),
+// H^H (alpha; x) = (beta; 0), beta real.
 template <class T>
-__device__ inline void householder(T alpha, double xn2, T& tau, T& scal, T& beta) {
+__device__ inline void householder(T alpha, typename Traits<T>::R xn2, T& tau, T& scal, T& beta) {
   using R = typename Traits<T>::R;
-  const double ar = (double)re(alpha), ai = (double)im(alpha);
-  if (xn2 == 0.0 && ai == 0.0) {
+  const R ar = re(alpha), ai = im(alpha);
+  if (xn2 == R(0) && ai == R(0)) {
     tau = zero<T>(); scal = zero<T>(); beta = alpha;
     return;
   }
-  double b = sqrt(ar * ar + ai * ai + xn2);
-  if (ar >= 0.0) b = -b;
+  R b = sqrt(ar * ar + ai * ai + xn2);
+  if (ar >= R(0)) b = -b;
   tau = make_scalar<T>((b - ar) / b, -ai / b);
-  // scal = 1 / (alpha - beta)
-  const double dr = ar - b, di = ai;
-  const double d2 = dr * dr + di * di;
+  const R dr = ar - b, di = ai;
+  const R d2 = dr * dr + di * di;
   scal = make_scalar<T>(dr / d2, -di / d2);
-  beta = make_scalar<T>(b, 0.0);
-  (void)sizeof(R);
+  beta = make_scalar<T>(b, R(0));
 }
 
 // In-place Householder QR of A (m x n): on return the upper triangle of the
 // leading k = min(m,n) rows holds R, the part below the diagonal holds the
 // reflector vectors, tau[0..k) their factors.  `red` is shared scratch (64 doubles).
 template <class T>
-__device__ __noinline__ void cta_qr(int m, int n, T* A, int sm, int sn, T* tau, double* red) {
+__device__ __noinline__ void cta_qr(int m, int n, T* A, int sm, int sn, T* tau, double* red_) {
+  using R = typename Traits<T>::R;
+  R* red = (R*)red_;
   const int k = min(m, n);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = 0; j < k; ++j) {
-    double part = 0.0;
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) part += (double)abs2(A[i * sm + j * sn]);
-    const double xn2 = block_sum(part, red);
+    R part = R(0);
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) part += abs2(A[i * sm + j * sn]);
+    const R xn2 = block_sum_r<R>(part, red);
     const T alpha = A[j * sm + j * sn];
     T t, sc, beta;
     householder(alpha, xn2, t, sc, beta);
@@ -150,7 +151,7 @@ __device__ __noinline__ int cta_jacobi_svd(int p, int q, T* W, int sWm, int sWn,
     J[i * sJm + c * sJn] = (i == c) ? one<T>() : zero<T>();
   }
   const int n = q + (q & 1);
-  const double tol = 8.0 * (double)Traits<T>::eps();
+  const R tol = R(8) * Traits<T>::eps();
   int sweep = 0;
   if (converged) *converged = 1;
   for (; sweep < max_sweeps; ++sweep) {
@@ -163,21 +164,21 @@ __device__ __noinline__ int cta_jacobi_svd(int p, int q, T* W, int sWm, int sWn,
         else { a = (r + kp) % (n - 1); b = (r - kp + n - 1) % (n - 1); }
         if (a >= q || b >= q) continue;
         if (a > b) { int t = a; a = b; b = t; }
-        double al = 0.0, be = 0.0;
+        R al = R(0), be = R(0);
         T g = zero<T>();
         for (int i = lane; i < p; i += 32) {
           const T wa = W[i * sWm + a * sWn], wb = W[i * sWm + b * sWn];
-          al += (double)abs2(wa);
-          be += (double)abs2(wb);
+          al += abs2(wa);
+          be += abs2(wb);
           g = fmac(g, conjg(wa), wb);
         }
         al = warp_sum(al); be = warp_sum(be); g = warp_sum_scalar(g);
-        const double gr = (double)re(g), gi = (double)im(g);
-        const double ga = sqrt(gr * gr + gi * gi);
-        if (ga == 0.0 || !(ga > tol * sqrt(al * be))) continue;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        const R gr = re(g), gi = im(g);
+        const R ga = sqrt(gr * gr + gi * gi);
+        if (ga == R(0) || !(ga > tol * sqrt(al * be))) continue;
+        const R zeta = (be - al) / (R(2) * ga);
+        const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+        const R c = R(1) / sqrt(R(1) + t * t), s = c * t;
         // G = [[c, s e^{i phi}], [-s e^{-i phi}, c]], e^{i phi} = g / |g|
         const T eph = make_scalar<T>(gr / ga, gi / ga);
         const T s_e = scale(eph, (R)s);                 // s e^{i phi}

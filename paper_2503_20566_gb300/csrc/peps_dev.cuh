@@ -31,6 +31,7 @@ struct KParams {
   int N, Lx, Ly, Dk, chi, matter, P;
   int n_h, n_v, n_s, cfg_len, n_plaq, n_slots;
   double h, g, J, m;
+  double elink[8];         // g (2 - 2 cos(2 pi n / N)) for n = 0..N-1
   const int* Q;            // [Ly*Lx]
   const long long* voff;   // [Lx*Ly] parameter offset of each vertex
   const int* vbs;          // [Lx*Ly] block size of each vertex
@@ -53,9 +54,12 @@ struct KParams {
   int max_sweeps_svd;
   // hot buffers: in dynamic shared memory when hot_in_smem, else in scratch
   int hot_in_smem;
-  long long dense_max, o_Z, z_size, q_pack, o_X, o_W1, o_W2, o_W3, o_W4;
+  long long o_sigma, o_sel, dense_max, o_Z, z_size, q_pack, o_X, o_W1, o_W2, o_W3, o_W4;
   long long so_net, so_prop, so_cop, so_envL, so_envX, so_envY, so_env3L, so_env3X, so_env3Y,
       so_t1, so_t2, smem_cfg_bytes;
+  // right environments and the staged B / T rows of the current pass
+  int env_in_smem;
+  long long so_envR, so_env3R, so_sB, so_sT;
   // per-run
   int n_chains, n_sweeps, mode, want;  // mode 0: measure given configs, 1: sample
   unsigned long long seed;
@@ -82,8 +86,6 @@ struct Shared {
   int qoff[MAX_L + 1];
   int bd_off[MAX_L + 1];
   int bd_off2[MAX_L + 1];
-  int sel[4 * MAX_L * 4];
-  double sigma[4 * MAX_L * 4];
 };
 
 __device__ inline int hl_dim(int c, int Dk) { return c == 0 ? 1 : Dk; }
@@ -163,43 +165,48 @@ __device__ inline void mps_offsets(const int* bd, int phys, int Lx, int* off) {
 }
 
 // ---------------------------------------------------------------------------
-// Rescaling: divide a tensor by its largest |component|, return log(scale).
+// Rescaling by exact powers of two; the returned integer e means
+// "tensor_in = 2^e * tensor_out".
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ __noinline__ double rescale(T* a, int n, double* red) {
+__device__ __noinline__ int rescale(T* a, int n, double* red_) {
   using R = typename Traits<T>::R;
-  double mx = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, (double)absmax1(a[i]));
-  mx = block_max(mx, red);
-  if (!(mx > 0.0) || !isfinite(mx)) return 0.0;
-  const R s = (R)(1.0 / mx);
+  float mx = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmaxf(mx, (float)absmax1(a[i]));
+  mx = block_maxf(mx, (float*)red_);
+  if (!(mx > 0.f) || !isfinite(mx)) return 0;
+  const int e = exp2_of(mx);
+  const R s = pow2r<R>(-e);
   for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = scale(a[i], s);
   __syncthreads();
-  return log(mx);
+  return e;
 }
 
+// the same with the scale chosen from the Frobenius norm (|a| -> [0.5, 1))
 template <class T>
-__device__ __noinline__ double frob_rescale(T* a, int n, double* red) {
+__device__ __noinline__ int frob_rescale(T* a, int n, double* red_) {
   using R = typename Traits<T>::R;
-  double s2 = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s2 += (double)abs2(a[i]);
-  s2 = block_sum(s2, red);
-  if (!(s2 > 0.0) || !isfinite(s2)) return 0.0;
-  const double nr = sqrt(s2);
-  const R s = (R)(1.0 / nr);
+  R s2 = R(0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s2 += abs2(a[i]);
+  s2 = block_sum_r<R>(s2, (R*)red_);
+  if (!(s2 > R(0)) || !isfinite((float)s2)) return 0;
+  const int e = exp2_of((float)sqrt(s2));
+  const R s = pow2r<R>(-e);
   for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = scale(a[i], s);
   __syncthreads();
-  return log(nr);
+  return e;
 }
 
 // sum_k A[k] B[k] (no conjugation), broadcast to all threads as (re, im)
 template <class T>
-__device__ inline void cta_dot(const T* A, const T* B, int n, double* red, double& r, double& i) {
+__device__ inline void cta_dot(const T* A, const T* B, int n, double* red_, typename Traits<T>::R& r,
+                               typename Traits<T>::R& i) {
+  using R = typename Traits<T>::R;
   T s = zero<T>();
   for (int k = threadIdx.x; k < n; k += blockDim.x) s = fmac(s, A[k], B[k]);
-  r = (double)re(s);
-  i = (double)im(s);
-  block_sum2(r, i, red);
+  r = re(s);
+  i = im(s);
+  block_sum2_r<R>(r, i, (R*)red_);
 }
 
 // ---------------------------------------------------------------------------
@@ -212,10 +219,10 @@ __device__ inline void cta_dot(const T* A, const T* B, int n, double* red, doubl
 // v[(u_0..u_{m-1})][u_m][(u_{m+1}..u_{L-1})].  It is the same state the QR /
 // LQ sweep produces, in a different gauge.  The dense state is obtained by
 // contracting the input MPS to a vector and applying the row MPO site by site.
-// Returns the log of the scale factor.
+// Returns the binary exponent e of the scale (state = 2^e * output).
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ __noinline__ double dense_absorb(const KParams<T>& k, Shared& sh, const T* net, const T* mps_in,
+__device__ __noinline__ int dense_absorb(const KParams<T>& k, Shared& sh, const T* net, const T* mps_in,
                                             const int* bdi, int pin, int row, int flip, T* mout,
                                             const int* bdo, int pout, T* bufA, T* bufB) {
   const int Lx = k.Lx, Dk = k.Dk;
@@ -256,13 +263,14 @@ __device__ __noinline__ double dense_absorb(const KParams<T>& k, Shared& sh, con
     NU *= pout;
     if (c < Lx - 1) ND /= pin;
   }
-  // 3. normalise v' (length pout^L, bufA)
-  const int nv = NU;
-  double s2 = 0.0;
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) s2 += (double)abs2(bufA[i]);
-  s2 = block_sum(s2, sh.red);
+  // 3. scale v' (length pout^L, bufA) by a power of two near its norm
   using R = typename Traits<T>::R;
-  const R inv = s2 > 0.0 ? R(1.0 / sqrt(s2)) : R(1);
+  const int nv = NU;
+  R s2 = R(0);
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) s2 += abs2(bufA[i]);
+  s2 = block_sum_r<R>(s2, (R*)sh.red);
+  const int e = (s2 > R(0) && isfinite((float)s2)) ? exp2_of((float)sqrt(s2)) : 0;
+  const R inv = pow2r<R>(-e);
   // 4. identity sites and the core
   const int m = Lx / 2;
   for (int c = 0; c < Lx; ++c) {
@@ -280,7 +288,7 @@ __device__ __noinline__ double dense_absorb(const KParams<T>& k, Shared& sh, con
     }
   }
   __syncthreads();
-  return s2 > 0.0 ? -log((double)inv) : 0.0;
+  return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -289,14 +297,14 @@ __device__ __noinline__ double dense_absorb(const KParams<T>& k, Shared& sh, con
 //        tensors are boxes net_box(x=c, y=row); flip=1 swaps the d and u legs
 //        (absorption from above).
 //   out: MPS `mout` with bond table bdo, physical dim pout; qr/svd: the
-//        step's QR left dims and SVD flags.  Returns log of the scale factor
-//        (output state = exp(ret) * mout, up to the discarded weight).
+//        step's QR left dims and SVD flags.  Returns the binary exponent e of
+//        the scale (output state = 2^e * mout, up to the discarded weight).
 // Algorithm: QR left to right on the absorbed MPS (left-canonical form),
 // then right to left: LQ where no truncation is needed, one-sided Jacobi SVD
 // keeping the chi largest singular values otherwise.
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ __noinline__ double absorb_compress(const KParams<T>& k, T* ws, T* hot_base, Shared& sh, const T* net,
+__device__ __noinline__ int absorb_compress(const KParams<T>& k, T* ws, T* hot_base, Shared& sh, const T* net,
                                   const T* mps_in, const int* bdi, int pin, int row, int flip, T* mout,
                                   const int* bdo, int pout, const int* qr, const int* svd) {
   const int Lx = k.Lx, Dk = k.Dk;
@@ -308,7 +316,7 @@ __device__ __noinline__ double absorb_compress(const KParams<T>& k, T* ws, T* ho
   T* tau = ws + k.o_tau;
   T* Jm = ws + k.o_J;
   T* Qs = ws + k.o_Q;
-  double logs = 0.0;
+  int logs = 0;
   mps_offsets(bdi, pin, Lx, sh.bd_off);
   mps_offsets(bdo, pout, Lx, sh.bd_off2);
 
@@ -449,26 +457,30 @@ __device__ __noinline__ double absorb_compress(const KParams<T>& k, T* ws, T* ho
         int conv = 1;
         cta_jacobi_svd<T>(yr, k0, Lc, k0, 1, Jm, k0, 1, &sh.iflag[0], k.max_sweeps_svd, &conv);
         if (!conv && threadIdx.x == 0) atomicAdd(&k.status[ST_SVD], 1);
+        // squared column norms -> sigma, selected columns -> sel (scratch)
+        using RR = typename Traits<T>::R;
+        RR* sigma = (RR*)(ws + k.o_sigma);
+        int* sel = (int*)(ws + k.o_sel);
         for (int j = threadIdx.x; j < k0; j += blockDim.x) {
-          double s2 = 0.0;
-          for (int i = 0; i < yr; ++i) s2 += (double)abs2(Lc[i * k0 + j]);
-          sh.sigma[j] = s2;
+          RR s2 = RR(0);
+          for (int i = 0; i < yr; ++i) s2 += abs2(Lc[i * k0 + j]);
+          sigma[j] = s2;
         }
         __syncthreads();
         for (int j = threadIdx.x; j < k0; j += blockDim.x) {
           int rank = 0;
-          const double sj = sh.sigma[j];
+          const RR sj = sigma[j];
           for (int i = 0; i < k0; ++i) {
-            const double si = sh.sigma[i];
+            const RR si = sigma[i];
             rank += (si > sj) || (si == sj && i < j);
           }
-          if (rank < kk) sh.sel[rank] = j;
+          if (rank < kk) sel[rank] = j;
         }
         __syncthreads();
         // site[n][x] = sum_j conj(J[j][sel n]) Q'^H[j][x]
         for (int idx = threadIdx.x; idx < kk * yc; idx += blockDim.x) {
           const int n = idx / yc, x = idx - (idx / yc) * yc;
-          const int jn = sh.sel[n];
+          const int jn = sel[n];
           T s = zero<T>();
           for (int j = 0; j < k0; ++j) s = fmac(s, conjg(Jm[j * k0 + jn]), conjg(Qp[x * k0 + j]));
           site[idx] = s;
@@ -476,7 +488,7 @@ __device__ __noinline__ double absorb_compress(const KParams<T>& k, T* ws, T* ho
         // carry U S = W[:, sel] (yr x kk)
         for (int idx = threadIdx.x; idx < yr * kk; idx += blockDim.x) {
           const int i = idx / kk, n = idx - (idx / kk) * kk;
-          Yh[idx] = Lc[i * k0 + sh.sel[n]];
+          Yh[idx] = Lc[i * k0 + sel[n]];
         }
         __syncthreads();
         for (int idx = threadIdx.x; idx < yr * kk; idx += blockDim.x) Lc[idx] = Yh[idx];

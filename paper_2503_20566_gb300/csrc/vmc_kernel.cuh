@@ -20,16 +20,18 @@ struct SharedV {
   Shared base;
   int offB[MAX_L + 1];
   int offT[MAX_L + 1];
-  double logB[MAX_L + 2];
-  double logT[MAX_L + 2];
-  double logR[MAX_L + 2];
+  int logB[MAX_L + 2];   // binary exponents of the stored MPS scales
+  int logT[MAX_L + 2];
+  int logR[MAX_L + 2];   // of the right environments of the current pass
   double eacc[2];
+  int flag;
   float redf[32];
   int n_acc, n_prop;
 };
 
 template <class T>
 struct Chain {
+  using R = typename Traits<T>::R;
   const KParams<T>& k;
   T* ws;
   SharedV& sv;
@@ -39,6 +41,7 @@ struct Chain {
   // hot buffers (shared memory when they fit, else scratch)
   T *net, *props, *cop, *envL, *envX, *envY, *env3L, *env3X, *env3Y, *t1, *t2;
   T* hot;
+  T *eR, *e3R, *sB, *sT;  // right environments; staged MPS rows (or the slots)
 
   __device__ Chain(const KParams<T>& kk, T* w, SharedV& s, int8_t* c, int ch, T* hot_)
       : k(kk), ws(w), sv(s), cfg(c), chain(ch), hot(hot_) {
@@ -48,7 +51,13 @@ struct Chain {
       envL = hot_ + k.so_envL; envX = hot_ + k.so_envX; envY = hot_ + k.so_envY;
       env3L = hot_ + k.so_env3L; env3X = hot_ + k.so_env3X; env3Y = hot_ + k.so_env3Y;
       t1 = hot_ + k.so_t1; t2 = hot_ + k.so_t2;
+    }
+    if (k.hot_in_smem && k.env_in_smem) {
+      eR = hot_ + k.so_envR; e3R = hot_ + k.so_env3R; sB = hot_ + k.so_sB; sT = hot_ + k.so_sT;
     } else {
+      eR = ws + k.o_envR; e3R = ws + k.o_env3R; sB = nullptr; sT = nullptr;
+    }
+    if (!k.hot_in_smem) {
       net = ws + k.o_net; props = ws + k.o_prop; cop = ws + k.o_t3;
       envL = ws + k.o_envL; envX = ws + k.o_envX; envY = ws + k.o_envY;
       env3L = ws + k.o_env3L; env3X = ws + k.o_env3X; env3Y = ws + k.o_env3Y;
@@ -137,14 +146,14 @@ struct Chain {
 
   // ---- boundary MPS --------------------------------------------------------
   __device__ __noinline__ void absorb_B(int r) {  // B[r] = absorb(B[r-1], row r)
-    const double ls = absorb_compress(k, ws, hot, sv.base, net, Bslot(r), bdB(r), physB(r), r, 0, Bslot(r + 1),
+    const int ls = absorb_compress(k, ws, hot, sv.base, net, Bslot(r), bdB(r), physB(r), r, 0, Bslot(r + 1),
                                       bdB(r + 1), physB(r + 1), k.qrB + r * (k.Lx + 1),
                                       k.svdB + r * (k.Lx + 1));
     if (threadIdx.x == 0) sv.logB[r + 1] = sv.logB[r] + ls;
     __syncthreads();
   }
   __device__ __noinline__ void absorb_T(int r) {  // T[r] = absorb(T[r+1], row r flipped)
-    const double ls = absorb_compress(k, ws, hot, sv.base, net, Tslot(r + 1), bdT(r + 1), physT(r + 1), r, 1,
+    const int ls = absorb_compress(k, ws, hot, sv.base, net, Tslot(r + 1), bdT(r + 1), physT(r + 1), r, 1,
                                       Tslot(r), bdT(r), physT(r), k.qrT + r * (k.Lx + 1),
                                       k.svdT + r * (k.Lx + 1));
     if (threadIdx.x == 0) sv.logT[r] = sv.logT[r + 1] + ls;
@@ -166,34 +175,56 @@ struct Chain {
   __device__ int env_size(const SDims& d, bool right) const {
     return right ? d.nA2 * d.nI2 * d.nJ2 * d.nB2 : d.nA * d.nI * d.nJ * d.nB;
   }
-  __device__ T* envR(int c) const { return ws + k.o_envR + (long long)c * k.env_stride; }
+  __device__ T* envR(int c) const { return eR + (long long)c * k.env_stride; }
+  // B / T rows used by the current strip or row pass: staged copies in shared
+  // memory when available, else the scratch slots
+  const T* curB;
+  const T* curT;
+  __device__ void stage(int jb, int jt, int physb, int physt) {
+    const T* b = Bslot(jb);
+    const T* t = Tslot(jt);
+    if (sB) {
+      const int nb = sv.offB[k.Lx], nt = sv.offT[k.Lx];
+      for (int i = threadIdx.x; i < nb; i += blockDim.x) sB[i] = b[i];
+      for (int i = threadIdx.x; i < nt; i += blockDim.x) sT[i] = t[i];
+      __syncthreads();
+      curB = sB;
+      curT = sT;
+    } else {
+      curB = b;
+      curT = t;
+    }
+    (void)physb; (void)physt;
+  }
 
-  // builds R_c for c = Lx..0 (logs in sv.logR), returns strip value (re, im) and log
-  __device__ __noinline__ void strip_right_envs(int r, double& vr, double& vi, double& vlog) {
+  // builds R_c for c = Lx..0 (exponents in sv.logR), returns the strip value
+  // as mantissa (vr, vi) and binary exponent ve
+  __device__ __noinline__ void strip_right_envs(int r, R& vr, R& vi, int& ve) {
     const int Lx = k.Lx;
     mps_offsets(bdB(r), physB(r), Lx, sv.offB);
     mps_offsets(bdT(r + 2), physT(r + 2), Lx, sv.offT);
-    if (threadIdx.x == 0) { envR(Lx)[0] = one<T>(); sv.logR[Lx] = 0.0; }
+    stage(r, r + 2, physB(r), physT(r + 2));
+    if (threadIdx.x == 0) { envR(Lx)[0] = one<T>(); sv.logR[Lx] = 0; }
     __syncthreads();
     for (int c = Lx - 1; c >= 0; --c) {
       const SDims d = sdims(r, c);
-      const double ls = sright(d, envR(c + 1), Bslot(r) + sv.offB[c], box(c, r), box(c, r + 1),
-                              Tslot(r + 2) + sv.offT[c], envR(c));
+      const int ls = sright(d, envR(c + 1), curB + sv.offB[c], box(c, r), box(c, r + 1),
+                           curT + sv.offT[c], envR(c));
       if (threadIdx.x == 0) sv.logR[c] = sv.logR[c + 1] + ls;
       __syncthreads();
     }
-    vr = (double)re(envR(0)[0]);
-    vi = (double)im(envR(0)[0]);
-    vlog = sv.logR[0];
+    vr = re(envR(0)[0]);
+    vi = im(envR(0)[0]);
+    ve = sv.logR[0];
     __syncthreads();
   }
 
-  __device__ __noinline__ double strip_step_left(int r, int c, const T* Lin, const T* W1, const T* W2, T* out) {
+  __device__ __noinline__ int strip_step_left(int r, int c, const T* Lin, const T* W1, const T* W2, T* out) {
     const SDims d = sdims(r, c);
-    return sleft(d, Lin, Bslot(r) + sv.offB[c], W1, W2, Tslot(r + 2) + sv.offT[c], out);
+    return sleft(d, Lin, curB + sv.offB[c], W1, W2, curT + sv.offT[c], out);
   }
 
-  __device__ double sleft(const SDims& d, const T* L, const T* Bs, const T* W1, const T* W2, const T* Ts,
+  __device__ int sleft(const SDims& d, const T* L, const T* Bs, const T* W1, const T* W2, const T* Ts,
                          T* out) {
     switch (k.Dk) {
       case 1: return strip_left<T, 1>(d, L, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
@@ -201,7 +232,7 @@ struct Chain {
       default: return strip_left<T, 3>(d, L, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
     }
   }
-  __device__ double sright(const SDims& d, const T* R2, const T* Bs, const T* W1, const T* W2, const T* Ts,
+  __device__ int sright(const SDims& d, const T* R2, const T* Bs, const T* W1, const T* W2, const T* Ts,
                           T* out) {
     switch (k.Dk) {
       case 1: return strip_right<T, 1>(d, R2, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
@@ -209,14 +240,14 @@ struct Chain {
       default: return strip_right<T, 3>(d, R2, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
     }
   }
-  __device__ double rleft(const RDims& d, const T* L, const T* Bs, const T* W, const T* Ts, T* out) {
+  __device__ int rleft(const RDims& d, const T* L, const T* Bs, const T* W, const T* Ts, T* out) {
     switch (k.Dk) {
       case 1: return row_left<T, 1>(d, L, Bs, W, Ts, out, t1, t2, sv.redf);
       case 2: return row_left<T, 2>(d, L, Bs, W, Ts, out, t1, t2, sv.redf);
       default: return row_left<T, 3>(d, L, Bs, W, Ts, out, t1, t2, sv.redf);
     }
   }
-  __device__ double rright(const RDims& d, const T* R2, const T* Bs, const T* W, const T* Ts, T* out) {
+  __device__ int rright(const RDims& d, const T* R2, const T* Bs, const T* W, const T* Ts, T* out) {
     switch (k.Dk) {
       case 1: return row_right<T, 1>(d, R2, Bs, W, Ts, out, t1, t2, sv.redf);
       case 2: return row_right<T, 2>(d, R2, Bs, W, Ts, out, t1, t2, sv.redf);
@@ -241,30 +272,60 @@ struct Chain {
     d.pB = physB(r); d.pT = physT(r + 1);
     return d;
   }
-  __device__ T* env3R(int c) const { return ws + k.o_env3R + (long long)c * k.env3_stride; }
+  __device__ T* env3R(int c) const { return e3R + (long long)c * k.env3_stride; }
 
-  __device__ __noinline__ void row_right_envs(int r, double& vr, double& vi, double& vlog) {
+  __device__ __noinline__ void row_right_envs(int r, R& vr, R& vi, int& ve) {
     const int Lx = k.Lx;
     mps_offsets(bdB(r), physB(r), Lx, sv.offB);
     mps_offsets(bdT(r + 1), physT(r + 1), Lx, sv.offT);
-    if (threadIdx.x == 0) { env3R(Lx)[0] = one<T>(); sv.logR[Lx] = 0.0; }
+    stage(r, r + 1, physB(r), physT(r + 1));
+    if (threadIdx.x == 0) { env3R(Lx)[0] = one<T>(); sv.logR[Lx] = 0; }
     __syncthreads();
     for (int c = Lx - 1; c >= 0; --c) {
       const RDims d = rdims(r, c);
-      const double ls = rright(d, env3R(c + 1), Bslot(r) + sv.offB[c], box(c, r), Tslot(r + 1) + sv.offT[c],
-                              env3R(c));
+      const int ls = rright(d, env3R(c + 1), curB + sv.offB[c], box(c, r), curT + sv.offT[c], env3R(c));
       if (threadIdx.x == 0) sv.logR[c] = sv.logR[c + 1] + ls;
       __syncthreads();
     }
-    vr = (double)re(env3R(0)[0]);
-    vi = (double)im(env3R(0)[0]);
-    vlog = sv.logR[0];
+    vr = re(env3R(0)[0]);
+    vi = im(env3R(0)[0]);
+    ve = sv.logR[0];
     __syncthreads();
   }
 
-  __device__ __noinline__ double row_step_left(int r, int c, const T* Lin, const T* W, T* out) {
+  __device__ __noinline__ int row_step_left(int r, int c, const T* Lin, const T* W, T* out) {
     const RDims d = rdims(r, c);
-    return rleft(d, Lin, Bslot(r) + sv.offB[c], W, Tslot(r + 1) + sv.offT[c], out);
+    return rleft(d, Lin, curB + sv.offB[c], W, curT + sv.offT[c], out);
+  }
+
+  // Metropolis decision (Sec. S-1): accept iff u |den|^2 < |num|^2, with
+  // den = (dr + i di) 2^de and num = (nr + i ni) 2^ne; evaluated once on
+  // thread 0 (exact powers of two, no logarithms) and broadcast.
+  __device__ bool metro_accept(double u, R dr, R di, int de, R nr, R ni, int ne) {
+    if (threadIdx.x == 0) {
+      const double d2 = (double)dr * dr + (double)di * di;
+      const double n2 = (double)nr * nr + (double)ni * ni;
+      bool acc;
+      if (!(n2 > 0.0)) acc = false;
+      else if (!(d2 > 0.0)) acc = true;
+      else acc = u * d2 < ldexp(n2, 2 * (ne - de));
+      sv.flag = acc ? 1 : 0;
+    }
+    __syncthreads();
+    const bool a = sv.flag != 0;
+    __syncthreads();
+    return a;
+  }
+  // eacc += coef * num / den (thread 0)
+  __device__ void add_ratio(double coef, R nr, R ni, int ne, R dr, R di, int de) {
+    if (threadIdx.x == 0) {
+      const double d2 = (double)dr * dr + (double)di * di;
+      const double f = ldexp(1.0, ne - de) / d2;
+      const double rr = ((double)nr * dr + (double)ni * di) * f;
+      const double ri = ((double)ni * dr - (double)nr * di) * f;
+      sv.eacc[0] += coef * rr;
+      sv.eacc[1] += coef * ri;
+    }
   }
 
   // ---- RNG -------------------------------------------------------------------
@@ -277,22 +338,6 @@ struct Chain {
   }
 };
 
-// log|z|^2 helper with z = (vr, vi) * exp(vlog); -inf for z = 0
-__device__ inline double log_abs2(double vr, double vi, double vlog) {
-  const double a2 = vr * vr + vi * vi;
-  if (!(a2 > 0.0)) return -INFINITY;
-  return log(a2) + 2.0 * vlog;
-}
-
-// ratio (nr + i ni) e^{nl} / ((dr + i di) e^{dl})
-__device__ inline void ratio_of(double nr, double ni, double nl, double dr, double di, double dl,
-                                double& rr, double& ri) {
-  const double d2 = dr * dr + di * di;
-  const double f = exp(nl - dl) / d2;
-  rr = (nr * dr + ni * di) * f;
-  ri = (ni * dr - nr * di) * f;
-}
-
 template <class T>
 __device__ void copy_box(T* dst, const T* src, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
@@ -302,20 +347,22 @@ __device__ void copy_box(T* dst, const T* src, int n) {
 // Passes
 // ---------------------------------------------------------------------------
 
-// plaquette pass, bottom-up, Metropolis
+// plaquette pass, bottom-up, Metropolis (Sec. S-1 rule, Sec. S-2 moves)
 template <class T>
 __device__ __noinline__ void plaquette_pass(Chain<T>& ch, int w) {
+  using R = typename Traits<T>::R;
   const KParams<T>& k = ch.k;
   const int Lx = k.Lx, Ly = k.Ly, D4 = k.Dk * k.Dk * k.Dk * k.Dk;
   T* Lc = ch.envL;
   T* X1 = ch.envX;
   T* X2 = ch.envY;
   for (int r = 0; r < Ly - 1; ++r) {
-    double dr, di, dl;
-    ch.strip_right_envs(r, dr, di, dl);
+    R dr, di;
+    int de;
+    ch.strip_right_envs(r, dr, di, de);
     if (threadIdx.x == 0) Lc[0] = one<T>();
     __syncthreads();
-    double logL = 0.0;
+    int eL = 0;
     for (int c = 0; c < Lx - 1; ++c) {
       const int j = r * (Lx - 1) + c;
       const unsigned long long base = (unsigned long long)w * k.n_slots;
@@ -327,32 +374,28 @@ __device__ __noinline__ void plaquette_pass(Chain<T>& ch, int w) {
       ch.gather_into(c, r + 1, ch.prop(2));
       ch.gather_into(c + 1, r + 1, ch.prop(3));
       __syncthreads();
-      const double l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
-      const double l2 = ch.strip_step_left(r, c + 1, X1, ch.prop(1), ch.prop(3), X2);
-      double nr, ni;
+      const int l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
+      const int l2 = ch.strip_step_left(r, c + 1, X1, ch.prop(1), ch.prop(3), X2);
+      R nr, ni;
       const SDims d2 = ch.sdims(r, c + 1);
       cta_dot(X2, ch.envR(c + 2), ch.env_size(d2, true), ch.sv.base.red, nr, ni);
-      const double nl = logL + l1 + l2 + ch.sv.logR[c + 2];
-      const bool acc = (log(u) + log_abs2(dr, di, dl)) < log_abs2(nr, ni, nl) ||
-                       (u == 0.0 && (nr != 0.0 || ni != 0.0));
+      const int ne = eL + l1 + l2 + ch.sv.logR[c + 2];
+      const bool acc = ch.metro_accept(u, dr, di, de, nr, ni, ne);
       if (threadIdx.x == 0) { ch.sv.n_prop += 1; if (acc) ch.sv.n_acc += 1; }
+      const SDims d1 = ch.sdims(r, c);
+      const int n1 = ch.env_size(d1, true);
       if (acc) {
         copy_box(ch.box(c, r), ch.prop(0), D4);
         copy_box(ch.box(c + 1, r), ch.prop(1), D4);
         copy_box(ch.box(c, r + 1), ch.prop(2), D4);
         copy_box(ch.box(c + 1, r + 1), ch.prop(3), D4);
-        dr = nr; di = ni; dl = nl;
+        dr = nr; di = ni; de = ne;
         // L_{c+1} is X1 (built from the accepted column c)
-        const SDims d1 = ch.sdims(r, c);
-        const int n1 = ch.env_size(d1, true);
-        __syncthreads();
         for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
-        logL += l1;
+        eL += l1;
       } else {
         ch.plaq_apply(c, r, k.N - t);  // revert
-        logL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), X1);
-        const SDims d1 = ch.sdims(r, c);
-        const int n1 = ch.env_size(d1, true);
+        eL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), X1);
         for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
       }
       __syncthreads();
@@ -364,40 +407,41 @@ __device__ __noinline__ void plaquette_pass(Chain<T>& ch, int w) {
 // horizontal-hop pass (matter), top-down with row environments
 template <class T>
 __device__ __noinline__ void hhop_pass(Chain<T>& ch, int w) {
+  using R = typename Traits<T>::R;
   const KParams<T>& k = ch.k;
   const int Lx = k.Lx, Ly = k.Ly, D4 = k.Dk * k.Dk * k.Dk * k.Dk;
   T* Lc = ch.env3L;
   T* X1 = ch.env3X;
   T* X2 = ch.env3Y;
   for (int r = Ly - 1; r >= 0; --r) {
-    double dr, di, dl;
-    ch.row_right_envs(r, dr, di, dl);
+    R dr, di;
+    int de;
+    ch.row_right_envs(r, dr, di, de);
     if (threadIdx.x == 0) Lc[0] = one<T>();
     __syncthreads();
-    double logL = 0.0;
+    int eL = 0;
     for (int c = 0; c < Lx - 1; ++c) {
       const unsigned long long ctr =
           (unsigned long long)w * k.n_slots + 2 * k.n_plaq + r * (Lx - 1) + c;
       const double u = ch.uniform_at(ctr);
       bool acc = false;
-      double l1 = 0.0;
+      int l1 = 0;
       if (ch.hop_apply(c, r, 1)) {
         ch.gather_into(c, r, ch.prop(0));
         ch.gather_into(c + 1, r, ch.prop(1));
         __syncthreads();
         l1 = ch.row_step_left(r, c, Lc, ch.prop(0), X1);
-        const double l2 = ch.row_step_left(r, c + 1, X1, ch.prop(1), X2);
-        double nr, ni;
+        const int l2 = ch.row_step_left(r, c + 1, X1, ch.prop(1), X2);
+        R nr, ni;
         const RDims d2 = ch.rdims(r, c + 1);
         cta_dot(X2, ch.env3R(c + 2), d2.nA2 * d2.nH2 * d2.nB2, ch.sv.base.red, nr, ni);
-        const double nl = logL + l1 + l2 + ch.sv.logR[c + 2];
-        acc = (log(u) + log_abs2(dr, di, dl)) < log_abs2(nr, ni, nl) ||
-              (u == 0.0 && (nr != 0.0 || ni != 0.0));
+        const int ne = eL + l1 + l2 + ch.sv.logR[c + 2];
+        acc = ch.metro_accept(u, dr, di, de, nr, ni, ne);
         if (threadIdx.x == 0) { ch.sv.n_prop += 1; if (acc) ch.sv.n_acc += 1; }
         if (acc) {
           copy_box(ch.box(c, r), ch.prop(0), D4);
           copy_box(ch.box(c + 1, r), ch.prop(1), D4);
-          dr = nr; di = ni; dl = nl;
+          dr = nr; di = ni; de = ne;
         } else {
           ch.hop_apply(c, r, 1);
         }
@@ -407,9 +451,9 @@ __device__ __noinline__ void hhop_pass(Chain<T>& ch, int w) {
       const int n1 = d1.nA2 * d1.nH2 * d1.nB2;
       if (acc) {
         for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
-        logL += l1;
+        eL += l1;
       } else {
-        logL += ch.row_step_left(r, c, Lc, ch.box(c, r), X1);
+        eL += ch.row_step_left(r, c, Lc, ch.box(c, r), X1);
         for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
       }
       __syncthreads();
@@ -421,38 +465,40 @@ __device__ __noinline__ void hhop_pass(Chain<T>& ch, int w) {
 // vertical-hop pass (matter), bottom-up with strip environments
 template <class T>
 __device__ __noinline__ void vhop_pass(Chain<T>& ch, int w) {
+  using R = typename Traits<T>::R;
   const KParams<T>& k = ch.k;
   const int Lx = k.Lx, Ly = k.Ly, D4 = k.Dk * k.Dk * k.Dk * k.Dk;
   T* Lc = ch.envL;
   T* X1 = ch.envX;
+  T* Lnext = ch.envY;
   for (int r = 0; r < Ly - 1; ++r) {
-    double dr, di, dl;
-    ch.strip_right_envs(r, dr, di, dl);
+    R dr, di;
+    int de;
+    ch.strip_right_envs(r, dr, di, de);
     if (threadIdx.x == 0) Lc[0] = one<T>();
     __syncthreads();
-    double logL = 0.0;
+    int eL = 0;
     for (int c = 0; c < Lx; ++c) {
       const unsigned long long ctr =
           (unsigned long long)w * k.n_slots + 2 * k.n_plaq + k.n_h + r * Lx + c;
       const double u = ch.uniform_at(ctr);
       bool acc = false;
-      double l1 = 0.0;
+      int l1 = 0;
       if (ch.hop_apply(c, r, 2)) {
         ch.gather_into(c, r, ch.prop(0));
         ch.gather_into(c, r + 1, ch.prop(2));
         __syncthreads();
         l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
-        double nr, ni;
+        R nr, ni;
         const SDims d1 = ch.sdims(r, c);
         cta_dot(X1, ch.envR(c + 1), ch.env_size(d1, true), ch.sv.base.red, nr, ni);
-        const double nl = logL + l1 + ch.sv.logR[c + 1];
-        acc = (log(u) + log_abs2(dr, di, dl)) < log_abs2(nr, ni, nl) ||
-              (u == 0.0 && (nr != 0.0 || ni != 0.0));
+        const int ne = eL + l1 + ch.sv.logR[c + 1];
+        acc = ch.metro_accept(u, dr, di, de, nr, ni, ne);
         if (threadIdx.x == 0) { ch.sv.n_prop += 1; if (acc) ch.sv.n_acc += 1; }
         if (acc) {
           copy_box(ch.box(c, r), ch.prop(0), D4);
           copy_box(ch.box(c, r + 1), ch.prop(2), D4);
-          dr = nr; di = ni; dl = nl;
+          dr = nr; di = ni; de = ne;
         } else {
           ch.hop_apply(c, r, 2);
         }
@@ -460,12 +506,11 @@ __device__ __noinline__ void vhop_pass(Chain<T>& ch, int w) {
       __syncthreads();
       const SDims d1 = ch.sdims(r, c);
       const int n1 = ch.env_size(d1, true);
-      T* Lnext = ch.envY;
       if (acc) {
         for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
-        logL += l1;
+        eL += l1;
       } else {
-        logL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), Lnext);
+        eL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), Lnext);
         for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = Lnext[i];
       }
       __syncthreads();
@@ -477,6 +522,7 @@ __device__ __noinline__ void vhop_pass(Chain<T>& ch, int w) {
 // measurement pass, top-down; writes sample s
 template <class T>
 __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
+  using R = typename Traits<T>::R;
   const KParams<T>& k = ch.k;
   const int Lx = k.Lx, Ly = k.Ly, Dk = k.Dk, D4 = Dk * Dk * Dk * Dk;
   const bool want_e = (k.want & WANT_ELOC) && k.e_loc;
@@ -488,28 +534,31 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
     // ---- row r: gradient, horizontal hops, amplitude
     const bool need_row = want_g || (r == Ly - 1 && want_a) || (want_e && k.matter && k.J != 0.0);
     if (need_row) {
-      double dr, di, dl;
-      ch.row_right_envs(r, dr, di, dl);
+      R dr, di;
+      int de;
+      ch.row_right_envs(r, dr, di, de);
       if (r == Ly - 1 && want_a && threadIdx.x == 0) {
-        const double a2 = dr * dr + di * di;
-        const double la = (a2 > 0.0) ? ch.sv.logB[Ly - 1] + dl + 0.5 * log(a2) : -INFINITY;
+        // psi = <B[Ly-2] | row Ly-1> = (dr + i di) 2^(de + e_B)
+        const double a2 = (double)dr * dr + (double)di * di;
+        const double ln2 = 0.69314718055994530942;
+        const double la = (a2 > 0.0) ? (double)(ch.sv.logB[Ly - 1] + de) * ln2 + 0.5 * log(a2) : -INFINITY;
         if (k.log_abs) k.log_abs[s] = la;
-        if (k.phase) k.phase[s] = (a2 > 0.0) ? atan2(di, dr) : 0.0;
+        if (k.phase) k.phase[s] = (a2 > 0.0) ? atan2((double)di, (double)dr) : 0.0;
       }
       T* Lc = ch.env3L;
       T* X1 = ch.env3X;
       T* X2 = ch.env3Y;
       if (threadIdx.x == 0) Lc[0] = one<T>();
       __syncthreads();
-      double logL = 0.0;
-      const double den2 = dr * dr + di * di;
+      int eL = 0;
+      const R den2 = dr * dr + di * di;
       for (int c = 0; c < Lx; ++c) {
         const RDims d = ch.rdims(r, c);
         if (want_g) {
           T* G = ch.ws + k.o_G;
-          ch.ropen(d, Lc, ch.Bslot(r) + ch.sv.offB[c], ch.Tslot(r + 1) + ch.sv.offT[c], ch.env3R(c + 1), G);
-          // O = G * exp(logL + logR[c+1] - dl) / (dr + i di)
-          const double f = exp(logL + ch.sv.logR[c + 1] - dl) / den2;
+          ch.ropen(d, Lc, ch.curB + ch.sv.offB[c], ch.curT + ch.sv.offT[c], ch.env3R(c + 1), G);
+          // O = G 2^(eL + eR[c+1] - de) / (dr + i di)
+          const R f = pow2r<R>(eL + ch.sv.logR[c + 1] - de) / den2;
           const T fac = make_scalar<T>(dr * f, -di * f);
           const int v = r * Lx + c;
           const int n = d.nH * d.nH2 * d.pB * d.pT;
@@ -524,19 +573,17 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
             ch.gather_into(c, r, ch.prop(0));
             ch.gather_into(c + 1, r, ch.prop(1));
             __syncthreads();
-            const double l1 = ch.row_step_left(r, c, Lc, ch.prop(0), X1);
-            const double l2 = ch.row_step_left(r, c + 1, X1, ch.prop(1), X2);
-            double nr, ni;
+            const int l1 = ch.row_step_left(r, c, Lc, ch.prop(0), X1);
+            const int l2 = ch.row_step_left(r, c + 1, X1, ch.prop(1), X2);
+            R nr, ni;
             const RDims d2 = ch.rdims(r, c + 1);
             cta_dot(X2, ch.env3R(c + 2), d2.nA2 * d2.nH2 * d2.nB2, ch.sv.base.red, nr, ni);
-            double rr, ri;
-            ratio_of(nr, ni, logL + l1 + l2 + ch.sv.logR[c + 2], dr, di, dl, rr, ri);
-            if (threadIdx.x == 0) { ch.sv.eacc[0] += k.J * rr; ch.sv.eacc[1] += k.J * ri; }
+            ch.add_ratio(k.J, nr, ni, eL + l1 + l2 + ch.sv.logR[c + 2], dr, di, de);
             ch.hop_apply(c, r, 1);
           }
         }
         if (c < Lx - 1) {
-          logL += ch.row_step_left(r, c, Lc, ch.box(c, r), X1);
+          eL += ch.row_step_left(r, c, Lc, ch.box(c, r), X1);
           const int n1 = d.nA2 * d.nH2 * d.nB2;
           for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
           __syncthreads();
@@ -545,14 +592,15 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
     }
     // ---- strip (r, r+1): plaquettes and vertical hops
     if (want_e && r <= Ly - 2) {
-      double dr, di, dl;
-      ch.strip_right_envs(r, dr, di, dl);
+      R dr, di;
+      int de;
+      ch.strip_right_envs(r, dr, di, de);
       T* Lc = ch.envL;
       T* X1 = ch.envX;
       T* X2 = ch.envY;
       if (threadIdx.x == 0) Lc[0] = one<T>();
       __syncthreads();
-      double logL = 0.0;
+      int eL = 0;
       const int npow = k.N == 2 ? 1 : 2;
       const double amp = k.N == 2 ? -2.0 * k.h : -k.h;
       for (int c = 0; c < Lx; ++c) {
@@ -565,14 +613,12 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
             ch.gather_into(c, r + 1, ch.prop(2));
             ch.gather_into(c + 1, r + 1, ch.prop(3));
             __syncthreads();
-            const double l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
-            const double l2 = ch.strip_step_left(r, c + 1, X1, ch.prop(1), ch.prop(3), X2);
-            double nr, ni;
+            const int l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
+            const int l2 = ch.strip_step_left(r, c + 1, X1, ch.prop(1), ch.prop(3), X2);
+            R nr, ni;
             const SDims d2 = ch.sdims(r, c + 1);
             cta_dot(X2, ch.envR(c + 2), ch.env_size(d2, true), ch.sv.base.red, nr, ni);
-            double rr, ri;
-            ratio_of(nr, ni, logL + l1 + l2 + ch.sv.logR[c + 2], dr, di, dl, rr, ri);
-            if (threadIdx.x == 0) { ch.sv.eacc[0] += amp * rr; ch.sv.eacc[1] += amp * ri; }
+            ch.add_ratio(amp, nr, ni, eL + l1 + l2 + ch.sv.logR[c + 2], dr, di, de);
             ch.plaq_apply(c, r, k.N - t);
           }
         }
@@ -581,19 +627,17 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
             ch.gather_into(c, r, ch.prop(0));
             ch.gather_into(c, r + 1, ch.prop(2));
             __syncthreads();
-            const double l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
-            double nr, ni;
+            const int l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
+            R nr, ni;
             const SDims d1 = ch.sdims(r, c);
             cta_dot(X1, ch.envR(c + 1), ch.env_size(d1, true), ch.sv.base.red, nr, ni);
-            double rr, ri;
-            ratio_of(nr, ni, logL + l1 + ch.sv.logR[c + 1], dr, di, dl, rr, ri);
-            if (threadIdx.x == 0) { ch.sv.eacc[0] += k.J * rr; ch.sv.eacc[1] += k.J * ri; }
+            ch.add_ratio(k.J, nr, ni, eL + l1 + ch.sv.logR[c + 1], dr, di, de);
             ch.hop_apply(c, r, 2);
           }
         }
         if (c < Lx - 1) {
           const SDims d1 = ch.sdims(r, c);
-          logL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), X1);
+          eL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), X1);
           const int n1 = ch.env_size(d1, true);
           for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
           __syncthreads();
@@ -604,10 +648,9 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
     if (r >= 1 && (k.mode == 1 || want_e || want_g)) ch.absorb_T(r);
   }
   if (want_e && threadIdx.x == 0) {
-    // diagonal part: g sum_links (2 - 2 cos(2 pi n / N)) + m sum_x p_x
+    // diagonal part: g sum_links (2 - 2 cos(2 pi n / N)) (table) + m sum_x p_x
     double e = 0.0;
-    const double w0 = 2.0 * 3.14159265358979323846 / k.N;
-    for (int i = 0; i < k.n_h + k.n_v; ++i) e += k.g * (2.0 - 2.0 * cos(w0 * ch.cfg[i]));
+    for (int i = 0; i < k.n_h + k.n_v; ++i) e += k.elink[ch.cfg[i]];
     if (k.matter)
       for (int i = 0; i < k.n_s; ++i) e += k.m * ch.cfg[k.n_h + k.n_v + i];
     k.e_loc[2 * s] = e + ch.sv.eacc[0];
@@ -637,7 +680,7 @@ __global__ void __launch_bounds__(256, 2) vmc_kernel(KParams<T> k) {
     int8_t* gcfg = k.configs + (long long)chain * k.cfg_len;
     for (int i = threadIdx.x; i < k.cfg_len; i += blockDim.x) dyn_cfg[i] = gcfg[i];
     if (threadIdx.x == 0) {
-      sv.logB[0] = 0.0; sv.logT[k.Ly] = 0.0; sv.n_acc = 0; sv.n_prop = 0;
+      sv.logB[0] = 0; sv.logT[k.Ly] = 0; sv.n_acc = 0; sv.n_prop = 0;
     }
     __syncthreads();
     Chain<T> ch(k, ws, sv, dyn_cfg, chain, hot);
