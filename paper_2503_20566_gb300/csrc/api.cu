@@ -462,12 +462,31 @@ gcf_status ensure_sr(gcf_ctx* c, long long Ns, int n_chains) {
     if (cudaMalloc(&c->sr.tbar, sizeof(cdouble)) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR");
     if (cudaMalloc(&c->sr.scal, 32 * sizeof(double)) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR");
   }
+  if (!c->sr.seg) {
+    int maxnb = 1;
+    for (int v = 0; v < c->n_s; ++v) maxnb = std::max(maxnb, c->vnb[v]);
+    std::vector<int> sv, sb;
+    for (int v = 0; v < c->n_s; ++v)
+      for (int b = 0; b < c->vnb[v]; ++b) { sv.push_back(v); sb.push_back(b); }
+    c->sr.maxnb = maxnb;
+    c->sr.n_seg = (int)sv.size();
+    if (cudaMalloc(&c->sr.seg, sizeof(int) * ((size_t)c->n_s * (maxnb + 1) + 1)) != cudaSuccess ||
+        cudaMalloc(&c->sr.seg_v, sizeof(int) * sv.size()) != cudaSuccess ||
+        cudaMalloc(&c->sr.seg_b, sizeof(int) * sb.size()) != cudaSuccess)
+      return fail(c, GCF_ENOMEM, "SR segment tables");
+    if (cudaMemcpy(c->sr.seg_v, sv.data(), sizeof(int) * sv.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->sr.seg_b, sb.data(), sizeof(int) * sb.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(c, GCF_ECUDA, "SR segment tables");
+  }
   if (Ns > c->sr_ns_cap) {
     if (c->sr.t) cudaFree(c->sr.t);
     if (c->sr.coef) cudaFree(c->sr.coef);
+    if (c->sr.perm) cudaFree(c->sr.perm);
     c->sr.t = c->sr.coef = nullptr;
+    c->sr.perm = nullptr;
     if (cudaMalloc(&c->sr.t, sizeof(cdouble) * Ns) != cudaSuccess ||
-        cudaMalloc(&c->sr.coef, sizeof(cdouble) * Ns) != cudaSuccess)
+        cudaMalloc(&c->sr.coef, sizeof(cdouble) * Ns) != cudaSuccess ||
+        cudaMalloc(&c->sr.perm, sizeof(int) * Ns * c->n_s) != cudaSuccess)
       return fail(c, GCF_ENOMEM, "SR sample vectors");
     c->sr_ns_cap = Ns;
   }
@@ -565,7 +584,8 @@ void gcf_destroy(gcf_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->d_params, c->d_Q, c->d_voff, c->d_vbs, c->d_vnb, c->d_tables, c->d_status,
                   c->d_scratch, c->sr.obar, c->sr.F, c->sr.x, c->sr.r, c->sr.p, c->sr.Ap,
-                  c->sr.t, c->sr.coef, c->sr.chain_mean, c->sr.tbar, c->sr.scal, c->d_cfg, c->d_e,
+                  c->sr.t, c->sr.coef, c->sr.chain_mean, c->sr.tbar, c->sr.scal, c->sr.perm, c->sr.seg,
+                  c->sr.seg_v, c->sr.seg_b, c->d_cfg, c->d_e,
                   c->d_la, c->d_ph, c->d_bid, c->d_O, c->d_acc};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -180,6 +180,152 @@ __global__ void k_update(T* params, const cdouble* x, double cr, double ci, long
   params[k] = make_scalar<T>((double)re(v) + dr, (double)im(v) + di);
 }
 
+// ---------------------------------------------------------------------------
+// Sample order grouped by (vertex, block): for every vertex a stable counting
+// sort of the samples by the block they select.  seg[v * (maxnb + 1) + b] is
+// the start of block b of vertex v inside perm[v * Ns ...]; built once per SR
+// step (block ids do not change during the solve).  One CTA per vertex.
+// ---------------------------------------------------------------------------
+__global__ void k_sort_by_block(SrGeom g, const int* bids, int maxnb, int* perm, int* seg) {
+  __shared__ int wsum[32];
+  __shared__ int base_s;
+  const int v = blockIdx.x;
+  const int nb = g.vnb[v];
+  const long long Ns = g.Ns;
+  int* pv = perm + (long long)v * Ns;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) base_s = 0;
+  __syncthreads();
+  for (int b = 0; b < nb; ++b) {
+    if (threadIdx.x == 0) seg[v * (maxnb + 1) + b] = base_s;
+    __syncthreads();
+    for (long long s0 = 0; s0 < Ns; s0 += blockDim.x) {
+      const long long s = s0 + threadIdx.x;
+      const int hit = (s < Ns && bids[s * g.n_s + v] == b) ? 1 : 0;
+      // block-wide exclusive scan of hit (stable order)
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      const int before = __popc(m & ((1u << lane) - 1u));
+      if (lane == 0) wsum[wid] = __popc(m);
+      __syncthreads();
+      int off = 0, tot = 0;
+      for (int w = 0; w < nw; ++w) {
+        if (w < wid) off += wsum[w];
+        tot += wsum[w];
+      }
+      if (hit) pv[base_s + off + before] = (int)s;
+      __syncthreads();
+      if (threadIdx.x == 0) base_s += tot;
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) seg[v * (maxnb + 1) + nb] = base_s;
+}
+
+// storage-precision accumulator type: FP32 forms accumulate short partial
+// sums in float before adding them into FP64
+template <class T> struct PartialOf { using type = double; };
+template <> struct PartialOf<float> { using type = float; };
+template <> struct PartialOf<cfloat> { using type = float; };
+
+// t_s = sum_v sum_e O[s][v][e] x[off(v, bid) + e]: one warp per sample, lanes
+// over vertices; the per-vertex block dot in the storage precision, the sum
+// over vertices in FP64.  CPLX selects complex arithmetic.
+template <class T, bool CPLX>
+__global__ void k_gather2(SrGeom g, const int* bids, const T* O, const cdouble* x, cdouble* t) {
+  using P = typename PartialOf<T>::type;
+  const int lane = threadIdx.x & 31;
+  const long long s = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (s >= g.Ns) return;
+  double ar = 0.0, ai = 0.0;
+  for (int v = lane; v < g.n_s; v += 32) {
+    const int bid = bids[s * g.n_s + v];
+    const int bs = g.vbs[v];
+    const cdouble* xb = x + g.voff[v] + (long long)bid * bs;
+    const T* o = O + (s * g.n_s + v) * (long long)g.D4;
+    P pr = P(0), pi = P(0);
+#pragma unroll 4
+    for (int e = 0; e < bs; ++e) {
+      const T ov = o[e];
+      const cdouble xv = xb[e];
+      if (CPLX) {
+        pr += (P)re(ov) * (P)xv.x - (P)im(ov) * (P)xv.y;
+        pi += (P)re(ov) * (P)xv.y + (P)im(ov) * (P)xv.x;
+      } else {
+        pr += (P)re(ov) * (P)xv.x;
+      }
+    }
+    ar += (double)pr;
+    if (CPLX) ai += (double)pi;
+  }
+  ar = warp_sum(ar);
+  if (CPLX) ai = warp_sum(ai);
+  if (lane == 0) t[s] = {ar, CPLX ? ai : 0.0};
+}
+
+// out[off(v, b) + e] += sum_{s in segment (v, b)} coef_s op(O[s][v][e]),
+// op = conj if CONJ.  Grid = segments x split: CTA (segment, part) takes one
+// contiguous part of its segment; threads = streams x entries; each stream
+// sums chunks of 32 samples in the storage precision, then FP64; parts are
+// combined with FP64 atomics (split x block-size of them per segment).
+template <class T, bool CONJ, bool CPLX>
+__global__ void k_scatter2(SrGeom g, const int* perm, const int* seg, int maxnb, int split, const T* O,
+                           const cdouble* coef, cdouble* out, const int* seg_v, const int* seg_b) {
+  using P = typename PartialOf<T>::type;
+  __shared__ double red[2 * 256];
+  const int sid = blockIdx.x / split, part = blockIdx.x - (blockIdx.x / split) * split;
+  const int v = seg_v[sid], b = seg_b[sid];
+  const int bs = g.vbs[v];
+  const int seg0 = seg[v * (maxnb + 1) + b], seg1 = seg[v * (maxnb + 1) + b + 1];
+  const int len = seg1 - seg0;
+  const int per = (len + split - 1) / split;
+  const int s_begin = seg0 + part * per, s_end = min(seg1, s_begin + per);
+  if (s_begin >= s_end) return;
+  const int* pv = perm + (long long)v * g.Ns;
+  const int streams = max(1, (int)blockDim.x / bs);
+  const int e = threadIdx.x % bs;
+  const int st = threadIdx.x / bs;
+  double ar = 0.0, ai = 0.0;
+  if (st < streams) {
+    int cnt = 0;
+    P pr = P(0), pi = P(0);
+#pragma unroll 4
+    for (int q = s_begin + st; q < s_end; q += streams) {
+      const long long s = pv[q];
+      const T ov = O[(s * g.n_s + v) * (long long)g.D4 + e];
+      const cdouble c = coef[s];
+      const P orr = (P)re(ov), oi = CONJ ? -(P)im(ov) : (P)im(ov);
+      if (CPLX) {
+        pr += (P)c.x * orr - (P)c.y * oi;
+        pi += (P)c.x * oi + (P)c.y * orr;
+      } else {
+        pr += (P)c.x * orr;
+      }
+      if (++cnt == 32) {
+        ar += (double)pr;
+        ai += (double)pi;
+        pr = P(0);
+        pi = P(0);
+        cnt = 0;
+      }
+    }
+    ar += (double)pr;
+    ai += (double)pi;
+  }
+  red[threadIdx.x] = ar;
+  red[256 + threadIdx.x] = ai;
+  __syncthreads();
+  if (threadIdx.x < bs) {
+    double sr = 0.0, si = 0.0;
+    for (int q = 0; q < streams; ++q) {
+      sr += red[q * bs + threadIdx.x];
+      si += red[256 + q * bs + threadIdx.x];
+    }
+    cdouble* dst = out + g.voff[v] + (long long)b * bs + threadIdx.x;
+    atomicAdd(&dst->x, sr);
+    if (CPLX) atomicAdd(&dst->y, si);
+  }
+}
+
 __global__ void k_fill_c(cdouble* v, long long n, double r, double i) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) v[k] = {r, i};
@@ -198,15 +344,15 @@ __global__ void k_copy_scalar(double* sc) { sc[0] = sc[4]; sc[1] = sc[5]; }
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
 template <class T>
-static cudaError_t scatter(const SrGeom& g, const int* bids, const T* O, const cdouble* coef,
+static cudaError_t scatter(const SrGeom& g, const SrWork& w, const T* O, const cdouble* coef,
                            cdouble* out, bool conj, cudaStream_t st, long long* launches) {
-  const int chunk = 4096;
-  dim3 grid((unsigned)((g.Ns + chunk - 1) / chunk), (unsigned)g.n_s);
-  const size_t smem = 2 * sizeof(double) * (size_t)g.max_nb_bs;
+  constexpr bool C = Traits<T>::cplx;
+  const int split = (int)std::max<long long>(1, std::min<long long>(512, g.Ns / 1024));
+  const unsigned grid = (unsigned)(w.n_seg * split);
   if (conj)
-    k_scatter<T, true><<<grid, 256, smem, st>>>(g, bids, O, coef, out, chunk);
+    k_scatter2<T, true, C><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, O, coef, out, w.seg_v, w.seg_b);
   else
-    k_scatter<T, false><<<grid, 256, smem, st>>>(g, bids, O, coef, out, chunk);
+    k_scatter2<T, false, C><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, O, coef, out, w.seg_v, w.seg_b);
   ++*launches;
   return cudaGetLastError();
 }
@@ -246,16 +392,19 @@ cudaError_t sr_solve_update(const SrGeom& g, SrWork& w, const double* e_loc, con
   }
   ++*launches;
   CK(cudaGetLastError());
+  // samples grouped by (vertex, block) for the atomic-free scatter
+  k_sort_by_block<<<g.n_s, 1024, 0, st>>>(g, bids, w.maxnb, w.perm, w.seg);
+  ++*launches;
   // Obar = (1/Ns) sum_s O_s
   CK(cudaMemsetAsync(w.obar, 0, sizeof(cdouble) * Np, st));
   k_fill_c<<<nblk(Ns, 256), 256, 0, st>>>(w.coef, Ns, 1.0 / (double)Ns, 0.0);
   ++*launches;
-  CK(scatter<T>(g, bids, O, w.coef, w.obar, false, st, launches));
+  CK(scatter<T>(g, w, O, w.coef, w.obar, false, st, launches));
   // F = (1/Ns) sum_s conj(O_s) (E_s - Ebar)
   k_f_coef<<<nblk(Ns, 256), 256, 0, st>>>(e_loc, Ns, w.scal, w.coef);
   ++*launches;
   CK(cudaMemsetAsync(w.F, 0, sizeof(cdouble) * Np, st));
-  CK(scatter<T>(g, bids, O, w.coef, w.F, true, st, launches));
+  CK(scatter<T>(g, w, O, w.coef, w.F, true, st, launches));
   // CG: x = 0, r = p = F
   CK(cudaMemsetAsync(w.x, 0, sizeof(cdouble) * Np, st));
   CK(cudaMemcpyAsync(w.r, w.F, sizeof(cdouble) * Np, cudaMemcpyDeviceToDevice, st));
@@ -274,14 +423,14 @@ cudaError_t sr_solve_update(const SrGeom& g, SrWork& w, const double* e_loc, con
   bool converged = !(fnorm > 0.0);
   while (!converged && it < max_iter) {
     // Ap = S p + shift p
-    k_gather_dot<T><<<nblk(Ns * 32, 256), 256, 0, st>>>(g, bids, O, w.p, w.t);
+    k_gather2<T, Traits<T>::cplx><<<nblk(Ns * 32, 256), 256, 0, st>>>(g, bids, O, w.p, w.t);
     ++*launches;
     k_sum_c<<<1, 1024, 0, st>>>(w.t, Ns, w.tbar, 1.0 / (double)Ns);
     ++*launches;
     k_center<<<nblk(Ns, 256), 256, 0, st>>>(w.t, Ns, w.tbar);
     ++*launches;
     CK(cudaMemsetAsync(w.Ap, 0, sizeof(cdouble) * Np, st));
-    CK(scatter<T>(g, bids, O, w.t, w.Ap, true, st, launches));
+    CK(scatter<T>(g, w, O, w.t, w.Ap, true, st, launches));
     k_axpy_real<<<nblk(Np, 256), 256, 0, st>>>(w.Ap, w.p, shift, Np);
     ++*launches;
     CK(dot<T>(w.p, w.Ap, Np, sc + 2, st, launches));

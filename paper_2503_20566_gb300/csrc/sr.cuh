@@ -24,6 +24,12 @@ struct SrWork {
   cdouble *chain_mean;                 // [n_chains]
   cdouble *tbar;                       // [1]
   double* scal;                        // [16] device scalars
+  // sample order grouped by (vertex, block)
+  int* perm;      // [n_s * Ns]
+  int* seg;       // [n_s * (maxnb + 1)]
+  int* seg_v;     // [n_seg] vertex of segment
+  int* seg_b;     // [n_seg] block of segment
+  int maxnb, n_seg;
 };
 
 // Computes <E>, F, solves (S + shift) x = F by CG, then params += (cr + i ci) x.
