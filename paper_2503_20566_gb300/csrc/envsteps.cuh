@@ -42,6 +42,7 @@ __device__ __forceinline__ float gemm_tiles(int M, int N, int K, const T* __rest
     const T* b = B + n0 * sBn;
     const bool full = (m0 + TM <= M) && (n0 + TN <= N);
     if (full) {
+#pragma unroll 4
       for (int k = 0; k < K; ++k) {
         T av[TM], bv[TN];
 #pragma unroll

@@ -127,6 +127,50 @@ struct Chain {
     gather_box(k, x, y, bid, dst);
   }
 
+  // gather the selected blocks of n vertices (x[i], y[i]) into dst[i] in
+  // parallel (thread groups per vertex); caller synchronises
+  __device__ __noinline__ void gather_n(int n, const int* xs, const int* ys, T* const* dst) {
+    const int D4 = k.Dk * k.Dk * k.Dk * k.Dk;
+    const int per = blockDim.x / n;
+    const int g = threadIdx.x / per, tl = threadIdx.x - g * per;
+    if (g < n) {
+      const int x = xs[g], y = ys[g];
+      const int bid = block_of(k, cfg, x, y);
+      if (bid < 0) {
+        if (tl == 0) atomicAdd(&k.status[ST_GAUSS], 1);
+      } else {
+        const int Dk = k.Dk;
+        const int dl = hl_dim(x, Dk), dr = hr_dim(x, k.Lx, Dk), dd = dn_dim(y, Dk),
+                  du = up_dim(y, k.Ly, Dk);
+        const int v = y * k.Lx + x;
+        const T* src = k.params + k.voff[v] + (long long)bid * k.vbs[v];
+        const int bs = dl * dr * dd * du;
+        T* box = dst[g];
+        for (int e = tl; e < bs; e += per) {
+          int t = e;
+          const int iu = t % du; t /= du;
+          const int id = t % dd; t /= dd;
+          const int ir = t % dr; t /= dr;
+          const int il = t;
+          box[((il * Dk + ir) * Dk + id) * Dk + iu] = src[e];
+        }
+      }
+    }
+    (void)D4;
+  }
+  __device__ void gather_plaq(int c, int r) {
+    const int xs[4] = {c, c + 1, c, c + 1};
+    const int ys[4] = {r, r, r + 1, r + 1};
+    T* const dst[4] = {prop(0), prop(1), prop(2), prop(3)};
+    gather_n(4, xs, ys, dst);
+  }
+  __device__ void gather_pair(int x0, int y0, T* d0, int x1, int y1, T* d1) {
+    const int xs[2] = {x0, x1};
+    const int ys[2] = {y0, y1};
+    T* const dst[2] = {d0, d1};
+    gather_n(2, xs, ys, dst);
+  }
+
   __device__ __noinline__ bool check_and_gather_all() {
     __shared__ int bad;
     if (threadIdx.x == 0) bad = 0;
@@ -369,10 +413,7 @@ __device__ __noinline__ void plaquette_pass(Chain<T>& ch, int w) {
       const int t = ch.power_at(base + 2 * j);
       const double u = ch.uniform_at(base + 2 * j + 1);
       ch.plaq_apply(c, r, t);
-      ch.gather_into(c, r, ch.prop(0));
-      ch.gather_into(c + 1, r, ch.prop(1));
-      ch.gather_into(c, r + 1, ch.prop(2));
-      ch.gather_into(c + 1, r + 1, ch.prop(3));
+      ch.gather_plaq(c, r);
       __syncthreads();
       const int l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
       const int l2 = ch.strip_step_left(r, c + 1, X1, ch.prop(1), ch.prop(3), X2);
@@ -427,8 +468,7 @@ __device__ __noinline__ void hhop_pass(Chain<T>& ch, int w) {
       bool acc = false;
       int l1 = 0;
       if (ch.hop_apply(c, r, 1)) {
-        ch.gather_into(c, r, ch.prop(0));
-        ch.gather_into(c + 1, r, ch.prop(1));
+        ch.gather_pair(c, r, ch.prop(0), c + 1, r, ch.prop(1));
         __syncthreads();
         l1 = ch.row_step_left(r, c, Lc, ch.prop(0), X1);
         const int l2 = ch.row_step_left(r, c + 1, X1, ch.prop(1), X2);
@@ -485,8 +525,7 @@ __device__ __noinline__ void vhop_pass(Chain<T>& ch, int w) {
       bool acc = false;
       int l1 = 0;
       if (ch.hop_apply(c, r, 2)) {
-        ch.gather_into(c, r, ch.prop(0));
-        ch.gather_into(c, r + 1, ch.prop(2));
+        ch.gather_pair(c, r, ch.prop(0), c, r + 1, ch.prop(2));
         __syncthreads();
         l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
         R nr, ni;
@@ -570,8 +609,7 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
         }
         if (want_e && k.matter && k.J != 0.0 && c < Lx - 1) {
           if (ch.hop_apply(c, r, 1)) {
-            ch.gather_into(c, r, ch.prop(0));
-            ch.gather_into(c + 1, r, ch.prop(1));
+            ch.gather_pair(c, r, ch.prop(0), c + 1, r, ch.prop(1));
             __syncthreads();
             const int l1 = ch.row_step_left(r, c, Lc, ch.prop(0), X1);
             const int l2 = ch.row_step_left(r, c + 1, X1, ch.prop(1), X2);
@@ -608,10 +646,7 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
           for (int q = 0; q < npow; ++q) {
             const int t = q == 0 ? 1 : k.N - 1;
             ch.plaq_apply(c, r, t);
-            ch.gather_into(c, r, ch.prop(0));
-            ch.gather_into(c + 1, r, ch.prop(1));
-            ch.gather_into(c, r + 1, ch.prop(2));
-            ch.gather_into(c + 1, r + 1, ch.prop(3));
+            ch.gather_plaq(c, r);
             __syncthreads();
             const int l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
             const int l2 = ch.strip_step_left(r, c + 1, X1, ch.prop(1), ch.prop(3), X2);
@@ -624,8 +659,7 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
         }
         if (k.matter && k.J != 0.0) {
           if (ch.hop_apply(c, r, 2)) {
-            ch.gather_into(c, r, ch.prop(0));
-            ch.gather_into(c, r + 1, ch.prop(2));
+            ch.gather_pair(c, r, ch.prop(0), c, r + 1, ch.prop(2));
             __syncthreads();
             const int l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
             R nr, ni;
