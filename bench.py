@@ -233,6 +233,7 @@ def main():
     n_chains, n_sweeps = args.chains, args.sweeps
     ctx = G.Context(w["N"], w["Lx"], w["Ly"], w["D"], w["chi"], h=w["h_p"], g=w["g"], precision=args.precision,
                     seed=2 + 1000 * rank)
+    kernel_name = ctx.kernel_name + "<float>"
     powers = torch.from_numpy(synth.plaquette_powers(102 + rank, n_chains, (w["Lx"] - 1) * (w["Ly"] - 1), w["N"]))
     configs = ctx.init_configs(n_chains, powers=powers)
     samples = ctx.alloc_samples(n_chains, n_sweeps, grad=True)
@@ -317,7 +318,7 @@ def main():
             "sr_ms": float(np.mean([a - b for a, b in zip(t_steps, t_kernel)])),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": profiled_traffic(samples_per_step),
-                         "kernel": "gcf::vmc_kernel<float>",
+                         "kernel": kernel_name,
                          "algorithmic_flop_per_launch": fl,
                          "peak_source": "FP32 FMA units x max SM clock (152 x 128 x 2 x 2070 MHz)",
                          "tensor_peak_tf32_of_" + src: peaks.get("bf16_tflops", 0) / 2.0},

@@ -230,6 +230,14 @@ gcf_status gcf_amplitude_noalloc(gcf_ctx* ctx, int n, const int8_t* configs, dou
  * accounting in benchmarks). */
 int64_t gcf_launch_count(const gcf_ctx* ctx);
 
+/* Form of the sampling / measurement kernel this context launches (an
+ * implementation choice; the paper has no counterpart): 0 = one chain per
+ * CTA of 256 threads (gcf::vmc_kernel), 1 = two chains per CTA on groups of
+ * 128 threads (gcf::vmc_kernel_grouped).  Chosen at context creation from
+ * the shared-memory footprint; GCFVMC_EXEC=cta|group in the environment
+ * forces one.  Both compute the same results. */
+int gcf_executor(const gcf_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

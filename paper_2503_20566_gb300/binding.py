@@ -63,6 +63,7 @@ def load_library(path: str = LIB_PATH):
         "gcf_config_len": (i, [vp]),
         "gcf_scalar_bytes": (i, [vp]),
         "gcf_launch_count": (i64, [vp]),
+        "gcf_executor": (i, [vp]),
         "gcf_set_tensors": (i, [vp, vp, C.c_size_t]),
         "gcf_get_tensors": (i, [vp, vp, C.c_size_t]),
         "gcf_init_configs": (i, [vp, i, vp, vp, vp]),
@@ -84,7 +85,7 @@ def load_library(path: str = LIB_PATH):
 def exported_symbols():
     """Names the binding expects the library to export."""
     return ["gcf_init_peps", "gcf_destroy", "gcf_last_error", "gcf_num_params", "gcf_config_len",
-            "gcf_scalar_bytes", "gcf_launch_count", "gcf_set_tensors", "gcf_get_tensors",
+            "gcf_scalar_bytes", "gcf_launch_count", "gcf_executor", "gcf_set_tensors", "gcf_get_tensors",
             "gcf_init_configs", "gcf_amplitude", "gcf_local_energy", "gcf_log_grad",
             "gcf_sample_batch", "gcf_sr_step", "gcf_vmc_step_host"]
 
@@ -153,6 +154,11 @@ class Context:
     @property
     def launch_count(self):
         return int(self.lib.gcf_launch_count(self.ctx))
+
+    @property
+    def kernel_name(self):
+        """Name of the sampling / measurement kernel this context launches."""
+        return "gcf::vmc_kernel_grouped" if self.lib.gcf_executor(self.ctx) == 1 else "gcf::vmc_kernel"
 
     # ---- parameters -------------------------------------------------------
     def set_tensors(self, values):

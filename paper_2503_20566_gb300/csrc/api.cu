@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -38,6 +39,11 @@ struct Plan {
   long long so_net, so_prop, so_cop, so_envL, so_envX, so_envY, so_env3L, so_env3X, so_env3Y, so_t1,
       so_t2, hot_elems = 0, cfg_bytes = 0;
   size_t dyn_smem = 0;
+  // grouped kernel: hot buffers (without the right environments) per chain
+  // group in shared memory when group_hot_in_smem
+  long long hot_base_elems = 0;
+  int group_hot_in_smem = 0;
+  size_t group_smem = 0;
 };
 
 }  // namespace
@@ -54,6 +60,7 @@ struct gcf_ctx {
   cudaStream_t stream = nullptr;
   int device = 0, sms = 0;
   Plan plan;
+  int exec = 0, group_threads = 64;
   // device
   void* d_params = nullptr;
   int* d_Q = nullptr;
@@ -119,6 +126,29 @@ void plan_step(int Lx, int Dk, int chi, int pout, const int* bin, int* qr, int* 
   bout[0] = 1;
   svd[0] = 0;
   svd[Lx] = 0;
+}
+
+// Executor for the sampling / measurement kernel: the whole CTA on one chain,
+// or two chains per CTA on groups of 128 threads.  Groups halve the threads
+// that wait at each barrier but need their own hot buffers; they are the
+// default when two groups' hot buffers fit in shared memory next to a second
+// CTA.  GCFVMC_EXEC=cta|group and GCFVMC_GROUP_HOT=0|1 override the choice.
+enum ExecKind { EXEC_CTA = 0, EXEC_GROUP = 1 };
+
+void plan_group(gcf_ctx* c) {
+  Plan& p = c->plan;
+  const int G = 128, NG = 256 / G;
+  c->group_threads = G;
+  const size_t hot = (size_t)p.hot_base_elems * c->sbytes;
+  const size_t base = sharedv_bytes() + (size_t)p.cfg_bytes;
+  p.group_hot_in_smem = (size_t)NG * (base + hot) <= 110 * 1024 ? 1 : 0;
+  if (const char* e = std::getenv("GCFVMC_GROUP_HOT")) p.group_hot_in_smem = std::atoi(e) ? 1 : 0;
+  p.group_smem = (base + (p.group_hot_in_smem ? hot : 0) + 15) / 16 * 16;
+  c->exec = p.group_hot_in_smem ? EXEC_GROUP : EXEC_CTA;
+  if (const char* e = std::getenv("GCFVMC_EXEC")) {
+    if (!std::strcmp(e, "group")) c->exec = EXEC_GROUP;
+    if (!std::strcmp(e, "cta")) c->exec = EXEC_CTA;
+  }
 }
 
 void build_plan(gcf_ctx* c) {
@@ -306,6 +336,7 @@ void build_plan(gcf_ctx* c) {
   p.cfg_bytes = (c->cfg_len + 15) / 16 * 16;
   const size_t budget = 100 * 1024;
   const long long h_base = h;
+  p.hot_base_elems = h_base;
   p.so_envR = hot((long long)(Lx + 1) * p.env_stride);
   p.so_env3R = hot((long long)(Lx + 1) * p.env3_stride);
   p.so_sB = hot(p.mps_stride);
@@ -320,6 +351,7 @@ void build_plan(gcf_ctx* c) {
   }
   p.hot_elems = h;
   p.dyn_smem = (size_t)p.cfg_bytes + (p.hot_in_smem ? (size_t)h * c->sbytes : 0);
+  plan_group(c);
 }
 
 template <class T>
@@ -364,6 +396,8 @@ KParams<T> make_params(gcf_ctx* c) {
   k.so_envL = p.so_envL; k.so_envX = p.so_envX; k.so_envY = p.so_envY;
   k.so_env3L = p.so_env3L; k.so_env3X = p.so_env3X; k.so_env3Y = p.so_env3Y;
   k.so_t1 = p.so_t1; k.so_t2 = p.so_t2; k.smem_cfg_bytes = p.cfg_bytes;
+  k.group_smem_bytes = (long long)p.group_smem;
+  k.group_threads = c->group_threads;
   k.status = c->d_status;
   return k;
 }
@@ -380,7 +414,7 @@ int grid_for(gcf_ctx* c, int n_chains) {
   return (int)std::max<long long>(1, want);
 }
 
-gcf_status ensure_scratch(gcf_ctx* c, int ctas) {
+gcf_status ensure_scratch(gcf_ctx* c, long long ctas) {
   if (ctas <= c->scratch_ctas) return GCF_OK;
   if (c->d_scratch) cudaFree(c->d_scratch);
   c->d_scratch = nullptr;
@@ -395,10 +429,24 @@ gcf_status ensure_scratch(gcf_ctx* c, int ctas) {
 template <class T>
 gcf_status run_vmc(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t seed,
                    int8_t* configs, const gcf_samples* out, int* gauss_count) {
-  const int grid = grid_for(c, n);
-  gcf_status st = ensure_scratch(c, grid);
+  const bool warp = c->exec == EXEC_GROUP;
+  const int W = 256 / c->group_threads;  // chains per CTA
+  int grid = 1;
+  if (warp) {
+    const int per_sm = occupancy_vmc_grouped<T>(256, W * c->plan.group_smem);
+    if (per_sm < 1) return fail(c, GCF_EINVAL, "grouped launch does not fit an SM");
+    const long long ctas = (n + W - 1) / W;
+    grid = (int)std::max<long long>(1, std::min<long long>(ctas, (long long)c->sms * per_sm));
+  } else {
+    grid = grid_for(c, n);
+  }
+  gcf_status st = ensure_scratch(c, warp ? (long long)grid * W : grid);
   if (st != GCF_OK) return st;
   KParams<T> k = make_params<T>(c);
+  if (warp) {
+    k.hot_in_smem = c->plan.group_hot_in_smem;
+    k.env_in_smem = 0;
+  }
   k.n_chains = n; k.n_sweeps = n_sweeps; k.mode = mode; k.want = want; k.seed = seed;
   k.configs = configs;
   if (out) {
@@ -407,7 +455,10 @@ gcf_status run_vmc(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t
     k.accepted = out->accepted; k.proposed = out->proposed;
   }
   CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), c->stream));
-  CUDA_TRY(c, launch_vmc<T>(k, grid, 256, c->plan.dyn_smem, c->stream));
+  if (warp)
+    CUDA_TRY(c, launch_vmc_grouped<T>(k, grid, 256, W * c->plan.group_smem, c->stream));
+  else
+    CUDA_TRY(c, launch_vmc<T>(k, grid, 256, c->plan.dyn_smem, c->stream));
   c->launches += 1;
   int h_status[4];
   CUDA_TRY(c, cudaMemcpyAsync(h_status, c->d_status, sizeof(h_status), cudaMemcpyDeviceToHost, c->stream));
@@ -597,6 +648,8 @@ int64_t gcf_num_params(const gcf_ctx* c) { return c ? c->n_params : -1; }
 int gcf_config_len(const gcf_ctx* c) { return c ? c->cfg_len : -1; }
 int gcf_scalar_bytes(const gcf_ctx* c) { return c ? (int)c->sbytes : -1; }
 int64_t gcf_launch_count(const gcf_ctx* c) { return c ? c->launches : -1; }
+
+int gcf_executor(const gcf_ctx* ctx) { return ctx ? ctx->exec : -1; }
 
 gcf_status gcf_set_tensors(gcf_ctx* c, const void* host, size_t bytes) {
   if (!c || !host) return GCF_EINVAL;

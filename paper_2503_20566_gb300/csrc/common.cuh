@@ -237,6 +237,86 @@ __device__ inline void block_sum2_r(R& a, R& b, R* red) {
   __syncthreads();
 }
 
+// Execution groups.  Every cooperative routine is written once against an
+// executor: CtaExec (the whole CTA works on one chain, __syncthreads),
+// or GroupExec<G> (chains on groups of G threads, a hardware barrier per
+// group).
+// Executors hold no data, so passing them costs no registers; reductions use
+// one 64-double slot per group of this CTA-wide array.
+__shared__ double g_exec_red[4][64];
+
+struct CtaExec {
+  __device__ int tid() const { return threadIdx.x; }
+  __device__ int size() const { return blockDim.x; }
+  __device__ int lane() const { return threadIdx.x & 31; }
+  __device__ int warp() const { return threadIdx.x >> 5; }
+  __device__ int nwarps() const { return blockDim.x >> 5; }
+  __device__ bool leader() const { return threadIdx.x == 0; }
+  __device__ void sync() const { __syncthreads(); }
+  template <class R> __device__ R sum(R v) const { return block_sum_r<R>(v, (R*)g_exec_red[0]); }
+  template <class R> __device__ void sum2(R& a, R& b) const { block_sum2_r<R>(a, b, (R*)g_exec_red[0]); }
+  __device__ float maxf(float v) const {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_max(v);
+    float* r = (float*)g_exec_red[0];
+    if (lane == 0) r[wid] = v;
+    __syncthreads();
+    float t = (lane < nw) ? r[lane] : 0.f;
+    t = warp_max(t);
+    __syncthreads();
+    return t;
+  }
+};
+
+template <int G>
+struct GroupExec {
+  static_assert(G % 32 == 0 && G >= 64 && G <= 128, "group of 64 or 128 threads");
+  __device__ int group() const { return threadIdx.x / G; }
+  __device__ int tid() const { return threadIdx.x % G; }
+  __device__ int size() const { return G; }
+  __device__ int lane() const { return threadIdx.x & 31; }
+  __device__ int warp() const { return (threadIdx.x % G) >> 5; }
+  __device__ int nwarps() const { return G >> 5; }
+  __device__ bool leader() const { return threadIdx.x % G == 0; }
+  __device__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(1 + group()), "n"(G) : "memory"); }
+  template <class R> __device__ R sum(R v) const {
+    R* r = (R*)g_exec_red[group()];
+    const int l = lane(), w = warp();
+    v = warp_sum(v);
+    if (l == 0) r[w] = v;
+    sync();
+    R t = (l < G / 32) ? r[l] : R(0);
+    t = warp_sum(t);
+    sync();
+    return t;
+  }
+  template <class R> __device__ void sum2(R& a, R& b) const {
+    R* r = (R*)g_exec_red[group()];
+    const int l = lane(), w = warp();
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (l == 0) { r[w] = a; r[32 + w] = b; }
+    sync();
+    a = (l < G / 32) ? r[l] : R(0);
+    b = (l < G / 32) ? r[32 + l] : R(0);
+    a = warp_sum(a);
+    b = warp_sum(b);
+    sync();
+  }
+  __device__ float maxf(float v) const {
+    float* r = (float*)g_exec_red[group()];
+    const int l = lane(), w = warp();
+    v = warp_max(v);
+    if (l == 0) r[w] = v;
+    sync();
+    float t = (l < G / 32) ? r[l] : 0.f;
+    t = warp_max(t);
+    sync();
+    return t;
+  }
+};
+
+
 // Power-of-two scaling: the exponent e with m = f 2^e, f in [0.5, 1).
 // Scaling by 2^-e is exact, so log-scales are integers (units of ln 2).
 __device__ inline int exp2_of(float m) {

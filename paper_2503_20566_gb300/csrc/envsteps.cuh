@@ -23,14 +23,14 @@ namespace gcf {
 // TM x TN outputs per tile.  If rescale, the output is divided by its
 // largest |component| (CTA-wide) and log(max) is returned.
 // ---------------------------------------------------------------------------
-template <class T, int TM, int TN>
-__device__ __forceinline__ float gemm_tiles(int M, int N, int K, const T* __restrict__ A, int sAm,
+template <class T, int TM, int TN, class X>
+__device__ __forceinline__ float gemm_tiles(const X ex, int M, int N, int K, const T* __restrict__ A, int sAm,
                                             int sAk, const T* __restrict__ B, int sBk, int sBn,
                                             T* __restrict__ C, int ldc) {
   const int tilesN = (N + TN - 1) / TN;
   const int tiles = ((M + TM - 1) / TM) * tilesN;
   float mx = 0.f;
-  for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+  for (int t = ex.tid(); t < tiles; t += ex.size()) {
     const int tm = t / tilesN;
     const int m0 = tm * TM, n0 = (t - tm * tilesN) * TN;
     T acc[TM][TN];
@@ -79,55 +79,41 @@ __device__ __forceinline__ float gemm_tiles(int M, int N, int K, const T* __rest
   return mx;
 }
 
-// block-wide float max, all threads call; red: >= 32 floats of shared memory
-__device__ __forceinline__ float block_maxf(float v, float* red) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  float t = (lane < nw) ? red[lane] : 0.f;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
-  __syncthreads();
-  return t;
-}
-
 // Dispatch on the output size so that typically one tile per thread.  With
 // rescale, the output is multiplied by 2^-e (exact) with e the binary
 // exponent of its largest |component|, and e is returned.
-template <class T>
-__device__ __noinline__ int cta_gemm_scaled(int M, int N, int K, const T* A, int sAm, int sAk,
+template <class T, class X>
+__device__ __noinline__ int cta_gemm_scaled(const X ex, int M, int N, int K, const T* A, int sAm, int sAk,
                                               const T* B, int sBk, int sBn, T* C, int ldc,
-                                              bool rescale, float* red) {
+                                              bool rescale) {
   float mx;
   const int MN = M * N;
-  const int nt = blockDim.x;
+  const int nt = ex.size();
   if (MN >= 8 * nt && M % 4 == 0 && N % 2 == 0)
-    mx = gemm_tiles<T, 4, 2>(M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc);
+    mx = gemm_tiles<T, 4, 2>(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc);
   else if (MN >= 4 * nt && M % 2 == 0 && N % 2 == 0)
-    mx = gemm_tiles<T, 2, 2>(M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc);
+    mx = gemm_tiles<T, 2, 2>(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc);
   else if (MN >= 2 * nt && M % 2 == 0)
-    mx = gemm_tiles<T, 2, 1>(M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc);
+    mx = gemm_tiles<T, 2, 1>(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc);
   else
-    mx = gemm_tiles<T, 1, 1>(M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc);
+    mx = gemm_tiles<T, 1, 1>(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc);
   if (!rescale) {
-    __syncthreads();
+    ex.sync();
     return 0;
   }
-  mx = block_maxf(mx, red);
+  mx = ex.maxf(mx);
   if (mx > 0.f && isfinite(mx)) {
     using R = typename Traits<T>::R;
     const int e = exp2_of(mx);
     const R s = pow2r<R>(-e);
-    for (int i = threadIdx.x; i < MN; i += nt) {
+    for (int i = ex.tid(); i < MN; i += nt) {
       const int m = i / N, n = i - m * N;
       C[m * ldc + n] = scale(C[m * ldc + n], s);
     }
-    __syncthreads();
+    ex.sync();
     return e;
   }
-  __syncthreads();
+  ex.sync();
   return 0;
 }
 
@@ -142,10 +128,10 @@ struct SDims {
 
 // C[(i j d)][(u i2 j2)] = sum_m W1[i][i2][d][m] W2[j][j2][m][u], stored with
 // padded D_k strides: row (i*DK + j)*DK + d, column (u*DK + i2)*DK + j2.
-template <class T, int DK>
-__device__ __forceinline__ void build_column_op(const SDims& d, const T* W1, const T* W2, T* Cop) {
+template <class T, int DK, class X>
+__device__ __forceinline__ void build_column_op(const X ex, const SDims& d, const T* W1, const T* W2, T* Cop) {
   constexpr int D3 = DK * DK * DK;
-  for (int idx = threadIdx.x; idx < D3 * D3; idx += blockDim.x) {
+  for (int idx = ex.tid(); idx < D3 * D3; idx += ex.size()) {
     const int k = idx / D3, n = idx % D3;
     const int i = k / (DK * DK), j = (k / DK) % DK, dd = k % DK;
     const int u = n / (DK * DK), i2 = (n / DK) % DK, j2 = n % DK;
@@ -161,20 +147,19 @@ __device__ __forceinline__ void build_column_op(const SDims& d, const T* W1, con
 }
 
 // left step; returns log of the rescale factor of the output
-template <class T, int DK>
-__device__ __noinline__ int strip_left(const SDims& d, const T* L, const T* Bs, const T* W1,
-                                         const T* W2, const T* Ts, T* out, T* X1, T* X2, T* Cop,
-                                         float* red) {
-  build_column_op<T, DK>(d, W1, W2, Cop);
+template <class T, int DK, class X>
+__device__ __noinline__ int strip_left(const X ex, const SDims& d, const T* L, const T* Bs, const T* W1,
+                                         const T* W2, const T* Ts, T* out, T* X1, T* X2, T* Cop) {
+  build_column_op<T, DK>(ex, d, W1, W2, Cop);
   // G1: X1[(i j b)][(d a2)] = sum_a L[a][(i j b)] Bs[a][(d a2)]
   const int Mij = d.nI * d.nJ * d.nB, N1 = d.pB * d.nA2;
-  cta_gemm_scaled<T>(Mij, N1, d.nA, L, 1, Mij, Bs, N1, 1, X1, N1, false, red);
+  cta_gemm_scaled<T>(ex, Mij, N1, d.nA, L, 1, Mij, Bs, N1, 1, X1, N1, false);
   // G2: X2[(a2 i2 j2)][(b u)] = sum_{(i j d)} X1[(i j b)][(d a2)] C[(i j d)][(u i2 j2)]
   {
     constexpr int D3 = DK * DK * DK;
     const int ldx2 = d.nB * d.pT;
     const int sI = d.nJ * d.nB * N1, sJ = d.nB * N1;
-    for (int p = threadIdx.x; p < d.nB * d.nA2; p += blockDim.x) {
+    for (int p = ex.tid(); p < d.nB * d.nA2; p += ex.size()) {
       const int b = p / d.nA2, a2 = p - (p / d.nA2) * d.nA2;
       const T* x1 = X1 + b * N1 + a2;
       T x[D3];
@@ -202,27 +187,26 @@ __device__ __noinline__ int strip_left(const SDims& d, const T* L, const T* Bs, 
             }
           }
     }
-    __syncthreads();
+    ex.sync();
   }
   // G3: out[(a2 i2 j2)][b2] = sum_{(b u)} X2 Ts
-  return cta_gemm_scaled<T>(d.nA2 * d.nI2 * d.nJ2, d.nB2, d.nB * d.pT, X2, d.nB * d.pT, 1, Ts, d.nB2, 1,
-                            out, d.nB2, true, red);
+  return cta_gemm_scaled<T>(ex, d.nA2 * d.nI2 * d.nJ2, d.nB2, d.nB * d.pT, X2, d.nB * d.pT, 1, Ts, d.nB2, 1,
+                            out, d.nB2, true);
 }
 
 // right step: R[a][i][j][b] from R2[a2][i2][j2][b2]
-template <class T, int DK>
-__device__ __noinline__ int strip_right(const SDims& d, const T* R2, const T* Bs, const T* W1,
-                                          const T* W2, const T* Ts, T* out, T* Y1, T* Y2, T* Cop,
-                                          float* red) {
-  build_column_op<T, DK>(d, W1, W2, Cop);
+template <class T, int DK, class X>
+__device__ __noinline__ int strip_right(const X ex, const SDims& d, const T* R2, const T* Bs, const T* W1,
+                                          const T* W2, const T* Ts, T* out, T* Y1, T* Y2, T* Cop) {
+  build_column_op<T, DK>(ex, d, W1, W2, Cop);
   // G1: Y1[(a2 i2 j2)][(b u)] = sum_b2 R2[(a2 i2 j2)][b2] Ts[(b u)][b2]
   const int M1 = d.nA2 * d.nI2 * d.nJ2, N1 = d.nB * d.pT;
-  cta_gemm_scaled<T>(M1, N1, d.nB2, R2, d.nB2, 1, Ts, 1, d.nB2, Y1, N1, false, red);
+  cta_gemm_scaled<T>(ex, M1, N1, d.nB2, R2, d.nB2, 1, Ts, 1, d.nB2, Y1, N1, false);
   // G2: Y2[(d a2)][(i j b)] = sum_{(u i2 j2)} C[(i j d)][(u i2 j2)] Y1[(a2 i2 j2)][(b u)]
   {
     constexpr int D3 = DK * DK * DK;
     const int ldy2 = d.nI * d.nJ * d.nB;
-    for (int p = threadIdx.x; p < d.nA2 * d.nB; p += blockDim.x) {
+    for (int p = ex.tid(); p < d.nA2 * d.nB; p += ex.size()) {
       const int a2 = p / d.nB, b = p - (p / d.nB) * d.nB;
       const T* y1 = Y1 + a2 * d.nI2 * d.nJ2 * N1 + b * d.pT;
       T y[D3];
@@ -250,11 +234,11 @@ __device__ __noinline__ int strip_right(const SDims& d, const T* R2, const T* Bs
             }
           }
     }
-    __syncthreads();
+    ex.sync();
   }
   // G3: R[a][(i j b)] = sum_{(d a2)} Bs[a][(d a2)] Y2[(d a2)][(i j b)]
-  return cta_gemm_scaled<T>(d.nA, d.nI * d.nJ * d.nB, d.pB * d.nA2, Bs, d.pB * d.nA2, 1, Y2,
-                            d.nI * d.nJ * d.nB, 1, out, d.nI * d.nJ * d.nB, true, red);
+  return cta_gemm_scaled<T>(ex, d.nA, d.nI * d.nJ * d.nB, d.pB * d.nA2, Bs, d.pB * d.nA2, 1, Y2,
+                            d.nI * d.nJ * d.nB, 1, out, d.nI * d.nJ * d.nB, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -266,16 +250,16 @@ struct RDims {
   int pB, pT;
 };
 
-template <class T, int DK>
-__device__ __noinline__ int row_left(const RDims& d, const T* L, const T* Bs, const T* W, const T* Ts,
-                                       T* out, T* X1, T* X2, float* red, bool rescale = true) {
+template <class T, int DK, class X>
+__device__ __noinline__ int row_left(const X ex, const RDims& d, const T* L, const T* Bs, const T* W, const T* Ts,
+                                       T* out, T* X1, T* X2, bool rescale = true) {
   // G1: X1[(l b)][(d a2)] = sum_a L[a][(l b)] Bs[a][(d a2)]
   const int Mlb = d.nH * d.nB, N1 = d.pB * d.nA2;
-  cta_gemm_scaled<T>(Mlb, N1, d.nA, L, 1, Mlb, Bs, N1, 1, X1, N1, false, red);
+  cta_gemm_scaled<T>(ex, Mlb, N1, d.nA, L, 1, Mlb, Bs, N1, 1, X1, N1, false);
   // G2: X2[(a2 r)][(b u)] = sum_{l,d} X1[(l b)][(d a2)] W[l][r][d][u]
   {
     const int ldx2 = d.nB * d.pT;
-    for (int p = threadIdx.x; p < d.nB * d.nA2; p += blockDim.x) {
+    for (int p = ex.tid(); p < d.nB * d.nA2; p += ex.size()) {
       const int b = p / d.nA2, a2 = p - (p / d.nA2) * d.nA2;
       T x[DK][DK];
 #pragma unroll
@@ -294,23 +278,23 @@ __device__ __noinline__ int row_left(const RDims& d, const T* L, const T* Bs, co
           X2[(a2 * d.nH2 + r) * ldx2 + b * d.pT + u] = s;
         }
     }
-    __syncthreads();
+    ex.sync();
   }
   // G3: out[(a2 r)][b2] = sum_{(b u)} X2[(a2 r)][(b u)] Ts[(b u)][b2]
-  return cta_gemm_scaled<T>(d.nA2 * d.nH2, d.nB2, d.nB * d.pT, X2, d.nB * d.pT, 1, Ts, d.nB2, 1, out,
-                            d.nB2, rescale, red);
+  return cta_gemm_scaled<T>(ex, d.nA2 * d.nH2, d.nB2, d.nB * d.pT, X2, d.nB * d.pT, 1, Ts, d.nB2, 1, out,
+                            d.nB2, rescale);
 }
 
-template <class T, int DK>
-__device__ __noinline__ int row_right(const RDims& d, const T* R2, const T* Bs, const T* W, const T* Ts,
-                                        T* out, T* Y1, T* Y2, float* red) {
+template <class T, int DK, class X>
+__device__ __noinline__ int row_right(const X ex, const RDims& d, const T* R2, const T* Bs, const T* W, const T* Ts,
+                                        T* out, T* Y1, T* Y2) {
   // G1: Y1[(a2 r)][(b u)] = sum_b2 R2[(a2 r)][b2] Ts[(b u)][b2]
   const int M1 = d.nA2 * d.nH2, N1 = d.nB * d.pT;
-  cta_gemm_scaled<T>(M1, N1, d.nB2, R2, d.nB2, 1, Ts, 1, d.nB2, Y1, N1, false, red);
+  cta_gemm_scaled<T>(ex, M1, N1, d.nB2, R2, d.nB2, 1, Ts, 1, d.nB2, Y1, N1, false);
   // G2: Y2[(d a2)][(l b)] = sum_{r,u} Y1[(a2 r)][(b u)] W[l][r][d][u]
   {
     const int ldy2 = d.nH * d.nB;
-    for (int p = threadIdx.x; p < d.nA2 * d.nB; p += blockDim.x) {
+    for (int p = ex.tid(); p < d.nA2 * d.nB; p += ex.size()) {
       const int a2 = p / d.nB, b = p - (p / d.nB) * d.nB;
       T y[DK][DK];
 #pragma unroll
@@ -329,23 +313,23 @@ __device__ __noinline__ int row_right(const RDims& d, const T* R2, const T* Bs, 
           Y2[(dd * d.nA2 + a2) * ldy2 + l * d.nB + b] = s;
         }
     }
-    __syncthreads();
+    ex.sync();
   }
   // G3: R[a][(l b)] = sum_{(d a2)} Bs[a][(d a2)] Y2[(d a2)][(l b)]
-  return cta_gemm_scaled<T>(d.nA, d.nH * d.nB, d.pB * d.nA2, Bs, d.pB * d.nA2, 1, Y2, d.nH * d.nB, 1,
-                            out, d.nH * d.nB, true, red);
+  return cta_gemm_scaled<T>(ex, d.nA, d.nH * d.nB, d.pB * d.nA2, Bs, d.pB * d.nA2, 1, Y2, d.nH * d.nB, 1,
+                            out, d.nH * d.nB, true);
 }
 
 // Open tensor of one row vertex: G[l][r][d][u] = sum_{b,a2} X1[(l b)][(d a2)] Y1[(a2 r)][(b u)]
 // with X1 = L.Bs (left G1) and Y1 = R2.Ts (right G1); written over the actual dims.
-template <class T, int DK>
-__device__ __noinline__ void row_open(const RDims& d, const T* L, const T* Bs, const T* Ts, const T* R2,
-                                      T* G, T* X1, T* Y1, float* red) {
+template <class T, int DK, class X>
+__device__ __noinline__ void row_open(const X ex, const RDims& d, const T* L, const T* Bs, const T* Ts, const T* R2,
+                                      T* G, T* X1, T* Y1) {
   const int Mlb = d.nH * d.nB, N1 = d.pB * d.nA2;
-  cta_gemm_scaled<T>(Mlb, N1, d.nA, L, 1, Mlb, Bs, N1, 1, X1, N1, false, red);
+  cta_gemm_scaled<T>(ex, Mlb, N1, d.nA, L, 1, Mlb, Bs, N1, 1, X1, N1, false);
   const int M2 = d.nA2 * d.nH2, N2 = d.nB * d.pT;
-  cta_gemm_scaled<T>(M2, N2, d.nB2, R2, d.nB2, 1, Ts, 1, d.nB2, Y1, N2, false, red);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  cta_gemm_scaled<T>(ex, M2, N2, d.nB2, R2, d.nB2, 1, Ts, 1, d.nB2, Y1, N2, false);
+  const int lane = ex.lane(), wid = ex.warp(), nw = ex.nwarps();
   const int nout = d.nH * d.nH2 * d.pB * d.pT;
   const int K = d.nB * d.nA2;
   for (int o = wid; o < nout; o += nw) {
@@ -362,8 +346,7 @@ __device__ __noinline__ void row_open(const RDims& d, const T* L, const T* Bs, c
     s = warp_sum_scalar(s);
     if (lane == 0) G[o] = s;
   }
-  __syncthreads();
-  (void)red;
+  ex.sync();
 }
 
 }  // namespace gcf

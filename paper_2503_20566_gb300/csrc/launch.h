@@ -12,6 +12,14 @@ cudaError_t launch_vmc(const KParams<T>& k, int grid, int block, size_t smem, cu
 // resident blocks per SM of vmc_kernel<T> for this block size and dynamic smem
 template <class T>
 int occupancy_vmc(int block, size_t smem);
+// several chains per CTA (groups of k.group_threads threads); smem = groups x per-group bytes
+template <class T>
+cudaError_t launch_vmc_grouped(const KParams<T>& k, int grid, int block, size_t smem, cudaStream_t st);
+// resident blocks per SM of vmc_kernel_grouped<T>; 0 if the launch cannot fit
+template <class T>
+int occupancy_vmc_grouped(int block, size_t smem);
+// bytes of the per-chain shared state of the VMC kernels (16-byte aligned)
+size_t sharedv_bytes();
 cudaError_t launch_init_configs(int N, int Lx, int Ly, int matter, const int* Q, int n_chains,
                                 const int8_t* occ, const int8_t* powers, int8_t* configs,
                                 int* status, cudaStream_t st);

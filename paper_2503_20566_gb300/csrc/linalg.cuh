@@ -4,7 +4,7 @@
 // Every routine is called by all threads of the CTA with identical arguments;
 // matrices live in global scratch or shared memory and are addressed through
 // (row stride, column stride), so transposed views cost nothing.  Routines
-// end with __syncthreads() so their results are visible on return.
+// end with ex.sync() so their results are visible on return.
 //
 // The algorithms are the textbook ones: Householder QR (Golub & Van Loan,
 // "Matrix Computations", Alg. 5.1.1 / 5.2.1, with the complex reflector that
@@ -17,11 +17,11 @@
 namespace gcf {
 
 // C(i,j) = [C(i,j) +] sum_k op(A)(i,k) op(B)(k,j); op = optional conjugation.
-template <class T, bool CA = false, bool CB = false>
-__device__ __noinline__ void cta_gemm(int M, int N, int K, const T* A, int sAm, int sAk, const T* B,
+template <class T, bool CA = false, bool CB = false, class X>
+__device__ __noinline__ void cta_gemm(const X ex, int M, int N, int K, const T* A, int sAm, int sAk, const T* B,
                          int sBk, int sBn, T* C, int sCm, int sCn, bool accumulate) {
   const int MN = M * N;
-  for (int idx = threadIdx.x; idx < MN; idx += blockDim.x) {
+  for (int idx = ex.tid(); idx < MN; idx += ex.size()) {
     const int i = idx / N, j = idx - (idx / N) * N;
     T s = accumulate ? C[i * sCm + j * sCn] : zero<T>();
     const T* a = A + i * sAm;
@@ -34,7 +34,7 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, const T* A, int sAm, 
     }
     C[i * sCm + j * sCn] = s;
   }
-  __syncthreads();
+  ex.sync();
 }
 
 
@@ -61,23 +61,22 @@ __device__ inline void householder(T alpha, typename Traits<T>::R xn2, T& tau, T
 // In-place Householder QR of A (m x n): on return the upper triangle of the
 // leading k = min(m,n) rows holds R, the part below the diagonal holds the
 // reflector vectors, tau[0..k) their factors.  `red` is shared scratch (64 doubles).
-template <class T>
-__device__ __noinline__ void cta_qr(int m, int n, T* A, int sm, int sn, T* tau, double* red_) {
+template <class T, class X>
+__device__ __noinline__ void cta_qr(const X ex, int m, int n, T* A, int sm, int sn, T* tau) {
   using R = typename Traits<T>::R;
-  R* red = (R*)red_;
   const int k = min(m, n);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = ex.lane(), wid = ex.warp(), nw = ex.nwarps();
   for (int j = 0; j < k; ++j) {
     R part = R(0);
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) part += abs2(A[i * sm + j * sn]);
-    const R xn2 = block_sum_r<R>(part, red);
+    for (int i = j + 1 + ex.tid(); i < m; i += ex.size()) part += abs2(A[i * sm + j * sn]);
+    const R xn2 = ex.template sum<R>(part);
     const T alpha = A[j * sm + j * sn];
     T t, sc, beta;
     householder(alpha, xn2, t, sc, beta);
-    __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[i * sm + j * sn] = A[i * sm + j * sn] * sc;
-    if (threadIdx.x == 0) { A[j * sm + j * sn] = beta; tau[j] = t; }
-    __syncthreads();
+    ex.sync();
+    for (int i = j + 1 + ex.tid(); i < m; i += ex.size()) A[i * sm + j * sn] = A[i * sm + j * sn] * sc;
+    if (ex.tid() == 0) { A[j * sm + j * sn] = beta; tau[j] = t; }
+    ex.sync();
     const T ct = conjg(t);
     for (int c = j + 1 + wid; c < n; c += nw) {
       T w = zero<T>();
@@ -92,21 +91,21 @@ __device__ __noinline__ void cta_qr(int m, int n, T* A, int sm, int sn, T* tau, 
         A[i * sm + c * sn] -= v * f;
       }
     }
-    __syncthreads();
+    ex.sync();
   }
 }
 
 // Q = H_0 H_1 ... H_{k-1} restricted to its first k columns (m x k), from
 // the reflectors stored by cta_qr in A.
-template <class T>
-__device__ __noinline__ void cta_form_q(int m, int k, const T* A, int sm, int sn, const T* tau, T* Q, int sQm,
+template <class T, class X>
+__device__ __noinline__ void cta_form_q(const X ex, int m, int k, const T* A, int sm, int sn, const T* tau, T* Q, int sQm,
                            int sQn) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x) {
+  const int lane = ex.lane(), wid = ex.warp(), nw = ex.nwarps();
+  for (int idx = ex.tid(); idx < m * k; idx += ex.size()) {
     const int i = idx / k, c = idx - (idx / k) * k;
     Q[i * sQm + c * sQn] = (i == c) ? one<T>() : zero<T>();
   }
-  __syncthreads();
+  ex.sync();
   for (int j = k - 1; j >= 0; --j) {
     const T t = tau[j];
     for (int c = j + wid; c < k; c += nw) {
@@ -122,31 +121,31 @@ __device__ __noinline__ void cta_form_q(int m, int k, const T* A, int sm, int sn
         Q[i * sQm + c * sQn] -= v * f;
       }
     }
-    __syncthreads();
+    ex.sync();
   }
 }
 
 // Copy with optional conjugate-transpose: dst(i,j) = src(j,i)^* for i<rows, j<cols.
-template <class T>
-__device__ __noinline__ void cta_adjoint(int rows, int cols, const T* src, int sSm, int sSn, T* dst, int sDm,
+template <class T, class X>
+__device__ __noinline__ void cta_adjoint(const X ex, int rows, int cols, const T* src, int sSm, int sSn, T* dst, int sDm,
                             int sDn) {
-  for (int idx = threadIdx.x; idx < rows * cols; idx += blockDim.x) {
+  for (int idx = ex.tid(); idx < rows * cols; idx += ex.size()) {
     const int i = idx / cols, j = idx - (idx / cols) * cols;
     dst[i * sDm + j * sDn] = conjg(src[j * sSm + i * sSn]);
   }
-  __syncthreads();
+  ex.sync();
 }
 
 // One-sided Jacobi on the columns of W (p x q), accumulating J (q x q, reset
 // to the identity here) so that on return W = W_in J has mutually orthogonal
 // columns.  Returns the number of sweeps used; *converged set to 0 if the
 // sweep limit was hit.  sflag: shared int scratch.
-template <class T>
-__device__ __noinline__ int cta_jacobi_svd(int p, int q, T* W, int sWm, int sWn, T* J, int sJm, int sJn,
+template <class T, class X>
+__device__ __noinline__ int cta_jacobi_svd(const X ex, int p, int q, T* W, int sWm, int sWn, T* J, int sJm, int sJn,
                               int* sflag, int max_sweeps, int* converged) {
   using R = typename Traits<T>::R;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int idx = threadIdx.x; idx < q * q; idx += blockDim.x) {
+  const int lane = ex.lane(), wid = ex.warp(), nw = ex.nwarps();
+  for (int idx = ex.tid(); idx < q * q; idx += ex.size()) {
     const int i = idx / q, c = idx - (idx / q) * q;
     J[i * sJm + c * sJn] = (i == c) ? one<T>() : zero<T>();
   }
@@ -155,8 +154,8 @@ __device__ __noinline__ int cta_jacobi_svd(int p, int q, T* W, int sWm, int sWn,
   int sweep = 0;
   if (converged) *converged = 1;
   for (; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) *sflag = 0;
-    __syncthreads();
+    if (ex.tid() == 0) *sflag = 0;
+    ex.sync();
     for (int r = 0; r < n - 1; ++r) {
       for (int kp = wid; kp < n / 2; kp += nw) {
         int a, b;
@@ -195,14 +194,14 @@ __device__ __noinline__ int cta_jacobi_svd(int p, int q, T* W, int sWm, int sWn,
         }
         if (lane == 0) *sflag = 1;
       }
-      __syncthreads();
+      ex.sync();
     }
     const int any = *sflag;
-    __syncthreads();
+    ex.sync();
     if (!any) break;
   }
   if (sweep >= max_sweeps && converged) *converged = 0;
-  __syncthreads();
+  ex.sync();
   return sweep;
 }
 

@@ -57,6 +57,8 @@ struct KParams {
   long long o_sigma, o_sel, dense_max, o_Z, z_size, q_pack, o_X, o_W1, o_W2, o_W3, o_W4;
   long long so_net, so_prop, so_cop, so_envL, so_envX, so_envY, so_env3L, so_env3X, so_env3Y,
       so_t1, so_t2, smem_cfg_bytes;
+  long long group_smem_bytes;  // grouped kernel: shared bytes per chain group
+  int group_threads;          // grouped kernel: threads per chain (128)
   // right environments and the staged B / T rows of the current pass
   int env_in_smem;
   long long so_envR, so_env3R, so_sB, so_sT;
@@ -126,15 +128,15 @@ __device__ inline int block_of(const KParams<T>& k, const int8_t* cfg, int x, in
 }
 
 // Copy the selected block of (x, y) into a D_k^4 box (thread-parallel).
-template <class T>
-__device__ inline void gather_box(const KParams<T>& k, int x, int y, int bid, T* box) {
+template <class T, class X>
+__device__ inline void gather_box(const X ex, const KParams<T>& k, int x, int y, int bid, T* box) {
   const int Dk = k.Dk;
   const int dl = hl_dim(x, Dk), dr = hr_dim(x, k.Lx, Dk), dd = dn_dim(y, Dk),
             du = up_dim(y, k.Ly, Dk);
   const int v = y * k.Lx + x;
   const T* src = k.params + k.voff[v] + (long long)bid * k.vbs[v];
   const int bs = dl * dr * dd * du;
-  for (int e = threadIdx.x; e < bs; e += blockDim.x) {
+  for (int e = ex.tid(); e < bs; e += ex.size()) {
     int t = e;
     const int iu = t % du; t /= du;
     const int id = t % dd; t /= dd;
@@ -155,58 +157,59 @@ __device__ inline T* net_box(const KParams<T>& k, T* ws, int x, int y) {
 }
 
 // site offsets of a packed MPS with bond table bd and physical dim phys
-__device__ inline void mps_offsets(const int* bd, int phys, int Lx, int* off) {
-  if (threadIdx.x == 0) {
+template <class X>
+__device__ inline void mps_offsets(const X ex, const int* bd, int phys, int Lx, int* off) {
+  if (ex.tid() == 0) {
     int o = 0;
     for (int c = 0; c < Lx; ++c) { off[c] = o; o += bd[c] * phys * bd[c + 1]; }
     off[Lx] = o;
   }
-  __syncthreads();
+  ex.sync();
 }
 
 // ---------------------------------------------------------------------------
 // Rescaling by exact powers of two; the returned integer e means
 // "tensor_in = 2^e * tensor_out".
 // ---------------------------------------------------------------------------
-template <class T>
-__device__ __noinline__ int rescale(T* a, int n, double* red_) {
+template <class T, class X>
+__device__ __noinline__ int rescale(const X ex, T* a, int n) {
   using R = typename Traits<T>::R;
   float mx = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmaxf(mx, (float)absmax1(a[i]));
-  mx = block_maxf(mx, (float*)red_);
+  for (int i = ex.tid(); i < n; i += ex.size()) mx = fmaxf(mx, (float)absmax1(a[i]));
+  mx = ex.maxf(mx);
   if (!(mx > 0.f) || !isfinite(mx)) return 0;
   const int e = exp2_of(mx);
   const R s = pow2r<R>(-e);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = scale(a[i], s);
-  __syncthreads();
+  for (int i = ex.tid(); i < n; i += ex.size()) a[i] = scale(a[i], s);
+  ex.sync();
   return e;
 }
 
 // the same with the scale chosen from the Frobenius norm (|a| -> [0.5, 1))
-template <class T>
-__device__ __noinline__ int frob_rescale(T* a, int n, double* red_) {
+template <class T, class X>
+__device__ __noinline__ int frob_rescale(const X ex, T* a, int n) {
   using R = typename Traits<T>::R;
   R s2 = R(0);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s2 += abs2(a[i]);
-  s2 = block_sum_r<R>(s2, (R*)red_);
+  for (int i = ex.tid(); i < n; i += ex.size()) s2 += abs2(a[i]);
+  s2 = ex.template sum<R>(s2);
   if (!(s2 > R(0)) || !isfinite((float)s2)) return 0;
   const int e = exp2_of((float)sqrt(s2));
   const R s = pow2r<R>(-e);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = scale(a[i], s);
-  __syncthreads();
+  for (int i = ex.tid(); i < n; i += ex.size()) a[i] = scale(a[i], s);
+  ex.sync();
   return e;
 }
 
 // sum_k A[k] B[k] (no conjugation), broadcast to all threads as (re, im)
-template <class T>
-__device__ inline void cta_dot(const T* A, const T* B, int n, double* red_, typename Traits<T>::R& r,
+template <class T, class X>
+__device__ inline void cta_dot(const X ex, const T* A, const T* B, int n, typename Traits<T>::R& r,
                                typename Traits<T>::R& i) {
   using R = typename Traits<T>::R;
   T s = zero<T>();
-  for (int k = threadIdx.x; k < n; k += blockDim.x) s = fmac(s, A[k], B[k]);
+  for (int k = ex.tid(); k < n; k += ex.size()) s = fmac(s, A[k], B[k]);
   r = re(s);
   i = im(s);
-  block_sum2_r<R>(r, i, (R*)red_);
+  ex.template sum2<R>(r, i);
 }
 
 // ---------------------------------------------------------------------------
@@ -221,21 +224,21 @@ __device__ inline void cta_dot(const T* A, const T* B, int n, double* red_, type
 // contracting the input MPS to a vector and applying the row MPO site by site.
 // Returns the binary exponent e of the scale (state = 2^e * output).
 // ---------------------------------------------------------------------------
-template <class T>
-__device__ __noinline__ int dense_absorb(const KParams<T>& k, Shared& sh, const T* net, const T* mps_in,
+template <class T, class X>
+__device__ __noinline__ int dense_absorb(const X ex, const KParams<T>& k, Shared& sh, const T* net, const T* mps_in,
                                             const int* bdi, int pin, int row, int flip, T* mout,
                                             const int* bdo, int pout, T* bufA, T* bufB) {
   const int Lx = k.Lx, Dk = k.Dk;
   const int D3 = Dk * Dk * Dk, D2 = Dk * Dk;
   const int sd = flip ? 1 : Dk, su = flip ? Dk : 1;
   // 1. input vector v[(i_0..i_{L-1})], i_0 most significant
-  if (threadIdx.x == 0) bufA[0] = one<T>();
-  __syncthreads();
+  if (ex.tid() == 0) bufA[0] = one<T>();
+  ex.sync();
   int rows = 1;
   for (int c = 0; c < Lx; ++c) {
     const T* M = mps_in + sh.bd_off[c];
     // bufB[(p, i)][b] = sum_a bufA[p][a] M[a][(i b)]
-    cta_gemm<T>(rows, pin * bdi[c + 1], bdi[c], bufA, bdi[c], 1, M, pin * bdi[c + 1], 1, bufB,
+    cta_gemm<T>(ex, rows, pin * bdi[c + 1], bdi[c], bufA, bdi[c], 1, M, pin * bdi[c + 1], 1, bufB,
                 pin * bdi[c + 1], 1, false);
     rows *= pin;
     T* t = bufA; bufA = bufB; bufB = t;
@@ -246,7 +249,7 @@ __device__ __noinline__ int dense_absorb(const KParams<T>& k, Shared& sh, const 
     const int hl = hl_dim(c, Dk), hr = hr_dim(c, Lx, Dk);
     const T* W = net + (long long)(row * Lx + c) * (Dk * Dk * Dk * Dk);
     const int nout = hr * NU * pout * ND;
-    for (int idx = threadIdx.x; idx < nout; idx += blockDim.x) {
+    for (int idx = ex.tid(); idx < nout; idx += ex.size()) {
       int t = idx;
       const int Dr = t % ND; t /= ND;
       const int u = t % pout; t /= pout;
@@ -258,7 +261,7 @@ __device__ __noinline__ int dense_absorb(const KParams<T>& k, Shared& sh, const 
           s = fmac(s, W[hp * D3 + h * D2 + d * sd + u * su], bufA[((hp * NU + U) * pin + d) * ND + Dr]);
       bufB[idx] = s;
     }
-    __syncthreads();
+    ex.sync();
     T* tt = bufA; bufA = bufB; bufB = tt;
     NU *= pout;
     if (c < Lx - 1) ND /= pin;
@@ -267,8 +270,8 @@ __device__ __noinline__ int dense_absorb(const KParams<T>& k, Shared& sh, const 
   using R = typename Traits<T>::R;
   const int nv = NU;
   R s2 = R(0);
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) s2 += abs2(bufA[i]);
-  s2 = block_sum_r<R>(s2, (R*)sh.red);
+  for (int i = ex.tid(); i < nv; i += ex.size()) s2 += abs2(bufA[i]);
+  s2 = ex.template sum<R>(s2);
   const int e = (s2 > R(0) && isfinite((float)s2)) ? exp2_of((float)sqrt(s2)) : 0;
   const R inv = pow2r<R>(-e);
   // 4. identity sites and the core
@@ -278,16 +281,16 @@ __device__ __noinline__ int dense_absorb(const KParams<T>& k, Shared& sh, const 
     T* site = mout + sh.bd_off2[c];
     const int n = a * pout * b;
     if (c == m) {
-      for (int i = threadIdx.x; i < n; i += blockDim.x) site[i] = scale(bufA[i], inv);
+      for (int i = ex.tid(); i < n; i += ex.size()) site[i] = scale(bufA[i], inv);
     } else {
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      for (int i = ex.tid(); i < n; i += ex.size()) {
         const int ib = i % b, ii = (i / b) % pout, ia = i / (b * pout);
         const bool on = (c < m) ? (ib == ia * pout + ii) : (ia == ii * b + ib);
         site[i] = on ? one<T>() : zero<T>();
       }
     }
   }
-  __syncthreads();
+  ex.sync();
   return e;
 }
 
@@ -303,8 +306,8 @@ __device__ __noinline__ int dense_absorb(const KParams<T>& k, Shared& sh, const 
 // then right to left: LQ where no truncation is needed, one-sided Jacobi SVD
 // keeping the chi largest singular values otherwise.
 // ---------------------------------------------------------------------------
-template <class T>
-__device__ __noinline__ int absorb_compress(const KParams<T>& k, T* ws, T* hot_base, Shared& sh, const T* net,
+template <class T, class X>
+__device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* ws, T* hot_base, Shared& sh, const T* net,
                                   const T* mps_in, const int* bdi, int pin, int row, int flip, T* mout,
                                   const int* bdo, int pout, const int* qr, const int* svd) {
   const int Lx = k.Lx, Dk = k.Dk;
@@ -317,12 +320,12 @@ __device__ __noinline__ int absorb_compress(const KParams<T>& k, T* ws, T* hot_b
   T* Jm = ws + k.o_J;
   T* Qs = ws + k.o_Q;
   int logs = 0;
-  mps_offsets(bdi, pin, Lx, sh.bd_off);
-  mps_offsets(bdo, pout, Lx, sh.bd_off2);
+  mps_offsets(ex, bdi, pin, Lx, sh.bd_off);
+  mps_offsets(ex, bdo, pout, Lx, sh.bd_off2);
 
   // Dense (identity + core) path: every output bond at full rank and the
   // dense state small enough.
-  if (threadIdx.x == 0) {
+  if (ex.tid() == 0) {
     int ok = (pout == Dk) ? 1 : 0;
     long long pw = 1;
     for (int c = 0; c <= Lx; ++c) {
@@ -340,11 +343,11 @@ __device__ __noinline__ int absorb_compress(const KParams<T>& k, T* ws, T* hot_b
     }
     sh.iflag[2] = ok;
   }
-  __syncthreads();
+  ex.sync();
   if (sh.iflag[2]) {
     T* bufA = k.hot_in_smem ? hot_base + k.so_t1 : ws + k.o_t1;
     T* bufB = k.hot_in_smem ? hot_base + k.so_t2 : ws + k.o_t2;
-    return dense_absorb<T>(k, sh, net, mps_in, bdi, pin, row, flip, mout, bdo, pout, bufA, bufB);
+    return dense_absorb<T>(ex, k, sh, net, mps_in, bdi, pin, row, flip, mout, bdo, pout, bufA, bufB);
   }
 
   // General path.  Z_c (absorbed sites) for all c; then a QR sweep from the
@@ -353,7 +356,7 @@ __device__ __noinline__ int absorb_compress(const KParams<T>& k, T* ws, T* hot_b
   // shrink; sites in between are the absorbed tensors with the carries
   // multiplied in.  Without truncation this reaches the exact state with the
   // step's bond dimensions; with truncation it is the full canonical sweep.
-  if (threadIdx.x == 0) {
+  if (ex.tid() == 0) {
     int any_svd = 0;
     for (int c = 1; c < Lx; ++c) any_svd |= svd[c];
     int zo = 0, qo = 0;
@@ -368,7 +371,7 @@ __device__ __noinline__ int absorb_compress(const KParams<T>& k, T* ws, T* hot_b
     while (cl < Lx - 1 && (any_svd || qr[cl] * pout < sh.ab[cl + 1])) ++cl;
     sh.iflag[1] = cl;
   }
-  __syncthreads();
+  ex.sync();
   const int cL = sh.iflag[1];
   T* Z = ws + k.o_Z;
   T* Xb = ws + k.o_X;
@@ -383,7 +386,7 @@ __device__ __noinline__ int absorb_compress(const KParams<T>& k, T* ws, T* hot_b
     const T* W = net + (long long)(row * Lx + c) * (Dk * Dk * Dk * Dk);
     const int nZ = a * l * pout * b * r;
     T* Zc = Z + sh.zoff[c];
-    for (int idx = threadIdx.x; idx < nZ; idx += blockDim.x) {
+    for (int idx = ex.tid(); idx < nZ; idx += ex.size()) {
       int t = idx;
       const int ir = t % r; t /= r;
       const int ib = t % b; t /= b;
@@ -397,25 +400,25 @@ __device__ __noinline__ int absorb_compress(const KParams<T>& k, T* ws, T* hot_b
     }
   }
   // ---- left QR sweep over sites 0..cL-1; R carry in M3 (Rrows x ab[c])
-  if (threadIdx.x == 0) M3[0] = one<T>();
-  __syncthreads();
+  if (ex.tid() == 0) M3[0] = one<T>();
+  ex.sync();
   int Rrows = 1;
   for (int c = 0; c <= cL; ++c) {
     const int abl = sh.ab[c], abr = sh.ab[c + 1];
     const int rows = Rrows * pout, cols = abr;
     // X = R (Rrows x abl) * Z_c (abl x pout*abr) -> (Rrows*pout) x abr
     T* X = (c == cL) ? Xb : M1;
-    cta_gemm<T>(Rrows, pout * abr, abl, M3, abl, 1, Z + sh.zoff[c], pout * abr, 1, X, pout * abr, 1, false);
+    cta_gemm<T>(ex, Rrows, pout * abr, abl, M3, abl, 1, Z + sh.zoff[c], pout * abr, 1, X, pout * abr, 1, false);
     if (c == cL) break;
-    cta_qr<T>(rows, cols, M1, cols, 1, tau, sh.red);
+    cta_qr<T>(ex, rows, cols, M1, cols, 1, tau);
     const int kq = min(rows, cols);
-    cta_form_q<T>(rows, kq, M1, cols, 1, tau, Qs + sh.qoff[c], kq, 1);
-    for (int idx = threadIdx.x; idx < kq * cols; idx += blockDim.x) {
+    cta_form_q<T>(ex, rows, kq, M1, cols, 1, tau, Qs + sh.qoff[c], kq, 1);
+    for (int idx = ex.tid(); idx < kq * cols; idx += ex.size()) {
       const int i = idx / cols, j = idx - (idx / cols) * cols;
       M3[idx] = (j >= i) ? M1[i * cols + j] : zero<T>();
     }
-    __syncthreads();
-    logs += frob_rescale(M3, kq * cols, sh.red);
+    ex.sync();
+    logs += frob_rescale(ex, M3, kq * cols);
     Rrows = kq;
   }
   // ---- right sweep over every site.  The carry Lc (rdim x kc) is the
@@ -433,7 +436,7 @@ __device__ __noinline__ int absorb_compress(const KParams<T>& k, T* ws, T* hot_b
       yc = pout * rd;
     } else {
       // Y = S ((cur*pout) x rdim) * Lc (rdim x kc), viewed cur x (pout*kc)
-      cta_gemm<T>(cur * pout, kc, rdim, S, rdim, 1, Lc, kc, 1, Y, kc, 1, false);
+      cta_gemm<T>(ex, cur * pout, kc, rdim, S, rdim, 1, Lc, kc, 1, Y, kc, 1, false);
       Yp = Y;
       yc = pout * kc;
     }
@@ -441,33 +444,33 @@ __device__ __noinline__ int absorb_compress(const KParams<T>& k, T* ws, T* hot_b
     T* site = mout + sh.bd_off2[c];
     if (c >= 1 && (svd[c] || bdo[c] < cur)) {
       const int kk = bdo[c];
-      cta_adjoint<T>(yc, yr, Yp, yc, 1, Yh, yr, 1);
-      cta_qr<T>(yc, yr, Yh, yr, 1, tau, sh.red);
+      cta_adjoint<T>(ex, yc, yr, Yp, yc, 1, Yh, yr, 1);
+      cta_qr<T>(ex, yc, yr, Yh, yr, 1, tau);
       const int k0 = min(yr, yc);
-      cta_form_q<T>(yc, k0, Yh, yr, 1, tau, Qp, k0, 1);
+      cta_form_q<T>(ex, yc, k0, Yh, yr, 1, tau, Qp, k0, 1);
       // L = R'^H (yr x k0)
-      for (int idx = threadIdx.x; idx < yr * k0; idx += blockDim.x) {
+      for (int idx = ex.tid(); idx < yr * k0; idx += ex.size()) {
         const int i = idx / k0, j = idx - (idx / k0) * k0;
         Lc[idx] = (i >= j) ? conjg(Yh[j * yr + i]) : zero<T>();
       }
-      __syncthreads();
+      ex.sync();
       if (!svd[c]) {
-        cta_adjoint<T>(k0, yc, Qp, k0, 1, site, yc, 1);
+        cta_adjoint<T>(ex, k0, yc, Qp, k0, 1, site, yc, 1);
       } else {
         int conv = 1;
-        cta_jacobi_svd<T>(yr, k0, Lc, k0, 1, Jm, k0, 1, &sh.iflag[0], k.max_sweeps_svd, &conv);
-        if (!conv && threadIdx.x == 0) atomicAdd(&k.status[ST_SVD], 1);
+        cta_jacobi_svd<T>(ex, yr, k0, Lc, k0, 1, Jm, k0, 1, &sh.iflag[0], k.max_sweeps_svd, &conv);
+        if (!conv && ex.tid() == 0) atomicAdd(&k.status[ST_SVD], 1);
         // squared column norms -> sigma, selected columns -> sel (scratch)
         using RR = typename Traits<T>::R;
         RR* sigma = (RR*)(ws + k.o_sigma);
         int* sel = (int*)(ws + k.o_sel);
-        for (int j = threadIdx.x; j < k0; j += blockDim.x) {
+        for (int j = ex.tid(); j < k0; j += ex.size()) {
           RR s2 = RR(0);
           for (int i = 0; i < yr; ++i) s2 += abs2(Lc[i * k0 + j]);
           sigma[j] = s2;
         }
-        __syncthreads();
-        for (int j = threadIdx.x; j < k0; j += blockDim.x) {
+        ex.sync();
+        for (int j = ex.tid(); j < k0; j += ex.size()) {
           int rank = 0;
           const RR sj = sigma[j];
           for (int i = 0; i < k0; ++i) {
@@ -476,9 +479,9 @@ __device__ __noinline__ int absorb_compress(const KParams<T>& k, T* ws, T* hot_b
           }
           if (rank < kk) sel[rank] = j;
         }
-        __syncthreads();
+        ex.sync();
         // site[n][x] = sum_j conj(J[j][sel n]) Q'^H[j][x]
-        for (int idx = threadIdx.x; idx < kk * yc; idx += blockDim.x) {
+        for (int idx = ex.tid(); idx < kk * yc; idx += ex.size()) {
           const int n = idx / yc, x = idx - (idx / yc) * yc;
           const int jn = sel[n];
           T s = zero<T>();
@@ -486,23 +489,23 @@ __device__ __noinline__ int absorb_compress(const KParams<T>& k, T* ws, T* hot_b
           site[idx] = s;
         }
         // carry U S = W[:, sel] (yr x kk)
-        for (int idx = threadIdx.x; idx < yr * kk; idx += blockDim.x) {
+        for (int idx = ex.tid(); idx < yr * kk; idx += ex.size()) {
           const int i = idx / kk, n = idx - (idx / kk) * kk;
           Yh[idx] = Lc[i * k0 + sel[n]];
         }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < yr * kk; idx += blockDim.x) Lc[idx] = Yh[idx];
-        __syncthreads();
+        ex.sync();
+        for (int idx = ex.tid(); idx < yr * kk; idx += ex.size()) Lc[idx] = Yh[idx];
+        ex.sync();
       }
-      logs += frob_rescale(Lc, yr * kk, sh.red);
+      logs += frob_rescale(ex, Lc, yr * kk);
       kc = kk;
       rdim = yr;
       ident = false;
     } else {
       // no reduction at this site's left bond (cur == bdo[c]): keep Y
-      for (int idx = threadIdx.x; idx < yr * yc; idx += blockDim.x) site[idx] = Yp[idx];
-      __syncthreads();
-      logs += rescale(site, yr * yc, sh.red);
+      for (int idx = ex.tid(); idx < yr * yc; idx += ex.size()) site[idx] = Yp[idx];
+      ex.sync();
+      logs += rescale(ex, site, yr * yc);
       ident = true;
     }
   }

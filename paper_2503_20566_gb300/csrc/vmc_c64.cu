@@ -21,4 +21,22 @@ int occupancy_vmc<cfloat>(int block, size_t smem) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, vmc_kernel<cfloat>, block, smem) != cudaSuccess) return 1;
   return n > 0 ? n : 1;
 }
+template <>
+cudaError_t launch_vmc_grouped<cfloat>(const KParams<cfloat>& k, int grid, int block, size_t smem,
+                                 cudaStream_t st) {
+  {
+    cudaError_t e = cudaFuncSetAttribute(vmc_kernel_grouped<cfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  vmc_kernel_grouped<cfloat><<<grid, block, smem, st>>>(k);
+  return cudaGetLastError();
+}
+template <>
+int occupancy_vmc_grouped<cfloat>(int block, size_t smem) {
+  if (cudaFuncSetAttribute(vmc_kernel_grouped<cfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, vmc_kernel_grouped<cfloat>, block, smem) != cudaSuccess) return 0;
+  return n;
+}
 }  // namespace gcf

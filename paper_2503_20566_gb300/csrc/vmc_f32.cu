@@ -21,4 +21,23 @@ int occupancy_vmc<float>(int block, size_t smem) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, vmc_kernel<float>, block, smem) != cudaSuccess) return 1;
   return n > 0 ? n : 1;
 }
+template <>
+cudaError_t launch_vmc_grouped<float>(const KParams<float>& k, int grid, int block, size_t smem,
+                                 cudaStream_t st) {
+  {
+    cudaError_t e = cudaFuncSetAttribute(vmc_kernel_grouped<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  vmc_kernel_grouped<float><<<grid, block, smem, st>>>(k);
+  return cudaGetLastError();
+}
+template <>
+int occupancy_vmc_grouped<float>(int block, size_t smem) {
+  if (cudaFuncSetAttribute(vmc_kernel_grouped<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, vmc_kernel_grouped<float>, block, smem) != cudaSuccess) return 0;
+  return n;
+}
+size_t sharedv_bytes() { return sizeof_sharedv_aligned(); }
 }  // namespace gcf

@@ -16,6 +16,8 @@
 
 namespace gcf {
 
+struct SharedV;
+__host__ __device__ constexpr unsigned long sizeof_sharedv_aligned();
 struct SharedV {
   Shared base;
   int offB[MAX_L + 1];
@@ -24,14 +26,19 @@ struct SharedV {
   int logT[MAX_L + 2];
   int logR[MAX_L + 2];   // of the right environments of the current pass
   double eacc[2];
-  int flag;
+  int flag, ok, bad;
   float redf[32];
   int n_acc, n_prop;
 };
 
-template <class T>
+__host__ __device__ constexpr unsigned long sizeof_sharedv_aligned() {
+  return (sizeof(SharedV) + 15) / 16 * 16;
+}
+
+template <class T, class X>
 struct Chain {
   using R = typename Traits<T>::R;
+  X ex;
   const KParams<T>& k;
   T* ws;
   SharedV& sv;
@@ -43,8 +50,8 @@ struct Chain {
   T* hot;
   T *eR, *e3R, *sB, *sT;  // right environments; staged MPS rows (or the slots)
 
-  __device__ Chain(const KParams<T>& kk, T* w, SharedV& s, int8_t* c, int ch, T* hot_)
-      : k(kk), ws(w), sv(s), cfg(c), chain(ch), hot(hot_) {
+  __device__ Chain(const X ex_, const KParams<T>& kk, T* w, SharedV& s, int8_t* c, int ch, T* hot_)
+      : ex(ex_), k(kk), ws(w), sv(s), cfg(c), chain(ch), hot(hot_) {
     key = stream_key(k.seed, (unsigned long long)ch);
     if (k.hot_in_smem) {
       net = hot_ + k.so_net; props = hot_ + k.so_prop; cop = hot_ + k.so_cop;
@@ -78,7 +85,7 @@ struct Chain {
 
   // ---- configuration moves on the shared copy (thread 0 writes) ---------
   __device__ void plaq_apply(int x, int y, int t) {
-    if (threadIdx.x == 0) {
+    if (ex.tid() == 0) {
       const int N = k.N;
       int8_t* h = cfg;
       int8_t* v = cfg + k.n_h;
@@ -87,14 +94,14 @@ struct Chain {
       h[(y + 1) * (k.Lx - 1) + x] = (int8_t)((h[(y + 1) * (k.Lx - 1) + x] - t + N) % N);
       v[y * k.Lx + x] = (int8_t)((v[y * k.Lx + x] - t + N) % N);
     }
-    __syncthreads();
+    ex.sync();
   }
   // Hop across link (x,a): returns 1 if a move exists (and applies it).
   // On a hard-core lattice the hop available after a hop is its inverse, so
   // calling this again reverts the move.
   __device__ int hop_apply(int x, int y, int a) {
-    __shared__ int ok;
-    if (threadIdx.x == 0) {
+    int& ok = sv.ok;
+    if (ex.tid() == 0) {
       const int N = k.N;
       const int x2 = a == 1 ? x + 1 : x, y2 = a == 1 ? y : y + 1;
       int8_t* p = cfg + k.n_h + k.n_v;
@@ -112,27 +119,27 @@ struct Chain {
         ok = 1;
       }
     }
-    __syncthreads();
+    ex.sync();
     const int r = ok;
-    __syncthreads();
+    ex.sync();
     return r;
   }
 
   __device__ __noinline__ void gather_into(int x, int y, T* dst) {
     const int bid = block_of(k, cfg, x, y);
     if (bid < 0) {
-      if (threadIdx.x == 0) atomicAdd(&k.status[ST_GAUSS], 1);
+      if (ex.tid() == 0) atomicAdd(&k.status[ST_GAUSS], 1);
       return;
     }
-    gather_box(k, x, y, bid, dst);
+    gather_box(ex, k, x, y, bid, dst);
   }
 
   // gather the selected blocks of n vertices (x[i], y[i]) into dst[i] in
   // parallel (thread groups per vertex); caller synchronises
   __device__ __noinline__ void gather_n(int n, const int* xs, const int* ys, T* const* dst) {
     const int D4 = k.Dk * k.Dk * k.Dk * k.Dk;
-    const int per = blockDim.x / n;
-    const int g = threadIdx.x / per, tl = threadIdx.x - g * per;
+    const int per = ex.size() / n;
+    const int g = ex.tid() / per, tl = ex.tid() - g * per;
     if (g < n) {
       const int x = xs[g], y = ys[g];
       const int bid = block_of(k, cfg, x, y);
@@ -172,36 +179,36 @@ struct Chain {
   }
 
   __device__ __noinline__ bool check_and_gather_all() {
-    __shared__ int bad;
-    if (threadIdx.x == 0) bad = 0;
-    __syncthreads();
-    for (int v = threadIdx.x; v < k.n_s; v += blockDim.x) {
+    int& bad = sv.bad;
+    if (ex.tid() == 0) bad = 0;
+    ex.sync();
+    for (int v = ex.tid(); v < k.n_s; v += ex.size()) {
       if (block_of(k, cfg, v % k.Lx, v / k.Lx) < 0) bad = 1;
     }
-    __syncthreads();
+    ex.sync();
     const bool ok = bad == 0;
-    __syncthreads();
+    ex.sync();
     if (!ok) return false;
     for (int y = 0; y < k.Ly; ++y)
-      for (int x = 0; x < k.Lx; ++x) gather_box(k, x, y, block_of(k, cfg, x, y), box(x, y));
-    __syncthreads();
+      for (int x = 0; x < k.Lx; ++x) gather_box(ex, k, x, y, block_of(k, cfg, x, y), box(x, y));
+    ex.sync();
     return true;
   }
 
   // ---- boundary MPS --------------------------------------------------------
   __device__ __noinline__ void absorb_B(int r) {  // B[r] = absorb(B[r-1], row r)
-    const int ls = absorb_compress(k, ws, hot, sv.base, net, Bslot(r), bdB(r), physB(r), r, 0, Bslot(r + 1),
+    const int ls = absorb_compress(ex, k, ws, hot, sv.base, net, Bslot(r), bdB(r), physB(r), r, 0, Bslot(r + 1),
                                       bdB(r + 1), physB(r + 1), k.qrB + r * (k.Lx + 1),
                                       k.svdB + r * (k.Lx + 1));
-    if (threadIdx.x == 0) sv.logB[r + 1] = sv.logB[r] + ls;
-    __syncthreads();
+    if (ex.tid() == 0) sv.logB[r + 1] = sv.logB[r] + ls;
+    ex.sync();
   }
   __device__ __noinline__ void absorb_T(int r) {  // T[r] = absorb(T[r+1], row r flipped)
-    const int ls = absorb_compress(k, ws, hot, sv.base, net, Tslot(r + 1), bdT(r + 1), physT(r + 1), r, 1,
+    const int ls = absorb_compress(ex, k, ws, hot, sv.base, net, Tslot(r + 1), bdT(r + 1), physT(r + 1), r, 1,
                                       Tslot(r), bdT(r), physT(r), k.qrT + r * (k.Lx + 1),
                                       k.svdT + r * (k.Lx + 1));
-    if (threadIdx.x == 0) sv.logT[r] = sv.logT[r + 1] + ls;
-    __syncthreads();
+    if (ex.tid() == 0) sv.logT[r] = sv.logT[r + 1] + ls;
+    ex.sync();
   }
 
   // ---- strip (rows r, r+1) between B[r-1] (slot r) and T[r+2] -------------
@@ -229,9 +236,9 @@ struct Chain {
     const T* t = Tslot(jt);
     if (sB) {
       const int nb = sv.offB[k.Lx], nt = sv.offT[k.Lx];
-      for (int i = threadIdx.x; i < nb; i += blockDim.x) sB[i] = b[i];
-      for (int i = threadIdx.x; i < nt; i += blockDim.x) sT[i] = t[i];
-      __syncthreads();
+      for (int i = ex.tid(); i < nb; i += ex.size()) sB[i] = b[i];
+      for (int i = ex.tid(); i < nt; i += ex.size()) sT[i] = t[i];
+      ex.sync();
       curB = sB;
       curT = sT;
     } else {
@@ -245,22 +252,22 @@ struct Chain {
   // as mantissa (vr, vi) and binary exponent ve
   __device__ __noinline__ void strip_right_envs(int r, R& vr, R& vi, int& ve) {
     const int Lx = k.Lx;
-    mps_offsets(bdB(r), physB(r), Lx, sv.offB);
-    mps_offsets(bdT(r + 2), physT(r + 2), Lx, sv.offT);
+    mps_offsets(ex, bdB(r), physB(r), Lx, sv.offB);
+    mps_offsets(ex, bdT(r + 2), physT(r + 2), Lx, sv.offT);
     stage(r, r + 2, physB(r), physT(r + 2));
-    if (threadIdx.x == 0) { envR(Lx)[0] = one<T>(); sv.logR[Lx] = 0; }
-    __syncthreads();
+    if (ex.tid() == 0) { envR(Lx)[0] = one<T>(); sv.logR[Lx] = 0; }
+    ex.sync();
     for (int c = Lx - 1; c >= 0; --c) {
       const SDims d = sdims(r, c);
       const int ls = sright(d, envR(c + 1), curB + sv.offB[c], box(c, r), box(c, r + 1),
                            curT + sv.offT[c], envR(c));
-      if (threadIdx.x == 0) sv.logR[c] = sv.logR[c + 1] + ls;
-      __syncthreads();
+      if (ex.tid() == 0) sv.logR[c] = sv.logR[c + 1] + ls;
+      ex.sync();
     }
     vr = re(envR(0)[0]);
     vi = im(envR(0)[0]);
     ve = sv.logR[0];
-    __syncthreads();
+    ex.sync();
   }
 
   __device__ __noinline__ int strip_step_left(int r, int c, const T* Lin, const T* W1, const T* W2, T* out) {
@@ -271,38 +278,38 @@ struct Chain {
   __device__ int sleft(const SDims& d, const T* L, const T* Bs, const T* W1, const T* W2, const T* Ts,
                          T* out) {
     switch (k.Dk) {
-      case 1: return strip_left<T, 1>(d, L, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
-      case 2: return strip_left<T, 2>(d, L, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
-      default: return strip_left<T, 3>(d, L, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
+      case 1: return strip_left<T, 1>(ex, d, L, Bs, W1, W2, Ts, out, t1, t2, cop);
+      case 2: return strip_left<T, 2>(ex, d, L, Bs, W1, W2, Ts, out, t1, t2, cop);
+      default: return strip_left<T, 3>(ex, d, L, Bs, W1, W2, Ts, out, t1, t2, cop);
     }
   }
   __device__ int sright(const SDims& d, const T* R2, const T* Bs, const T* W1, const T* W2, const T* Ts,
                           T* out) {
     switch (k.Dk) {
-      case 1: return strip_right<T, 1>(d, R2, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
-      case 2: return strip_right<T, 2>(d, R2, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
-      default: return strip_right<T, 3>(d, R2, Bs, W1, W2, Ts, out, t1, t2, cop, sv.redf);
+      case 1: return strip_right<T, 1>(ex, d, R2, Bs, W1, W2, Ts, out, t1, t2, cop);
+      case 2: return strip_right<T, 2>(ex, d, R2, Bs, W1, W2, Ts, out, t1, t2, cop);
+      default: return strip_right<T, 3>(ex, d, R2, Bs, W1, W2, Ts, out, t1, t2, cop);
     }
   }
   __device__ int rleft(const RDims& d, const T* L, const T* Bs, const T* W, const T* Ts, T* out) {
     switch (k.Dk) {
-      case 1: return row_left<T, 1>(d, L, Bs, W, Ts, out, t1, t2, sv.redf);
-      case 2: return row_left<T, 2>(d, L, Bs, W, Ts, out, t1, t2, sv.redf);
-      default: return row_left<T, 3>(d, L, Bs, W, Ts, out, t1, t2, sv.redf);
+      case 1: return row_left<T, 1>(ex, d, L, Bs, W, Ts, out, t1, t2);
+      case 2: return row_left<T, 2>(ex, d, L, Bs, W, Ts, out, t1, t2);
+      default: return row_left<T, 3>(ex, d, L, Bs, W, Ts, out, t1, t2);
     }
   }
   __device__ int rright(const RDims& d, const T* R2, const T* Bs, const T* W, const T* Ts, T* out) {
     switch (k.Dk) {
-      case 1: return row_right<T, 1>(d, R2, Bs, W, Ts, out, t1, t2, sv.redf);
-      case 2: return row_right<T, 2>(d, R2, Bs, W, Ts, out, t1, t2, sv.redf);
-      default: return row_right<T, 3>(d, R2, Bs, W, Ts, out, t1, t2, sv.redf);
+      case 1: return row_right<T, 1>(ex, d, R2, Bs, W, Ts, out, t1, t2);
+      case 2: return row_right<T, 2>(ex, d, R2, Bs, W, Ts, out, t1, t2);
+      default: return row_right<T, 3>(ex, d, R2, Bs, W, Ts, out, t1, t2);
     }
   }
   __device__ void ropen(const RDims& d, const T* L, const T* Bs, const T* Ts, const T* R2, T* G) {
     switch (k.Dk) {
-      case 1: row_open<T, 1>(d, L, Bs, Ts, R2, G, t1, t2, sv.redf); break;
-      case 2: row_open<T, 2>(d, L, Bs, Ts, R2, G, t1, t2, sv.redf); break;
-      default: row_open<T, 3>(d, L, Bs, Ts, R2, G, t1, t2, sv.redf); break;
+      case 1: row_open<T, 1>(ex, d, L, Bs, Ts, R2, G, t1, t2); break;
+      case 2: row_open<T, 2>(ex, d, L, Bs, Ts, R2, G, t1, t2); break;
+      default: row_open<T, 3>(ex, d, L, Bs, Ts, R2, G, t1, t2); break;
     }
   }
 
@@ -320,21 +327,21 @@ struct Chain {
 
   __device__ __noinline__ void row_right_envs(int r, R& vr, R& vi, int& ve) {
     const int Lx = k.Lx;
-    mps_offsets(bdB(r), physB(r), Lx, sv.offB);
-    mps_offsets(bdT(r + 1), physT(r + 1), Lx, sv.offT);
+    mps_offsets(ex, bdB(r), physB(r), Lx, sv.offB);
+    mps_offsets(ex, bdT(r + 1), physT(r + 1), Lx, sv.offT);
     stage(r, r + 1, physB(r), physT(r + 1));
-    if (threadIdx.x == 0) { env3R(Lx)[0] = one<T>(); sv.logR[Lx] = 0; }
-    __syncthreads();
+    if (ex.tid() == 0) { env3R(Lx)[0] = one<T>(); sv.logR[Lx] = 0; }
+    ex.sync();
     for (int c = Lx - 1; c >= 0; --c) {
       const RDims d = rdims(r, c);
       const int ls = rright(d, env3R(c + 1), curB + sv.offB[c], box(c, r), curT + sv.offT[c], env3R(c));
-      if (threadIdx.x == 0) sv.logR[c] = sv.logR[c + 1] + ls;
-      __syncthreads();
+      if (ex.tid() == 0) sv.logR[c] = sv.logR[c + 1] + ls;
+      ex.sync();
     }
     vr = re(env3R(0)[0]);
     vi = im(env3R(0)[0]);
     ve = sv.logR[0];
-    __syncthreads();
+    ex.sync();
   }
 
   __device__ __noinline__ int row_step_left(int r, int c, const T* Lin, const T* W, T* out) {
@@ -346,7 +353,7 @@ struct Chain {
   // den = (dr + i di) 2^de and num = (nr + i ni) 2^ne; evaluated once on
   // thread 0 (exact powers of two, no logarithms) and broadcast.
   __device__ bool metro_accept(double u, R dr, R di, int de, R nr, R ni, int ne) {
-    if (threadIdx.x == 0) {
+    if (ex.tid() == 0) {
       const double d2 = (double)dr * dr + (double)di * di;
       const double n2 = (double)nr * nr + (double)ni * ni;
       bool acc;
@@ -355,14 +362,14 @@ struct Chain {
       else acc = u * d2 < ldexp(n2, 2 * (ne - de));
       sv.flag = acc ? 1 : 0;
     }
-    __syncthreads();
+    ex.sync();
     const bool a = sv.flag != 0;
-    __syncthreads();
+    ex.sync();
     return a;
   }
   // eacc += coef * num / den (thread 0)
   __device__ void add_ratio(double coef, R nr, R ni, int ne, R dr, R di, int de) {
-    if (threadIdx.x == 0) {
+    if (ex.tid() == 0) {
       const double d2 = (double)dr * dr + (double)di * di;
       const double f = ldexp(1.0, ne - de) / d2;
       const double rr = ((double)nr * dr + (double)ni * di) * f;
@@ -382,9 +389,9 @@ struct Chain {
   }
 };
 
-template <class T>
-__device__ void copy_box(T* dst, const T* src, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+template <class T, class X>
+__device__ void copy_box(const X ex, T* dst, const T* src, int n) {
+  for (int i = ex.tid(); i < n; i += ex.size()) dst[i] = src[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -392,8 +399,9 @@ __device__ void copy_box(T* dst, const T* src, int n) {
 // ---------------------------------------------------------------------------
 
 // plaquette pass, bottom-up, Metropolis (Sec. S-1 rule, Sec. S-2 moves)
-template <class T>
-__device__ __noinline__ void plaquette_pass(Chain<T>& ch, int w) {
+template <class T, class X>
+__device__ __noinline__ void plaquette_pass(Chain<T, X>& ch, int w) {
+  const X ex = ch.ex;
   using R = typename Traits<T>::R;
   const KParams<T>& k = ch.k;
   const int Lx = k.Lx, Ly = k.Ly, D4 = k.Dk * k.Dk * k.Dk * k.Dk;
@@ -404,8 +412,8 @@ __device__ __noinline__ void plaquette_pass(Chain<T>& ch, int w) {
     R dr, di;
     int de;
     ch.strip_right_envs(r, dr, di, de);
-    if (threadIdx.x == 0) Lc[0] = one<T>();
-    __syncthreads();
+    if (ex.tid() == 0) Lc[0] = one<T>();
+    ex.sync();
     int eL = 0;
     for (int c = 0; c < Lx - 1; ++c) {
       const int j = r * (Lx - 1) + c;
@@ -414,40 +422,41 @@ __device__ __noinline__ void plaquette_pass(Chain<T>& ch, int w) {
       const double u = ch.uniform_at(base + 2 * j + 1);
       ch.plaq_apply(c, r, t);
       ch.gather_plaq(c, r);
-      __syncthreads();
+      ex.sync();
       const int l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
       const int l2 = ch.strip_step_left(r, c + 1, X1, ch.prop(1), ch.prop(3), X2);
       R nr, ni;
       const SDims d2 = ch.sdims(r, c + 1);
-      cta_dot(X2, ch.envR(c + 2), ch.env_size(d2, true), ch.sv.base.red, nr, ni);
+      cta_dot(ex, X2, ch.envR(c + 2), ch.env_size(d2, true), nr, ni);
       const int ne = eL + l1 + l2 + ch.sv.logR[c + 2];
       const bool acc = ch.metro_accept(u, dr, di, de, nr, ni, ne);
-      if (threadIdx.x == 0) { ch.sv.n_prop += 1; if (acc) ch.sv.n_acc += 1; }
+      if (ex.tid() == 0) { ch.sv.n_prop += 1; if (acc) ch.sv.n_acc += 1; }
       const SDims d1 = ch.sdims(r, c);
       const int n1 = ch.env_size(d1, true);
       if (acc) {
-        copy_box(ch.box(c, r), ch.prop(0), D4);
-        copy_box(ch.box(c + 1, r), ch.prop(1), D4);
-        copy_box(ch.box(c, r + 1), ch.prop(2), D4);
-        copy_box(ch.box(c + 1, r + 1), ch.prop(3), D4);
+        copy_box(ex, ch.box(c, r), ch.prop(0), D4);
+        copy_box(ex, ch.box(c + 1, r), ch.prop(1), D4);
+        copy_box(ex, ch.box(c, r + 1), ch.prop(2), D4);
+        copy_box(ex, ch.box(c + 1, r + 1), ch.prop(3), D4);
         dr = nr; di = ni; de = ne;
         // L_{c+1} is X1 (built from the accepted column c)
-        for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
+        for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = X1[i];
         eL += l1;
       } else {
         ch.plaq_apply(c, r, k.N - t);  // revert
         eL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), X1);
-        for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
+        for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = X1[i];
       }
-      __syncthreads();
+      ex.sync();
     }
     ch.absorb_B(r);
   }
 }
 
 // horizontal-hop pass (matter), top-down with row environments
-template <class T>
-__device__ __noinline__ void hhop_pass(Chain<T>& ch, int w) {
+template <class T, class X>
+__device__ __noinline__ void hhop_pass(Chain<T, X>& ch, int w) {
+  const X ex = ch.ex;
   using R = typename Traits<T>::R;
   const KParams<T>& k = ch.k;
   const int Lx = k.Lx, Ly = k.Ly, D4 = k.Dk * k.Dk * k.Dk * k.Dk;
@@ -458,8 +467,8 @@ __device__ __noinline__ void hhop_pass(Chain<T>& ch, int w) {
     R dr, di;
     int de;
     ch.row_right_envs(r, dr, di, de);
-    if (threadIdx.x == 0) Lc[0] = one<T>();
-    __syncthreads();
+    if (ex.tid() == 0) Lc[0] = one<T>();
+    ex.sync();
     int eL = 0;
     for (int c = 0; c < Lx - 1; ++c) {
       const unsigned long long ctr =
@@ -469,42 +478,43 @@ __device__ __noinline__ void hhop_pass(Chain<T>& ch, int w) {
       int l1 = 0;
       if (ch.hop_apply(c, r, 1)) {
         ch.gather_pair(c, r, ch.prop(0), c + 1, r, ch.prop(1));
-        __syncthreads();
+        ex.sync();
         l1 = ch.row_step_left(r, c, Lc, ch.prop(0), X1);
         const int l2 = ch.row_step_left(r, c + 1, X1, ch.prop(1), X2);
         R nr, ni;
         const RDims d2 = ch.rdims(r, c + 1);
-        cta_dot(X2, ch.env3R(c + 2), d2.nA2 * d2.nH2 * d2.nB2, ch.sv.base.red, nr, ni);
+        cta_dot(ex, X2, ch.env3R(c + 2), d2.nA2 * d2.nH2 * d2.nB2, nr, ni);
         const int ne = eL + l1 + l2 + ch.sv.logR[c + 2];
         acc = ch.metro_accept(u, dr, di, de, nr, ni, ne);
-        if (threadIdx.x == 0) { ch.sv.n_prop += 1; if (acc) ch.sv.n_acc += 1; }
+        if (ex.tid() == 0) { ch.sv.n_prop += 1; if (acc) ch.sv.n_acc += 1; }
         if (acc) {
-          copy_box(ch.box(c, r), ch.prop(0), D4);
-          copy_box(ch.box(c + 1, r), ch.prop(1), D4);
+          copy_box(ex, ch.box(c, r), ch.prop(0), D4);
+          copy_box(ex, ch.box(c + 1, r), ch.prop(1), D4);
           dr = nr; di = ni; de = ne;
         } else {
           ch.hop_apply(c, r, 1);
         }
       }
-      __syncthreads();
+      ex.sync();
       const RDims d1 = ch.rdims(r, c);
       const int n1 = d1.nA2 * d1.nH2 * d1.nB2;
       if (acc) {
-        for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
+        for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = X1[i];
         eL += l1;
       } else {
         eL += ch.row_step_left(r, c, Lc, ch.box(c, r), X1);
-        for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
+        for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = X1[i];
       }
-      __syncthreads();
+      ex.sync();
     }
     if (r >= 1) ch.absorb_T(r);
   }
 }
 
 // vertical-hop pass (matter), bottom-up with strip environments
-template <class T>
-__device__ __noinline__ void vhop_pass(Chain<T>& ch, int w) {
+template <class T, class X>
+__device__ __noinline__ void vhop_pass(Chain<T, X>& ch, int w) {
+  const X ex = ch.ex;
   using R = typename Traits<T>::R;
   const KParams<T>& k = ch.k;
   const int Lx = k.Lx, Ly = k.Ly, D4 = k.Dk * k.Dk * k.Dk * k.Dk;
@@ -515,8 +525,8 @@ __device__ __noinline__ void vhop_pass(Chain<T>& ch, int w) {
     R dr, di;
     int de;
     ch.strip_right_envs(r, dr, di, de);
-    if (threadIdx.x == 0) Lc[0] = one<T>();
-    __syncthreads();
+    if (ex.tid() == 0) Lc[0] = one<T>();
+    ex.sync();
     int eL = 0;
     for (int c = 0; c < Lx; ++c) {
       const unsigned long long ctr =
@@ -526,49 +536,50 @@ __device__ __noinline__ void vhop_pass(Chain<T>& ch, int w) {
       int l1 = 0;
       if (ch.hop_apply(c, r, 2)) {
         ch.gather_pair(c, r, ch.prop(0), c, r + 1, ch.prop(2));
-        __syncthreads();
+        ex.sync();
         l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
         R nr, ni;
         const SDims d1 = ch.sdims(r, c);
-        cta_dot(X1, ch.envR(c + 1), ch.env_size(d1, true), ch.sv.base.red, nr, ni);
+        cta_dot(ex, X1, ch.envR(c + 1), ch.env_size(d1, true), nr, ni);
         const int ne = eL + l1 + ch.sv.logR[c + 1];
         acc = ch.metro_accept(u, dr, di, de, nr, ni, ne);
-        if (threadIdx.x == 0) { ch.sv.n_prop += 1; if (acc) ch.sv.n_acc += 1; }
+        if (ex.tid() == 0) { ch.sv.n_prop += 1; if (acc) ch.sv.n_acc += 1; }
         if (acc) {
-          copy_box(ch.box(c, r), ch.prop(0), D4);
-          copy_box(ch.box(c, r + 1), ch.prop(2), D4);
+          copy_box(ex, ch.box(c, r), ch.prop(0), D4);
+          copy_box(ex, ch.box(c, r + 1), ch.prop(2), D4);
           dr = nr; di = ni; de = ne;
         } else {
           ch.hop_apply(c, r, 2);
         }
       }
-      __syncthreads();
+      ex.sync();
       const SDims d1 = ch.sdims(r, c);
       const int n1 = ch.env_size(d1, true);
       if (acc) {
-        for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
+        for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = X1[i];
         eL += l1;
       } else {
         eL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), Lnext);
-        for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = Lnext[i];
+        for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = Lnext[i];
       }
-      __syncthreads();
+      ex.sync();
     }
     ch.absorb_B(r);
   }
 }
 
 // measurement pass, top-down; writes sample s
-template <class T>
-__device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
+template <class T, class X>
+__device__ __noinline__ void measure_pass(Chain<T, X>& ch, long long s) {
+  const X ex = ch.ex;
   using R = typename Traits<T>::R;
   const KParams<T>& k = ch.k;
   const int Lx = k.Lx, Ly = k.Ly, Dk = k.Dk, D4 = Dk * Dk * Dk * Dk;
   const bool want_e = (k.want & WANT_ELOC) && k.e_loc;
   const bool want_g = (k.want & WANT_GRAD) && (k.O || k.block_ids);
   const bool want_a = (k.want & WANT_AMP) && (k.log_abs || k.phase);
-  if (threadIdx.x == 0) { ch.sv.eacc[0] = 0.0; ch.sv.eacc[1] = 0.0; }
-  __syncthreads();
+  if (ex.tid() == 0) { ch.sv.eacc[0] = 0.0; ch.sv.eacc[1] = 0.0; }
+  ex.sync();
   for (int r = Ly - 1; r >= 0; --r) {
     // ---- row r: gradient, horizontal hops, amplitude
     const bool need_row = want_g || (r == Ly - 1 && want_a) || (want_e && k.matter && k.J != 0.0);
@@ -576,7 +587,7 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
       R dr, di;
       int de;
       ch.row_right_envs(r, dr, di, de);
-      if (r == Ly - 1 && want_a && threadIdx.x == 0) {
+      if (r == Ly - 1 && want_a && ex.tid() == 0) {
         // psi = <B[Ly-2] | row Ly-1> = (dr + i di) 2^(de + e_B)
         const double a2 = (double)dr * dr + (double)di * di;
         const double ln2 = 0.69314718055994530942;
@@ -587,8 +598,8 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
       T* Lc = ch.env3L;
       T* X1 = ch.env3X;
       T* X2 = ch.env3Y;
-      if (threadIdx.x == 0) Lc[0] = one<T>();
-      __syncthreads();
+      if (ex.tid() == 0) Lc[0] = one<T>();
+      ex.sync();
       int eL = 0;
       const R den2 = dr * dr + di * di;
       for (int c = 0; c < Lx; ++c) {
@@ -603,19 +614,19 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
           const int n = d.nH * d.nH2 * d.pB * d.pT;
           if (k.O) {
             T* dst = k.O + (s * k.n_s + v) * (long long)D4;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = G[i] * fac;
+            for (int i = ex.tid(); i < n; i += ex.size()) dst[i] = G[i] * fac;
           }
-          if (k.block_ids && threadIdx.x == 0) k.block_ids[s * k.n_s + v] = block_of(k, ch.cfg, c, r);
+          if (k.block_ids && ex.tid() == 0) k.block_ids[s * k.n_s + v] = block_of(k, ch.cfg, c, r);
         }
         if (want_e && k.matter && k.J != 0.0 && c < Lx - 1) {
           if (ch.hop_apply(c, r, 1)) {
             ch.gather_pair(c, r, ch.prop(0), c + 1, r, ch.prop(1));
-            __syncthreads();
+            ex.sync();
             const int l1 = ch.row_step_left(r, c, Lc, ch.prop(0), X1);
             const int l2 = ch.row_step_left(r, c + 1, X1, ch.prop(1), X2);
             R nr, ni;
             const RDims d2 = ch.rdims(r, c + 1);
-            cta_dot(X2, ch.env3R(c + 2), d2.nA2 * d2.nH2 * d2.nB2, ch.sv.base.red, nr, ni);
+            cta_dot(ex, X2, ch.env3R(c + 2), d2.nA2 * d2.nH2 * d2.nB2, nr, ni);
             ch.add_ratio(k.J, nr, ni, eL + l1 + l2 + ch.sv.logR[c + 2], dr, di, de);
             ch.hop_apply(c, r, 1);
           }
@@ -623,8 +634,8 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
         if (c < Lx - 1) {
           eL += ch.row_step_left(r, c, Lc, ch.box(c, r), X1);
           const int n1 = d.nA2 * d.nH2 * d.nB2;
-          for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
-          __syncthreads();
+          for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = X1[i];
+          ex.sync();
         }
       }
     }
@@ -636,8 +647,8 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
       T* Lc = ch.envL;
       T* X1 = ch.envX;
       T* X2 = ch.envY;
-      if (threadIdx.x == 0) Lc[0] = one<T>();
-      __syncthreads();
+      if (ex.tid() == 0) Lc[0] = one<T>();
+      ex.sync();
       int eL = 0;
       const int npow = k.N == 2 ? 1 : 2;
       const double amp = k.N == 2 ? -2.0 * k.h : -k.h;
@@ -647,12 +658,12 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
             const int t = q == 0 ? 1 : k.N - 1;
             ch.plaq_apply(c, r, t);
             ch.gather_plaq(c, r);
-            __syncthreads();
+            ex.sync();
             const int l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
             const int l2 = ch.strip_step_left(r, c + 1, X1, ch.prop(1), ch.prop(3), X2);
             R nr, ni;
             const SDims d2 = ch.sdims(r, c + 1);
-            cta_dot(X2, ch.envR(c + 2), ch.env_size(d2, true), ch.sv.base.red, nr, ni);
+            cta_dot(ex, X2, ch.envR(c + 2), ch.env_size(d2, true), nr, ni);
             ch.add_ratio(amp, nr, ni, eL + l1 + l2 + ch.sv.logR[c + 2], dr, di, de);
             ch.plaq_apply(c, r, k.N - t);
           }
@@ -660,11 +671,11 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
         if (k.matter && k.J != 0.0) {
           if (ch.hop_apply(c, r, 2)) {
             ch.gather_pair(c, r, ch.prop(0), c, r + 1, ch.prop(2));
-            __syncthreads();
+            ex.sync();
             const int l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
             R nr, ni;
             const SDims d1 = ch.sdims(r, c);
-            cta_dot(X1, ch.envR(c + 1), ch.env_size(d1, true), ch.sv.base.red, nr, ni);
+            cta_dot(ex, X1, ch.envR(c + 1), ch.env_size(d1, true), nr, ni);
             ch.add_ratio(k.J, nr, ni, eL + l1 + ch.sv.logR[c + 1], dr, di, de);
             ch.hop_apply(c, r, 2);
           }
@@ -673,15 +684,15 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
           const SDims d1 = ch.sdims(r, c);
           eL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), X1);
           const int n1 = ch.env_size(d1, true);
-          for (int i = threadIdx.x; i < n1; i += blockDim.x) Lc[i] = X1[i];
-          __syncthreads();
+          for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = X1[i];
+          ex.sync();
         }
       }
     }
     // ---- T[r]
     if (r >= 1 && (k.mode == 1 || want_e || want_g)) ch.absorb_T(r);
   }
-  if (want_e && threadIdx.x == 0) {
+  if (want_e && ex.tid() == 0) {
     // diagonal part: g sum_links (2 - 2 cos(2 pi n / N)) (table) + m sum_x p_x
     double e = 0.0;
     for (int i = 0; i < k.n_h + k.n_v; ++i) e += k.elink[ch.cfg[i]];
@@ -690,70 +701,102 @@ __device__ __noinline__ void measure_pass(Chain<T>& ch, long long s) {
     k.e_loc[2 * s] = e + ch.sv.eacc[0];
     k.e_loc[2 * s + 1] = ch.sv.eacc[1];
   }
-  __syncthreads();
+  ex.sync();
 }
 
-template <class T>
-__device__ void init_trivial_slots(const KParams<T>& k, T* ws) {
-  for (int c = threadIdx.x; c < k.Lx; c += blockDim.x) {
+template <class T, class X>
+__device__ void init_trivial_slots(const X ex, const KParams<T>& k, T* ws) {
+  for (int c = ex.tid(); c < k.Lx; c += ex.size()) {
     (ws + k.o_B)[c] = one<T>();                                     // B[-1]
     (ws + k.o_T + (long long)k.Ly * k.mps_stride)[c] = one<T>();    // T[Ly]
   }
-  __syncthreads();
+  ex.sync();
 }
 
+// Per-chain body shared by both kernels.
+template <class T, class X>
+__device__ void run_chain(const X ex, const KParams<T>& k, T* ws, SharedV& sv, int8_t* cfg, T* hot,
+                          int chain) {
+  int8_t* gcfg = k.configs + (long long)chain * k.cfg_len;
+  for (int i = ex.tid(); i < k.cfg_len; i += ex.size()) cfg[i] = gcfg[i];
+  if (ex.leader()) {
+    sv.logB[0] = 0; sv.logT[k.Ly] = 0; sv.n_acc = 0; sv.n_prop = 0;
+  }
+  ex.sync();
+  Chain<T, X> ch(ex, k, ws, sv, cfg, chain, hot);
+  const bool ok = ch.check_and_gather_all();
+  if (!ok) {
+    if (ex.leader()) {
+      atomicAdd(&k.status[ST_GAUSS], 1);
+      const int ns = k.mode == 1 ? k.n_sweeps : 1;
+      for (int w = 0; w < ns; ++w) {
+        const long long s = (long long)chain * ns + w;
+        if (k.log_abs) k.log_abs[s] = -INFINITY;
+        if (k.phase) k.phase[s] = 0.0;
+        if (k.e_loc) { k.e_loc[2 * s] = NAN; k.e_loc[2 * s + 1] = NAN; }
+      }
+    }
+    ex.sync();
+    return;
+  }
+  if (k.mode == 0) {
+    for (int r = 0; r < k.Ly - 1; ++r) ch.absorb_B(r);
+    measure_pass(ch, (long long)chain);
+  } else {
+    for (int r = k.Ly - 1; r >= 2; --r) ch.absorb_T(r);
+    for (int w = 0; w < k.n_sweeps; ++w) {
+      plaquette_pass(ch, w);
+      if (k.matter) {
+        hhop_pass(ch, w);
+        vhop_pass(ch, w);
+      }
+      measure_pass(ch, (long long)chain * k.n_sweeps + w);
+    }
+    for (int i = ex.tid(); i < k.cfg_len; i += ex.size()) gcfg[i] = cfg[i];
+    if (ex.leader()) {
+      if (k.accepted) k.accepted[chain] = sv.n_acc;
+      if (k.proposed) k.proposed[chain] = sv.n_prop;
+    }
+  }
+  ex.sync();
+}
+
+// One CTA per chain (any size; the general form).
 template <class T>
 __global__ void __launch_bounds__(256, 2) vmc_kernel(KParams<T> k) {
   extern __shared__ __align__(16) int8_t dyn_smem[];
   int8_t* dyn_cfg = dyn_smem;
   T* hot = (T*)(dyn_smem + k.smem_cfg_bytes);
   __shared__ SharedV sv;
-  T* ws = ws_of(k);
-  init_trivial_slots(k, ws);
-  for (int chain = blockIdx.x; chain < k.n_chains; chain += gridDim.x) {
-    int8_t* gcfg = k.configs + (long long)chain * k.cfg_len;
-    for (int i = threadIdx.x; i < k.cfg_len; i += blockDim.x) dyn_cfg[i] = gcfg[i];
-    if (threadIdx.x == 0) {
-      sv.logB[0] = 0; sv.logT[k.Ly] = 0; sv.n_acc = 0; sv.n_prop = 0;
-    }
-    __syncthreads();
-    Chain<T> ch(k, ws, sv, dyn_cfg, chain, hot);
-    const bool ok = ch.check_and_gather_all();
-    if (!ok) {
-      if (threadIdx.x == 0) {
-        atomicAdd(&k.status[ST_GAUSS], 1);
-        const int ns = k.mode == 1 ? k.n_sweeps : 1;
-        for (int w = 0; w < ns; ++w) {
-          const long long s = (long long)chain * ns + w;
-          if (k.log_abs) k.log_abs[s] = -INFINITY;
-          if (k.phase) k.phase[s] = 0.0;
-          if (k.e_loc) { k.e_loc[2 * s] = NAN; k.e_loc[2 * s + 1] = NAN; }
-        }
-      }
-      __syncthreads();
-      continue;
-    }
-    if (k.mode == 0) {
-      for (int r = 0; r < k.Ly - 1; ++r) ch.absorb_B(r);
-      measure_pass(ch, (long long)chain);
-    } else {
-      for (int r = k.Ly - 1; r >= 2; --r) ch.absorb_T(r);
-      for (int w = 0; w < k.n_sweeps; ++w) {
-        plaquette_pass(ch, w);
-        if (k.matter) {
-          hhop_pass(ch, w);
-          vhop_pass(ch, w);
-        }
-        measure_pass(ch, (long long)chain * k.n_sweeps + w);
-      }
-      for (int i = threadIdx.x; i < k.cfg_len; i += blockDim.x) gcfg[i] = dyn_cfg[i];
-      if (threadIdx.x == 0) {
-        if (k.accepted) k.accepted[chain] = sv.n_acc;
-        if (k.proposed) k.proposed[chain] = sv.n_prop;
-      }
-    }
-    __syncthreads();
-  }
+  CtaExec ex;
+  T* ws = k.scratch + (long long)blockIdx.x * k.ws_stride;
+  init_trivial_slots(ex, k, ws);
+  for (int chain = blockIdx.x; chain < k.n_chains; chain += gridDim.x)
+    run_chain(ex, k, ws, sv, dyn_cfg, hot, chain);
+}
+
+// Several chains per CTA, one per group of G = 128 threads (GroupExec, a
+// hardware barrier per group).  Groups never wait on one another.  Dynamic
+// shared memory per group: [SharedV][configuration][hot buffers].
+template <class T, class X, int G>
+__device__ void grouped_body(const KParams<T>& k) {
+  extern __shared__ __align__(16) int8_t dyn_smem[];
+  const int g = threadIdx.x / G, NG = blockDim.x / G;
+  int8_t* base = dyn_smem + g * k.group_smem_bytes;
+  SharedV& sv = *reinterpret_cast<SharedV*>(base);
+  int8_t* cfg = base + sizeof_sharedv_aligned();
+  T* hot = (T*)(cfg + k.smem_cfg_bytes);
+  X ex;
+  const long long slot = (long long)blockIdx.x * NG + g;
+  T* ws = k.scratch + slot * k.ws_stride;
+  init_trivial_slots(ex, k, ws);
+  for (long long chain = slot; chain < k.n_chains; chain += (long long)gridDim.x * NG)
+    run_chain(ex, k, ws, sv, cfg, hot, (int)chain);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256, 2) vmc_kernel_grouped(KParams<T> k) {
+  grouped_body<T, GroupExec<128>, 128>(k);
 }
 
 }  // namespace gcf

@@ -1,0 +1,60 @@
+"""Both executors of the sampling kernel give the oracle's results.
+
+The library runs a chain either on a whole CTA or on one of two 128-thread
+groups of a CTA (the default when the group's hot buffers fit in shared
+memory).  GCFVMC_EXEC forces one or the other at context creation; each
+setting is checked against the FP64 oracle on the same seeded inputs, with
+the amplitude and a replayed Markov chain.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import vmc
+
+from gpu_helpers import TOL, amp_err, configs_for, setup
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+CASES = [
+    (8, 8, 2, 4, 16, False, False, "fp32"),  # the 8x8 Z2 D=4 chi=16 workload shape
+    (3, 7, 3, 6, 4, True, False, "fp32"),    # Z3 complex, ragged, truncated
+    (4, 3, 2, 4, 4, False, True, "fp32"),    # Z2 + hard-core bosons
+]
+
+
+def _ids(c):
+    return "{}x{}-Z{}-D{}-chi{}{}{}".format(c[0], c[1], c[2], c[3], c[4], "-c" if c[5] else "", "-m" if c[6] else "")
+
+
+@pytest.mark.parametrize("executor", ["cta", "group"])
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+def test_executor_amplitude_and_chain(case, executor, monkeypatch):
+    monkeypatch.setenv("GCFVMC_EXEC", executor)
+    monkeypatch.setenv("GCFVMC_GROUP_HOT", "1" if executor == "group" else "0")
+    Lx, Ly, N, D, chi, cplx, matter, prec = case
+    h, g, J = 1.0, 0.4, (0.5 if matter else 0.0)
+    lat, pe, ctx = setup(Lx, Ly, N, D, chi, seed=61, complex_=cplx, matter=matter, precision=prec, h=h, g=g, J=J)
+    nb = (Lx * Ly) // 2 if matter else 0
+    # amplitudes of independent configurations
+    cfgs, _, _ = configs_for(lat, 12, seed=62, n_bosons=nb)
+    la, ph = ctx.amplitude(torch.from_numpy(cfgs).cuda())
+    la, ph = la.cpu().numpy(), ph.cpu().numpy()
+    for i in range(len(cfgs)):
+        ref = vmc.amplitude(pe, cfgs[i], chi)
+        assert amp_err(la[i], ph[i], ref[0], ref[1]) < TOL[prec], i
+    # a short chain, replayed by the oracle
+    n_chains, n_sweeps = 3, 2
+    dev = torch.from_numpy(cfgs[:n_chains].copy()).cuda()
+    out = ctx.sample_batch(dev, n_sweeps, seed=4242)
+    torch.cuda.synchronize()
+    la = out["log_abs"].cpu().numpy()
+    final = dev.cpu().numpy()
+    model = vmc.Model(h=h, g=g, J=J)
+    for c in range(n_chains):
+        recs = vmc.run_chain(pe, model, cfgs[c], chi, 4242, c, n_sweeps, measure=True)
+        assert np.array_equal(final[c], recs[-1]["cfg"].astype(np.int8)), c
+        for w, rec in enumerate(recs):
+            assert amp_err(la[c * n_sweeps + w], 0.0, rec["log_abs"], 0.0) < TOL[prec] * 10
