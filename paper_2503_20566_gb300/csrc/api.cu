@@ -30,20 +30,20 @@ struct Plan {
   long long ws_stride = 0;
   long long o_net, o_prop, o_B, o_T, o_Q, o_M1, o_M2, o_M3, o_tau, o_J, o_envR, o_envL, o_envX,
       o_envY, o_t1, o_t2, o_t3, o_env3R, o_env3L, o_env3X, o_env3Y, o_G;
-  // hot buffers in dynamic shared memory (elements from the hot base)
-  int hot_in_smem = 0;
+  // buffers in dynamic shared memory (elements from the hot base)
   long long o_sigma = 0, o_sel = 0;
-  int env_in_smem = 0;
   long long so_envR = 0, so_env3R = 0, so_sB = 0, so_sT = 0;
   long long o_Z = 0, z_size = 0, q_pack = 0, o_X = 0, o_W1 = 0, o_W2 = 0, o_W3 = 0, o_W4 = 0;
   long long so_net, so_prop, so_cop, so_envL, so_envX, so_envY, so_env3L, so_env3X, so_env3Y, so_t1,
       so_t2, hot_elems = 0, cfg_bytes = 0;
   size_t dyn_smem = 0;
-  // grouped kernel: hot buffers (without the right environments) per chain
-  // group in shared memory when group_hot_in_smem
-  long long hot_base_elems = 0;
-  int group_hot_in_smem = 0;
+  // shared-memory placement levels of the two kernel forms (see plan_group)
+  long long hot_base_elems = 0, hot_mps_elems = 0, hot_all_elems = 0;
+  int cta_level = 0, group_level = 0;
   size_t group_smem = 0;
+  long long level_elems(int lv) const {
+    return lv <= 0 ? 0 : lv == 1 ? hot_base_elems : lv == 2 ? hot_mps_elems : hot_all_elems;
+  }
 };
 
 }  // namespace
@@ -130,21 +130,24 @@ void plan_step(int Lx, int Dk, int chi, int pout, const int* bin, int* qr, int* 
 
 // Executor for the sampling / measurement kernel: the whole CTA on one chain,
 // or two chains per CTA on groups of 128 threads.  Groups halve the threads
-// that wait at each barrier but need their own hot buffers; they are the
+// that wait at each barrier but need their own shared buffers; they are the
 // default when two groups' hot buffers fit in shared memory next to a second
-// CTA.  GCFVMC_EXEC=cta|group and GCFVMC_GROUP_HOT=0|1 override the choice.
+// CTA.  GCFVMC_EXEC=cta|group and GCFVMC_SMEM / GCFVMC_SMEM_CTA (placement
+// level 0-3) override the choice.
 enum ExecKind { EXEC_CTA = 0, EXEC_GROUP = 1 };
 
 void plan_group(gcf_ctx* c) {
   Plan& p = c->plan;
   const int G = 128, NG = 256 / G;
   c->group_threads = G;
-  const size_t hot = (size_t)p.hot_base_elems * c->sbytes;
   const size_t base = sharedv_bytes() + (size_t)p.cfg_bytes;
-  p.group_hot_in_smem = (size_t)NG * (base + hot) <= 110 * 1024 ? 1 : 0;
-  if (const char* e = std::getenv("GCFVMC_GROUP_HOT")) p.group_hot_in_smem = std::atoi(e) ? 1 : 0;
-  p.group_smem = (base + (p.group_hot_in_smem ? hot : 0) + 15) / 16 * 16;
-  c->exec = p.group_hot_in_smem ? EXEC_GROUP : EXEC_CTA;
+  // the largest level whose two groups fit next to a second CTA
+  p.group_level = 0;
+  for (int lv = 1; lv <= 3; ++lv)
+    if ((size_t)NG * (base + (size_t)p.level_elems(lv) * c->sbytes) <= 110 * 1024) p.group_level = lv;
+  if (const char* e = std::getenv("GCFVMC_SMEM")) p.group_level = std::max(0, std::min(3, std::atoi(e)));
+  p.group_smem = (base + (size_t)p.level_elems(p.group_level) * c->sbytes + 15) / 16 * 16;
+  c->exec = p.group_level >= 1 ? EXEC_GROUP : EXEC_CTA;
   if (const char* e = std::getenv("GCFVMC_EXEC")) {
     if (!std::strcmp(e, "group")) c->exec = EXEC_GROUP;
     if (!std::strcmp(e, "cta")) c->exec = EXEC_CTA;
@@ -334,23 +337,23 @@ void build_plan(gcf_ctx* c) {
   p.so_t1 = hot(p.tmp_max);
   p.so_t2 = hot(p.tmp_max);
   p.cfg_bytes = (c->cfg_len + 15) / 16 * 16;
-  const size_t budget = 100 * 1024;
-  const long long h_base = h;
-  p.hot_base_elems = h_base;
-  p.so_envR = hot((long long)(Lx + 1) * p.env_stride);
-  p.so_env3R = hot((long long)(Lx + 1) * p.env3_stride);
+  // shared-memory placement levels: 1 = hot buffers, 2 = + the staged B / T
+  // rows of the current pass, 3 = + the right environments of the pass
+  p.hot_base_elems = h;
   p.so_sB = hot(p.mps_stride);
   p.so_sT = hot(p.mps_stride);
-  if ((size_t)h * c->sbytes <= budget) {
-    p.hot_in_smem = 1;
-    p.env_in_smem = 1;
-  } else {
-    h = h_base;
-    p.hot_in_smem = (size_t)h * c->sbytes <= budget ? 1 : 0;
-    p.env_in_smem = 0;
-  }
-  p.hot_elems = h;
-  p.dyn_smem = (size_t)p.cfg_bytes + (p.hot_in_smem ? (size_t)h * c->sbytes : 0);
+  p.hot_mps_elems = h;
+  p.so_envR = hot((long long)(Lx + 1) * p.env_stride);
+  p.so_env3R = hot((long long)(Lx + 1) * p.env3_stride);
+  p.hot_all_elems = h;
+  // one chain per CTA: the largest level that keeps two CTAs on an SM
+  const size_t budget = 100 * 1024;
+  p.cta_level = 0;
+  for (int lv = 1; lv <= 3; ++lv)
+    if ((size_t)p.level_elems(lv) * c->sbytes <= budget) p.cta_level = lv;
+  if (const char* e = std::getenv("GCFVMC_SMEM_CTA")) p.cta_level = std::max(0, std::min(3, std::atoi(e)));
+  p.hot_elems = p.level_elems(p.cta_level);
+  p.dyn_smem = (size_t)p.cfg_bytes + (size_t)p.hot_elems * c->sbytes;
   plan_group(c);
 }
 
@@ -384,8 +387,9 @@ KParams<T> make_params(gcf_ctx* c) {
   k.mps_stride = p.mps_stride; k.qsite_stride = p.qsite_stride;
   k.env_stride = p.env_stride; k.env3_stride = p.env3_stride;
   k.max_sweeps_svd = 40;
-  k.hot_in_smem = p.hot_in_smem;
-  k.env_in_smem = p.env_in_smem;
+  k.hot_in_smem = p.cta_level >= 1;
+  k.mps_in_smem = p.cta_level >= 2;
+  k.renv_in_smem = p.cta_level >= 3;
   k.so_envR = p.so_envR; k.so_env3R = p.so_env3R; k.so_sB = p.so_sB; k.so_sT = p.so_sT;
   k.o_sigma = p.o_sigma; k.o_sel = p.o_sel;
   k.dense_max = p.tmp_max;
@@ -398,8 +402,26 @@ KParams<T> make_params(gcf_ctx* c) {
   k.so_t1 = p.so_t1; k.so_t2 = p.so_t2; k.smem_cfg_bytes = p.cfg_bytes;
   k.group_smem_bytes = (long long)p.group_smem;
   k.group_threads = c->group_threads;
+  // tensor-core forms exist for FP32 storage only
+  k.gemm_mode = GEMM_FFMA;
+  if (c->kind == S_F32 || c->kind == S_C64) {
+    if (c->m.precision == GCF_TF32) k.gemm_mode = GEMM_TF32X3;
+    if (c->m.precision == GCF_BF16) k.gemm_mode = GEMM_BF16;
+  }
+  // BF16 form: the row environments (amplitude, O, horizontal-hop ratios)
+  // run in the 3-pass TF32 form, which halves the BF16 error of O
+  k.row_gemm_mode = k.gemm_mode == GEMM_BF16 ? GEMM_TF32X3 : k.gemm_mode;
   k.status = c->d_status;
   return k;
+}
+
+// Chain slots for n chains when at most max_slots run at once: the fewest
+// slots that still need the same number of rounds, so every slot runs the
+// same number of chains (no partly filled last round).
+long long balanced_slots(long long n, long long max_slots) {
+  max_slots = std::max<long long>(1, max_slots);
+  const long long rounds = (n + max_slots - 1) / max_slots;
+  return std::max<long long>(1, (n + rounds - 1) / std::max<long long>(1, rounds));
 }
 
 int grid_for(gcf_ctx* c, int n_chains) {
@@ -410,8 +432,7 @@ int grid_for(gcf_ctx* c, int n_chains) {
     case S_C64: per_sm = occupancy_vmc<cfloat>(256, c->plan.dyn_smem); break;
     default: per_sm = occupancy_vmc<cdouble>(256, c->plan.dyn_smem); break;
   }
-  const long long want = std::min<long long>(n_chains, (long long)c->sms * std::max(1, per_sm));
-  return (int)std::max<long long>(1, want);
+  return (int)balanced_slots(n_chains, (long long)c->sms * std::max(1, per_sm));
 }
 
 gcf_status ensure_scratch(gcf_ctx* c, long long ctas) {
@@ -435,8 +456,8 @@ gcf_status run_vmc(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t
   if (warp) {
     const int per_sm = occupancy_vmc_grouped<T>(256, W * c->plan.group_smem);
     if (per_sm < 1) return fail(c, GCF_EINVAL, "grouped launch does not fit an SM");
-    const long long ctas = (n + W - 1) / W;
-    grid = (int)std::max<long long>(1, std::min<long long>(ctas, (long long)c->sms * per_sm));
+    const long long slots = balanced_slots(n, (long long)c->sms * per_sm * W);
+    grid = (int)std::max<long long>(1, (slots + W - 1) / W);
   } else {
     grid = grid_for(c, n);
   }
@@ -444,8 +465,9 @@ gcf_status run_vmc(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t
   if (st != GCF_OK) return st;
   KParams<T> k = make_params<T>(c);
   if (warp) {
-    k.hot_in_smem = c->plan.group_hot_in_smem;
-    k.env_in_smem = 0;
+    k.hot_in_smem = c->plan.group_level >= 1;
+    k.mps_in_smem = c->plan.group_level >= 2;
+    k.renv_in_smem = c->plan.group_level >= 3;
   }
   k.n_chains = n; k.n_sweeps = n_sweeps; k.mode = mode; k.want = want; k.seed = seed;
   k.configs = configs;

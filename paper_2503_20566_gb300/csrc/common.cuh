@@ -244,6 +244,10 @@ __device__ inline void block_sum2_r(R& a, R& b, R* red) {
 // Executors hold no data, so passing them costs no registers; reductions use
 // one 64-double slot per group of this CTA-wide array.
 __shared__ double g_exec_red[4][64];
+// Arithmetic of the contraction GEMMs of each group (a GemmMode of mma.cuh),
+// set at kernel entry from the launch parameters; a chain may switch its
+// own slot between passes.
+__shared__ int g_gemm_mode[4];
 
 struct CtaExec {
   __device__ int tid() const { return threadIdx.x; }
@@ -253,6 +257,7 @@ struct CtaExec {
   __device__ int nwarps() const { return blockDim.x >> 5; }
   __device__ bool leader() const { return threadIdx.x == 0; }
   __device__ void sync() const { __syncthreads(); }
+  __device__ int slot() const { return 0; }
   template <class R> __device__ R sum(R v) const { return block_sum_r<R>(v, (R*)g_exec_red[0]); }
   template <class R> __device__ void sum2(R& a, R& b) const { block_sum2_r<R>(a, b, (R*)g_exec_red[0]); }
   __device__ float maxf(float v) const {
@@ -272,6 +277,7 @@ template <int G>
 struct GroupExec {
   static_assert(G % 32 == 0 && G >= 64 && G <= 128, "group of 64 or 128 threads");
   __device__ int group() const { return threadIdx.x / G; }
+  __device__ int slot() const { return threadIdx.x / G; }
   __device__ int tid() const { return threadIdx.x % G; }
   __device__ int size() const { return G; }
   __device__ int lane() const { return threadIdx.x & 31; }

@@ -14,6 +14,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "mma.cuh"
 
 namespace gcf {
 
@@ -30,6 +31,7 @@ __device__ __forceinline__ float gemm_tiles(const X ex, int M, int N, int K, con
   const int tilesN = (N + TN - 1) / TN;
   const int tiles = ((M + TM - 1) / TM) * tilesN;
   float mx = 0.f;
+#pragma unroll 1
   for (int t = ex.tid(); t < tiles; t += ex.size()) {
     const int tm = t / tilesN;
     const int m0 = tm * TM, n0 = (t - tm * tilesN) * TN;
@@ -55,6 +57,7 @@ __device__ __forceinline__ float gemm_tiles(const X ex, int M, int N, int K, con
           for (int j = 0; j < TN; ++j) acc[i][j] = fmac(acc[i][j], av[i], bv[j]);
       }
     } else {
+#pragma unroll 1
       for (int k = 0; k < K; ++k) {
         T av[TM], bv[TN];
 #pragma unroll
@@ -89,12 +92,22 @@ __device__ __noinline__ int cta_gemm_scaled(const X ex, int M, int N, int K, con
   float mx;
   const int MN = M * N;
   const int nt = ex.size();
-  if (MN >= 8 * nt && M % 4 == 0 && N % 2 == 0)
+  bool done = false;
+  if constexpr (MmaOk<T>::value) {
+    const int mode = g_gemm_mode[ex.slot()];
+    if (mode != GEMM_FFMA) {
+      if (mode == GEMM_BF16)
+        mx = mma_gemm<T, GEMM_BF16>(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc, 1, false);
+      else
+        mx = mma_gemm<T, GEMM_TF32X3>(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc, 1, false);
+      done = true;
+    }
+  }
+  if (done) {
+  } else if (MN >= 8 * nt && M % 4 == 0 && N % 2 == 0)
     mx = gemm_tiles<T, 4, 2>(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc);
   else if (MN >= 4 * nt && M % 2 == 0 && N % 2 == 0)
     mx = gemm_tiles<T, 2, 2>(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc);
-  else if (MN >= 2 * nt && M % 2 == 0)
-    mx = gemm_tiles<T, 2, 1>(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc);
   else
     mx = gemm_tiles<T, 1, 1>(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc);
   if (!rescale) {
@@ -106,6 +119,7 @@ __device__ __noinline__ int cta_gemm_scaled(const X ex, int M, int N, int K, con
     using R = typename Traits<T>::R;
     const int e = exp2_of(mx);
     const R s = pow2r<R>(-e);
+#pragma unroll 1
     for (int i = ex.tid(); i < MN; i += nt) {
       const int m = i / N, n = i - m * N;
       C[m * ldc + n] = scale(C[m * ldc + n], s);
@@ -131,6 +145,7 @@ struct SDims {
 template <class T, int DK, class X>
 __device__ __forceinline__ void build_column_op(const X ex, const SDims& d, const T* W1, const T* W2, T* Cop) {
   constexpr int D3 = DK * DK * DK;
+#pragma unroll 1
   for (int idx = ex.tid(); idx < D3 * D3; idx += ex.size()) {
     const int k = idx / D3, n = idx % D3;
     const int i = k / (DK * DK), j = (k / DK) % DK, dd = k % DK;
@@ -159,6 +174,7 @@ __device__ __noinline__ int strip_left(const X ex, const SDims& d, const T* L, c
     constexpr int D3 = DK * DK * DK;
     const int ldx2 = d.nB * d.pT;
     const int sI = d.nJ * d.nB * N1, sJ = d.nB * N1;
+#pragma unroll 1
     for (int p = ex.tid(); p < d.nB * d.nA2; p += ex.size()) {
       const int b = p / d.nA2, a2 = p - (p / d.nA2) * d.nA2;
       const T* x1 = X1 + b * N1 + a2;
@@ -206,6 +222,7 @@ __device__ __noinline__ int strip_right(const X ex, const SDims& d, const T* R2,
   {
     constexpr int D3 = DK * DK * DK;
     const int ldy2 = d.nI * d.nJ * d.nB;
+#pragma unroll 1
     for (int p = ex.tid(); p < d.nA2 * d.nB; p += ex.size()) {
       const int a2 = p / d.nB, b = p - (p / d.nB) * d.nB;
       const T* y1 = Y1 + a2 * d.nI2 * d.nJ2 * N1 + b * d.pT;
@@ -259,6 +276,7 @@ __device__ __noinline__ int row_left(const X ex, const RDims& d, const T* L, con
   // G2: X2[(a2 r)][(b u)] = sum_{l,d} X1[(l b)][(d a2)] W[l][r][d][u]
   {
     const int ldx2 = d.nB * d.pT;
+#pragma unroll 1
     for (int p = ex.tid(); p < d.nB * d.nA2; p += ex.size()) {
       const int b = p / d.nA2, a2 = p - (p / d.nA2) * d.nA2;
       T x[DK][DK];
@@ -294,6 +312,7 @@ __device__ __noinline__ int row_right(const X ex, const RDims& d, const T* R2, c
   // G2: Y2[(d a2)][(l b)] = sum_{r,u} Y1[(a2 r)][(b u)] W[l][r][d][u]
   {
     const int ldy2 = d.nH * d.nB;
+#pragma unroll 1
     for (int p = ex.tid(); p < d.nA2 * d.nB; p += ex.size()) {
       const int a2 = p / d.nB, b = p - (p / d.nB) * d.nB;
       T y[DK][DK];

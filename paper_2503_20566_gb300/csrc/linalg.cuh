@@ -13,6 +13,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "mma.cuh"
 
 namespace gcf {
 
@@ -20,7 +21,19 @@ namespace gcf {
 template <class T, bool CA = false, bool CB = false, class X>
 __device__ __noinline__ void cta_gemm(const X ex, int M, int N, int K, const T* A, int sAm, int sAk, const T* B,
                          int sBk, int sBn, T* C, int sCm, int sCn, bool accumulate) {
+  if constexpr (!CA && !CB && MmaOk<T>::value) {
+    const int mode = g_gemm_mode[ex.slot()];
+    if (mode != GEMM_FFMA) {
+      if (mode == GEMM_BF16)
+        mma_gemm<T, GEMM_BF16>(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, sCm, sCn, accumulate);
+      else
+        mma_gemm<T, GEMM_TF32X3>(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, sCm, sCn, accumulate);
+      ex.sync();
+      return;
+    }
+  }
   const int MN = M * N;
+#pragma unroll 1
   for (int idx = ex.tid(); idx < MN; idx += ex.size()) {
     const int i = idx / N, j = idx - (idx / N) * N;
     T s = accumulate ? C[i * sCm + j * sCn] : zero<T>();
@@ -68,12 +81,14 @@ __device__ __noinline__ void cta_qr(const X ex, int m, int n, T* A, int sm, int 
   const int lane = ex.lane(), wid = ex.warp(), nw = ex.nwarps();
   for (int j = 0; j < k; ++j) {
     R part = R(0);
+#pragma unroll 1
     for (int i = j + 1 + ex.tid(); i < m; i += ex.size()) part += abs2(A[i * sm + j * sn]);
     const R xn2 = ex.template sum<R>(part);
     const T alpha = A[j * sm + j * sn];
     T t, sc, beta;
     householder(alpha, xn2, t, sc, beta);
     ex.sync();
+#pragma unroll 1
     for (int i = j + 1 + ex.tid(); i < m; i += ex.size()) A[i * sm + j * sn] = A[i * sm + j * sn] * sc;
     if (ex.tid() == 0) { A[j * sm + j * sn] = beta; tau[j] = t; }
     ex.sync();
@@ -101,6 +116,7 @@ template <class T, class X>
 __device__ __noinline__ void cta_form_q(const X ex, int m, int k, const T* A, int sm, int sn, const T* tau, T* Q, int sQm,
                            int sQn) {
   const int lane = ex.lane(), wid = ex.warp(), nw = ex.nwarps();
+#pragma unroll 1
   for (int idx = ex.tid(); idx < m * k; idx += ex.size()) {
     const int i = idx / k, c = idx - (idx / k) * k;
     Q[i * sQm + c * sQn] = (i == c) ? one<T>() : zero<T>();
@@ -129,6 +145,7 @@ __device__ __noinline__ void cta_form_q(const X ex, int m, int k, const T* A, in
 template <class T, class X>
 __device__ __noinline__ void cta_adjoint(const X ex, int rows, int cols, const T* src, int sSm, int sSn, T* dst, int sDm,
                             int sDn) {
+#pragma unroll 1
   for (int idx = ex.tid(); idx < rows * cols; idx += ex.size()) {
     const int i = idx / cols, j = idx - (idx / cols) * cols;
     dst[i * sDm + j * sDn] = conjg(src[j * sSm + i * sSn]);
@@ -145,6 +162,7 @@ __device__ __noinline__ int cta_jacobi_svd(const X ex, int p, int q, T* W, int s
                               int* sflag, int max_sweeps, int* converged) {
   using R = typename Traits<T>::R;
   const int lane = ex.lane(), wid = ex.warp(), nw = ex.nwarps();
+#pragma unroll 1
   for (int idx = ex.tid(); idx < q * q; idx += ex.size()) {
     const int i = idx / q, c = idx - (idx / q) * q;
     J[i * sJm + c * sJn] = (i == c) ? one<T>() : zero<T>();

@@ -59,8 +59,10 @@ struct KParams {
       so_t1, so_t2, smem_cfg_bytes;
   long long group_smem_bytes;  // grouped kernel: shared bytes per chain group
   int group_threads;          // grouped kernel: threads per chain (128)
+  int gemm_mode;              // GemmMode of the contraction GEMMs
+  int row_gemm_mode;          // GemmMode of the row environments (O, amplitude, hops)
   // right environments and the staged B / T rows of the current pass
-  int env_in_smem;
+  int mps_in_smem, renv_in_smem;
   long long so_envR, so_env3R, so_sB, so_sT;
   // per-run
   int n_chains, n_sweeps, mode, want;  // mode 0: measure given configs, 1: sample
@@ -136,6 +138,7 @@ __device__ inline void gather_box(const X ex, const KParams<T>& k, int x, int y,
   const int v = y * k.Lx + x;
   const T* src = k.params + k.voff[v] + (long long)bid * k.vbs[v];
   const int bs = dl * dr * dd * du;
+#pragma unroll 1
   for (int e = ex.tid(); e < bs; e += ex.size()) {
     int t = e;
     const int iu = t % du; t /= du;
@@ -175,11 +178,13 @@ template <class T, class X>
 __device__ __noinline__ int rescale(const X ex, T* a, int n) {
   using R = typename Traits<T>::R;
   float mx = 0.f;
+#pragma unroll 1
   for (int i = ex.tid(); i < n; i += ex.size()) mx = fmaxf(mx, (float)absmax1(a[i]));
   mx = ex.maxf(mx);
   if (!(mx > 0.f) || !isfinite(mx)) return 0;
   const int e = exp2_of(mx);
   const R s = pow2r<R>(-e);
+#pragma unroll 1
   for (int i = ex.tid(); i < n; i += ex.size()) a[i] = scale(a[i], s);
   ex.sync();
   return e;
@@ -190,11 +195,13 @@ template <class T, class X>
 __device__ __noinline__ int frob_rescale(const X ex, T* a, int n) {
   using R = typename Traits<T>::R;
   R s2 = R(0);
+#pragma unroll 1
   for (int i = ex.tid(); i < n; i += ex.size()) s2 += abs2(a[i]);
   s2 = ex.template sum<R>(s2);
   if (!(s2 > R(0)) || !isfinite((float)s2)) return 0;
   const int e = exp2_of((float)sqrt(s2));
   const R s = pow2r<R>(-e);
+#pragma unroll 1
   for (int i = ex.tid(); i < n; i += ex.size()) a[i] = scale(a[i], s);
   ex.sync();
   return e;
@@ -202,10 +209,11 @@ __device__ __noinline__ int frob_rescale(const X ex, T* a, int n) {
 
 // sum_k A[k] B[k] (no conjugation), broadcast to all threads as (re, im)
 template <class T, class X>
-__device__ inline void cta_dot(const X ex, const T* A, const T* B, int n, typename Traits<T>::R& r,
+__device__ __noinline__ void cta_dot(const X ex, const T* A, const T* B, int n, typename Traits<T>::R& r,
                                typename Traits<T>::R& i) {
   using R = typename Traits<T>::R;
   T s = zero<T>();
+#pragma unroll 1
   for (int k = ex.tid(); k < n; k += ex.size()) s = fmac(s, A[k], B[k]);
   r = re(s);
   i = im(s);
@@ -249,6 +257,7 @@ __device__ __noinline__ int dense_absorb(const X ex, const KParams<T>& k, Shared
     const int hl = hl_dim(c, Dk), hr = hr_dim(c, Lx, Dk);
     const T* W = net + (long long)(row * Lx + c) * (Dk * Dk * Dk * Dk);
     const int nout = hr * NU * pout * ND;
+#pragma unroll 1
     for (int idx = ex.tid(); idx < nout; idx += ex.size()) {
       int t = idx;
       const int Dr = t % ND; t /= ND;
@@ -270,6 +279,7 @@ __device__ __noinline__ int dense_absorb(const X ex, const KParams<T>& k, Shared
   using R = typename Traits<T>::R;
   const int nv = NU;
   R s2 = R(0);
+#pragma unroll 1
   for (int i = ex.tid(); i < nv; i += ex.size()) s2 += abs2(bufA[i]);
   s2 = ex.template sum<R>(s2);
   const int e = (s2 > R(0) && isfinite((float)s2)) ? exp2_of((float)sqrt(s2)) : 0;
@@ -281,8 +291,10 @@ __device__ __noinline__ int dense_absorb(const X ex, const KParams<T>& k, Shared
     T* site = mout + sh.bd_off2[c];
     const int n = a * pout * b;
     if (c == m) {
+#pragma unroll 1
       for (int i = ex.tid(); i < n; i += ex.size()) site[i] = scale(bufA[i], inv);
     } else {
+#pragma unroll 1
       for (int i = ex.tid(); i < n; i += ex.size()) {
         const int ib = i % b, ii = (i / b) % pout, ia = i / (b * pout);
         const bool on = (c < m) ? (ib == ia * pout + ii) : (ia == ii * b + ib);
@@ -386,6 +398,7 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
     const T* W = net + (long long)(row * Lx + c) * (Dk * Dk * Dk * Dk);
     const int nZ = a * l * pout * b * r;
     T* Zc = Z + sh.zoff[c];
+#pragma unroll 1
     for (int idx = ex.tid(); idx < nZ; idx += ex.size()) {
       int t = idx;
       const int ir = t % r; t /= r;
@@ -413,6 +426,7 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
     cta_qr<T>(ex, rows, cols, M1, cols, 1, tau);
     const int kq = min(rows, cols);
     cta_form_q<T>(ex, rows, kq, M1, cols, 1, tau, Qs + sh.qoff[c], kq, 1);
+#pragma unroll 1
     for (int idx = ex.tid(); idx < kq * cols; idx += ex.size()) {
       const int i = idx / cols, j = idx - (idx / cols) * cols;
       M3[idx] = (j >= i) ? M1[i * cols + j] : zero<T>();
@@ -449,6 +463,7 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
       const int k0 = min(yr, yc);
       cta_form_q<T>(ex, yc, k0, Yh, yr, 1, tau, Qp, k0, 1);
       // L = R'^H (yr x k0)
+#pragma unroll 1
       for (int idx = ex.tid(); idx < yr * k0; idx += ex.size()) {
         const int i = idx / k0, j = idx - (idx / k0) * k0;
         Lc[idx] = (i >= j) ? conjg(Yh[j * yr + i]) : zero<T>();
@@ -464,12 +479,14 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
         using RR = typename Traits<T>::R;
         RR* sigma = (RR*)(ws + k.o_sigma);
         int* sel = (int*)(ws + k.o_sel);
+#pragma unroll 1
         for (int j = ex.tid(); j < k0; j += ex.size()) {
           RR s2 = RR(0);
           for (int i = 0; i < yr; ++i) s2 += abs2(Lc[i * k0 + j]);
           sigma[j] = s2;
         }
         ex.sync();
+#pragma unroll 1
         for (int j = ex.tid(); j < k0; j += ex.size()) {
           int rank = 0;
           const RR sj = sigma[j];
@@ -481,6 +498,7 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
         }
         ex.sync();
         // site[n][x] = sum_j conj(J[j][sel n]) Q'^H[j][x]
+#pragma unroll 1
         for (int idx = ex.tid(); idx < kk * yc; idx += ex.size()) {
           const int n = idx / yc, x = idx - (idx / yc) * yc;
           const int jn = sel[n];
@@ -489,11 +507,13 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
           site[idx] = s;
         }
         // carry U S = W[:, sel] (yr x kk)
+#pragma unroll 1
         for (int idx = ex.tid(); idx < yr * kk; idx += ex.size()) {
           const int i = idx / kk, n = idx - (idx / kk) * kk;
           Yh[idx] = Lc[i * k0 + sel[n]];
         }
         ex.sync();
+#pragma unroll 1
         for (int idx = ex.tid(); idx < yr * kk; idx += ex.size()) Lc[idx] = Yh[idx];
         ex.sync();
       }
@@ -503,6 +523,7 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
       ident = false;
     } else {
       // no reduction at this site's left bond (cur == bdo[c]): keep Y
+#pragma unroll 1
       for (int idx = ex.tid(); idx < yr * yc; idx += ex.size()) site[idx] = Yp[idx];
       ex.sync();
       logs += rescale(ex, site, yr * yc);

@@ -59,10 +59,15 @@ struct Chain {
       env3L = hot_ + k.so_env3L; env3X = hot_ + k.so_env3X; env3Y = hot_ + k.so_env3Y;
       t1 = hot_ + k.so_t1; t2 = hot_ + k.so_t2;
     }
-    if (k.hot_in_smem && k.env_in_smem) {
-      eR = hot_ + k.so_envR; e3R = hot_ + k.so_env3R; sB = hot_ + k.so_sB; sT = hot_ + k.so_sT;
+    if (k.hot_in_smem && k.mps_in_smem) {
+      sB = hot_ + k.so_sB; sT = hot_ + k.so_sT;
     } else {
-      eR = ws + k.o_envR; e3R = ws + k.o_env3R; sB = nullptr; sT = nullptr;
+      sB = nullptr; sT = nullptr;
+    }
+    if (k.hot_in_smem && k.mps_in_smem && k.renv_in_smem) {
+      eR = hot_ + k.so_envR; e3R = hot_ + k.so_env3R;
+    } else {
+      eR = ws + k.o_envR; e3R = ws + k.o_env3R;
     }
     if (!k.hot_in_smem) {
       net = ws + k.o_net; props = ws + k.o_prop; cop = ws + k.o_t3;
@@ -70,6 +75,13 @@ struct Chain {
       env3L = ws + k.o_env3L; env3X = ws + k.o_env3X; env3Y = ws + k.o_env3Y;
       t1 = ws + k.o_t1; t2 = ws + k.o_t2;
     }
+  }
+
+  // arithmetic of this chain's contraction GEMMs from here on
+  __device__ void set_gemm_mode(int m) {
+    ex.sync();
+    if (ex.leader()) g_gemm_mode[ex.slot()] = m;
+    ex.sync();
   }
 
   __device__ T* Bslot(int j) const { return ws + k.o_B + (long long)j * k.mps_stride; }
@@ -84,7 +96,7 @@ struct Chain {
   __device__ T* prop(int i) const { return props + i * (k.Dk * k.Dk * k.Dk * k.Dk); }
 
   // ---- configuration moves on the shared copy (thread 0 writes) ---------
-  __device__ void plaq_apply(int x, int y, int t) {
+  __device__ __noinline__ void plaq_apply(int x, int y, int t) {
     if (ex.tid() == 0) {
       const int N = k.N;
       int8_t* h = cfg;
@@ -99,7 +111,7 @@ struct Chain {
   // Hop across link (x,a): returns 1 if a move exists (and applies it).
   // On a hard-core lattice the hop available after a hop is its inverse, so
   // calling this again reverts the move.
-  __device__ int hop_apply(int x, int y, int a) {
+  __device__ __noinline__ int hop_apply(int x, int y, int a) {
     int& ok = sv.ok;
     if (ex.tid() == 0) {
       const int N = k.N;
@@ -153,6 +165,7 @@ struct Chain {
         const T* src = k.params + k.voff[v] + (long long)bid * k.vbs[v];
         const int bs = dl * dr * dd * du;
         T* box = dst[g];
+#pragma unroll 1
         for (int e = tl; e < bs; e += per) {
           int t = e;
           const int iu = t % du; t /= du;
@@ -165,13 +178,13 @@ struct Chain {
     }
     (void)D4;
   }
-  __device__ void gather_plaq(int c, int r) {
+  __device__ __noinline__ void gather_plaq(int c, int r) {
     const int xs[4] = {c, c + 1, c, c + 1};
     const int ys[4] = {r, r, r + 1, r + 1};
     T* const dst[4] = {prop(0), prop(1), prop(2), prop(3)};
     gather_n(4, xs, ys, dst);
   }
-  __device__ void gather_pair(int x0, int y0, T* d0, int x1, int y1, T* d1) {
+  __device__ __noinline__ void gather_pair(int x0, int y0, T* d0, int x1, int y1, T* d1) {
     const int xs[2] = {x0, x1};
     const int ys[2] = {y0, y1};
     T* const dst[2] = {d0, d1};
@@ -182,6 +195,7 @@ struct Chain {
     int& bad = sv.bad;
     if (ex.tid() == 0) bad = 0;
     ex.sync();
+#pragma unroll 1
     for (int v = ex.tid(); v < k.n_s; v += ex.size()) {
       if (block_of(k, cfg, v % k.Lx, v / k.Lx) < 0) bad = 1;
     }
@@ -231,12 +245,14 @@ struct Chain {
   // memory when available, else the scratch slots
   const T* curB;
   const T* curT;
-  __device__ void stage(int jb, int jt, int physb, int physt) {
+  __device__ __noinline__ void stage(int jb, int jt, int physb, int physt) {
     const T* b = Bslot(jb);
     const T* t = Tslot(jt);
     if (sB) {
       const int nb = sv.offB[k.Lx], nt = sv.offT[k.Lx];
+#pragma unroll 1
       for (int i = ex.tid(); i < nb; i += ex.size()) sB[i] = b[i];
+#pragma unroll 1
       for (int i = ex.tid(); i < nt; i += ex.size()) sT[i] = t[i];
       ex.sync();
       curB = sB;
@@ -352,7 +368,7 @@ struct Chain {
   // Metropolis decision (Sec. S-1): accept iff u |den|^2 < |num|^2, with
   // den = (dr + i di) 2^de and num = (nr + i ni) 2^ne; evaluated once on
   // thread 0 (exact powers of two, no logarithms) and broadcast.
-  __device__ bool metro_accept(double u, R dr, R di, int de, R nr, R ni, int ne) {
+  __device__ __noinline__ bool metro_accept(double u, R dr, R di, int de, R nr, R ni, int ne) {
     if (ex.tid() == 0) {
       const double d2 = (double)dr * dr + (double)di * di;
       const double n2 = (double)nr * nr + (double)ni * ni;
@@ -368,7 +384,7 @@ struct Chain {
     return a;
   }
   // eacc += coef * num / den (thread 0)
-  __device__ void add_ratio(double coef, R nr, R ni, int ne, R dr, R di, int de) {
+  __device__ __noinline__ void add_ratio(double coef, R nr, R ni, int ne, R dr, R di, int de) {
     if (ex.tid() == 0) {
       const double d2 = (double)dr * dr + (double)di * di;
       const double f = ldexp(1.0, ne - de) / d2;
@@ -383,6 +399,34 @@ struct Chain {
   __device__ double uniform_at(unsigned long long ctr) const {
     return word_to_uniform(stream_word(key, ctr));
   }
+  // E_loc term of the hop across horizontal link (c, r) -> (c+1, r), from the
+  // row environments of the measurement pass (left env Lc at column c)
+  __device__ __noinline__ void hhop_ratio(int r, int c, const T* Lc, T* X1, T* X2, int eL, R dr, R di, int de) {
+    if (!hop_apply(c, r, 1)) return;
+    gather_pair(c, r, prop(0), c + 1, r, prop(1));
+    ex.sync();
+    const int l1 = row_step_left(r, c, Lc, prop(0), X1);
+    const int l2 = row_step_left(r, c + 1, X1, prop(1), X2);
+    R nr, ni;
+    const RDims d2 = rdims(r, c + 1);
+    cta_dot(ex, X2, env3R(c + 2), d2.nA2 * d2.nH2 * d2.nB2, nr, ni);
+    add_ratio(k.J, nr, ni, eL + l1 + l2 + sv.logR[c + 2], dr, di, de);
+    hop_apply(c, r, 1);
+  }
+  // E_loc term of the hop across vertical link (c, r) -> (c, r+1), from the
+  // strip environments of the measurement pass (left env Lc at column c)
+  __device__ __noinline__ void vhop_ratio(int r, int c, const T* Lc, T* X1, int eL, R dr, R di, int de) {
+    if (!hop_apply(c, r, 2)) return;
+    gather_pair(c, r, prop(0), c, r + 1, prop(2));
+    ex.sync();
+    const int l1 = strip_step_left(r, c, Lc, prop(0), prop(2), X1);
+    R nr, ni;
+    const SDims d1 = sdims(r, c);
+    cta_dot(ex, X1, envR(c + 1), env_size(d1, true), nr, ni);
+    add_ratio(k.J, nr, ni, eL + l1 + sv.logR[c + 1], dr, di, de);
+    hop_apply(c, r, 2);
+  }
+
   __device__ int power_at(unsigned long long ctr) const {
     if (k.N == 2) return 1;
     return 1 + (int)(stream_word(key, ctr) % (unsigned long long)(k.N - 1));
@@ -391,6 +435,7 @@ struct Chain {
 
 template <class T, class X>
 __device__ void copy_box(const X ex, T* dst, const T* src, int n) {
+#pragma unroll 1
   for (int i = ex.tid(); i < n; i += ex.size()) dst[i] = src[i];
 }
 
@@ -440,11 +485,13 @@ __device__ __noinline__ void plaquette_pass(Chain<T, X>& ch, int w) {
         copy_box(ex, ch.box(c + 1, r + 1), ch.prop(3), D4);
         dr = nr; di = ni; de = ne;
         // L_{c+1} is X1 (built from the accepted column c)
+#pragma unroll 1
         for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = X1[i];
         eL += l1;
       } else {
         ch.plaq_apply(c, r, k.N - t);  // revert
         eL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), X1);
+#pragma unroll 1
         for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = X1[i];
       }
       ex.sync();
@@ -499,10 +546,12 @@ __device__ __noinline__ void hhop_pass(Chain<T, X>& ch, int w) {
       const RDims d1 = ch.rdims(r, c);
       const int n1 = d1.nA2 * d1.nH2 * d1.nB2;
       if (acc) {
+#pragma unroll 1
         for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = X1[i];
         eL += l1;
       } else {
         eL += ch.row_step_left(r, c, Lc, ch.box(c, r), X1);
+#pragma unroll 1
         for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = X1[i];
       }
       ex.sync();
@@ -556,10 +605,12 @@ __device__ __noinline__ void vhop_pass(Chain<T, X>& ch, int w) {
       const SDims d1 = ch.sdims(r, c);
       const int n1 = ch.env_size(d1, true);
       if (acc) {
+#pragma unroll 1
         for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = X1[i];
         eL += l1;
       } else {
         eL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), Lnext);
+#pragma unroll 1
         for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = Lnext[i];
       }
       ex.sync();
@@ -584,6 +635,7 @@ __device__ __noinline__ void measure_pass(Chain<T, X>& ch, long long s) {
     // ---- row r: gradient, horizontal hops, amplitude
     const bool need_row = want_g || (r == Ly - 1 && want_a) || (want_e && k.matter && k.J != 0.0);
     if (need_row) {
+      ch.set_gemm_mode(k.row_gemm_mode);
       R dr, di;
       int de;
       ch.row_right_envs(r, dr, di, de);
@@ -614,31 +666,22 @@ __device__ __noinline__ void measure_pass(Chain<T, X>& ch, long long s) {
           const int n = d.nH * d.nH2 * d.pB * d.pT;
           if (k.O) {
             T* dst = k.O + (s * k.n_s + v) * (long long)D4;
+#pragma unroll 1
             for (int i = ex.tid(); i < n; i += ex.size()) dst[i] = G[i] * fac;
           }
           if (k.block_ids && ex.tid() == 0) k.block_ids[s * k.n_s + v] = block_of(k, ch.cfg, c, r);
         }
-        if (want_e && k.matter && k.J != 0.0 && c < Lx - 1) {
-          if (ch.hop_apply(c, r, 1)) {
-            ch.gather_pair(c, r, ch.prop(0), c + 1, r, ch.prop(1));
-            ex.sync();
-            const int l1 = ch.row_step_left(r, c, Lc, ch.prop(0), X1);
-            const int l2 = ch.row_step_left(r, c + 1, X1, ch.prop(1), X2);
-            R nr, ni;
-            const RDims d2 = ch.rdims(r, c + 1);
-            cta_dot(ex, X2, ch.env3R(c + 2), d2.nA2 * d2.nH2 * d2.nB2, nr, ni);
-            ch.add_ratio(k.J, nr, ni, eL + l1 + l2 + ch.sv.logR[c + 2], dr, di, de);
-            ch.hop_apply(c, r, 1);
-          }
-        }
+        if (want_e && k.matter && k.J != 0.0 && c < Lx - 1) ch.hhop_ratio(r, c, Lc, X1, X2, eL, dr, di, de);
         if (c < Lx - 1) {
           eL += ch.row_step_left(r, c, Lc, ch.box(c, r), X1);
           const int n1 = d.nA2 * d.nH2 * d.nB2;
+#pragma unroll 1
           for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = X1[i];
           ex.sync();
         }
       }
     }
+    ch.set_gemm_mode(k.gemm_mode);
     // ---- strip (r, r+1): plaquettes and vertical hops
     if (want_e && r <= Ly - 2) {
       R dr, di;
@@ -668,22 +711,12 @@ __device__ __noinline__ void measure_pass(Chain<T, X>& ch, long long s) {
             ch.plaq_apply(c, r, k.N - t);
           }
         }
-        if (k.matter && k.J != 0.0) {
-          if (ch.hop_apply(c, r, 2)) {
-            ch.gather_pair(c, r, ch.prop(0), c, r + 1, ch.prop(2));
-            ex.sync();
-            const int l1 = ch.strip_step_left(r, c, Lc, ch.prop(0), ch.prop(2), X1);
-            R nr, ni;
-            const SDims d1 = ch.sdims(r, c);
-            cta_dot(ex, X1, ch.envR(c + 1), ch.env_size(d1, true), nr, ni);
-            ch.add_ratio(k.J, nr, ni, eL + l1 + ch.sv.logR[c + 1], dr, di, de);
-            ch.hop_apply(c, r, 2);
-          }
-        }
+        if (k.matter && k.J != 0.0) ch.vhop_ratio(r, c, Lc, X1, eL, dr, di, de);
         if (c < Lx - 1) {
           const SDims d1 = ch.sdims(r, c);
           eL += ch.strip_step_left(r, c, Lc, ch.box(c, r), ch.box(c, r + 1), X1);
           const int n1 = ch.env_size(d1, true);
+#pragma unroll 1
           for (int i = ex.tid(); i < n1; i += ex.size()) Lc[i] = X1[i];
           ex.sync();
         }
@@ -706,6 +739,7 @@ __device__ __noinline__ void measure_pass(Chain<T, X>& ch, long long s) {
 
 template <class T, class X>
 __device__ void init_trivial_slots(const X ex, const KParams<T>& k, T* ws) {
+#pragma unroll 1
   for (int c = ex.tid(); c < k.Lx; c += ex.size()) {
     (ws + k.o_B)[c] = one<T>();                                     // B[-1]
     (ws + k.o_T + (long long)k.Ly * k.mps_stride)[c] = one<T>();    // T[Ly]
@@ -718,6 +752,7 @@ template <class T, class X>
 __device__ void run_chain(const X ex, const KParams<T>& k, T* ws, SharedV& sv, int8_t* cfg, T* hot,
                           int chain) {
   int8_t* gcfg = k.configs + (long long)chain * k.cfg_len;
+#pragma unroll 1
   for (int i = ex.tid(); i < k.cfg_len; i += ex.size()) cfg[i] = gcfg[i];
   if (ex.leader()) {
     sv.logB[0] = 0; sv.logT[k.Ly] = 0; sv.n_acc = 0; sv.n_prop = 0;
@@ -752,6 +787,7 @@ __device__ void run_chain(const X ex, const KParams<T>& k, T* ws, SharedV& sv, i
       }
       measure_pass(ch, (long long)chain * k.n_sweeps + w);
     }
+#pragma unroll 1
     for (int i = ex.tid(); i < k.cfg_len; i += ex.size()) gcfg[i] = cfg[i];
     if (ex.leader()) {
       if (k.accepted) k.accepted[chain] = sv.n_acc;
@@ -769,6 +805,8 @@ __global__ void __launch_bounds__(256, 2) vmc_kernel(KParams<T> k) {
   T* hot = (T*)(dyn_smem + k.smem_cfg_bytes);
   __shared__ SharedV sv;
   CtaExec ex;
+  if (threadIdx.x < 4) g_gemm_mode[threadIdx.x] = k.gemm_mode;
+  __syncthreads();
   T* ws = k.scratch + (long long)blockIdx.x * k.ws_stride;
   init_trivial_slots(ex, k, ws);
   for (int chain = blockIdx.x; chain < k.n_chains; chain += gridDim.x)
@@ -781,6 +819,8 @@ __global__ void __launch_bounds__(256, 2) vmc_kernel(KParams<T> k) {
 template <class T, class X, int G>
 __device__ void grouped_body(const KParams<T>& k) {
   extern __shared__ __align__(16) int8_t dyn_smem[];
+  if (threadIdx.x < 4) g_gemm_mode[threadIdx.x] = k.gemm_mode;
+  __syncthreads();
   const int g = threadIdx.x / G, NG = blockDim.x / G;
   int8_t* base = dyn_smem + g * k.group_smem_bytes;
   SharedV& sv = *reinterpret_cast<SharedV*>(base);

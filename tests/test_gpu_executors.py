@@ -1,10 +1,12 @@
-"""Both executors of the sampling kernel give the oracle's results.
+"""Both executors of the sampling kernel, at every shared-memory placement
+level, give the oracle's results.
 
 The library runs a chain either on a whole CTA or on one of two 128-thread
-groups of a CTA (the default when the group's hot buffers fit in shared
-memory).  GCFVMC_EXEC forces one or the other at context creation; each
-setting is checked against the FP64 oracle on the same seeded inputs, with
-the amplitude and a replayed Markov chain.
+groups of a CTA, and keeps none, the hot buffers (1), also the staged B / T
+rows (2), or also the right environments (3) in shared memory.  GCFVMC_EXEC
+and GCFVMC_SMEM / GCFVMC_SMEM_CTA force a form at context creation; each is
+checked against the FP64 oracle on the same seeded inputs, with amplitudes
+and a replayed Markov chain.  Forms that do not fit an SM are skipped.
 """
 
 import numpy as np
@@ -29,18 +31,26 @@ def _ids(c):
     return "{}x{}-Z{}-D{}-chi{}{}{}".format(c[0], c[1], c[2], c[3], c[4], "-c" if c[5] else "", "-m" if c[6] else "")
 
 
-@pytest.mark.parametrize("executor", ["cta", "group"])
+@pytest.mark.parametrize("executor,level", [("cta", 0), ("cta", 1), ("cta", 3), ("group", 1), ("group", 2),
+                                            ("group", 3)])
 @pytest.mark.parametrize("case", CASES, ids=_ids)
-def test_executor_amplitude_and_chain(case, executor, monkeypatch):
+def test_executor_amplitude_and_chain(case, executor, level, monkeypatch):
+    import paper_2503_20566_gb300 as G
+
     monkeypatch.setenv("GCFVMC_EXEC", executor)
-    monkeypatch.setenv("GCFVMC_GROUP_HOT", "1" if executor == "group" else "0")
+    monkeypatch.setenv("GCFVMC_SMEM" if executor == "group" else "GCFVMC_SMEM_CTA", str(level))
     Lx, Ly, N, D, chi, cplx, matter, prec = case
     h, g, J = 1.0, 0.4, (0.5 if matter else 0.0)
     lat, pe, ctx = setup(Lx, Ly, N, D, chi, seed=61, complex_=cplx, matter=matter, precision=prec, h=h, g=g, J=J)
     nb = (Lx * Ly) // 2 if matter else 0
     # amplitudes of independent configurations
     cfgs, _, _ = configs_for(lat, 12, seed=62, n_bosons=nb)
-    la, ph = ctx.amplitude(torch.from_numpy(cfgs).cuda())
+    try:
+        la, ph = ctx.amplitude(torch.from_numpy(cfgs).cuda())
+    except G.GcfError as err:
+        if "does not fit" in str(err) or "too many resources" in str(err) or "invalid argument" in str(err):
+            pytest.skip(f"{executor} level {level} does not fit an SM: {err}")
+        raise
     la, ph = la.cpu().numpy(), ph.cpu().numpy()
     for i in range(len(cfgs)):
         ref = vmc.amplitude(pe, cfgs[i], chi)
