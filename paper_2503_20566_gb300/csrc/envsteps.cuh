@@ -119,10 +119,15 @@ __device__ __noinline__ int cta_gemm_scaled(const X ex, int M, int N, int K, con
     using R = typename Traits<T>::R;
     const int e = exp2_of(mx);
     const R s = pow2r<R>(-e);
+    if (ldc == N) {
 #pragma unroll 1
-    for (int i = ex.tid(); i < MN; i += nt) {
-      const int m = i / N, n = i - m * N;
-      C[m * ldc + n] = scale(C[m * ldc + n], s);
+      for (int i = ex.tid(); i < MN; i += nt) C[i] = scale(C[i], s);
+    } else {
+#pragma unroll 1
+      for (int i = ex.tid(); i < MN; i += nt) {
+        const int m = i / N, n = i - m * N;
+        C[m * ldc + n] = scale(C[m * ldc + n], s);
+      }
     }
     ex.sync();
     return e;

@@ -799,7 +799,7 @@ __device__ void run_chain(const X ex, const KParams<T>& k, T* ws, SharedV& sv, i
 
 // One CTA per chain (any size; the general form).
 template <class T>
-__global__ void __launch_bounds__(256, 2) vmc_kernel(KParams<T> k) {
+__global__ void __launch_bounds__(256, 2) vmc_kernel(const __grid_constant__ KParams<T> k) {
   extern __shared__ __align__(16) int8_t dyn_smem[];
   int8_t* dyn_cfg = dyn_smem;
   T* hot = (T*)(dyn_smem + k.smem_cfg_bytes);
@@ -835,7 +835,7 @@ __device__ void grouped_body(const KParams<T>& k) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(256, 2) vmc_kernel_grouped(KParams<T> k) {
+__global__ void __launch_bounds__(256, 2) vmc_kernel_grouped(const __grid_constant__ KParams<T> k) {
   grouped_body<T, GroupExec<128>, 128>(k);
 }
 
