@@ -10,8 +10,9 @@ solve + parameter update).  Metric: VMC samples/s (one sample = one measured
 configuration).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun (N > 1) every rank runs an independent replica of the
-workload (chains are independent; no collective on the data path).
+Under torchrun (N > 1) every rank runs the workload on its own chains with
+the same tensors (chains are independent; no collective on the data path);
+the slowest rank's time sets the whole-job rate.
 """
 
 from __future__ import annotations
@@ -223,6 +224,7 @@ def main():
 
     import paper_2503_20566_gb300 as G
     import synth
+    from paper_2503_20566_gb300 import replicas
 
     torch.cuda.set_device(local)
     dist = None
@@ -231,10 +233,12 @@ def main():
         dist.init_process_group("nccl")
     w = WORKLOAD
     n_chains, n_sweeps = args.chains, args.sweeps
+    seeds = replicas.rank_seeds(rank)
     ctx = G.Context(w["N"], w["Lx"], w["Ly"], w["D"], w["chi"], h=w["h_p"], g=w["g"], precision=args.precision,
-                    seed=2 + 1000 * rank)
+                    seed=seeds["tensors"])
     kernel_name = ctx.kernel_name + "<float>"
-    powers = torch.from_numpy(synth.plaquette_powers(102 + rank, n_chains, (w["Lx"] - 1) * (w["Ly"] - 1), w["N"]))
+    powers = torch.from_numpy(synth.plaquette_powers(seeds["chains"], n_chains, (w["Lx"] - 1) * (w["Ly"] - 1),
+                                                     w["N"]))
     configs = ctx.init_configs(n_chains, powers=powers)
     samples = ctx.alloc_samples(n_chains, n_sweeps, grad=True)
     stream = ctx.stream
@@ -262,7 +266,7 @@ def main():
         flush.fill_(float(i))  # 256 MiB write evicts L2 between steps (outside the events)
         with torch.cuda.stream(stream):
             ev[i][0].record(stream)
-            ctx.sample_batch(configs, n_sweeps, seed=10_000 + 1000 * i + rank, out=samples)
+            ctx.sample_batch(configs, n_sweeps, seed=seeds["step"](i), out=samples)
             ev[i][1].record(stream)
             stats = ctx.sr_step(samples, n_chains, **SR_ARGS)
             ev[i][2].record(stream)
@@ -271,13 +275,10 @@ def main():
     launches = ctx.launch_count - launches0
     t_steps = [ev[i][0].elapsed_time(ev[i][2]) for i in range(args.steps)]
     t_kernel = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
-    total_ms = float(sum(t_steps))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    group = dist.group.WORLD if dist else None
+    total_ms = replicas.max_over_ranks(float(sum(t_steps)), group, "cuda")
     samples_per_step = n_chains * n_sweeps
-    value = samples_per_step * args.steps * world / (total_ms / 1000.0)
+    value = replicas.whole_job_rate(samples_per_step, args.steps, world, total_ms)
 
     # end to end through the host-buffer C call
     e2e = None
@@ -291,12 +292,9 @@ def main():
         for i in range(args.steps):
             ctx.vmc_step_host(host_cfg, n_sweeps, 50_000 + 1000 * i + rank, **SR_ARGS)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": samples_per_step * args.steps * world / e2e_s, "unit": "samples/s",
+        e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, group, "cuda")
+        e2e = {"value": replicas.whole_job_rate(samples_per_step, args.steps, world, 1000.0 * e2e_s),
+               "unit": "samples/s",
                "h2d_bytes_per_step": cfg_bytes, "d2h_bytes_per_step": cfg_bytes + 8 * 8}
 
     if rank == 0:
