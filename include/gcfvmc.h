@@ -155,6 +155,19 @@ gcf_status gcf_local_energy(gcf_ctx* ctx, int n, const int8_t* configs, double* 
 gcf_status gcf_log_grad(gcf_ctx* ctx, int n, const int8_t* configs, int32_t* block_ids,
                         void* O);
 
+/* Vector-Jacobian product of the log-amplitudes, the adjoint of Eq. S3
+ * summed over samples: grad = sum_s w_s d ln psi(s) / d theta, with theta the
+ * parameter vector in the layout of gcf_set_tensors.  Each sample touches one
+ * block per vertex, so grad is the scatter of w_s O_s (gcf_log_grad) into the
+ * blocks the samples selected.  For real tensors d ln psi / d theta =
+ * d ln|psi| / d theta.
+ * weights: device, [n] doubles (real tensors) or [2n] (re, im) (complex);
+ * grad: device output, [n_params] doubles or [2*n_params] (re, im); overwritten.
+ * Work buffers are owned by the context.  GCF_EGAUSS if any configuration is
+ * unphysical.  Synchronises the context's stream. */
+gcf_status gcf_log_grad_vjp(gcf_ctx* ctx, int n, const int8_t* configs, const double* weights,
+                            double* grad);
+
 /* Markov-chain sampling (Sec. S-1 Metropolis rule, Sec. S-2 moves and
  * sequential order): n_sweeps sweeps of every chain in one persistent launch;
  * each sweep visits the plaquettes (row pairs bottom to top, left to right,

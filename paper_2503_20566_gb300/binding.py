@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH):
         "gcf_amplitude": (i, [vp, i, vp, vp, vp]),
         "gcf_local_energy": (i, [vp, i, vp, vp]),
         "gcf_log_grad": (i, [vp, i, vp, vp, vp]),
+        "gcf_log_grad_vjp": (i, [vp, i, vp, vp, vp]),
         "gcf_sample_batch": (i, [vp, i, i, u64, vp, C.POINTER(_Samples)]),
         "gcf_sr_step": (i, [vp, i, i, vp, vp, vp, d, d, i, d, i, d, C.POINTER(C.c_double)]),
         "gcf_vmc_step_host": (i, [vp, i, i, u64, vp, d, d, i, d, i, d, C.POINTER(C.c_double)]),
@@ -86,7 +87,7 @@ def exported_symbols():
     """Names the binding expects the library to export."""
     return ["gcf_init_peps", "gcf_destroy", "gcf_last_error", "gcf_num_params", "gcf_config_len",
             "gcf_scalar_bytes", "gcf_launch_count", "gcf_executor", "gcf_set_tensors", "gcf_get_tensors",
-            "gcf_init_configs", "gcf_amplitude", "gcf_local_energy", "gcf_log_grad",
+            "gcf_init_configs", "gcf_amplitude", "gcf_local_energy", "gcf_log_grad", "gcf_log_grad_vjp",
             "gcf_sample_batch", "gcf_sr_step", "gcf_vmc_step_host"]
 
 
@@ -216,6 +217,23 @@ class Context:
         O = torch.zeros((n, self.n_s, D4), dtype=self.o_dtype, device="cuda")
         self._check(self.lib.gcf_log_grad(self.ctx, n, _ptr(c), _ptr(bid), _ptr(O)), "log_grad")
         return bid, O
+
+    def log_grad_vjp(self, configs, weights):
+        """sum_s w_s d ln psi(s) / d theta as a device tensor of n_params
+        (complex128 for complex tensors)."""
+        torch = self._torch
+        c = self._configs(configs)
+        n = c.shape[0]
+        if self.complex:
+            w = torch.view_as_real(torch.as_tensor(weights, dtype=torch.complex128).to("cuda").contiguous())
+            g = torch.empty((self.n_params, 2), dtype=torch.float64, device="cuda")
+        else:
+            w = torch.as_tensor(weights, dtype=torch.float64).to("cuda").contiguous()
+            g = torch.empty(self.n_params, dtype=torch.float64, device="cuda")
+        if w.shape[0] != n:
+            raise ValueError(f"expected {n} weights")
+        self._check(self.lib.gcf_log_grad_vjp(self.ctx, n, _ptr(c), _ptr(w), _ptr(g)), "log_grad_vjp")
+        return torch.view_as_complex(g) if self.complex else g
 
     # ---- sampling and SR ---------------------------------------------------------
     def alloc_samples(self, n_chains, n_sweeps, grad=True):

@@ -84,6 +84,12 @@ struct gcf_ctx {
   void* d_O = nullptr;
   int* d_acc = nullptr;
   long long e2e_cap = 0;
+  // gcf_log_grad_vjp work buffers
+  int* vjp_bid = nullptr;
+  void* vjp_O = nullptr;
+  cdouble* vjp_coef = nullptr;
+  cdouble* vjp_acc = nullptr;
+  long long vjp_cap = 0;
   int e2e_chains = 0;
   long long launches = 0;
   std::string err;
@@ -659,7 +665,8 @@ void gcf_destroy(gcf_ctx* c) {
                   c->d_scratch, c->sr.obar, c->sr.F, c->sr.x, c->sr.r, c->sr.p, c->sr.Ap,
                   c->sr.t, c->sr.coef, c->sr.chain_mean, c->sr.tbar, c->sr.scal, c->sr.perm, c->sr.seg,
                   c->sr.seg_v, c->sr.seg_b, c->d_cfg, c->d_e,
-                  c->d_la, c->d_ph, c->d_bid, c->d_O, c->d_acc};
+                  c->d_la, c->d_ph, c->d_bid, c->d_O, c->d_acc, c->vjp_bid, c->vjp_O, c->vjp_coef,
+                  c->vjp_acc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -745,6 +752,62 @@ gcf_status gcf_log_grad(gcf_ctx* c, int n, const int8_t* configs, int32_t* block
   gcf_status st = dispatch(c, 0, WANT_GRAD, n, 1, 0, (int8_t*)configs, &out, &gauss);
   if (st != GCF_OK) return st;
   if (gauss) return fail(c, GCF_EGAUSS, "configuration violates the Gauss law");
+  return GCF_OK;
+}
+
+gcf_status gcf_log_grad_vjp(gcf_ctx* c, int n, const int8_t* configs, const double* weights, double* grad) {
+  if (!c || n < 0 || !grad || (n > 0 && (!configs || !weights))) return GCF_EINVAL;
+  const bool cplx = c->m.dtype == GCF_COMPLEX;
+  if (n == 0) {
+    CUDA_TRY(c, cudaMemsetAsync(grad, 0, sizeof(double) * (cplx ? 2 : 1) * c->n_params, c->stream));
+    return GCF_OK;
+  }
+  const long long D4 = (long long)c->Dk * c->Dk * c->Dk * c->Dk;
+  if (n > c->vjp_cap) {
+    cudaFree(c->vjp_bid); cudaFree(c->vjp_O); cudaFree(c->vjp_coef);
+    c->vjp_bid = nullptr; c->vjp_O = nullptr; c->vjp_coef = nullptr; c->vjp_cap = 0;
+    if (cudaMalloc(&c->vjp_bid, sizeof(int) * (size_t)n * c->n_s) != cudaSuccess ||
+        cudaMalloc(&c->vjp_O, c->sbytes * (size_t)n * c->n_s * D4) != cudaSuccess ||
+        cudaMalloc(&c->vjp_coef, sizeof(cdouble) * (size_t)n) != cudaSuccess)
+      return fail(c, GCF_ENOMEM, "log_grad_vjp buffers");
+    c->vjp_cap = n;
+  }
+  if (!c->vjp_acc && cudaMalloc(&c->vjp_acc, sizeof(cdouble) * c->n_params) != cudaSuccess)
+    return fail(c, GCF_ENOMEM, "log_grad_vjp buffers");
+  gcf_samples out{};
+  out.block_ids = c->vjp_bid;
+  out.O = c->vjp_O;
+  int gauss = 0;
+  gcf_status st = dispatch(c, 0, WANT_GRAD, n, 1, 0, (int8_t*)configs, &out, &gauss);
+  if (st != GCF_OK) return st;
+  if (gauss) return fail(c, GCF_EGAUSS, "configuration violates the Gauss law");
+  SrGeom g{};
+  g.Np = c->n_params; g.Ns = n; g.n_s = c->n_s; g.D4 = (int)D4;
+  g.voff = c->d_voff; g.vbs = c->d_vbs; g.vnb = c->d_vnb;
+  int mx = 1;
+  for (int v = 0; v < c->n_s; ++v) mx = std::max(mx, c->vbs[v] * c->vnb[v]);
+  g.max_nb_bs = mx;
+  cudaError_t e;
+  switch (c->kind) {
+    case S_F32:
+      e = log_grad_vjp<float>(g, c->vjp_bid, c->vjp_O, weights, cplx, c->vjp_coef, c->vjp_acc, grad, c->stream,
+                              &c->launches);
+      break;
+    case S_F64:
+      e = log_grad_vjp<double>(g, c->vjp_bid, c->vjp_O, weights, cplx, c->vjp_coef, c->vjp_acc, grad, c->stream,
+                               &c->launches);
+      break;
+    case S_C64:
+      e = log_grad_vjp<cfloat>(g, c->vjp_bid, c->vjp_O, weights, cplx, c->vjp_coef, c->vjp_acc, grad, c->stream,
+                               &c->launches);
+      break;
+    default:
+      e = log_grad_vjp<cdouble>(g, c->vjp_bid, c->vjp_O, weights, cplx, c->vjp_coef, c->vjp_acc, grad,
+                                c->stream, &c->launches);
+      break;
+  }
+  CUDA_TRY(c, e);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return GCF_OK;
 }
 

@@ -464,6 +464,51 @@ cudaError_t sr_solve_update(const SrGeom& g, SrWork& w, const double* e_loc, con
 #undef CK
 }
 
+// ---------------------------------------------------------------------------
+// Vector-Jacobian product of the log-amplitudes (the adjoint of Eq. S3 per
+// sample): grad = sum_s w_s d ln psi(s) / d theta, gathered from the sparse
+// per-sample blocks O_s.
+__global__ void k_weights_to_c(const double* w, int cplx, long long n, cdouble* c) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) c[s] = cplx ? cdouble{w[2 * s], w[2 * s + 1]} : cdouble{w[s], 0.0};
+}
+__global__ void k_c_to_grad(const cdouble* a, int cplx, long long np, double* grad) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  if (cplx) {
+    grad[2 * i] = a[i].x;
+    grad[2 * i + 1] = a[i].y;
+  } else {
+    grad[i] = a[i].x;
+  }
+}
+
+template <class T>
+cudaError_t log_grad_vjp(const SrGeom& g, const int* bids, const void* O, const double* w, int cplx,
+                         cdouble* coef, cdouble* acc, double* grad, cudaStream_t st, long long* launches) {
+  const int chunk = 64;
+  const size_t smem = 2 * sizeof(double) * (size_t)g.max_nb_bs;
+  cudaError_t e = cudaFuncSetAttribute(k_scatter<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_weights_to_c<<<(unsigned)((g.Ns + 255) / 256), 256, 0, st>>>(w, cplx, g.Ns, coef);
+  e = cudaMemsetAsync(acc, 0, sizeof(cdouble) * g.Np, st);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((g.Ns + chunk - 1) / chunk), (unsigned)g.n_s);
+  k_scatter<T, false><<<grid, 256, smem, st>>>(g, bids, (const T*)O, coef, acc, chunk);
+  k_c_to_grad<<<(unsigned)((g.Np + 255) / 256), 256, 0, st>>>(acc, cplx, g.Np, grad);
+  *launches += 3;
+  return cudaGetLastError();
+}
+
+template cudaError_t log_grad_vjp<float>(const SrGeom&, const int*, const void*, const double*, int, cdouble*,
+                                         cdouble*, double*, cudaStream_t, long long*);
+template cudaError_t log_grad_vjp<double>(const SrGeom&, const int*, const void*, const double*, int, cdouble*,
+                                          cdouble*, double*, cudaStream_t, long long*);
+template cudaError_t log_grad_vjp<cfloat>(const SrGeom&, const int*, const void*, const double*, int, cdouble*,
+                                          cdouble*, double*, cudaStream_t, long long*);
+template cudaError_t log_grad_vjp<cdouble>(const SrGeom&, const int*, const void*, const double*, int, cdouble*,
+                                           cdouble*, double*, cudaStream_t, long long*);
+
 template cudaError_t sr_solve_update<float>(const SrGeom&, SrWork&, const double*, const int*,
                                             const void*, void*, int, double, double, double, int,
                                             double, double*, cudaStream_t, long long*);

@@ -40,4 +40,11 @@ cudaError_t sr_solve_update(const SrGeom& g, SrWork& w, const double* e_loc, con
                             double ci, int max_iter, double tol, double* stats, cudaStream_t st,
                             long long* launches);
 
+// grad = sum_s w_s O_s scattered into the parameter layout (real: grad[Np],
+// complex: grad[2 Np] interleaved; w real [Ns] or complex [2 Ns]).  coef [Ns]
+// and acc [Np] are work buffers.
+template <class T>
+cudaError_t log_grad_vjp(const SrGeom& g, const int* bids, const void* O, const double* w, int cplx,
+                         cdouble* coef, cdouble* acc, double* grad, cudaStream_t st, long long* launches);
+
 }  // namespace gcf
