@@ -155,6 +155,20 @@ gcf_status gcf_local_energy(gcf_ctx* ctx, int n, const int8_t* configs, double* 
 gcf_status gcf_log_grad(gcf_ctx* ctx, int n, const int8_t* configs, int32_t* block_ids,
                         void* O);
 
+/* Sampling of several contexts (lattices of different sizes, Sec. S-2 moves
+ * and order on each) in one persistent launch: context i advances its
+ * n_chains[i] chains exactly as gcf_sample_batch(ctxs[i], n_chains[i],
+ * n_sweeps, seeds[i], configs[i], &outs[i]) would, chain c of context i
+ * drawing from the stream of (seeds[i], c).  All contexts must have the same
+ * tensor type and precision and live on the same device; the launch runs on
+ * ctxs[0]'s stream after the other contexts' streams are synchronised.
+ * ctxs, n_chains, seeds, configs: host arrays of n_ctx entries; configs[i]
+ * and the members of outs[i] are device pointers as for gcf_sample_batch;
+ * outs may be NULL.  Scratch is owned by ctxs[0].  GCF_EGAUSS if a starting
+ * configuration is unphysical.  Synchronises ctxs[0]'s stream. */
+gcf_status gcf_sample_multi(gcf_ctx* const* ctxs, int n_ctx, const int* n_chains, int n_sweeps,
+                            const uint64_t* seeds, int8_t* const* configs, const gcf_samples* outs);
+
 /* Vector-Jacobian product of the log-amplitudes, the adjoint of Eq. S3
  * summed over samples: grad = sum_s w_s d ln psi(s) / d theta, with theta the
  * parameter vector in the layout of gcf_set_tensors.  Each sample touches one

@@ -71,6 +71,8 @@ def load_library(path: str = LIB_PATH):
         "gcf_local_energy": (i, [vp, i, vp, vp]),
         "gcf_log_grad": (i, [vp, i, vp, vp, vp]),
         "gcf_log_grad_vjp": (i, [vp, i, vp, vp, vp]),
+        "gcf_sample_multi": (i, [C.POINTER(vp), i, C.POINTER(C.c_int), i, C.POINTER(C.c_uint64), C.POINTER(vp),
+                                 C.POINTER(_Samples)]),
         "gcf_sample_batch": (i, [vp, i, i, u64, vp, C.POINTER(_Samples)]),
         "gcf_sr_step": (i, [vp, i, i, vp, vp, vp, d, d, i, d, i, d, C.POINTER(C.c_double)]),
         "gcf_vmc_step_host": (i, [vp, i, i, u64, vp, d, d, i, d, i, d, C.POINTER(C.c_double)]),
@@ -87,7 +89,7 @@ def exported_symbols():
     """Names the binding expects the library to export."""
     return ["gcf_init_peps", "gcf_destroy", "gcf_last_error", "gcf_num_params", "gcf_config_len",
             "gcf_scalar_bytes", "gcf_launch_count", "gcf_executor", "gcf_set_tensors", "gcf_get_tensors",
-            "gcf_init_configs", "gcf_amplitude", "gcf_local_energy", "gcf_log_grad", "gcf_log_grad_vjp",
+            "gcf_init_configs", "gcf_amplitude", "gcf_local_energy", "gcf_log_grad", "gcf_log_grad_vjp", "gcf_sample_multi",
             "gcf_sample_batch", "gcf_sr_step", "gcf_vmc_step_host"]
 
 
@@ -282,3 +284,28 @@ class Context:
                                         max_iter, tol, stats)
         self._check(st, "vmc_step_host", allow=(GCF_ETIMEOUT,))
         return list(stats)
+
+
+def _samples_struct(out):
+    return _Samples(*[C.c_void_p(out[k].data_ptr()) if k in out else None
+                      for k in ("log_abs", "phase", "e_loc", "block_ids", "O", "accepted", "proposed")])
+
+
+def sample_multi(contexts, configs, n_sweeps, seeds, outs=None, grad=True):
+    """gcf_sample_multi: the chains of several contexts (lattices of different
+    sizes) in one launch.  configs[i]: device int8 (n_chains_i, cfg_len_i),
+    updated in place; seeds[i]: the seed context i would get from
+    sample_batch.  Returns the per-context output dicts."""
+    n = len(contexts)
+    if not (len(configs) == len(seeds) == n) or n == 0:
+        raise ValueError("one configs tensor and one seed per context")
+    if outs is None:
+        outs = [ctx.alloc_samples(c.shape[0], n_sweeps, grad) for ctx, c in zip(contexts, configs)]
+    lib = contexts[0].lib
+    ctxs = (C.c_void_p * n)(*[ctx.ctx for ctx in contexts])
+    nch = (C.c_int * n)(*[int(c.shape[0]) for c in configs])
+    sds = (C.c_uint64 * n)(*[int(v) for v in seeds])
+    cfg = (C.c_void_p * n)(*[c.data_ptr() for c in configs])
+    smp = (_Samples * n)(*[_samples_struct(o) for o in outs])
+    contexts[0]._check(lib.gcf_sample_multi(ctxs, n, nch, int(n_sweeps), sds, cfg, smp), "sample_multi")
+    return outs

@@ -90,6 +90,12 @@ struct gcf_ctx {
   cdouble* vjp_coef = nullptr;
   cdouble* vjp_acc = nullptr;
   long long vjp_cap = 0;
+  // gcf_sample_multi: scratch arena and launch tables (owned by the first
+  // context of the call)
+  void* multi_arena = nullptr;
+  size_t multi_arena_bytes = 0;
+  void* multi_tab = nullptr;
+  size_t multi_tab_bytes = 0;
   int e2e_chains = 0;
   long long launches = 0;
   std::string err;
@@ -495,6 +501,67 @@ gcf_status run_vmc(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t
   return GCF_OK;
 }
 
+template <class T>
+gcf_status run_multi(gcf_ctx* const* cs, int n_ctx, const int* n_chains, int n_sweeps, const uint64_t* seeds,
+                     int8_t* const* configs, const gcf_samples* outs) {
+  gcf_ctx* c0 = cs[0];
+  std::vector<KParams<T>> ks(n_ctx);
+  std::vector<long long> start(n_ctx + 1, 0);
+  size_t smem = 0;
+  long long ws = 0;
+  for (int i = 0; i < n_ctx; ++i) {
+    gcf_ctx* c = cs[i];
+    KParams<T> k = make_params<T>(c);
+    gcf_samples o{};
+    if (outs) o = outs[i];
+    k.n_chains = n_chains[i]; k.n_sweeps = n_sweeps; k.mode = 1; k.seed = seeds[i]; k.configs = configs[i];
+    k.want = (o.log_abs || o.phase ? WANT_AMP : 0) | (o.e_loc ? WANT_ELOC : 0) | (o.O || o.block_ids ? WANT_GRAD : 0);
+    k.log_abs = o.log_abs; k.phase = o.phase; k.e_loc = o.e_loc; k.block_ids = o.block_ids; k.O = (T*)o.O;
+    k.accepted = o.accepted; k.proposed = o.proposed;
+    ks[i] = k;
+    start[i + 1] = start[i] + n_chains[i];
+    smem = std::max(smem, c->plan.dyn_smem);
+    ws = std::max(ws, c->plan.ws_stride);
+    CUDA_TRY(c0, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), c0->stream));
+  }
+  const long long total = start[n_ctx];
+  if (total == 0) return GCF_OK;
+  const int per_sm = occupancy_vmc_multi<T>(smem);
+  if (per_sm < 1) return fail(c0, GCF_EINVAL, "gcf_sample_multi: the largest context does not fit an SM");
+  const long long grid = balanced_slots(total, (long long)c0->sms * per_sm);
+  const size_t arena = (size_t)grid * ws * c0->sbytes;
+  if (arena > c0->multi_arena_bytes) {
+    if (c0->multi_arena) cudaFree(c0->multi_arena);
+    c0->multi_arena = nullptr;
+    c0->multi_arena_bytes = 0;
+    if (cudaMalloc(&c0->multi_arena, arena) != cudaSuccess) return fail(c0, GCF_ENOMEM, "multi-context scratch");
+    c0->multi_arena_bytes = arena;
+  }
+  const size_t kb = sizeof(KParams<T>) * n_ctx, tb = (kb + 15) / 16 * 16 + sizeof(long long) * (n_ctx + 1);
+  if (tb > c0->multi_tab_bytes) {
+    if (c0->multi_tab) cudaFree(c0->multi_tab);
+    c0->multi_tab = nullptr;
+    c0->multi_tab_bytes = 0;
+    if (cudaMalloc(&c0->multi_tab, tb) != cudaSuccess) return fail(c0, GCF_ENOMEM, "multi-context tables");
+    c0->multi_tab_bytes = tb;
+  }
+  KParams<T>* d_ks = (KParams<T>*)c0->multi_tab;
+  long long* d_start = (long long*)((char*)c0->multi_tab + (kb + 15) / 16 * 16);
+  CUDA_TRY(c0, cudaMemcpyAsync(d_ks, ks.data(), kb, cudaMemcpyHostToDevice, c0->stream));
+  CUDA_TRY(c0, cudaMemcpyAsync(d_start, start.data(), sizeof(long long) * (n_ctx + 1), cudaMemcpyHostToDevice,
+                               c0->stream));
+  CUDA_TRY(c0, launch_vmc_multi<T>(d_ks, n_ctx, d_start, total, (T*)c0->multi_arena, ws, (int)grid, smem,
+                                   c0->stream));
+  c0->launches += 1;
+  std::vector<int> h(4 * n_ctx);
+  for (int i = 0; i < n_ctx; ++i)
+    CUDA_TRY(c0, cudaMemcpyAsync(&h[4 * i], cs[i]->d_status, 4 * sizeof(int), cudaMemcpyDeviceToHost, c0->stream));
+  CUDA_TRY(c0, cudaStreamSynchronize(c0->stream));
+  for (int i = 0; i < n_ctx; ++i)
+    if (h[4 * i + ST_GAUSS]) return fail(c0, GCF_EGAUSS, "a starting configuration violates the Gauss law");
+  return GCF_OK;
+}
+
 gcf_status dispatch(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t seed, int8_t* cfg,
                     const gcf_samples* out, int* gauss) {
   switch (c->kind) {
@@ -666,7 +733,7 @@ void gcf_destroy(gcf_ctx* c) {
                   c->sr.t, c->sr.coef, c->sr.chain_mean, c->sr.tbar, c->sr.scal, c->sr.perm, c->sr.seg,
                   c->sr.seg_v, c->sr.seg_b, c->d_cfg, c->d_e,
                   c->d_la, c->d_ph, c->d_bid, c->d_O, c->d_acc, c->vjp_bid, c->vjp_O, c->vjp_coef,
-                  c->vjp_acc};
+                  c->vjp_acc, c->multi_arena, c->multi_tab};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -809,6 +876,27 @@ gcf_status gcf_log_grad_vjp(gcf_ctx* c, int n, const int8_t* configs, const doub
   CUDA_TRY(c, e);
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return GCF_OK;
+}
+
+gcf_status gcf_sample_multi(gcf_ctx* const* ctxs, int n_ctx, const int* n_chains, int n_sweeps,
+                            const uint64_t* seeds, int8_t* const* configs, const gcf_samples* outs) {
+  if (!ctxs || n_ctx < 1 || !n_chains || !seeds || !configs || n_sweeps < 1) return GCF_EINVAL;
+  gcf_ctx* c0 = ctxs[0];
+  if (!c0) return GCF_EINVAL;
+  for (int i = 0; i < n_ctx; ++i) {
+    if (!ctxs[i] || n_chains[i] < 0 || (n_chains[i] > 0 && !configs[i])) return fail(c0, GCF_EINVAL, "bad argument");
+    if (ctxs[i]->kind != c0->kind) return fail(c0, GCF_EINVAL, "contexts differ in scalar type");
+    if (ctxs[i]->device != c0->device) return fail(c0, GCF_EINVAL, "contexts on different devices");
+  }
+  // the other contexts' work (parameter uploads) precedes this launch
+  for (int i = 1; i < n_ctx; ++i)
+    if (ctxs[i]->stream != c0->stream) CUDA_TRY(c0, cudaStreamSynchronize(ctxs[i]->stream));
+  switch (c0->kind) {
+    case S_F32: return run_multi<float>(ctxs, n_ctx, n_chains, n_sweeps, seeds, configs, outs);
+    case S_F64: return run_multi<double>(ctxs, n_ctx, n_chains, n_sweeps, seeds, configs, outs);
+    case S_C64: return run_multi<cfloat>(ctxs, n_ctx, n_chains, n_sweeps, seeds, configs, outs);
+    default: return run_multi<cdouble>(ctxs, n_ctx, n_chains, n_sweeps, seeds, configs, outs);
+  }
 }
 
 gcf_status gcf_sample_batch(gcf_ctx* c, int n_chains, int n_sweeps, uint64_t seed, int8_t* configs,

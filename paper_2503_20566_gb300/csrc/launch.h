@@ -18,6 +18,12 @@ cudaError_t launch_vmc_grouped(const KParams<T>& k, int grid, int block, size_t 
 // resident blocks per SM of vmc_kernel_grouped<T>; 0 if the launch cannot fit
 template <class T>
 int occupancy_vmc_grouped(int block, size_t smem);
+// chains of several contexts in one launch (one chain per CTA of 256 threads)
+template <class T>
+cudaError_t launch_vmc_multi(const KParams<T>* ks, int n_ctx, const long long* start, long long total, T* arena,
+                             long long ws_stride, int grid, size_t smem, cudaStream_t st);
+template <class T>
+int occupancy_vmc_multi(size_t smem);
 // bytes of the per-chain shared state of the VMC kernels (16-byte aligned)
 size_t sharedv_bytes();
 cudaError_t launch_init_configs(int N, int Lx, int Ly, int matter, const int* Q, int n_chains,

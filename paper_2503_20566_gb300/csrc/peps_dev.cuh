@@ -150,11 +150,6 @@ __device__ inline void gather_box(const X ex, const KParams<T>& k, int x, int y,
 }
 
 template <class T>
-__device__ inline T* ws_of(const KParams<T>& k) {
-  return k.scratch + (long long)blockIdx.x * k.ws_stride;
-}
-
-template <class T>
 __device__ inline T* net_box(const KParams<T>& k, T* ws, int x, int y) {
   return ws + k.o_net + (long long)(y * k.Lx + x) * (k.Dk * k.Dk * k.Dk * k.Dk);
 }

@@ -839,4 +839,32 @@ __global__ void __launch_bounds__(256, 2) vmc_kernel_grouped(const __grid_consta
   grouped_body<T, GroupExec<128>, 128>(k);
 }
 
+// Chains of several contexts (lattices of different sizes) in one persistent
+// launch: global chain g belongs to context i with start[i] <= g <
+// start[i+1] and is that context's chain g - start[i].  One chain per CTA;
+// the scratch arena has a slot of ws_stride (the largest of the contexts)
+// per CTA; dynamic shared memory is the largest of the contexts' needs.
+template <class T>
+__global__ void __launch_bounds__(256, 2)
+    vmc_kernel_multi(const KParams<T>* __restrict__ ks, int n_ctx, const long long* __restrict__ start,
+                     long long total, T* arena, long long ws_stride) {
+  extern __shared__ __align__(16) int8_t dyn_smem[];
+  __shared__ SharedV sv;
+  CtaExec ex;
+  T* ws = arena + (long long)blockIdx.x * ws_stride;
+  int cur = -1;
+  for (long long gidx = blockIdx.x; gidx < total; gidx += gridDim.x) {
+    int i = 0;
+    while (i + 1 < n_ctx && gidx >= start[i + 1]) ++i;
+    const KParams<T>& k = ks[i];
+    if (i != cur) {
+      if (threadIdx.x < 4) g_gemm_mode[threadIdx.x] = k.gemm_mode;
+      __syncthreads();
+      init_trivial_slots(ex, k, ws);
+      cur = i;
+    }
+    run_chain(ex, k, ws, sv, dyn_smem, (T*)(dyn_smem + k.smem_cfg_bytes), (int)(gidx - start[i]));
+  }
+}
+
 }  // namespace gcf
