@@ -236,10 +236,12 @@ def main():
     seeds = replicas.rank_seeds(rank)
     ctx = G.Context(w["N"], w["Lx"], w["Ly"], w["D"], w["chi"], h=w["h_p"], g=w["g"], precision=args.precision,
                     seed=seeds["tensors"])
-    kernel_name = ctx.kernel_name + "<float>"
     powers = torch.from_numpy(synth.plaquette_powers(seeds["chains"], n_chains, (w["Lx"] - 1) * (w["Ly"] - 1),
                                                      w["N"]))
     configs = ctx.init_configs(n_chains, powers=powers)
+    # the library's autotuner picks the kernel form (executor x shared-memory level) on this workload
+    tune_ms = ctx.autotune(configs, n_sweeps=1)
+    kernel_name = ctx.kernel_name + "<float>"
     samples = ctx.alloc_samples(n_chains, n_sweeps, grad=True)
     stream = ctx.stream
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -310,7 +312,10 @@ def main():
             "config": {"workload": w["workload"], "lattice": "8x8 open", "gauge": "Z2", "D": w["D"],
                        "chi": w["chi"], "chains": n_chains, "sweeps_per_step": n_sweeps, "h": w["g"],
                        "precision": args.precision, "sr": SR_ARGS, "parallelism": f"replicas{world}",
-                       "l2": "256 MiB buffer written between timed steps (outside the events)"},
+                       "l2": "256 MiB buffer written between timed steps (outside the events)",
+                       "kernel_form": {"kernel": kernel_name, "smem_level": ctx.smem_level,
+                                       "autotune_ms_per_form": [round(t, 3) if t < 1e299 else None
+                                                                for t in tune_ms]}},
             "gpu_launches": launches,
             "kernel_ms": float(np.mean(t_kernel)),
             "sr_ms": float(np.mean([a - b for a, b in zip(t_steps, t_kernel)])),

@@ -265,6 +265,24 @@ int64_t gcf_launch_count(const gcf_ctx* ctx);
  * forces one.  Both compute the same results. */
 int gcf_executor(const gcf_ctx* ctx);
 
+/* Shared-memory placement level of the kernel form this context launches
+ * (implementation choice; no counterpart in the paper): 0 = configuration
+ * only, 1 = + hot buffers (network boxes, proposals, current environments,
+ * GEMM temporaries), 2 = + the staged boundary-MPS rows of the current pass,
+ * 3 = + the right environments of the pass. */
+int gcf_smem_level(const gcf_ctx* ctx);
+
+/* Autotuner (implementation choice; no counterpart in the paper): times every
+ * kernel form that fits an SM (executor x shared-memory level) on
+ * gcf_sample_batch of a copy of `configs` (device, n_chains x cfg_len, left
+ * unchanged) for n_sweeps sweeps, after one warm-up run per form, and keeps
+ * the fastest for this context's later launches.  ms (host, optional): the
+ * time of form i (1e300 if it did not launch) for i < *n_forms on entry;
+ * *n_forms (optional) is set to the number of forms tried.  Allocates and
+ * frees its own work buffers; synchronises the context's stream. */
+gcf_status gcf_autotune(gcf_ctx* ctx, int n_chains, int n_sweeps, const int8_t* configs, double* ms,
+                        int* n_forms);
+
 #ifdef __cplusplus
 }
 #endif

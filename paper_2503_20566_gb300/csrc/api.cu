@@ -166,6 +166,20 @@ void plan_group(gcf_ctx* c) {
   }
 }
 
+// Kernel form: executor and shared-memory level (sizes follow from the plan).
+void set_form(gcf_ctx* c, int exec, int level) {
+  Plan& p = c->plan;
+  c->exec = exec;
+  if (exec == EXEC_GROUP) {
+    p.group_level = level;
+    p.group_smem = (sharedv_bytes() + (size_t)p.cfg_bytes + (size_t)p.level_elems(level) * c->sbytes + 15) / 16 * 16;
+  } else {
+    p.cta_level = level;
+    p.hot_elems = p.level_elems(level);
+    p.dyn_smem = (size_t)p.cfg_bytes + (size_t)p.hot_elems * c->sbytes;
+  }
+}
+
 void build_plan(gcf_ctx* c) {
   const int Lx = c->m.Lx, Ly = c->m.Ly, Dk = c->Dk, chi = c->m.chi;
   const int W = Lx + 1;
@@ -876,6 +890,78 @@ gcf_status gcf_log_grad_vjp(gcf_ctx* c, int n, const int8_t* configs, const doub
   CUDA_TRY(c, e);
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return GCF_OK;
+}
+
+gcf_status gcf_autotune(gcf_ctx* c, int n_chains, int n_sweeps, const int8_t* configs, double* ms, int* n_forms) {
+  if (!c || n_chains < 1 || n_sweeps < 1 || !configs) return GCF_EINVAL;
+  // candidate forms that fit an SM (227 KB of shared memory per block)
+  const size_t limit = 227 * 1024 - 8 * 1024;
+  std::vector<std::pair<int, int>> forms;
+  for (int lv = 0; lv <= 3; ++lv) {
+    const size_t cta = (size_t)c->plan.cfg_bytes + (size_t)c->plan.level_elems(lv) * c->sbytes;
+    if (cta <= limit) forms.push_back({EXEC_CTA, lv});
+    const size_t grp = 2 * (sharedv_bytes() + (size_t)c->plan.cfg_bytes + (size_t)c->plan.level_elems(lv) * c->sbytes);
+    if (lv >= 1 && grp <= limit) forms.push_back({EXEC_GROUP, lv});
+  }
+  const int keep_exec = c->exec, keep_cta = c->plan.cta_level, keep_grp = c->plan.group_level;
+  const size_t bytes = (size_t)n_chains * c->cfg_len;
+  int8_t* work = nullptr;
+  double* la = nullptr;
+  if (cudaMalloc(&work, bytes) != cudaSuccess || cudaMalloc(&la, sizeof(double) * (size_t)n_chains * n_sweeps) != cudaSuccess) {
+    cudaFree(work);
+    return fail(c, GCF_ENOMEM, "autotune buffers");
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  gcf_samples out{};
+  out.log_abs = la;
+  double best = 1e300;
+  int best_i = -1;
+  gcf_status st = GCF_OK;
+  for (size_t i = 0; i < forms.size() && st == GCF_OK; ++i) {
+    set_form(c, forms[i].first, forms[i].second);
+    double t = 1e300;
+    for (int rep = 0; rep < 2 && st == GCF_OK; ++rep) {  // first run warms up
+      if (cudaMemcpyAsync(work, configs, bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
+        st = fail(c, GCF_ECUDA, "autotune copy");
+        break;
+      }
+      cudaEventRecord(e0, c->stream);
+      int gauss = 0;
+      const gcf_status r = dispatch(c, 1, WANT_AMP, n_chains, n_sweeps, 1, work, &out, &gauss);
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      if (r == GCF_EINVAL || r == GCF_ECUDA) { t = 1e300; c->err.clear(); break; }  // form does not launch
+      if (r != GCF_OK) { st = r; break; }
+      if (gauss) { st = fail(c, GCF_EGAUSS, "configuration violates the Gauss law"); break; }
+      float f = 0.f;
+      cudaEventElapsedTime(&f, e0, e1);
+      t = f;
+    }
+    if (ms && n_forms && (int)i < *n_forms) ms[i] = t;
+    if (t < best) { best = t; best_i = (int)i; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(work);
+  cudaFree(la);
+  if (n_forms) *n_forms = (int)forms.size();
+  // restore the planned levels of both executors, then take the winner
+  c->plan.cta_level = keep_cta;
+  c->plan.group_level = keep_grp;
+  set_form(c, EXEC_CTA, keep_cta);
+  set_form(c, EXEC_GROUP, keep_grp);
+  c->exec = keep_exec;
+  if (st != GCF_OK) return st;
+  if (best_i < 0) return fail(c, GCF_ECUDA, "no kernel form launched");
+  set_form(c, forms[best_i].first, forms[best_i].second);
+  return GCF_OK;
+}
+
+int gcf_smem_level(const gcf_ctx* c) {
+  if (!c) return -1;
+  return c->exec == EXEC_GROUP ? c->plan.group_level : c->plan.cta_level;
 }
 
 gcf_status gcf_sample_multi(gcf_ctx* const* ctxs, int n_ctx, const int* n_chains, int n_sweeps,
