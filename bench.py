@@ -66,7 +66,7 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-PROFILE = os.path.join(ROOT, "profiles", "vmc_kernel_f32_z2_8x8_D4_chi16.md")
+PROFILE = os.path.join(ROOT, "profiles", "vmc_kernel_grouped_f32_z2_8x8_D4_chi16.md")
 
 
 def profiled_traffic(samples_per_launch):
@@ -198,9 +198,10 @@ def main():
     ap.add_argument("--impl", default="gcf", choices=["gcf", "reference"])
     ap.add_argument("--chains", type=int, default=WORKLOAD["chains"])
     ap.add_argument("--sweeps", type=int, default=WORKLOAD["sweeps"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the planner's kernel form")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -240,7 +241,7 @@ def main():
                                                      w["N"]))
     configs = ctx.init_configs(n_chains, powers=powers)
     # the library's autotuner picks the kernel form (executor x shared-memory level) on this workload
-    tune_ms = ctx.autotune(configs, n_sweeps=1)
+    tune_ms = [] if args.no_autotune else ctx.autotune(configs, n_sweeps=1)
     kernel_name = ctx.kernel_name + "<float>"
     samples = ctx.alloc_samples(n_chains, n_sweeps, grad=True)
     stream = ctx.stream
