@@ -61,6 +61,7 @@ struct gcf_ctx {
   int device = 0, sms = 0;
   Plan plan;
   int exec = 0, group_threads = 64;
+  int tab_ints = 0;  // ints in d_tables
   // device
   void* d_params = nullptr;
   int* d_Q = nullptr;
@@ -164,6 +165,50 @@ void plan_group(gcf_ctx* c) {
     if (!std::strcmp(e, "group")) c->exec = EXEC_GROUP;
     if (!std::strcmp(e, "cta")) c->exec = EXEC_CTA;
   }
+}
+
+// Tables derived from the bond dimensions, appended after the six plan
+// tables (bondB, bondT, qrB, svdB, qrT, svdT; (Ly+1) x (Lx+1) each):
+//   offB[j][c]: offset of site c in B slot j (packed bd[c] x phys x bd[c+1]);
+//   offT[r][c]: the same for T slot r;
+//   denseB[r], denseT[r]: 1 if absorbing row r into B (slot r -> r+1) or into
+//   T (slot r+1 -> r) takes the exact identity + core form: every output bond
+//   at full rank min(p^c, p^(L-c)) and the dense state within the buffers.
+void append_derived_tables(const gcf_ctx* c, std::vector<int>& t) {
+  const Plan& p = c->plan;
+  const int Lx = c->m.Lx, Ly = c->m.Ly, Dk = c->Dk, W = Lx + 1, R = Ly + 1;
+  auto physB = [&](int j) { return j == 0 ? 1 : Dk; };
+  auto physT = [&](int r) { return r == Ly ? 1 : Dk; };
+  auto offsets = [&](const int* bd, int phys) {
+    int o = 0;
+    for (int cc = 0; cc < Lx; ++cc) { t.push_back(o); o += bd[cc] * phys * bd[cc + 1]; }
+    t.push_back(o);
+  };
+  for (int j = 0; j < R; ++j) offsets(&p.bondB[j * W], physB(j));
+  for (int r = 0; r < R; ++r) offsets(&p.bondT[r * W], physT(r));
+  const long long dmax = p.tmp_max;
+  auto dense = [&](const int* bdi, int pin, const int* bdo, int pout) {
+    int ok = (pout == Dk) ? 1 : 0;
+    for (int cc = 0; cc <= Lx; ++cc) {
+      long long lo = 1, hi = 1;
+      for (int i = 0; i < cc; ++i) lo *= pout;
+      for (int i = 0; i < Lx - cc; ++i) hi *= pout;
+      if (bdo[cc] != (lo < hi ? lo : hi)) ok = 0;
+    }
+    long long pw = 1;
+    for (int i = 0; i < Lx && pw <= dmax; ++i) pw *= pout;
+    if (pw * Dk > dmax) ok = 0;
+    long long rows = 1;
+    for (int cc = 0; cc < Lx && ok; ++cc) {
+      rows *= pin;
+      if (rows * bdi[cc + 1] > dmax) ok = 0;
+    }
+    return ok;
+  };
+  for (int r = 0; r < R; ++r)
+    t.push_back(r + 1 < R ? dense(&p.bondB[r * W], physB(r), &p.bondB[(r + 1) * W], physB(r + 1)) : 0);
+  for (int r = 0; r < R; ++r)
+    t.push_back(r + 1 < R ? dense(&p.bondT[(r + 1) * W], physT(r + 1), &p.bondT[r * W], physT(r)) : 0);
 }
 
 // Kernel form: executor and shared-memory level (sizes follow from the plan).
@@ -402,6 +447,8 @@ KParams<T> make_params(gcf_ctx* c) {
   k.svdB = c->d_tables + 3 * R * W;
   k.qrT = c->d_tables + 4 * R * W;
   k.svdT = c->d_tables + 5 * R * W;
+  k.tab = c->d_tables;
+  k.tab_ints = c->tab_ints;
   k.scratch = (T*)c->d_scratch;
   k.ws_stride = p.ws_stride;
   k.o_net = p.o_net; k.o_prop = p.o_prop; k.o_B = p.o_B; k.o_T = p.o_T; k.o_Q = p.o_Q;
@@ -714,6 +761,8 @@ gcf_status gcf_init_peps(const gcf_model* model, uint64_t seed, void* cuda_strea
   std::vector<int> tables;
   for (auto* v : {&c->plan.bondB, &c->plan.bondT, &c->plan.qrB, &c->plan.svdB, &c->plan.qrT, &c->plan.svdT})
     tables.insert(tables.end(), v->begin(), v->end());
+  append_derived_tables(c, tables);
+  c->tab_ints = (int)tables.size();
   bool ok = cudaMalloc(&c->d_params, c->n_params * c->sbytes) == cudaSuccess &&
             cudaMalloc(&c->d_Q, sizeof(int) * c->n_s) == cudaSuccess &&
             cudaMalloc(&c->d_voff, sizeof(long long) * c->n_s) == cudaSuccess &&

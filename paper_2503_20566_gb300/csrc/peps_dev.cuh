@@ -44,6 +44,11 @@ struct KParams {
   const int* svdB;
   const int* qrT;    // T-step r, r = 1..Ly-1
   const int* svdT;
+  // all tables in one block: the six above, then the derived offB, offT
+  // (site offsets per B / T slot, rows of Lx+1) and denseB, denseT (Ly+1
+  // flags each: the step takes the identity + core form)
+  const int* tab;
+  int tab_ints;
   // scratch
   T* scratch;
   long long ws_stride;     // elements per CTA
@@ -152,17 +157,6 @@ __device__ inline void gather_box(const X ex, const KParams<T>& k, int x, int y,
 template <class T>
 __device__ inline T* net_box(const KParams<T>& k, T* ws, int x, int y) {
   return ws + k.o_net + (long long)(y * k.Lx + x) * (k.Dk * k.Dk * k.Dk * k.Dk);
-}
-
-// site offsets of a packed MPS with bond table bd and physical dim phys
-template <class X>
-__device__ inline void mps_offsets(const X ex, const int* bd, int phys, int Lx, int* off) {
-  if (ex.tid() == 0) {
-    int o = 0;
-    for (int c = 0; c < Lx; ++c) { off[c] = o; o += bd[c] * phys * bd[c + 1]; }
-    off[Lx] = o;
-  }
-  ex.sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -316,7 +310,8 @@ __device__ __noinline__ int dense_absorb(const X ex, const KParams<T>& k, Shared
 template <class T, class X>
 __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* ws, T* hot_base, Shared& sh, const T* net,
                                   const T* mps_in, const int* bdi, int pin, int row, int flip, T* mout,
-                                  const int* bdo, int pout, const int* qr, const int* svd) {
+                                  const int* bdo, int pout, const int* qr, const int* svd, const int* offi,
+                                  const int* offo, int dense) {
   const int Lx = k.Lx, Dk = k.Dk;
   const int D3 = Dk * Dk * Dk, D2 = Dk * Dk;
   const int sd = flip ? 1 : Dk, su = flip ? Dk : 1;
@@ -327,31 +322,15 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
   T* Jm = ws + k.o_J;
   T* Qs = ws + k.o_Q;
   int logs = 0;
-  mps_offsets(ex, bdi, pin, Lx, sh.bd_off);
-  mps_offsets(ex, bdo, pout, Lx, sh.bd_off2);
-
-  // Dense (identity + core) path: every output bond at full rank and the
-  // dense state small enough.
-  if (ex.tid() == 0) {
-    int ok = (pout == Dk) ? 1 : 0;
-    long long pw = 1;
-    for (int c = 0; c <= Lx; ++c) {
-      long long lo = 1, hi = 1;
-      for (int i = 0; i < c; ++i) lo *= pout;
-      for (int i = 0; i < Lx - c; ++i) hi *= pout;
-      if (bdo[c] != (lo < hi ? lo : hi)) ok = 0;
-    }
-    for (int i = 0; i < Lx && pw <= k.dense_max; ++i) pw *= pout;
-    if (pw * Dk > k.dense_max) ok = 0;
-    long long rows = 1;
-    for (int c = 0; c < Lx && ok; ++c) {
-      rows *= pin;
-      if (rows * bdi[c + 1] > k.dense_max) ok = 0;
-    }
-    sh.iflag[2] = ok;
+#pragma unroll 1
+  for (int c = ex.tid(); c <= Lx; c += ex.size()) {
+    sh.bd_off[c] = offi[c];
+    sh.bd_off2[c] = offo[c];
   }
   ex.sync();
-  if (sh.iflag[2]) {
+  // Dense (identity + core) path: every output bond at full rank and the
+  // dense state small enough (flag planned on the host).
+  if (dense) {
     T* bufA = k.hot_in_smem ? hot_base + k.so_t1 : ws + k.o_t1;
     T* bufB = k.hot_in_smem ? hot_base + k.so_t2 : ws + k.o_t2;
     return dense_absorb<T>(ex, k, sh, net, mps_in, bdi, pin, row, flip, mout, bdo, pout, bufA, bufB);

@@ -49,9 +49,10 @@ struct Chain {
   T *net, *props, *cop, *envL, *envX, *envY, *env3L, *env3X, *env3Y, *t1, *t2;
   T* hot;
   T *eR, *e3R, *sB, *sT;  // right environments; staged MPS rows (or the slots)
+  const int* tab;         // the context's tables (shared-memory copy when it fits)
 
-  __device__ Chain(const X ex_, const KParams<T>& kk, T* w, SharedV& s, int8_t* c, int ch, T* hot_)
-      : ex(ex_), k(kk), ws(w), sv(s), cfg(c), chain(ch), hot(hot_) {
+  __device__ Chain(const X ex_, const KParams<T>& kk, T* w, SharedV& s, int8_t* c, int ch, T* hot_, const int* tab_)
+      : ex(ex_), k(kk), ws(w), sv(s), cfg(c), chain(ch), hot(hot_), tab(tab_) {
     key = stream_key(k.seed, (unsigned long long)ch);
     if (k.hot_in_smem) {
       net = hot_ + k.so_net; props = hot_ + k.so_prop; cop = hot_ + k.so_cop;
@@ -86,8 +87,24 @@ struct Chain {
 
   __device__ T* Bslot(int j) const { return ws + k.o_B + (long long)j * k.mps_stride; }
   __device__ T* Tslot(int r) const { return ws + k.o_T + (long long)r * k.mps_stride; }
-  __device__ const int* bdB(int j) const { return k.bondB + j * (k.Lx + 1); }
-  __device__ const int* bdT(int r) const { return k.bondT + r * (k.Lx + 1); }
+  __device__ int tW() const { return k.Lx + 1; }
+  __device__ int tR() const { return k.Ly + 1; }
+  __device__ const int* bdB(int j) const { return tab + j * tW(); }
+  __device__ const int* bdT(int r) const { return tab + (tR() + r) * tW(); }
+  __device__ const int* qrBt(int r) const { return tab + (2 * tR() + r) * tW(); }
+  __device__ const int* svdBt(int r) const { return tab + (3 * tR() + r) * tW(); }
+  __device__ const int* qrTt(int r) const { return tab + (4 * tR() + r) * tW(); }
+  __device__ const int* svdTt(int r) const { return tab + (5 * tR() + r) * tW(); }
+  __device__ const int* offBt(int j) const { return tab + (6 * tR() + j) * tW(); }
+  __device__ const int* offTt(int r) const { return tab + (7 * tR() + r) * tW(); }
+  __device__ int denseB(int r) const { return tab[8 * tR() * tW() + r]; }
+  __device__ int denseT(int r) const { return tab[8 * tR() * tW() + tR() + r]; }
+  // site offsets of the MPS rows of the current pass into shared memory
+  __device__ void load_offsets(const int* src, int* dst) {
+#pragma unroll 1
+    for (int c = ex.tid(); c <= k.Lx; c += ex.size()) dst[c] = src[c];
+    ex.sync();
+  }
   __device__ int physB(int j) const { return j == 0 ? 1 : k.Dk; }   // B[j-1] phys = up dim of row j-1
   __device__ int physT(int r) const { return r == k.Ly ? 1 : k.Dk; } // T[r] phys = down dim of row r
   __device__ T* box(int x, int y) const {
@@ -212,15 +229,15 @@ struct Chain {
   // ---- boundary MPS --------------------------------------------------------
   __device__ __noinline__ void absorb_B(int r) {  // B[r] = absorb(B[r-1], row r)
     const int ls = absorb_compress(ex, k, ws, hot, sv.base, net, Bslot(r), bdB(r), physB(r), r, 0, Bslot(r + 1),
-                                      bdB(r + 1), physB(r + 1), k.qrB + r * (k.Lx + 1),
-                                      k.svdB + r * (k.Lx + 1));
+                                      bdB(r + 1), physB(r + 1), qrBt(r), svdBt(r), offBt(r), offBt(r + 1),
+                                      denseB(r));
     if (ex.tid() == 0) sv.logB[r + 1] = sv.logB[r] + ls;
     ex.sync();
   }
   __device__ __noinline__ void absorb_T(int r) {  // T[r] = absorb(T[r+1], row r flipped)
     const int ls = absorb_compress(ex, k, ws, hot, sv.base, net, Tslot(r + 1), bdT(r + 1), physT(r + 1), r, 1,
-                                      Tslot(r), bdT(r), physT(r), k.qrT + r * (k.Lx + 1),
-                                      k.svdT + r * (k.Lx + 1));
+                                      Tslot(r), bdT(r), physT(r), qrTt(r), svdTt(r), offTt(r + 1), offTt(r),
+                                      denseT(r));
     if (ex.tid() == 0) sv.logT[r] = sv.logT[r + 1] + ls;
     ex.sync();
   }
@@ -268,8 +285,8 @@ struct Chain {
   // as mantissa (vr, vi) and binary exponent ve
   __device__ __noinline__ void strip_right_envs(int r, R& vr, R& vi, int& ve) {
     const int Lx = k.Lx;
-    mps_offsets(ex, bdB(r), physB(r), Lx, sv.offB);
-    mps_offsets(ex, bdT(r + 2), physT(r + 2), Lx, sv.offT);
+    load_offsets(offBt(r), sv.offB);
+    load_offsets(offTt(r + 2), sv.offT);
     stage(r, r + 2, physB(r), physT(r + 2));
     if (ex.tid() == 0) { envR(Lx)[0] = one<T>(); sv.logR[Lx] = 0; }
     ex.sync();
@@ -343,8 +360,8 @@ struct Chain {
 
   __device__ __noinline__ void row_right_envs(int r, R& vr, R& vi, int& ve) {
     const int Lx = k.Lx;
-    mps_offsets(ex, bdB(r), physB(r), Lx, sv.offB);
-    mps_offsets(ex, bdT(r + 1), physT(r + 1), Lx, sv.offT);
+    load_offsets(offBt(r), sv.offB);
+    load_offsets(offTt(r + 1), sv.offT);
     stage(r, r + 1, physB(r), physT(r + 1));
     if (ex.tid() == 0) { env3R(Lx)[0] = one<T>(); sv.logR[Lx] = 0; }
     ex.sync();
@@ -747,9 +764,28 @@ __device__ void init_trivial_slots(const X ex, const KParams<T>& k, T* ws) {
   ex.sync();
 }
 
+// The context's integer tables (bond dimensions, QR / SVD plans, MPS site
+// offsets, dense-step flags) are read in every environment step and by the
+// serial bookkeeping of each absorption; a shared-memory copy per CTA turns
+// those dependent global loads into shared-memory loads.  Lattices whose
+// tables exceed the copy (above about 16 x 16) read them from global memory.
+constexpr int kTabCap = 2560;
+__shared__ int g_tab[kTabCap];
+
+template <class T>
+__device__ const int* stage_tables(const KParams<T>& k) {
+  const bool fits = k.tab_ints <= kTabCap;
+  if (fits) {
+#pragma unroll 1
+    for (int i = threadIdx.x; i < k.tab_ints; i += blockDim.x) g_tab[i] = k.tab[i];
+  }
+  __syncthreads();
+  return fits ? g_tab : k.tab;
+}
+
 // Per-chain body shared by both kernels.
 template <class T, class X>
-__device__ void run_chain(const X ex, const KParams<T>& k, T* ws, SharedV& sv, int8_t* cfg, T* hot,
+__device__ void run_chain(const X ex, const KParams<T>& k, T* ws, SharedV& sv, int8_t* cfg, T* hot, const int* tab,
                           int chain) {
   int8_t* gcfg = k.configs + (long long)chain * k.cfg_len;
 #pragma unroll 1
@@ -758,7 +794,7 @@ __device__ void run_chain(const X ex, const KParams<T>& k, T* ws, SharedV& sv, i
     sv.logB[0] = 0; sv.logT[k.Ly] = 0; sv.n_acc = 0; sv.n_prop = 0;
   }
   ex.sync();
-  Chain<T, X> ch(ex, k, ws, sv, cfg, chain, hot);
+  Chain<T, X> ch(ex, k, ws, sv, cfg, chain, hot, tab);
   const bool ok = ch.check_and_gather_all();
   if (!ok) {
     if (ex.leader()) {
@@ -806,11 +842,11 @@ __global__ void __launch_bounds__(256, 2) vmc_kernel(const __grid_constant__ KPa
   __shared__ SharedV sv;
   CtaExec ex;
   if (threadIdx.x < 4) g_gemm_mode[threadIdx.x] = k.gemm_mode;
-  __syncthreads();
+  const int* tab = stage_tables(k);
   T* ws = k.scratch + (long long)blockIdx.x * k.ws_stride;
   init_trivial_slots(ex, k, ws);
   for (int chain = blockIdx.x; chain < k.n_chains; chain += gridDim.x)
-    run_chain(ex, k, ws, sv, dyn_cfg, hot, chain);
+    run_chain(ex, k, ws, sv, dyn_cfg, hot, tab, chain);
 }
 
 // Several chains per CTA, one per group of G = 128 threads (GroupExec, a
@@ -820,7 +856,7 @@ template <class T, class X, int G>
 __device__ void grouped_body(const KParams<T>& k) {
   extern __shared__ __align__(16) int8_t dyn_smem[];
   if (threadIdx.x < 4) g_gemm_mode[threadIdx.x] = k.gemm_mode;
-  __syncthreads();
+  const int* tab = stage_tables(k);
   const int g = threadIdx.x / G, NG = blockDim.x / G;
   int8_t* base = dyn_smem + g * k.group_smem_bytes;
   SharedV& sv = *reinterpret_cast<SharedV*>(base);
@@ -831,7 +867,7 @@ __device__ void grouped_body(const KParams<T>& k) {
   T* ws = k.scratch + slot * k.ws_stride;
   init_trivial_slots(ex, k, ws);
   for (long long chain = slot; chain < k.n_chains; chain += (long long)gridDim.x * NG)
-    run_chain(ex, k, ws, sv, cfg, hot, (int)chain);
+    run_chain(ex, k, ws, sv, cfg, hot, tab, (int)chain);
 }
 
 template <class T>
@@ -852,18 +888,20 @@ __global__ void __launch_bounds__(256, 2)
   __shared__ SharedV sv;
   CtaExec ex;
   T* ws = arena + (long long)blockIdx.x * ws_stride;
+  const int* tab = nullptr;
   int cur = -1;
   for (long long gidx = blockIdx.x; gidx < total; gidx += gridDim.x) {
     int i = 0;
     while (i + 1 < n_ctx && gidx >= start[i + 1]) ++i;
     const KParams<T>& k = ks[i];
     if (i != cur) {
+      __syncthreads();  // the previous context's chain is done with the tables
       if (threadIdx.x < 4) g_gemm_mode[threadIdx.x] = k.gemm_mode;
-      __syncthreads();
+      tab = stage_tables(k);
       init_trivial_slots(ex, k, ws);
       cur = i;
     }
-    run_chain(ex, k, ws, sv, dyn_smem, (T*)(dyn_smem + k.smem_cfg_bytes), (int)(gidx - start[i]));
+    run_chain(ex, k, ws, sv, dyn_smem, (T*)(dyn_smem + k.smem_cfg_bytes), tab, (int)(gidx - start[i]));
   }
 }
 
