@@ -332,6 +332,12 @@ __device__ inline int exp2_of(float m) {
 }
 __device__ inline float pow2f(int e) { return ldexpf(1.0f, e); }
 __device__ inline double pow2d(int e) { return ldexp(1.0, e); }
+// 2^e built from its IEEE-754 binary64 fields (biased exponent e + 1023, zero
+// fraction) for normal e; ldexp outside that range.
+__device__ inline double pow2d_exact(int e) {
+  if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(e + 1023) << 52);
+  return ldexp(1.0, e);
+}
 template <class R> __device__ inline R pow2r(int e);
 template <> __device__ inline float pow2r<float>(int e) { return ldexpf(1.0f, e); }
 template <> __device__ inline double pow2r<double>(int e) { return ldexp(1.0, e); }

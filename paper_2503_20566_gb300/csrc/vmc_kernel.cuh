@@ -115,13 +115,17 @@ struct Chain {
   // ---- configuration moves on the shared copy (thread 0 writes) ---------
   __device__ __noinline__ void plaq_apply(int x, int y, int t) {
     if (ex.tid() == 0) {
+      // link values and t are in [0, N): one conditional add / subtract
+      // replaces the modulo
       const int N = k.N;
       int8_t* h = cfg;
       int8_t* v = cfg + k.n_h;
-      h[y * (k.Lx - 1) + x] = (int8_t)((h[y * (k.Lx - 1) + x] + t) % N);
-      v[y * k.Lx + x + 1] = (int8_t)((v[y * k.Lx + x + 1] + t) % N);
-      h[(y + 1) * (k.Lx - 1) + x] = (int8_t)((h[(y + 1) * (k.Lx - 1) + x] - t + N) % N);
-      v[y * k.Lx + x] = (int8_t)((v[y * k.Lx + x] - t + N) % N);
+      auto up = [N, t](int8_t& a) { const int s = a + t; a = (int8_t)(s >= N ? s - N : s); };
+      auto dn = [N, t](int8_t& a) { const int s = a - t; a = (int8_t)(s < 0 ? s + N : s); };
+      up(h[y * (k.Lx - 1) + x]);
+      up(v[y * k.Lx + x + 1]);
+      dn(h[(y + 1) * (k.Lx - 1) + x]);
+      dn(v[y * k.Lx + x]);
     }
     ex.sync();
   }
@@ -392,7 +396,7 @@ struct Chain {
       bool acc;
       if (!(n2 > 0.0)) acc = false;
       else if (!(d2 > 0.0)) acc = true;
-      else acc = u * d2 < ldexp(n2, 2 * (ne - de));
+      else acc = u * d2 < n2 * pow2d_exact(2 * (ne - de));
       sv.flag = acc ? 1 : 0;
     }
     ex.sync();
@@ -403,12 +407,18 @@ struct Chain {
   // eacc += coef * num / den (thread 0)
   __device__ __noinline__ void add_ratio(double coef, R nr, R ni, int ne, R dr, R di, int de) {
     if (ex.tid() == 0) {
-      const double d2 = (double)dr * dr + (double)di * di;
-      const double f = ldexp(1.0, ne - de) / d2;
-      const double rr = ((double)nr * dr + (double)ni * di) * f;
-      const double ri = ((double)ni * dr - (double)nr * di) * f;
-      sv.eacc[0] += coef * rr;
-      sv.eacc[1] += coef * ri;
+      // (nr + i ni) / (dr + i di) in the chain's precision, after scaling
+      // both by the same exact power of two (|d| in [0.5, 1), so d2 cannot
+      // underflow), then the exact power-of-two scale and FP64 accumulation
+      const float m = fmaxf(fabsf((float)dr), fabsf((float)di));
+      const R sc = m > 0.f ? pow2r<R>(-exp2_of(m)) : R(1);
+      dr *= sc; di *= sc; nr *= sc; ni *= sc;
+      const R d2 = dr * dr + di * di;
+      const R qr = (nr * dr + ni * di) / d2;
+      const R qi = (ni * dr - nr * di) / d2;
+      const double f = pow2d_exact(ne - de);
+      sv.eacc[0] += coef * ((double)qr * f);
+      sv.eacc[1] += coef * ((double)qi * f);
     }
   }
 
