@@ -203,7 +203,10 @@ gcf_status gcf_sample_batch(gcf_ctx* ctx, int n_chains, int n_sweeps, uint64_t s
 
 /* FP64 reductions and parameter update (Sec. S-1 Eq. S3; Sec. S-3 Eqs. S6-S8):
  *   F = <O^* E_loc> - <O^*><E_loc>,  S = <O^* O> - <O^*><O>   (Eq. S7)
- *   x = (S + diag_shift I)^{-1} F by conjugate gradient (S never formed).
+ *   x = (S + diag_shift I)^{-1} F by conjugate gradient (S never formed);
+ *   with n_samples >= n_params (S of full rank) the CG is preconditioned by
+ *   the diagonal of S + diag_shift I, otherwise it is plain CG, which ends in
+ *   about n_samples iterations on the low-rank-plus-shift system.
  *   mode GCF_SR:          A <- A - lr * x
  *   mode GCF_TDVP_STAGE1: A <- A + c1 * dt * (-i x),  c1 = (1+i)/2
  *   mode GCF_TDVP_STAGE2: A <- A + c2 * dt * (-i x),  c2 = (1-i)/2
@@ -211,7 +214,8 @@ gcf_status gcf_sample_batch(gcf_ctx* ctx, int n_chains, int n_sweeps, uint64_t s
  * gcf_sample_batch for n_samples samples, all with equal weight.
  * stats: host double[8] = {Re<E>, Im<E>, std error of Re<E> over chains
  * (n_chains > 1, else over samples), CG iterations, relative residual,
- * |F|, 0, 0}; n_chains is the number of chains the samples came from
+ * |F|, 1 if CG reached tol, 1 if the diagonal preconditioner was used};
+ * n_chains is the number of chains the samples came from
  * (chain-major order).  GCF_ETIMEOUT if CG hits max_iter before tol (the
  * update is still applied). */
 gcf_status gcf_sr_step(gcf_ctx* ctx, int n_samples, int n_chains, const double* e_loc,

@@ -663,9 +663,10 @@ gcf_status upload_params(gcf_ctx* c, const double* vals /* n_params or 2*n_param
 gcf_status ensure_sr(gcf_ctx* c, long long Ns, int n_chains) {
   if (!c->sr.obar) {
     const long long Np = c->n_params;
-    cdouble** vecs[6] = {&c->sr.obar, &c->sr.F, &c->sr.x, &c->sr.r, &c->sr.p, &c->sr.Ap};
+    cdouble** vecs[7] = {&c->sr.obar, &c->sr.F, &c->sr.x, &c->sr.r, &c->sr.p, &c->sr.Ap, &c->sr.z};
     for (auto v : vecs)
       if (cudaMalloc(v, sizeof(cdouble) * Np) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR vectors");
+    if (cudaMalloc(&c->sr.dinv, sizeof(double) * Np) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR vectors");
     if (cudaMalloc(&c->sr.tbar, sizeof(cdouble)) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR");
     if (cudaMalloc(&c->sr.scal, 32 * sizeof(double)) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR");
   }
@@ -792,7 +793,7 @@ gcf_status gcf_init_peps(const gcf_model* model, uint64_t seed, void* cuda_strea
 void gcf_destroy(gcf_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->d_params, c->d_Q, c->d_voff, c->d_vbs, c->d_vnb, c->d_tables, c->d_status,
-                  c->d_scratch, c->sr.obar, c->sr.F, c->sr.x, c->sr.r, c->sr.p, c->sr.Ap,
+                  c->d_scratch, c->sr.obar, c->sr.F, c->sr.x, c->sr.r, c->sr.p, c->sr.Ap, c->sr.z, c->sr.dinv,
                   c->sr.t, c->sr.coef, c->sr.chain_mean, c->sr.tbar, c->sr.scal, c->sr.perm, c->sr.seg,
                   c->sr.seg_v, c->sr.seg_b, c->d_cfg, c->d_e,
                   c->d_la, c->d_ph, c->d_bid, c->d_O, c->d_acc, c->vjp_bid, c->vjp_O, c->vjp_coef,

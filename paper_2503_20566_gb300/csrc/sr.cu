@@ -150,7 +150,7 @@ __global__ void k_axpy_real(cdouble* y, const cdouble* x, double a, long long n)
   if (k < n) { y[k].x += a * x[k].x; y[k].y += a * x[k].y; }
 }
 
-// CG vector update: x += alpha p; r -= alpha Ap; alpha = rr / pAp (real)
+// CG vector update: x += alpha p; r -= alpha Ap; alpha = rz / pAp (real)
 __global__ void k_cg_xr(cdouble* x, cdouble* r, const cdouble* p, const cdouble* Ap,
                         const double* sc, long long n) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -160,13 +160,14 @@ __global__ void k_cg_xr(cdouble* x, cdouble* r, const cdouble* p, const cdouble*
   r[k].x -= alpha * Ap[k].x; r[k].y -= alpha * Ap[k].y;
 }
 
-// p = r + beta p, beta = rr_new / rr_old
-__global__ void k_cg_p(cdouble* p, const cdouble* r, const double* sc, long long n) {
+// p = z + beta p, beta = rz_new / rz_old (z = M^-1 r; z = r without
+// preconditioning)
+__global__ void k_cg_p(cdouble* p, const cdouble* z, const double* sc, long long n) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const double beta = sc[4] / sc[0];
-  p[k].x = r[k].x + beta * p[k].x;
-  p[k].y = r[k].y + beta * p[k].y;
+  p[k].x = z[k].x + beta * p[k].x;
+  p[k].y = z[k].y + beta * p[k].y;
 }
 
 // params += c * x  (c complex); real storage takes the real part
@@ -263,11 +264,11 @@ __global__ void k_gather2(SrGeom g, const int* bids, const T* O, const cdouble* 
 }
 
 // out[off(v, b) + e] += sum_{s in segment (v, b)} coef_s op(O[s][v][e]),
-// op = conj if CONJ.  Grid = segments x split: CTA (segment, part) takes one
+// op = conj if CONJ, op = |.|^2 if SQ.  Grid = segments x split: CTA (segment, part) takes one
 // contiguous part of its segment; threads = streams x entries; each stream
 // sums chunks of 32 samples in the storage precision, then FP64; parts are
 // combined with FP64 atomics (split x block-size of them per segment).
-template <class T, bool CONJ, bool CPLX>
+template <class T, bool CONJ, bool CPLX, bool SQ = false>
 __global__ void k_scatter2(SrGeom g, const int* perm, const int* seg, int maxnb, int split, const T* O,
                            const cdouble* coef, cdouble* out, const int* seg_v, const int* seg_b) {
   using P = typename PartialOf<T>::type;
@@ -293,8 +294,12 @@ __global__ void k_scatter2(SrGeom g, const int* perm, const int* seg, int maxnb,
       const long long s = pv[q];
       const T ov = O[(s * g.n_s + v) * (long long)g.D4 + e];
       const cdouble c = coef[s];
-      const P orr = (P)re(ov), oi = CONJ ? -(P)im(ov) : (P)im(ov);
-      if (CPLX) {
+      P orr = (P)re(ov), oi = CONJ ? -(P)im(ov) : (P)im(ov);
+      if (SQ) {  // |O|^2 instead of O
+        orr = orr * orr + oi * oi;
+        oi = P(0);
+      }
+      if (CPLX && !SQ) {
         pr += (P)c.x * orr - (P)c.y * oi;
         pi += (P)c.x * oi + (P)c.y * orr;
       } else {
@@ -338,6 +343,25 @@ __global__ void k_e_to_c(const double* e, long long n, cdouble* v) {
 
 __global__ void k_copy_scalar(double* sc) { sc[0] = sc[4]; sc[1] = sc[5]; }
 
+// Jacobi preconditioner of S + shift: diag(S)_m = <|O_m|^2> - |<O_m>|^2
+// (clamped at 0 against rounding); dinv = 1 / (diag + shift).
+__global__ void k_jacobi(const cdouble* sq_mean, const cdouble* obar, double shift, double* dinv, long long n) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double d = sq_mean[k].x - (obar[k].x * obar[k].x + obar[k].y * obar[k].y);
+  dinv[k] = 1.0 / (fmax(d, 0.0) + shift);
+}
+__global__ void k_fill_d(double* v, long long n, double a) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) v[k] = a;
+}
+__global__ void k_precond(cdouble* z, const cdouble* r, const double* dinv, long long n) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  z[k].x = dinv[k] * r[k].x;
+  z[k].y = dinv[k] * r[k].y;
+}
+
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
@@ -345,11 +369,14 @@ static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
 template <class T>
 static cudaError_t scatter(const SrGeom& g, const SrWork& w, const T* O, const cdouble* coef,
-                           cdouble* out, bool conj, cudaStream_t st, long long* launches) {
+                           cdouble* out, bool conj, cudaStream_t st, long long* launches, bool sq = false) {
   constexpr bool C = Traits<T>::cplx;
   const int split = (int)std::max<long long>(1, std::min<long long>(512, g.Ns / 1024));
   const unsigned grid = (unsigned)(w.n_seg * split);
-  if (conj)
+  if (sq)
+    k_scatter2<T, false, C, true><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, O, coef, out, w.seg_v,
+                                                         w.seg_b);
+  else if (conj)
     k_scatter2<T, true, C><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, O, coef, out, w.seg_v, w.seg_b);
   else
     k_scatter2<T, false, C><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, O, coef, out, w.seg_v, w.seg_b);
@@ -405,21 +432,39 @@ cudaError_t sr_solve_update(const SrGeom& g, SrWork& w, const double* e_loc, con
   ++*launches;
   CK(cudaMemsetAsync(w.F, 0, sizeof(cdouble) * Np, st));
   CK(scatter<T>(g, w, O, w.coef, w.F, true, st, launches));
-  // CG: x = 0, r = p = F
+  // Preconditioner.  With Ns < Np, S has rank < Ns and S + shift is a
+  // low-rank matrix plus a multiple of the identity: plain CG ends in about Ns
+  // iterations, and a diagonal preconditioner would destroy that structure.
+  // With Ns >= Np (S full rank) the Jacobi preconditioner
+  // dinv = 1 / (<|O|^2> - |Obar|^2 + shift) evens out the per-parameter scales.
+  const bool jacobi = Ns >= Np;
+  if (jacobi) {
+    CK(cudaMemsetAsync(w.Ap, 0, sizeof(cdouble) * Np, st));
+    k_fill_c<<<nblk(Ns, 256), 256, 0, st>>>(w.t, Ns, 1.0 / (double)Ns, 0.0);
+    ++*launches;
+    CK(scatter<T>(g, w, O, w.t, w.Ap, false, st, launches, true));
+    k_jacobi<<<nblk(Np, 256), 256, 0, st>>>(w.Ap, w.obar, shift, w.dinv, Np);
+  } else {
+    k_fill_d<<<nblk(Np, 256), 256, 0, st>>>(w.dinv, Np, 1.0);
+  }
+  ++*launches;
+  // preconditioned CG: x = 0, r = F, z = M^-1 r, p = z
+  double* sc = w.scal + 8;  // sc[0..1] rz, sc[2..3] pAp, sc[4..5] rz_new, sc[6..7] rr
   CK(cudaMemsetAsync(w.x, 0, sizeof(cdouble) * Np, st));
   CK(cudaMemcpyAsync(w.r, w.F, sizeof(cdouble) * Np, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(w.p, w.F, sizeof(cdouble) * Np, cudaMemcpyDeviceToDevice, st));
-  CK(dot<T>(w.r, w.r, Np, w.scal + 8, st, launches));   // sc[0] = rr
-  double h_sc[8];
-  CK(cudaMemcpyAsync(h_sc, w.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  k_precond<<<nblk(Np, 256), 256, 0, st>>>(w.z, w.r, w.dinv, Np);
+  ++*launches;
+  CK(cudaMemcpyAsync(w.p, w.z, sizeof(cdouble) * Np, cudaMemcpyDeviceToDevice, st));
+  CK(dot<T>(w.r, w.z, Np, sc, st, launches));
+  CK(dot<T>(w.r, w.r, Np, sc + 6, st, launches));
+  double h_sc[16];
+  CK(cudaMemcpyAsync(h_sc, w.scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const double e_re = h_sc[0], e_im = h_sc[1], e_err = h_sc[2];
-  double rr0;
-  CK(cudaMemcpy(&rr0, w.scal + 8, sizeof(double), cudaMemcpyDeviceToHost));
+  const double rr0 = h_sc[8 + 6];
   const double fnorm = sqrt(rr0);
   double rr = rr0;
   int it = 0;
-  double* sc = w.scal + 8;  // sc[0..1] rr, sc[2..3] pAp, sc[4..5] rr_new
   bool converged = !(fnorm > 0.0);
   while (!converged && it < max_iter) {
     // Ap = S p + shift p
@@ -436,13 +481,16 @@ cudaError_t sr_solve_update(const SrGeom& g, SrWork& w, const double* e_loc, con
     CK(dot<T>(w.p, w.Ap, Np, sc + 2, st, launches));
     k_cg_xr<<<nblk(Np, 256), 256, 0, st>>>(w.x, w.r, w.p, w.Ap, sc, Np);
     ++*launches;
-    CK(dot<T>(w.r, w.r, Np, sc + 4, st, launches));
-    k_cg_p<<<nblk(Np, 256), 256, 0, st>>>(w.p, w.r, sc, Np);
+    k_precond<<<nblk(Np, 256), 256, 0, st>>>(w.z, w.r, w.dinv, Np);
+    ++*launches;
+    CK(dot<T>(w.r, w.z, Np, sc + 4, st, launches));
+    CK(dot<T>(w.r, w.r, Np, sc + 6, st, launches));
+    k_cg_p<<<nblk(Np, 256), 256, 0, st>>>(w.p, w.z, sc, Np);
     ++*launches;
     k_copy_scalar<<<1, 1, 0, st>>>(sc);
     ++*launches;
     double rn;
-    CK(cudaMemcpyAsync(&rn, sc + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&rn, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     rr = rn;
     ++it;
@@ -459,7 +507,7 @@ cudaError_t sr_solve_update(const SrGeom& g, SrWork& w, const double* e_loc, con
   stats[4] = fnorm > 0.0 ? sqrt(rr) / fnorm : 0.0;
   stats[5] = fnorm;
   stats[6] = converged ? 1.0 : 0.0;
-  stats[7] = 0.0;
+  stats[7] = jacobi ? 1.0 : 0.0;
   return cudaSuccess;
 #undef CK
 }

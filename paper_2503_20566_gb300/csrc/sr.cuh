@@ -20,6 +20,8 @@ struct SrGeom {
 
 struct SrWork {
   cdouble *obar, *F, *x, *r, *p, *Ap;  // [Np]
+  cdouble* z;                          // [Np] preconditioned residual
+  double* dinv;                        // [Np] inverse Jacobi preconditioner
   cdouble *t, *coef;                   // [Ns]
   cdouble *chain_mean;                 // [n_chains]
   cdouble *tbar;                       // [1]

@@ -227,3 +227,28 @@ def test_vmc_step_host_end_to_end():
     assert np.isfinite(stats[0]) and stats[3] >= 1
     for c in host:
         assert lat.is_physical(c)
+
+
+def test_sr_step_parity_fp64_full_rank_preconditioned():
+    """More samples than parameters (S of full rank): the CG runs with the
+    diagonal preconditioner and still lands on the oracle's dense solve."""
+    Lx, Ly, N, D, chi = 3, 3, 2, 2, 2
+    lat, pe, ctx = setup(Lx, Ly, N, D, chi, seed=16, precision="fp64", h=1.0, g=0.3)
+    n = 8 * ctx.n_params
+    cfgs, _, _ = configs_for(lat, n, seed=26)
+    dev = torch.from_numpy(cfgs).cuda()
+    e = ctx.local_energy(dev)
+    bid, O = ctx.log_grad(dev)
+    samples = {"e_loc": torch.view_as_real(e).reshape(-1).contiguous(), "block_ids": bid, "O": O}
+    p0 = ctx.get_tensors()
+    stats = ctx.sr_step(samples, n_chains=n, diag_shift=1e-3, lr=0.1, max_iter=500, tol=1e-12)
+    p1 = ctx.get_tensors()
+    assert stats[7] == 1.0 and stats[6] == 1.0
+    model = vmc.Model(h=1.0, g=0.3)
+    Ed = np.array([vmc.local_energy(pe, model, c, chi) for c in cfgs])
+    Od = np.array([vmc.log_grad_dense(pe, c, chi) for c in cfgs])
+    S, F, eb = vmc.sr_matrices(Od, Ed, np.full(len(cfgs), 1.0 / len(cfgs)))
+    x = vmc.sr_solve(S, F, 1e-3)
+    ref = -0.1 * x.real
+    dp = p1 - p0
+    assert np.linalg.norm(dp - ref) <= 1e-7 * np.linalg.norm(ref), (np.linalg.norm(dp - ref), np.linalg.norm(ref))
