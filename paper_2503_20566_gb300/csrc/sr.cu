@@ -263,6 +263,50 @@ __global__ void k_gather2(SrGeom g, const int* bids, const T* O, const cdouble* 
   if (lane == 0) t[s] = {ar, CPLX ? ai : 0.0};
 }
 
+// The same product with each sample's O row (n_s x D4 storage scalars,
+// contiguous) read by the whole warp in 16-byte vectors; needs D4 a multiple
+// of VE = 16 / sizeof(T).  Per-vector partials in the storage precision,
+// then FP64.
+template <class T, bool CPLX>
+__global__ void k_gather_vec(SrGeom g, const int* bids, const T* O, const cdouble* x, cdouble* t) {
+  using P = typename PartialOf<T>::type;
+  constexpr int VE = 16 / (int)sizeof(T);
+  const int lane = threadIdx.x & 31;
+  const long long s = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (s >= g.Ns) return;
+  const int nvec = g.n_s * g.D4 / VE;
+  const float4* row = reinterpret_cast<const float4*>(O + s * g.n_s * (long long)g.D4);
+  const int* brow = bids + s * g.n_s;
+  double ar = 0.0, ai = 0.0;
+#pragma unroll 2
+  for (int j = lane; j < nvec; j += 32) {
+    const int el = j * VE, v = el / g.D4, e0 = el - v * g.D4;
+    const int bs = g.vbs[v];
+    if (e0 >= bs) continue;
+    const float4 raw = row[j];
+    const T* ov = reinterpret_cast<const T*>(&raw);
+    const cdouble* xb = x + g.voff[v] + (long long)brow[v] * bs + e0;
+    P pr = P(0), pi = P(0);
+#pragma unroll
+    for (int i = 0; i < VE; ++i) {
+      if (e0 + i < bs) {
+        const cdouble xv = xb[i];
+        if (CPLX) {
+          pr += (P)re(ov[i]) * (P)xv.x - (P)im(ov[i]) * (P)xv.y;
+          pi += (P)re(ov[i]) * (P)xv.y + (P)im(ov[i]) * (P)xv.x;
+        } else {
+          pr += (P)re(ov[i]) * (P)xv.x;
+        }
+      }
+    }
+    ar += (double)pr;
+    if (CPLX) ai += (double)pi;
+  }
+  ar = warp_sum(ar);
+  if (CPLX) ai = warp_sum(ai);
+  if (lane == 0) t[s] = {ar, CPLX ? ai : 0.0};
+}
+
 // out[off(v, b) + e] += sum_{s in segment (v, b)} coef_s op(O[s][v][e]),
 // op = conj if CONJ, op = |.|^2 if SQ.  Grid = segments x split: CTA (segment, part) takes one
 // contiguous part of its segment; threads = streams x entries; each stream
@@ -371,7 +415,9 @@ template <class T>
 static cudaError_t scatter(const SrGeom& g, const SrWork& w, const T* O, const cdouble* coef,
                            cdouble* out, bool conj, cudaStream_t st, long long* launches, bool sq = false) {
   constexpr bool C = Traits<T>::cplx;
-  const int split = (int)std::max<long long>(1, std::min<long long>(512, g.Ns / 1024));
+  // about 2048 samples per CTA: the average segment holds Ns * n_s / n_seg
+  const long long per_seg = g.Ns * g.n_s / std::max(1, w.n_seg);
+  const int split = (int)std::max<long long>(1, std::min<long long>(512, per_seg / 2048));
   const unsigned grid = (unsigned)(w.n_seg * split);
   if (sq)
     k_scatter2<T, false, C, true><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, O, coef, out, w.seg_v,
@@ -402,6 +448,8 @@ cudaError_t sr_solve_update(const SrGeom& g, SrWork& w, const double* e_loc, con
                             long long* launches) {
   const T* O = (const T*)Ov;
   const long long Np = g.Np, Ns = g.Ns;
+  // 16-byte vector reads of O need a 16-byte aligned base and whole vectors per vertex
+  const bool vec_ok = (reinterpret_cast<uintptr_t>(Ov) % 16 == 0) && (g.D4 % (16 / (int)sizeof(T)) == 0);
   cudaError_t err;
 #define CK(x)                                   \
   do {                                          \
@@ -468,7 +516,10 @@ cudaError_t sr_solve_update(const SrGeom& g, SrWork& w, const double* e_loc, con
   bool converged = !(fnorm > 0.0);
   while (!converged && it < max_iter) {
     // Ap = S p + shift p
-    k_gather2<T, Traits<T>::cplx><<<nblk(Ns * 32, 256), 256, 0, st>>>(g, bids, O, w.p, w.t);
+    if (vec_ok)
+      k_gather_vec<T, Traits<T>::cplx><<<nblk(Ns * 32, 256), 256, 0, st>>>(g, bids, O, w.p, w.t);
+    else
+      k_gather2<T, Traits<T>::cplx><<<nblk(Ns * 32, 256), 256, 0, st>>>(g, bids, O, w.p, w.t);
     ++*launches;
     k_sum_c<<<1, 1024, 0, st>>>(w.t, Ns, w.tbar, 1.0 / (double)Ns);
     ++*launches;
