@@ -201,6 +201,16 @@ gcf_status gcf_log_grad_vjp(gcf_ctx* ctx, int n, const int8_t* configs, const do
 gcf_status gcf_sample_batch(gcf_ctx* ctx, int n_chains, int n_sweeps, uint64_t seed,
                             int8_t* configs, const gcf_samples* out);
 
+/* gcf_sample_batch enqueued on `stream` (NULL: the context's stream) with
+ * no host synchronisation and no allocation, so that the persistent launch
+ * can be recorded in a CUDA graph and replayed.  The kernel arguments (seed,
+ * pointers, sizes) are fixed at enqueue time.  The context's scratch must
+ * already cover n_chains (GCF_EINVAL otherwise): call gcf_sample_batch with
+ * at least as many chains first.  Unphysical starting configurations are not
+ * reported as a status; their samples get log|psi| = -inf and E_loc = NaN. */
+gcf_status gcf_sample_batch_async(gcf_ctx* ctx, int n_chains, int n_sweeps, uint64_t seed,
+                                  int8_t* configs, const gcf_samples* out, void* stream);
+
 /* FP64 reductions and parameter update (Sec. S-1 Eq. S3; Sec. S-3 Eqs. S6-S8):
  *   F = <O^* E_loc> - <O^*><E_loc>,  S = <O^* O> - <O^*><O>   (Eq. S7)
  *   x = (S + diag_shift I)^{-1} F by conjugate gradient (S never formed);

@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH):
         "gcf_sample_multi": (i, [C.POINTER(vp), i, C.POINTER(C.c_int), i, C.POINTER(C.c_uint64), C.POINTER(vp),
                                  C.POINTER(_Samples)]),
         "gcf_sample_batch": (i, [vp, i, i, u64, vp, C.POINTER(_Samples)]),
+        "gcf_sample_batch_async": (i, [vp, i, i, u64, vp, C.POINTER(_Samples), vp]),
         "gcf_sr_step": (i, [vp, i, i, vp, vp, vp, d, d, i, d, i, d, C.POINTER(C.c_double)]),
         "gcf_vmc_step_host": (i, [vp, i, i, u64, vp, d, d, i, d, i, d, C.POINTER(C.c_double)]),
     }
@@ -92,7 +93,7 @@ def exported_symbols():
     return ["gcf_init_peps", "gcf_destroy", "gcf_last_error", "gcf_num_params", "gcf_config_len",
             "gcf_scalar_bytes", "gcf_launch_count", "gcf_executor", "gcf_smem_level", "gcf_autotune", "gcf_set_tensors", "gcf_get_tensors",
             "gcf_init_configs", "gcf_amplitude", "gcf_local_energy", "gcf_log_grad", "gcf_log_grad_vjp", "gcf_sample_multi",
-            "gcf_sample_batch", "gcf_sr_step", "gcf_vmc_step_host"]
+            "gcf_sample_batch", "gcf_sample_batch_async", "gcf_sr_step", "gcf_vmc_step_host"]
 
 
 def _ptr(t):
@@ -278,6 +279,18 @@ class Context:
                        for k in ("log_abs", "phase", "e_loc", "block_ids", "O", "accepted", "proposed")])
         self._check(self.lib.gcf_sample_batch(self.ctx, n, n_sweeps, C.c_uint64(seed), _ptr(configs),
                                               C.byref(s)), "sample_batch")
+        return out
+
+    def sample_batch_async(self, configs, n_sweeps, seed, out, stream=None):
+        """Enqueue sample_batch on `stream` (a torch.cuda.Stream; default the
+        context's) without synchronising or allocating: the launch can be
+        recorded in a CUDA graph.  Call sample_batch with at least as many
+        chains once before (it sizes the scratch)."""
+        n = configs.shape[0]
+        h = None if stream is None else C.c_void_p(stream.cuda_stream)
+        s = _samples_struct(out)
+        self._check(self.lib.gcf_sample_batch_async(self.ctx, n, n_sweeps, C.c_uint64(seed), _ptr(configs),
+                                                    C.byref(s), h), "sample_batch_async")
         return out
 
     def sr_step(self, samples, n_chains, diag_shift=1e-4, lr=0.01, mode=SR, dt=0.0, max_iter=100,

@@ -522,7 +522,8 @@ gcf_status ensure_scratch(gcf_ctx* c, long long ctas) {
 
 template <class T>
 gcf_status run_vmc(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t seed,
-                   int8_t* configs, const gcf_samples* out, int* gauss_count) {
+                   int8_t* configs, const gcf_samples* out, int* gauss_count, cudaStream_t stream,
+                   bool async) {
   const bool warp = c->exec == EXEC_GROUP;
   const int W = 256 / c->group_threads;  // chains per CTA
   int grid = 1;
@@ -549,12 +550,13 @@ gcf_status run_vmc(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t
     k.block_ids = out->block_ids; k.O = (T*)out->O;
     k.accepted = out->accepted; k.proposed = out->proposed;
   }
-  CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), stream));
   if (warp)
-    CUDA_TRY(c, launch_vmc_grouped<T>(k, grid, 256, W * c->plan.group_smem, c->stream));
+    CUDA_TRY(c, launch_vmc_grouped<T>(k, grid, 256, W * c->plan.group_smem, stream));
   else
-    CUDA_TRY(c, launch_vmc<T>(k, grid, 256, c->plan.dyn_smem, c->stream));
+    CUDA_TRY(c, launch_vmc<T>(k, grid, 256, c->plan.dyn_smem, stream));
   c->launches += 1;
+  if (async) return GCF_OK;
   int h_status[4];
   CUDA_TRY(c, cudaMemcpyAsync(h_status, c->d_status, sizeof(h_status), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -624,12 +626,13 @@ gcf_status run_multi(gcf_ctx* const* cs, int n_ctx, const int* n_chains, int n_s
 }
 
 gcf_status dispatch(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t seed, int8_t* cfg,
-                    const gcf_samples* out, int* gauss) {
+                    const gcf_samples* out, int* gauss, cudaStream_t stream = nullptr, bool async = false) {
+  cudaStream_t st = async ? stream : c->stream;
   switch (c->kind) {
-    case S_F32: return run_vmc<float>(c, mode, want, n, n_sweeps, seed, cfg, out, gauss);
-    case S_F64: return run_vmc<double>(c, mode, want, n, n_sweeps, seed, cfg, out, gauss);
-    case S_C64: return run_vmc<cfloat>(c, mode, want, n, n_sweeps, seed, cfg, out, gauss);
-    default: return run_vmc<cdouble>(c, mode, want, n, n_sweeps, seed, cfg, out, gauss);
+    case S_F32: return run_vmc<float>(c, mode, want, n, n_sweeps, seed, cfg, out, gauss, st, async);
+    case S_F64: return run_vmc<double>(c, mode, want, n, n_sweeps, seed, cfg, out, gauss, st, async);
+    case S_C64: return run_vmc<cfloat>(c, mode, want, n, n_sweeps, seed, cfg, out, gauss, st, async);
+    default: return run_vmc<cdouble>(c, mode, want, n, n_sweeps, seed, cfg, out, gauss, st, async);
   }
 }
 
@@ -1033,6 +1036,40 @@ gcf_status gcf_sample_multi(gcf_ctx* const* ctxs, int n_ctx, const int* n_chains
     case S_C64: return run_multi<cfloat>(ctxs, n_ctx, n_chains, n_sweeps, seeds, configs, outs);
     default: return run_multi<cdouble>(ctxs, n_ctx, n_chains, n_sweeps, seeds, configs, outs);
   }
+}
+
+gcf_status gcf_sample_batch_async(gcf_ctx* c, int n_chains, int n_sweeps, uint64_t seed, int8_t* configs,
+                                  const gcf_samples* out, void* stream) {
+  if (!c || n_chains < 0 || n_sweeps < 1 || (n_chains > 0 && !configs)) return GCF_EINVAL;
+  if (n_chains == 0) return GCF_OK;
+  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  // scratch must already cover this launch: no allocation here
+  {
+    const bool grp = c->exec == EXEC_GROUP;
+    const int W = 256 / c->group_threads;
+    long long slots = 1;
+    if (grp) {
+      int per_sm = 0;
+      switch (c->kind) {
+        case S_F32: per_sm = occupancy_vmc_grouped<float>(256, W * c->plan.group_smem); break;
+        case S_F64: per_sm = occupancy_vmc_grouped<double>(256, W * c->plan.group_smem); break;
+        case S_C64: per_sm = occupancy_vmc_grouped<cfloat>(256, W * c->plan.group_smem); break;
+        default: per_sm = occupancy_vmc_grouped<cdouble>(256, W * c->plan.group_smem); break;
+      }
+      const long long sl = balanced_slots(n_chains, (long long)c->sms * std::max(1, per_sm) * W);
+      slots = (sl + W - 1) / W * W;
+    } else {
+      slots = grid_for(c, n_chains);
+    }
+    if (slots > c->scratch_ctas)
+      return fail(c, GCF_EINVAL, "gcf_sample_batch_async: scratch not yet sized for this many chains; call "
+                                 "gcf_sample_batch with at least as many chains first");
+  }
+  gcf_samples o{};
+  if (out) o = *out;
+  int want = (o.log_abs || o.phase ? WANT_AMP : 0) | (o.e_loc ? WANT_ELOC : 0) |
+             (o.O || o.block_ids ? WANT_GRAD : 0);
+  return dispatch(c, 1, want, n_chains, n_sweeps, seed, configs, &o, nullptr, st, true);
 }
 
 gcf_status gcf_sample_batch(gcf_ctx* c, int n_chains, int n_sweeps, uint64_t seed, int8_t* configs,
