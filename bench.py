@@ -241,7 +241,7 @@ def main():
                                                      w["N"]))
     configs = ctx.init_configs(n_chains, powers=powers)
     # the library's autotuner picks the kernel form (executor x shared-memory level) on this workload
-    tune_ms = [] if args.no_autotune else ctx.autotune(configs, n_sweeps=1)
+    tune_ms = [] if args.no_autotune else ctx.autotune(configs, n_sweeps=4)
     kernel_name = ctx.kernel_name + "<float>"
     samples = ctx.alloc_samples(n_chains, n_sweeps, grad=True)
     stream = ctx.stream

@@ -274,9 +274,13 @@ int64_t gcf_launch_count(const gcf_ctx* ctx);
 /* Form of the sampling / measurement kernel this context launches (an
  * implementation choice; the paper has no counterpart): 0 = one chain per
  * CTA of 256 threads (gcf::vmc_kernel), 1 = two chains per CTA on groups of
- * 128 threads (gcf::vmc_kernel_grouped).  Chosen at context creation from
- * the shared-memory footprint; GCFVMC_EXEC=cta|group in the environment
- * forces one.  Both compute the same results. */
+ * 128 threads (gcf::vmc_kernel_grouped), 2 = four chains per CTA of 512
+ * threads (gcf::vmc_kernel_grouped4).  In the grouped forms the chain groups
+ * of a CTA meet before every row of a pass (lockstep; bounded waits, no data
+ * exchanged), so the SM runs one region of code at a time.  Chosen at
+ * context creation from the shared-memory footprint (or by gcf_autotune);
+ * GCFVMC_EXEC=cta|group|group4 and GCFVMC_LOCK=0|1 in the environment force
+ * a form.  All forms compute the same results. */
 int gcf_executor(const gcf_ctx* ctx);
 
 /* Shared-memory placement level of the kernel form this context launches

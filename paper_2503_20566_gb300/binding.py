@@ -178,7 +178,8 @@ class Context:
     @property
     def kernel_name(self):
         """Name of the sampling / measurement kernel this context launches."""
-        return "gcf::vmc_kernel_grouped" if self.lib.gcf_executor(self.ctx) == 1 else "gcf::vmc_kernel"
+        return {1: "gcf::vmc_kernel_grouped", 2: "gcf::vmc_kernel_grouped4"}.get(
+            int(self.lib.gcf_executor(self.ctx)), "gcf::vmc_kernel")
 
     # ---- parameters -------------------------------------------------------
     def set_tensors(self, values):

@@ -61,6 +61,7 @@ struct gcf_ctx {
   int device = 0, sms = 0;
   Plan plan;
   int exec = 0, group_threads = 64;
+  int lockstep = 0;  // grouped kernels: chain groups of a CTA in lockstep
   int tab_ints = 0;  // ints in d_tables
   // device
   void* d_params = nullptr;
@@ -141,30 +142,56 @@ void plan_step(int Lx, int Dk, int chi, int pout, const int* bin, int* qr, int* 
   svd[Lx] = 0;
 }
 
-// Executor for the sampling / measurement kernel: the whole CTA on one chain,
-// or two chains per CTA on groups of 128 threads.  Groups halve the threads
-// that wait at each barrier but need their own shared buffers; they are the
-// default when two groups' hot buffers fit in shared memory next to a second
-// CTA.  GCFVMC_EXEC=cta|group and GCFVMC_SMEM / GCFVMC_SMEM_CTA (placement
-// level 0-3) override the choice.
-enum ExecKind { EXEC_CTA = 0, EXEC_GROUP = 1 };
+// Executor for the sampling / measurement kernel: the whole CTA on one
+// chain, or two or four chains per CTA on groups of 128 threads (optionally
+// in lockstep, see vmc_kernel.cuh).  GCFVMC_EXEC=cta|group|group4,
+// GCFVMC_SMEM / GCFVMC_SMEM_CTA (placement level 0-3) and GCFVMC_LOCK=0|1
+// override the planner's choice.
+enum ExecKind { EXEC_CTA = 0, EXEC_GROUP = 1, EXEC_GROUP4 = 2 };
+bool grouped(const gcf_ctx* c);
+int n_groups(const gcf_ctx* c);
 
 void plan_group(gcf_ctx* c) {
   Plan& p = c->plan;
-  const int G = 128, NG = 256 / G;
+  const int G = 128;
   c->group_threads = G;
   const size_t base = sharedv_bytes() + (size_t)p.cfg_bytes;
-  // the largest level whose two groups fit next to a second CTA
-  p.group_level = 0;
+  auto fits = [&](int ng, int lv, size_t budget) {
+    return (size_t)ng * (base + (size_t)p.level_elems(lv) * c->sbytes) <= budget;
+  };
+  // two groups per CTA: the largest level that leaves room for a second CTA
+  int lv2 = 0;
   for (int lv = 1; lv <= 3; ++lv)
-    if ((size_t)NG * (base + (size_t)p.level_elems(lv) * c->sbytes) <= 110 * 1024) p.group_level = lv;
-  if (const char* e = std::getenv("GCFVMC_SMEM")) p.group_level = std::max(0, std::min(3, std::atoi(e)));
-  p.group_smem = (base + (size_t)p.level_elems(p.group_level) * c->sbytes + 15) / 16 * 16;
-  c->exec = p.group_level >= 1 ? EXEC_GROUP : EXEC_CTA;
+    if (fits(2, lv, 110 * 1024)) lv2 = lv;
+  // Default form: four chain groups per CTA of 512 threads (one CTA per SM)
+  // in lockstep, with the hot buffers in shared memory (level 1; the larger
+  // levels measured slower for four groups); else two groups per CTA; else
+  // the whole CTA per chain.  The autotuner can pick any other form.
+  if (fits(4, 1, 216 * 1024)) {
+    c->exec = EXEC_GROUP4;
+    p.group_level = 1;
+  } else if (lv2 >= 1) {
+    c->exec = EXEC_GROUP;
+    p.group_level = lv2;
+  } else {
+    c->exec = EXEC_CTA;
+    p.group_level = 0;
+  }
+  c->lockstep = 1;
+  if (const char* e = std::getenv("GCFVMC_LOCK")) c->lockstep = std::atoi(e) ? 1 : 0;
   if (const char* e = std::getenv("GCFVMC_EXEC")) {
-    if (!std::strcmp(e, "group")) c->exec = EXEC_GROUP;
+    if (!std::strcmp(e, "group4")) {
+      c->exec = EXEC_GROUP4;
+      p.group_level = fits(4, 1, 216 * 1024) ? 1 : 0;
+    }
+    if (!std::strcmp(e, "group")) {
+      c->exec = EXEC_GROUP;
+      p.group_level = lv2;
+    }
     if (!std::strcmp(e, "cta")) c->exec = EXEC_CTA;
   }
+  if (const char* e = std::getenv("GCFVMC_SMEM")) p.group_level = std::max(0, std::min(3, std::atoi(e)));
+  p.group_smem = (base + (size_t)p.level_elems(p.group_level) * c->sbytes + 15) / 16 * 16;
 }
 
 // Tables derived from the bond dimensions, appended after the six plan
@@ -211,11 +238,14 @@ void append_derived_tables(const gcf_ctx* c, std::vector<int>& t) {
     t.push_back(r + 1 < R ? dense(&p.bondT[(r + 1) * W], physT(r + 1), &p.bondT[r * W], physT(r)) : 0);
 }
 
+bool grouped(const gcf_ctx* c) { return c->exec == EXEC_GROUP || c->exec == EXEC_GROUP4; }
+int n_groups(const gcf_ctx* c) { return c->exec == EXEC_GROUP4 ? 4 : 2; }
+
 // Kernel form: executor and shared-memory level (sizes follow from the plan).
 void set_form(gcf_ctx* c, int exec, int level) {
   Plan& p = c->plan;
   c->exec = exec;
-  if (exec == EXEC_GROUP) {
+  if (exec == EXEC_GROUP || exec == EXEC_GROUP4) {
     p.group_level = level;
     p.group_smem = (sharedv_bytes() + (size_t)p.cfg_bytes + (size_t)p.level_elems(level) * c->sbytes + 15) / 16 * 16;
   } else {
@@ -474,6 +504,7 @@ KParams<T> make_params(gcf_ctx* c) {
   k.so_env3L = p.so_env3L; k.so_env3X = p.so_env3X; k.so_env3Y = p.so_env3Y;
   k.so_t1 = p.so_t1; k.so_t2 = p.so_t2; k.smem_cfg_bytes = p.cfg_bytes;
   k.group_smem_bytes = (long long)p.group_smem;
+  k.lockstep = c->lockstep;
   k.group_threads = c->group_threads;
   // tensor-core forms exist for FP32 storage only
   k.gemm_mode = GEMM_FFMA;
@@ -524,11 +555,11 @@ template <class T>
 gcf_status run_vmc(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t seed,
                    int8_t* configs, const gcf_samples* out, int* gauss_count, cudaStream_t stream,
                    bool async) {
-  const bool warp = c->exec == EXEC_GROUP;
-  const int W = 256 / c->group_threads;  // chains per CTA
+  const bool warp = grouped(c);
+  const int W = n_groups(c);  // chains per CTA
   int grid = 1;
   if (warp) {
-    const int per_sm = occupancy_vmc_grouped<T>(256, W * c->plan.group_smem);
+    const int per_sm = occupancy_vmc_grouped<T>(128 * W, W * c->plan.group_smem);
     if (per_sm < 1) return fail(c, GCF_EINVAL, "grouped launch does not fit an SM");
     const long long slots = balanced_slots(n, (long long)c->sms * per_sm * W);
     grid = (int)std::max<long long>(1, (slots + W - 1) / W);
@@ -552,7 +583,7 @@ gcf_status run_vmc(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t
   }
   CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), stream));
   if (warp)
-    CUDA_TRY(c, launch_vmc_grouped<T>(k, grid, 256, W * c->plan.group_smem, stream));
+    CUDA_TRY(c, launch_vmc_grouped<T>(k, grid, 128 * W, W * c->plan.group_smem, stream));
   else
     CUDA_TRY(c, launch_vmc<T>(k, grid, 256, c->plan.dyn_smem, stream));
   c->launches += 1;
@@ -955,6 +986,7 @@ gcf_status gcf_autotune(gcf_ctx* c, int n_chains, int n_sweeps, const int8_t* co
     if (cta <= limit) forms.push_back({EXEC_CTA, lv});
     const size_t grp = 2 * (sharedv_bytes() + (size_t)c->plan.cfg_bytes + (size_t)c->plan.level_elems(lv) * c->sbytes);
     if (lv >= 1 && grp <= limit) forms.push_back({EXEC_GROUP, lv});
+    if (lv >= 1 && 2 * grp <= limit) forms.push_back({EXEC_GROUP4, lv});
   }
   const int keep_exec = c->exec, keep_cta = c->plan.cta_level, keep_grp = c->plan.group_level;
   const size_t bytes = (size_t)n_chains * c->cfg_len;
@@ -1014,7 +1046,7 @@ gcf_status gcf_autotune(gcf_ctx* c, int n_chains, int n_sweeps, const int8_t* co
 
 int gcf_smem_level(const gcf_ctx* c) {
   if (!c) return -1;
-  return c->exec == EXEC_GROUP ? c->plan.group_level : c->plan.cta_level;
+  return grouped(c) ? c->plan.group_level : c->plan.cta_level;
 }
 
 gcf_status gcf_sample_multi(gcf_ctx* const* ctxs, int n_ctx, const int* n_chains, int n_sweeps,
@@ -1045,16 +1077,16 @@ gcf_status gcf_sample_batch_async(gcf_ctx* c, int n_chains, int n_sweeps, uint64
   cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
   // scratch must already cover this launch: no allocation here
   {
-    const bool grp = c->exec == EXEC_GROUP;
-    const int W = 256 / c->group_threads;
+    const bool grp = grouped(c);
+    const int W = n_groups(c);
     long long slots = 1;
     if (grp) {
       int per_sm = 0;
       switch (c->kind) {
-        case S_F32: per_sm = occupancy_vmc_grouped<float>(256, W * c->plan.group_smem); break;
-        case S_F64: per_sm = occupancy_vmc_grouped<double>(256, W * c->plan.group_smem); break;
-        case S_C64: per_sm = occupancy_vmc_grouped<cfloat>(256, W * c->plan.group_smem); break;
-        default: per_sm = occupancy_vmc_grouped<cdouble>(256, W * c->plan.group_smem); break;
+        case S_F32: per_sm = occupancy_vmc_grouped<float>(128 * W, W * c->plan.group_smem); break;
+        case S_F64: per_sm = occupancy_vmc_grouped<double>(128 * W, W * c->plan.group_smem); break;
+        case S_C64: per_sm = occupancy_vmc_grouped<cfloat>(128 * W, W * c->plan.group_smem); break;
+        default: per_sm = occupancy_vmc_grouped<cdouble>(128 * W, W * c->plan.group_smem); break;
       }
       const long long sl = balanced_slots(n_chains, (long long)c->sms * std::max(1, per_sm) * W);
       slots = (sl + W - 1) / W * W;

@@ -12,7 +12,8 @@ cudaError_t launch_vmc(const KParams<T>& k, int grid, int block, size_t smem, cu
 // resident blocks per SM of vmc_kernel<T> for this block size and dynamic smem
 template <class T>
 int occupancy_vmc(int block, size_t smem);
-// several chains per CTA (groups of k.group_threads threads); smem = groups x per-group bytes
+// several chains per CTA (groups of 128 threads; block 256 = two groups, 512 = four);
+// smem = groups x per-group bytes
 template <class T>
 cudaError_t launch_vmc_grouped(const KParams<T>& k, int grid, int block, size_t smem, cudaStream_t st);
 // resident blocks per SM of vmc_kernel_grouped<T>; 0 if the launch cannot fit

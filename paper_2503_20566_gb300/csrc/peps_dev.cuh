@@ -64,6 +64,7 @@ struct KParams {
       so_t1, so_t2, smem_cfg_bytes;
   long long group_smem_bytes;  // grouped kernel: shared bytes per chain group
   int group_threads;          // grouped kernel: threads per chain (128)
+  int lockstep;               // grouped kernels: keep a CTA's chains at the same row
   int gemm_mode;              // GemmMode of the contraction GEMMs
   int row_gemm_mode;          // GemmMode of the row environments (O, amplitude, hops)
   // right environments and the staged B / T rows of the current pass
@@ -84,7 +85,7 @@ struct KParams {
 };
 
 enum { WANT_AMP = 1, WANT_ELOC = 2, WANT_GRAD = 4 };
-enum { ST_GAUSS = 0, ST_NUMERIC = 1, ST_SVD = 2 };
+enum { ST_GAUSS = 0, ST_NUMERIC = 1, ST_SVD = 2, ST_PHASE_TIMEOUT = 3 };
 
 struct Shared {
   double red[64];

@@ -24,19 +24,19 @@ int occupancy_vmc<cdouble>(int block, size_t smem) {
 template <>
 cudaError_t launch_vmc_grouped<cdouble>(const KParams<cdouble>& k, int grid, int block, size_t smem,
                                  cudaStream_t st) {
-  {
-    cudaError_t e = cudaFuncSetAttribute(vmc_kernel_grouped<cdouble>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  vmc_kernel_grouped<cdouble><<<grid, block, smem, st>>>(k);
+  // 256 threads: two chain groups per CTA; 512: four (one CTA per SM)
+  auto* fn = block == 512 ? vmc_kernel_grouped4<cdouble> : vmc_kernel_grouped<cdouble>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fn<<<grid, block, smem, st>>>(k);
   return cudaGetLastError();
 }
 template <>
 int occupancy_vmc_grouped<cdouble>(int block, size_t smem) {
-  if (cudaFuncSetAttribute(vmc_kernel_grouped<cdouble>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
+  auto* fn = block == 512 ? vmc_kernel_grouped4<cdouble> : vmc_kernel_grouped<cdouble>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, vmc_kernel_grouped<cdouble>, block, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem) != cudaSuccess) return 0;
   return n;
 }
 template <>

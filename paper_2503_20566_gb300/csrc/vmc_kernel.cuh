@@ -27,9 +27,20 @@ struct SharedV {
   int logR[MAX_L + 2];   // of the right environments of the current pass
   double eacc[2];
   int flag, ok, bad;
+  int lock, phase;   // lockstep with the CTA's other chain groups; phases passed
   float redf[32];
   int n_acc, n_prop;
 };
+
+// Lockstep of the chain groups of one CTA: before each row of a pass every
+// group's leader counts in on g_phase_arrive and waits (bounded) until all
+// locked groups have; the groups then work on the same rows at the same time,
+// so the SM fetches one region of code instead of one per chain.  No data is
+// exchanged: the rendezvous only aligns timing.  g_lock_ok[g]: group g has a
+// physical chain this round.
+__shared__ int g_phase_arrive;
+__shared__ int g_lock_ok[4];
+constexpr int kPhaseSpinLimit = 1 << 22;
 
 __host__ __device__ constexpr unsigned long sizeof_sharedv_aligned() {
   return (sizeof(SharedV) + 15) / 16 * 16;
@@ -78,6 +89,29 @@ struct Chain {
     }
   }
 
+  // rendezvous with the other locked groups of the CTA (no-op unless locked);
+  // a wait that runs out of iterations drops this group out of lockstep and
+  // records ST_PHASE_TIMEOUT
+  __device__ void phase_sync() {
+    if (!sv.lock) return;
+    const int n_groups = blockDim.x / ex.size();
+    ex.sync();
+    if (ex.leader()) {
+      sv.phase += 1;
+      const int target = sv.phase * n_groups;
+      atomicAdd(&g_phase_arrive, 1);
+      int it = 0;
+      while (*(volatile int*)&g_phase_arrive < target && it < kPhaseSpinLimit) {
+        __nanosleep(64);
+        ++it;
+      }
+      if (it >= kPhaseSpinLimit) {
+        sv.lock = 0;
+        atomicAdd(&k.status[ST_PHASE_TIMEOUT], 1);
+      }
+    }
+    ex.sync();
+  }
   // arithmetic of this chain's contraction GEMMs from here on
   __device__ void set_gemm_mode(int m) {
     ex.sync();
@@ -481,6 +515,7 @@ __device__ __noinline__ void plaquette_pass(Chain<T, X>& ch, int w) {
   T* X1 = ch.envX;
   T* X2 = ch.envY;
   for (int r = 0; r < Ly - 1; ++r) {
+    ch.phase_sync();
     R dr, di;
     int de;
     ch.strip_right_envs(r, dr, di, de);
@@ -538,6 +573,7 @@ __device__ __noinline__ void hhop_pass(Chain<T, X>& ch, int w) {
   T* X1 = ch.env3X;
   T* X2 = ch.env3Y;
   for (int r = Ly - 1; r >= 0; --r) {
+    ch.phase_sync();
     R dr, di;
     int de;
     ch.row_right_envs(r, dr, di, de);
@@ -598,6 +634,7 @@ __device__ __noinline__ void vhop_pass(Chain<T, X>& ch, int w) {
   T* X1 = ch.envX;
   T* Lnext = ch.envY;
   for (int r = 0; r < Ly - 1; ++r) {
+    ch.phase_sync();
     R dr, di;
     int de;
     ch.strip_right_envs(r, dr, di, de);
@@ -659,6 +696,7 @@ __device__ __noinline__ void measure_pass(Chain<T, X>& ch, long long s) {
   if (ex.tid() == 0) { ch.sv.eacc[0] = 0.0; ch.sv.eacc[1] = 0.0; }
   ex.sync();
   for (int r = Ly - 1; r >= 0; --r) {
+    ch.phase_sync();
     // ---- row r: gradient, horizontal hops, amplitude
     const bool need_row = want_g || (r == Ly - 1 && want_a) || (want_e && k.matter && k.J != 0.0);
     if (need_row) {
@@ -793,19 +831,37 @@ __device__ const int* stage_tables(const KParams<T>& k) {
   return fits ? g_tab : k.tab;
 }
 
-// Per-chain body shared by both kernels.
+// Lockstep decision of one chain round, taken by every group of the CTA (with
+// or without a chain): lock only if all groups have a physical chain.
+template <class X>
+__device__ void lock_exchange(const X ex, SharedV* sv, int grp, int n_groups, bool ok) {
+  if (ex.leader()) g_lock_ok[grp] = ok ? 1 : 0;
+  if (threadIdx.x == 0) g_phase_arrive = 0;  // the previous round's arrivals are complete
+  __syncthreads();
+  if (sv && ex.leader()) {
+    int all = 1;
+    for (int i = 0; i < n_groups; ++i) all &= g_lock_ok[i];
+    sv->lock = all;
+    sv->phase = 0;
+  }
+  __syncthreads();
+}
+
+// Per-chain body shared by the kernels.
 template <class T, class X>
 __device__ void run_chain(const X ex, const KParams<T>& k, T* ws, SharedV& sv, int8_t* cfg, T* hot, const int* tab,
-                          int chain) {
+                          int chain, int lock_group = -1, int n_groups = 1) {
   int8_t* gcfg = k.configs + (long long)chain * k.cfg_len;
 #pragma unroll 1
   for (int i = ex.tid(); i < k.cfg_len; i += ex.size()) cfg[i] = gcfg[i];
   if (ex.leader()) {
     sv.logB[0] = 0; sv.logT[k.Ly] = 0; sv.n_acc = 0; sv.n_prop = 0;
+    sv.lock = 0; sv.phase = 0;
   }
   ex.sync();
   Chain<T, X> ch(ex, k, ws, sv, cfg, chain, hot, tab);
   const bool ok = ch.check_and_gather_all();
+  if (lock_group >= 0) lock_exchange(ex, &sv, lock_group, n_groups, ok);
   if (!ok) {
     if (ex.leader()) {
       atomicAdd(&k.status[ST_GAUSS], 1);
@@ -821,10 +877,16 @@ __device__ void run_chain(const X ex, const KParams<T>& k, T* ws, SharedV& sv, i
     return;
   }
   if (k.mode == 0) {
-    for (int r = 0; r < k.Ly - 1; ++r) ch.absorb_B(r);
+    for (int r = 0; r < k.Ly - 1; ++r) {
+      ch.phase_sync();
+      ch.absorb_B(r);
+    }
     measure_pass(ch, (long long)chain);
   } else {
-    for (int r = k.Ly - 1; r >= 2; --r) ch.absorb_T(r);
+    for (int r = k.Ly - 1; r >= 2; --r) {
+      ch.phase_sync();
+      ch.absorb_T(r);
+    }
     for (int w = 0; w < k.n_sweeps; ++w) {
       plaquette_pass(ch, w);
       if (k.matter) {
@@ -876,12 +938,32 @@ __device__ void grouped_body(const KParams<T>& k) {
   const long long slot = (long long)blockIdx.x * NG + g;
   T* ws = k.scratch + slot * k.ws_stride;
   init_trivial_slots(ex, k, ws);
-  for (long long chain = slot; chain < k.n_chains; chain += (long long)gridDim.x * NG)
-    run_chain(ex, k, ws, sv, cfg, hot, tab, (int)chain);
+  const long long stride = (long long)gridDim.x * NG;
+  if (!k.lockstep) {
+    for (long long chain = slot; chain < k.n_chains; chain += stride)
+      run_chain(ex, k, ws, sv, cfg, hot, tab, (int)chain);
+    return;
+  }
+  // lockstep: every group takes part in every round's exchange and barrier
+  const long long rounds = (k.n_chains + stride - 1) / stride;
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long chain = slot + rd * stride;
+    if (chain < k.n_chains)
+      run_chain(ex, k, ws, sv, cfg, hot, tab, (int)chain, g, NG);
+    else
+      lock_exchange(ex, (SharedV*)nullptr, g, NG, false);
+    __syncthreads();
+  }
 }
 
 template <class T>
 __global__ void __launch_bounds__(256, 2) vmc_kernel_grouped(const __grid_constant__ KParams<T> k) {
+  grouped_body<T, GroupExec<128>, 128>(k);
+}
+
+// Four chains per CTA of 512 threads (one CTA per SM).
+template <class T>
+__global__ void __launch_bounds__(512, 1) vmc_kernel_grouped4(const __grid_constant__ KParams<T> k) {
   grouped_body<T, GroupExec<128>, 128>(k);
 }
 

@@ -1,12 +1,15 @@
 """Both executors of the sampling kernel, at every shared-memory placement
 level, give the oracle's results.
 
-The library runs a chain either on a whole CTA or on one of two 128-thread
-groups of a CTA, and keeps none, the hot buffers (1), also the staged B / T
-rows (2), or also the right environments (3) in shared memory.  GCFVMC_EXEC
-and GCFVMC_SMEM / GCFVMC_SMEM_CTA force a form at context creation; each is
-checked against the FP64 oracle on the same seeded inputs, with amplitudes
-and a replayed Markov chain.  Forms that do not fit an SM are skipped.
+The library runs a chain either on a whole CTA or on one of two or four
+128-thread groups of a CTA (optionally in lockstep: the groups meet before
+every row of a pass), and keeps none, the hot buffers (1), also the staged
+B / T rows (2), or also the right environments (3) in shared memory.
+GCFVMC_EXEC, GCFVMC_SMEM / GCFVMC_SMEM_CTA and GCFVMC_LOCK force a form at
+context creation; each is checked against the FP64 oracle on the same seeded
+inputs, with amplitudes and a replayed Markov chain (3 chains, so a
+four-group CTA also runs with groups that have no chain).  Forms that do not
+fit an SM are skipped.
 """
 
 import numpy as np
@@ -31,14 +34,16 @@ def _ids(c):
     return "{}x{}-Z{}-D{}-chi{}{}{}".format(c[0], c[1], c[2], c[3], c[4], "-c" if c[5] else "", "-m" if c[6] else "")
 
 
-@pytest.mark.parametrize("executor,level", [("cta", 0), ("cta", 1), ("cta", 3), ("group", 1), ("group", 2),
-                                            ("group", 3)])
+@pytest.mark.parametrize("executor,level,lock", [("cta", 0, 0), ("cta", 1, 0), ("cta", 3, 0), ("group", 1, 0),
+                                                 ("group", 2, 0), ("group", 3, 0), ("group", 1, 1),
+                                                 ("group4", 1, 0), ("group4", 1, 1), ("group4", 2, 1)])
 @pytest.mark.parametrize("case", CASES, ids=_ids)
-def test_executor_amplitude_and_chain(case, executor, level, monkeypatch):
+def test_executor_amplitude_and_chain(case, executor, level, lock, monkeypatch):
     import paper_2503_20566_gb300 as G
 
     monkeypatch.setenv("GCFVMC_EXEC", executor)
-    monkeypatch.setenv("GCFVMC_SMEM" if executor == "group" else "GCFVMC_SMEM_CTA", str(level))
+    monkeypatch.setenv("GCFVMC_SMEM" if executor.startswith("group") else "GCFVMC_SMEM_CTA", str(level))
+    monkeypatch.setenv("GCFVMC_LOCK", str(lock))
     Lx, Ly, N, D, chi, cplx, matter, prec = case
     h, g, J = 1.0, 0.4, (0.5 if matter else 0.0)
     lat, pe, ctx = setup(Lx, Ly, N, D, chi, seed=61, complex_=cplx, matter=matter, precision=prec, h=h, g=g, J=J)
