@@ -76,6 +76,7 @@ struct gcf_ctx {
   // SR work
   SrWork sr{};
   long long sr_ns_cap = 0;
+  long long sr_sum_bs = 0;
   int sr_chain_cap = 0;
   // e2e sample buffers
   int8_t* d_cfg = nullptr;
@@ -719,16 +720,29 @@ gcf_status ensure_sr(gcf_ctx* c, long long Ns, int n_chains) {
     if (cudaMemcpy(c->sr.seg_v, sv.data(), sizeof(int) * sv.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->sr.seg_b, sb.data(), sizeof(int) * sb.size(), cudaMemcpyHostToDevice) != cudaSuccess)
       return fail(c, GCF_ECUDA, "SR segment tables");
+    std::vector<long long> pbs(c->n_s);
+    long long acc = 0;
+    for (int v = 0; v < c->n_s; ++v) { pbs[v] = acc; acc += c->vbs[v]; }
+    c->sr_sum_bs = acc;
+    c->sr.all_bs4 = 1;
+    for (int v = 0; v < c->n_s; ++v)
+      if (c->vbs[v] % 4) c->sr.all_bs4 = 0;
+    if (cudaMalloc(&c->sr.pbs, sizeof(long long) * c->n_s) != cudaSuccess ||
+        cudaMemcpy(c->sr.pbs, pbs.data(), sizeof(long long) * c->n_s, cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(c, GCF_ENOMEM, "SR segment tables");
   }
   if (Ns > c->sr_ns_cap) {
     if (c->sr.t) cudaFree(c->sr.t);
     if (c->sr.coef) cudaFree(c->sr.coef);
     if (c->sr.perm) cudaFree(c->sr.perm);
+    if (c->sr.osort) cudaFree(c->sr.osort);
     c->sr.t = c->sr.coef = nullptr;
     c->sr.perm = nullptr;
+    c->sr.osort = nullptr;
     if (cudaMalloc(&c->sr.t, sizeof(cdouble) * Ns) != cudaSuccess ||
         cudaMalloc(&c->sr.coef, sizeof(cdouble) * Ns) != cudaSuccess ||
-        cudaMalloc(&c->sr.perm, sizeof(int) * Ns * c->n_s) != cudaSuccess)
+        cudaMalloc(&c->sr.perm, sizeof(int) * Ns * c->n_s) != cudaSuccess ||
+        cudaMalloc(&c->sr.osort, c->sbytes * (size_t)Ns * c->sr_sum_bs) != cudaSuccess)
       return fail(c, GCF_ENOMEM, "SR sample vectors");
     c->sr_ns_cap = Ns;
   }
@@ -829,6 +843,7 @@ void gcf_destroy(gcf_ctx* c) {
   void* ptrs[] = {c->d_params, c->d_Q, c->d_voff, c->d_vbs, c->d_vnb, c->d_tables, c->d_status,
                   c->d_scratch, c->sr.obar, c->sr.F, c->sr.x, c->sr.r, c->sr.p, c->sr.Ap, c->sr.z, c->sr.dinv,
                   c->sr.t, c->sr.coef, c->sr.chain_mean, c->sr.tbar, c->sr.scal, c->sr.perm, c->sr.seg,
+                  c->sr.pbs, c->sr.osort,
                   c->sr.seg_v, c->sr.seg_b, c->d_cfg, c->d_e,
                   c->d_la, c->d_ph, c->d_bid, c->d_O, c->d_acc, c->vjp_bid, c->vjp_O, c->vjp_coef,
                   c->vjp_acc, c->multi_arena, c->multi_tab};

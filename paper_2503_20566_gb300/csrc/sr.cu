@@ -6,6 +6,8 @@
 // sample s touches exactly one block per vertex.
 //   S v = (1/Ns) sum_s O_s^* (t_s - tbar),  t_s = O_s . v,  tbar = mean_s t_s.
 // Everything here runs in FP64 (complex FP64 for complex tensors).
+#include <type_traits>
+
 #include "sr.cuh"
 
 namespace gcf {
@@ -307,14 +309,33 @@ __global__ void k_gather_vec(SrGeom g, const int* bids, const T* O, const cdoubl
   if (lane == 0) t[s] = {ar, CPLX ? ai : 0.0};
 }
 
-// out[off(v, b) + e] += sum_{s in segment (v, b)} coef_s op(O[s][v][e]),
-// op = conj if CONJ, op = |.|^2 if SQ.  Grid = segments x split: CTA (segment, part) takes one
-// contiguous part of its segment; threads = streams x entries; each stream
-// sums chunks of 32 samples in the storage precision, then FP64; parts are
-// combined with FP64 atomics (split x block-size of them per segment).
-template <class T, bool CONJ, bool CPLX, bool SQ = false>
-__global__ void k_scatter2(SrGeom g, const int* perm, const int* seg, int maxnb, int split, const T* O,
-                           const cdouble* coef, cdouble* out, const int* seg_v, const int* seg_b) {
+// O in segment order: osort[Ns * pbs[v] + q * bs_v + e] = O[perm_v[q]][v][e].
+// Grid (row chunks, vertices); consecutive threads write consecutive entries.
+template <class T>
+__global__ void k_permute_O(SrGeom g, const int* perm, const long long* pbs, const T* O, T* osort) {
+  const int v = blockIdx.y;
+  const int bs = g.vbs[v];
+  const long long n = g.Ns * bs;
+  const int* pv = perm + (long long)v * g.Ns;
+  T* dst = osort + g.Ns * pbs[v];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long q = i / bs;
+    const int e = (int)(i - q * bs);
+    dst[i] = O[((long long)pv[q] * g.n_s + v) * g.D4 + e];
+  }
+}
+
+// out[off(v, b) + e] += sum_{s in segment (v, b)} coef_s op(O[s][v][e]) on
+// the segment-ordered copy of O.  Grid = segments x split: CTA (segment,
+// part) streams one contiguous part of its segment's rows (thread t keeps
+// entry e = t % bs of rows t / bs, t / bs + rows-per-step, ...), sums in the
+// storage precision in chunks of 32 rows, then FP64, and combines parts
+// with FP64 atomics; coef is gathered through perm (it stays in L2).
+// op = conj if CONJ, |.|^2 if SQ.
+template <class T, bool CONJ, bool CPLX, bool SQ>
+__global__ void k_scatter_sorted(SrGeom g, const int* perm, const int* seg, int maxnb, int split, const T* osort,
+                                 const long long* pbs, const cdouble* coef, cdouble* out, const int* seg_v,
+                                 const int* seg_b) {
   using P = typename PartialOf<T>::type;
   __shared__ double red[2 * 256];
   const int sid = blockIdx.x / split, part = blockIdx.x - (blockIdx.x / split) * split;
@@ -326,20 +347,19 @@ __global__ void k_scatter2(SrGeom g, const int* perm, const int* seg, int maxnb,
   const int s_begin = seg0 + part * per, s_end = min(seg1, s_begin + per);
   if (s_begin >= s_end) return;
   const int* pv = perm + (long long)v * g.Ns;
-  const int streams = max(1, (int)blockDim.x / bs);
-  const int e = threadIdx.x % bs;
-  const int st = threadIdx.x / bs;
+  const T* rows = osort + g.Ns * pbs[v];
+  const int rps = max(1, (int)blockDim.x / bs);  // rows per step
+  const int e = threadIdx.x % bs, rr = threadIdx.x / bs;
   double ar = 0.0, ai = 0.0;
-  if (st < streams) {
+  if (rr < rps) {
     int cnt = 0;
     P pr = P(0), pi = P(0);
 #pragma unroll 4
-    for (int q = s_begin + st; q < s_end; q += streams) {
-      const long long s = pv[q];
-      const T ov = O[(s * g.n_s + v) * (long long)g.D4 + e];
-      const cdouble c = coef[s];
+    for (int q = s_begin + rr; q < s_end; q += rps) {
+      const T ov = rows[(long long)q * bs + e];
+      const cdouble c = coef[pv[q]];
       P orr = (P)re(ov), oi = CONJ ? -(P)im(ov) : (P)im(ov);
-      if (SQ) {  // |O|^2 instead of O
+      if (SQ) {
         orr = orr * orr + oi * oi;
         oi = P(0);
       }
@@ -365,13 +385,66 @@ __global__ void k_scatter2(SrGeom g, const int* perm, const int* seg, int maxnb,
   __syncthreads();
   if (threadIdx.x < bs) {
     double sr = 0.0, si = 0.0;
-    for (int q = 0; q < streams; ++q) {
+    for (int q = 0; q < rps; ++q) {
       sr += red[q * bs + threadIdx.x];
       si += red[256 + q * bs + threadIdx.x];
     }
     cdouble* dst = out + g.voff[v] + (long long)b * bs + threadIdx.x;
     atomicAdd(&dst->x, sr);
     if (CPLX) atomicAdd(&dst->y, si);
+  }
+}
+
+// Real FP32 storage with bs a multiple of 4: each thread takes a 16-byte
+// quad (4 entries) of a row; otherwise as k_scatter_sorted.
+template <bool SQ>
+__global__ void k_scatter_sorted_f4(SrGeom g, const int* perm, const int* seg, int maxnb, int split,
+                                    const float* osort, const long long* pbs, const cdouble* coef, cdouble* out,
+                                    const int* seg_v, const int* seg_b) {
+  __shared__ double red[256 * 4];
+  const int sid = blockIdx.x / split, part = blockIdx.x - (blockIdx.x / split) * split;
+  const int v = seg_v[sid], b = seg_b[sid];
+  const int bs = g.vbs[v], nq = bs >> 2;
+  const int seg0 = seg[v * (maxnb + 1) + b], seg1 = seg[v * (maxnb + 1) + b + 1];
+  const int len = seg1 - seg0;
+  const int per = (len + split - 1) / split;
+  const int s_begin = seg0 + part * per, s_end = min(seg1, s_begin + per);
+  if (s_begin >= s_end) return;
+  const int* pv = perm + (long long)v * g.Ns;
+  const float* rows = osort + g.Ns * pbs[v];
+  const int rps = max(1, (int)blockDim.x / nq);  // rows per step
+  const int qi = threadIdx.x % nq, rr = threadIdx.x / nq;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  if (rr < rps) {
+    int cnt = 0;
+    float part4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+    for (int q = s_begin + rr; q < s_end; q += rps) {
+      const float4 o = *reinterpret_cast<const float4*>(rows + (long long)q * bs + 4 * qi);
+      const float c = (float)coef[pv[q]].x;
+      if (SQ) {
+        part4[0] += c * o.x * o.x; part4[1] += c * o.y * o.y;
+        part4[2] += c * o.z * o.z; part4[3] += c * o.w * o.w;
+      } else {
+        part4[0] += c * o.x; part4[1] += c * o.y; part4[2] += c * o.z; part4[3] += c * o.w;
+      }
+      if (++cnt == 32) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { acc[i] += (double)part4[i]; part4[i] = 0.f; }
+        cnt = 0;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] += (double)part4[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) red[4 * threadIdx.x + i] = acc[i];
+  __syncthreads();
+  if (threadIdx.x < bs) {
+    const int q4 = threadIdx.x >> 2, i = threadIdx.x & 3;
+    double sr = 0.0;
+    for (int r = 0; r < rps; ++r) sr += red[4 * (r * nq + q4) + i];
+    atomicAdd(&(out + g.voff[v] + (long long)b * bs + threadIdx.x)->x, sr);
   }
 }
 
@@ -419,13 +492,29 @@ static cudaError_t scatter(const SrGeom& g, const SrWork& w, const T* O, const c
   const long long per_seg = g.Ns * g.n_s / std::max(1, w.n_seg);
   const int split = (int)std::max<long long>(1, std::min<long long>(512, per_seg / 2048));
   const unsigned grid = (unsigned)(w.n_seg * split);
+  const T* os = (const T*)w.osort;
+  (void)O;
+  if constexpr (std::is_same<T, float>::value) {
+    if (w.all_bs4) {
+      if (sq)
+        k_scatter_sorted_f4<true><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, os, w.pbs, coef, out,
+                                                         w.seg_v, w.seg_b);
+      else
+        k_scatter_sorted_f4<false><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, os, w.pbs, coef, out,
+                                                          w.seg_v, w.seg_b);
+      ++*launches;
+      return cudaGetLastError();
+    }
+  }
   if (sq)
-    k_scatter2<T, false, C, true><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, O, coef, out, w.seg_v,
-                                                         w.seg_b);
+    k_scatter_sorted<T, false, C, true><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, os, w.pbs, coef,
+                                                               out, w.seg_v, w.seg_b);
   else if (conj)
-    k_scatter2<T, true, C><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, O, coef, out, w.seg_v, w.seg_b);
+    k_scatter_sorted<T, true, C, false><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, os, w.pbs, coef,
+                                                               out, w.seg_v, w.seg_b);
   else
-    k_scatter2<T, false, C><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, O, coef, out, w.seg_v, w.seg_b);
+    k_scatter_sorted<T, false, C, false><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, os, w.pbs, coef,
+                                                                out, w.seg_v, w.seg_b);
   ++*launches;
   return cudaGetLastError();
 }
@@ -470,6 +559,12 @@ cudaError_t sr_solve_update(const SrGeom& g, SrWork& w, const double* e_loc, con
   // samples grouped by (vertex, block) for the atomic-free scatter
   k_sort_by_block<<<g.n_s, 1024, 0, st>>>(g, bids, w.maxnb, w.perm, w.seg);
   ++*launches;
+  // O in segment order, streamed by every scatter of this step
+  {
+    dim3 grid((unsigned)std::min<long long>(1024, (Ns * 16 + 255) / 256), (unsigned)g.n_s);
+    k_permute_O<T><<<grid, 256, 0, st>>>(g, w.perm, w.pbs, O, (T*)w.osort);
+    ++*launches;
+  }
   // Obar = (1/Ns) sum_s O_s
   CK(cudaMemsetAsync(w.obar, 0, sizeof(cdouble) * Np, st));
   k_fill_c<<<nblk(Ns, 256), 256, 0, st>>>(w.coef, Ns, 1.0 / (double)Ns, 0.0);

@@ -32,6 +32,11 @@ struct SrWork {
   int* seg_v;     // [n_seg] vertex of segment
   int* seg_b;     // [n_seg] block of segment
   int maxnb, n_seg;
+  // O in segment order: vertex v's rows (bs_v entries each, samples in perm
+  // order) start at element Ns * pbs[v]
+  long long* pbs;  // [n_s] prefix sums of the block sizes
+  void* osort;     // [Ns * sum_v bs_v] storage scalars
+  int all_bs4;     // every block size is a multiple of 4
 };
 
 // Computes <E>, F, solves (S + shift) x = F by CG, then params += (cr + i ci) x.
