@@ -66,7 +66,7 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-PROFILE = os.path.join(ROOT, "profiles", "vmc_kernel_grouped_f32_z2_8x8_D4_chi16.md")
+PROFILE = os.path.join(ROOT, "profiles", "vmc_kernel_grouped4_f32_z2_8x8_D4_chi16.md")
 
 
 def profiled_traffic(samples_per_launch):
