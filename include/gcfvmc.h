@@ -283,6 +283,15 @@ int64_t gcf_launch_count(const gcf_ctx* ctx);
  * a form.  All forms compute the same results. */
 int gcf_executor(const gcf_ctx* ctx);
 
+/* Lockstep waits that ran out in the last synchronous sampling or
+ * measurement launch of this context (implementation detail; no counterpart
+ * in the paper).  A chain group whose wait for the other groups of its CTA
+ * exceeds its iteration limit leaves lockstep for the rest of that chain
+ * and counts here; results are unaffected, only the speed.  0 normally;
+ * GCFVMC_LOCK_FAULT=1 in the environment (a test hook) makes one group never
+ * count in, so the others' waits run out. */
+int gcf_phase_timeouts(const gcf_ctx* ctx);
+
 /* Shared-memory placement level of the kernel form this context launches
  * (implementation choice; no counterpart in the paper): 0 = configuration
  * only, 1 = + hot buffers (network boxes, proposals, current environments,

@@ -65,6 +65,7 @@ def load_library(path: str = LIB_PATH):
         "gcf_launch_count": (i64, [vp]),
         "gcf_executor": (i, [vp]),
         "gcf_smem_level": (i, [vp]),
+        "gcf_phase_timeouts": (i, [vp]),
         "gcf_autotune": (i, [vp, i, i, vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
         "gcf_set_tensors": (i, [vp, vp, C.c_size_t]),
         "gcf_get_tensors": (i, [vp, vp, C.c_size_t]),
@@ -91,7 +92,7 @@ def load_library(path: str = LIB_PATH):
 def exported_symbols():
     """Names the binding expects the library to export."""
     return ["gcf_init_peps", "gcf_destroy", "gcf_last_error", "gcf_num_params", "gcf_config_len",
-            "gcf_scalar_bytes", "gcf_launch_count", "gcf_executor", "gcf_smem_level", "gcf_autotune", "gcf_set_tensors", "gcf_get_tensors",
+            "gcf_scalar_bytes", "gcf_launch_count", "gcf_executor", "gcf_smem_level", "gcf_phase_timeouts", "gcf_autotune", "gcf_set_tensors", "gcf_get_tensors",
             "gcf_init_configs", "gcf_amplitude", "gcf_local_energy", "gcf_log_grad", "gcf_log_grad_vjp", "gcf_sample_multi",
             "gcf_sample_batch", "gcf_sample_batch_async", "gcf_sr_step", "gcf_vmc_step_host"]
 
@@ -170,6 +171,11 @@ class Context:
         self._check(self.lib.gcf_autotune(self.ctx, c.shape[0], int(n_sweeps), _ptr(c), ms, C.byref(nf)),
                     "autotune")
         return [float(ms[i]) for i in range(min(nf.value, 16))]
+
+    @property
+    def phase_timeouts(self):
+        """Lockstep waits that ran out in the last synchronous launch."""
+        return int(self.lib.gcf_phase_timeouts(self.ctx))
 
     @property
     def smem_level(self):

@@ -62,6 +62,8 @@ struct gcf_ctx {
   Plan plan;
   int exec = 0, group_threads = 64;
   int lockstep = 0;  // grouped kernels: chain groups of a CTA in lockstep
+  int lock_fault = 0;  // test hook (GCFVMC_LOCK_FAULT): one group never counts in
+  int last_phase_timeouts = 0;
   int tab_ints = 0;  // ints in d_tables
   // device
   void* d_params = nullptr;
@@ -180,6 +182,8 @@ void plan_group(gcf_ctx* c) {
   }
   c->lockstep = 1;
   if (const char* e = std::getenv("GCFVMC_LOCK")) c->lockstep = std::atoi(e) ? 1 : 0;
+  c->lock_fault = 0;
+  if (const char* e = std::getenv("GCFVMC_LOCK_FAULT")) c->lock_fault = std::atoi(e) ? 1 : 0;
   if (const char* e = std::getenv("GCFVMC_EXEC")) {
     if (!std::strcmp(e, "group4")) {
       c->exec = EXEC_GROUP4;
@@ -506,6 +510,7 @@ KParams<T> make_params(gcf_ctx* c) {
   k.so_t1 = p.so_t1; k.so_t2 = p.so_t2; k.smem_cfg_bytes = p.cfg_bytes;
   k.group_smem_bytes = (long long)p.group_smem;
   k.lockstep = c->lockstep;
+  k.lock_fault = c->lock_fault;
   k.group_threads = c->group_threads;
   // tensor-core forms exist for FP32 storage only
   k.gemm_mode = GEMM_FFMA;
@@ -593,6 +598,7 @@ gcf_status run_vmc(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t
   CUDA_TRY(c, cudaMemcpyAsync(h_status, c->d_status, sizeof(h_status), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (gauss_count) *gauss_count = h_status[ST_GAUSS];
+  c->last_phase_timeouts = h_status[ST_PHASE_TIMEOUT];
   return GCF_OK;
 }
 
@@ -1058,6 +1064,8 @@ gcf_status gcf_autotune(gcf_ctx* c, int n_chains, int n_sweeps, const int8_t* co
   set_form(c, forms[best_i].first, forms[best_i].second);
   return GCF_OK;
 }
+
+int gcf_phase_timeouts(const gcf_ctx* c) { return c ? c->last_phase_timeouts : -1; }
 
 int gcf_smem_level(const gcf_ctx* c) {
   if (!c) return -1;

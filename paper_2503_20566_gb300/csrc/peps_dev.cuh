@@ -65,6 +65,7 @@ struct KParams {
   long long group_smem_bytes;  // grouped kernel: shared bytes per chain group
   int group_threads;          // grouped kernel: threads per chain (128)
   int lockstep;               // grouped kernels: keep a CTA's chains at the same row
+  int lock_fault;             // test hook: group 0 never counts in, so the others' waits run out
   int gemm_mode;              // GemmMode of the contraction GEMMs
   int row_gemm_mode;          // GemmMode of the row environments (O, amplitude, hops)
   // right environments and the staged B / T rows of the current pass

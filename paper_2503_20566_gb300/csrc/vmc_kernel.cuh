@@ -99,7 +99,7 @@ struct Chain {
     if (ex.leader()) {
       sv.phase += 1;
       const int target = sv.phase * n_groups;
-      atomicAdd(&g_phase_arrive, 1);
+      if (!(k.lock_fault && ex.slot() == 0)) atomicAdd(&g_phase_arrive, 1);
       int it = 0;
       while (*(volatile int*)&g_phase_arrive < target && it < kPhaseSpinLimit) {
         __nanosleep(64);

@@ -73,3 +73,32 @@ def test_executor_amplitude_and_chain(case, executor, level, lock, monkeypatch):
         assert np.array_equal(final[c], recs[-1]["cfg"].astype(np.int8)), c
         for w, rec in enumerate(recs):
             assert amp_err(la[c * n_sweeps + w], 0.0, rec["log_abs"], 0.0) < TOL[prec] * 10
+
+
+def test_lockstep_wait_that_runs_out_is_reported_and_results_stay_exact(monkeypatch):
+    """A lockstep wait with nobody to meet: the test hook makes one group of a
+    four-group CTA never count in, so every wait runs to its iteration limit.
+    The kernel must end, report the timeouts through the status the host
+    reads, and still produce the oracle's chains; without the hook no wait
+    runs out."""
+    monkeypatch.setenv("GCFVMC_EXEC", "group4")
+    monkeypatch.setenv("GCFVMC_LOCK", "1")
+    for fault in (1, 0):
+        monkeypatch.setenv("GCFVMC_LOCK_FAULT", str(fault))
+        lat, pe, ctx = setup(4, 4, 2, 4, 4, seed=131, precision="fp32", h=1.0, g=0.4)
+        cfgs, _, _ = configs_for(lat, 4, seed=132)  # four chains: one CTA, every group busy
+        dev = torch.from_numpy(cfgs).cuda()
+        out = ctx.sample_batch(dev, 2, seed=77)
+        torch.cuda.synchronize()
+        if fault:
+            assert ctx.phase_timeouts >= 1
+        else:
+            assert ctx.phase_timeouts == 0
+        final = dev.cpu().numpy()
+        la = out["log_abs"].cpu().numpy()
+        model = vmc.Model(h=1.0, g=0.4)
+        for c in range(len(cfgs)):
+            recs = vmc.run_chain(pe, model, cfgs[c], 4, 77, c, 2, measure=True)
+            assert np.array_equal(final[c], recs[-1]["cfg"].astype(np.int8)), c
+            for w, rec in enumerate(recs):
+                assert amp_err(la[c * 2 + w], 0.0, rec["log_abs"], 0.0) < TOL["fp32"] * 10
