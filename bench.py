@@ -202,6 +202,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the planner's kernel form")
+    ap.add_argument("--no-forms", action="store_true", help="skip the precision-form comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -283,6 +284,26 @@ def main():
     samples_per_step = n_chains * n_sweeps
     value = replicas.whole_job_rate(samples_per_step, args.steps, world, total_ms)
 
+    # the contraction forms side by side (kernel only, same tensors and chains):
+    # plain FP32 on CUDA cores, TF32x3 and BF16 on tensor cores
+    forms = None
+    if rank == 0 and world == 1 and not args.no_forms:
+        forms = {"sweeps": 8, "chains": n_chains, "unit": "samples/s (sampling kernel only)"}
+        for prec in ("fp32", "tf32", "bf16"):
+            fctx = G.Context(w["N"], w["Lx"], w["Ly"], w["D"], w["chi"], h=w["h_p"], g=w["g"], precision=prec,
+                             seed=seeds["tensors"])
+            fcfg = fctx.init_configs(n_chains, powers=powers)
+            fout = fctx.alloc_samples(n_chains, 8, grad=True)
+            fctx.sample_batch(fcfg, 8, seed=1, out=fout)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(fctx.stream):
+                e0.record(fctx.stream)
+                fctx.sample_batch(fcfg, 8, seed=2, out=fout)
+                e1.record(fctx.stream)
+            torch.cuda.synchronize()
+            forms[{"fp32": "fp32", "tf32": "tf32x3", "bf16": "bf16"}[prec]] = n_chains * 8 / (e0.elapsed_time(e1) / 1e3)
+            del fctx, fcfg, fout
+
     # end to end through the host-buffer C call
     e2e = None
     if not args.no_e2e:
@@ -331,6 +352,8 @@ def main():
         }
         if e2e:
             line["e2e"] = e2e
+        if forms:
+            line["precision_forms"] = forms
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
