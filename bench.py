@@ -25,6 +25,7 @@ import os
 import re
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -200,6 +201,8 @@ def main():
     ap.add_argument("--sweeps", type=int, default=WORKLOAD["sweeps"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-log", default=None,
+                    help="keep the nvidia-smi clock samples of the timed region here ({rank} is replaced)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the planner's kernel form")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision-form comparison")
@@ -260,8 +263,8 @@ def main():
     launches0 = ctx.launch_count
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                            f".clocks_rank{rank}.csv")
+    clk_path = (args.clocks_log.format(rank=rank) if args.clocks_log
+                else os.path.join(tempfile.gettempdir(), f"gcfvmc_clocks_{os.getpid()}_rank{rank}.csv"))
     sampler, sf = clocks_sampler_start(clk_path)
     time.sleep(0.3)
     torch.cuda.synchronize()
