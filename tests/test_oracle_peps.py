@@ -63,9 +63,11 @@ def test_parameter_count_matches_block_counting():
     assert P.layout(lat, 2)[1] == 14 * 14 * 64 * 16 + 4 * 14 * 16 * 8 + 4 * 4 * 4
 
 
-@pytest.mark.parametrize("N,Dk,matter", [(2, 2, False), (3, 1, False), (2, 1, True)])
-def test_gi_peps_vanishes_off_gauss_and_matches_sampled_network(N, Dk, matter):
-    Lx, Ly = (3, 3) if (N == 2 and not matter) else (3, 2)
+@pytest.mark.parametrize("N,Dk,matter,Lx,Ly", [(2, 2, False, 3, 3), (3, 1, False, 3, 2), (2, 1, True, 3, 2),
+                                                (3, 1, True, 2, 2)])
+def test_gi_peps_vanishes_off_gauss_and_matches_sampled_network(N, Dk, matter, Lx, Ly):
+    # Z3 with matter fixes the sign of the matter charge against the leg sum
+    # (for Z2 both signs agree, and without matter the sum's overall sign is free).
     pe = make_peps(Lx, Ly, N, Dk, seed=1, matter=matter)
     lat = pe.lat
     A = [[pe.dense_A(x, y) for x in range(Lx)] for y in range(Ly)]

@@ -1,0 +1,119 @@
+"""Planted mistakes: each plausible error in the oracle fails at least one pin.
+
+Each case rewrites one expression of one oracle function, installs the
+altered function with monkeypatch (on the CPU, in this process only) and runs
+a pin from the oracle's own test modules, which must then fail.  The text to
+replace must occur exactly once in the function's source, so a refactor of
+the oracle makes this test fail loudly instead of checking nothing.  The
+unaltered oracle passes the same pins in test_oracle_model.py,
+test_oracle_peps.py and test_oracle_vmc.py.
+"""
+
+import inspect
+import textwrap
+
+import pytest
+
+from oracle import lattice as L
+from oracle import peps as P
+from oracle import rng
+from oracle import vmc
+
+import test_oracle_model as TM
+import test_oracle_peps as TP
+import test_oracle_vmc as TV
+
+
+def plant(monkeypatch, owner, name, old, new):
+    """Replace ``owner.name`` by a copy of it whose source has ``old`` -> ``new``."""
+    fn = getattr(owner, name)
+    src = textwrap.dedent(inspect.getsource(fn))
+    assert src.count(old) == 1, f"{name}: expected exactly one {old!r}"
+    ns = dict(vars(inspect.getmodule(fn)))
+    exec(compile(src.replace(old, new), f"<{name} with a planted mistake>", "exec"), ns)
+    monkeypatch.setattr(owner, name, ns[name])
+
+
+# (case id, owner, function, original text, planted text, pin that must fail;
+#  each pin is called with the monkeypatch fixture)
+CASES = [
+    # Hamiltonian, Eqs. (2-5)
+    ("z2-plaquette-counted-once", L.Lattice, "off_diagonal", "-2.0 * h", "-h",
+     lambda mp: TM.test_ed_pin_z2_hardcore_bosons_3x3()),
+    ("electric-term-halved", L.Lattice, "diagonal_energy", "2.0 - 2.0 * np.cos", "1.0 - np.cos",
+     lambda mp: TM.test_ed_pin_z2_hardcore_bosons_3x3()),
+    # Gauss law, Eq. (1), and the moves that preserve it
+    ("gauss-law-signs", L.Lattice, "gauss_residual", "p + nl + nd - nr - nu", "p + nl - nd - nr + nu",
+     lambda mp: TM.test_physical_basis_equals_brute_force(3, 2, 3, False)),
+    ("plaquette-orientation", L.Lattice, "plaquette", "c[self.hi(x, y + 1)] - t", "c[self.hi(x, y + 1)] + t",
+     lambda mp: TM.test_moves_preserve_gauss_law(3)),
+    ("hop-lowers-instead-of-raising", L.Lattice, "hop", "c[li] = (c[li] + 1) % self.N",
+     "c[li] = (c[li] - 1) % self.N", lambda mp: TM.test_moves_preserve_gauss_law(3)),
+    ("block-selection-leg-signs", P, "block_id", "tot = p + sum(", "tot = p - sum(",
+     lambda mp: TP.test_gi_peps_vanishes_off_gauss_and_matches_sampled_network(3, 1, True, 2, 2)),
+    # counter-based generator
+    ("splitmix-shift", rng, "mix64", "z ^ (z >> 30)", "z ^ (z >> 31)", lambda mp: TM.test_splitmix64_reference_vector()),
+    # boundary MPS (Sec. S-2)
+    ("absorb-transposed-bond", P, "absorb", '"adb,lrdu->alubr"', '"adb,lrdu->laubr"',
+     lambda mp: TP.test_boundary_mps_exact_when_chi_reaches_bound(6, 5, 2, 2, False)),
+    ("compress-drops-a-singular-value", P, "compress", "k = min(chi, len(S))",
+     "k = max(1, min(chi, len(S)) - 1)",
+     lambda mp: TP.test_boundary_mps_exact_when_chi_reaches_bound(6, 5, 2, 2, False)),
+    ("compress-drops-singular-weights", P, "compress", "U[:, :k] * S[:k]", "U[:, :k]",
+     lambda mp: TP.test_two_site_compression_is_eckart_young()),
+    ("strip-rows-swapped", P, "contract_strip", '"aijb,adA,iIdm,jJmu,buB->AIJB"', '"aijb,adA,iIdm,jJmu,buB->AJIB"',
+     lambda mp: TV.test_local_energy_equals_H_psi_over_psi(4, 4, 2, 2, False, 24)),
+    # E_loc, Eq. (S2)
+    ("eloc-z2-factor", vmc, "local_energy", "amp = -2.0 * model.h if", "amp = -1.0 * model.h if",
+     lambda mp: TV.test_local_energy_equals_H_psi_over_psi(4, 4, 2, 2, False, 24)),
+    ("eloc-missing-plaquette-dagger", vmc, "local_energy", "powers = (1,) if lat.N == 2 else (1, lat.N - 1)",
+     "powers = (1,)", lambda mp: TV.test_local_energy_equals_H_psi_over_psi(3, 3, 3, 2, True, 81)),
+    ("eloc-hop-sign", vmc, "local_energy", "e += model.J * _strip_value", "e -= model.J * _strip_value",
+     lambda mp: TV.test_local_energy_with_matter_hops()),
+    # O = d ln psi / d A (Eq. S3)
+    ("log-grad-not-divided-by-psi", vmc, "log_grad", "P.row_site_environment(Bm, rows[r], Tm, x) / val",
+     "P.row_site_environment(Bm, rows[r], Tm, x)", lambda mp: TV.test_log_grad_matches_finite_differences(False)),
+    ("log-grad-conjugated", vmc, "log_grad", "P.row_site_environment(Bm, rows[r], Tm, x) / val",
+     "np.conj(P.row_site_environment(Bm, rows[r], Tm, x) / val)",
+     lambda mp: TV.test_log_grad_matches_finite_differences(True)),
+    # Metropolis rule (Sec. S-1)
+    ("metropolis-ratio-not-squared", vmc, "_accept", "abs(den) ** 2 < abs(num) ** 2", "abs(den) < abs(num)",
+     lambda mp: TV.test_sampler_histogram_matches_born_weights(3, 3, 2, 0.05)),
+    ("proposal-without-inverse-power", rng, "power", "return 1 + word(seed, chain, counter) % (N - 1)",
+     "return 1", lambda mp: TV.test_sampler_histogram_matches_born_weights(3, 2, 3, 0.05)),
+    ("plaquette-pass-environment-from-stale-rows", vmc, "sweep",
+     "        rows = peps.sampled_network(cfg)\n        Bm, _ = P.compress(P.absorb(Bm, rows[r]), chi)",
+     "        Bm, _ = P.compress(P.absorb(Bm, rows[r]), chi)",
+     lambda mp: TV.test_sampler_histogram_matches_born_weights(3, 4, 2, 0.1)),
+    ("plaquette-pass-environment-from-stale-rows-ratios", vmc, "sweep",
+     "        rows = peps.sampled_network(cfg)\n        Bm, _ = P.compress(P.absorb(Bm, rows[r]), chi)",
+     "        Bm, _ = P.compress(P.absorb(Bm, rows[r]), chi)",
+     lambda mp: TV.test_sweep_ratios_equal_exact_amplitude_ratios(4, 4, 3, False, mp)),
+    ("horizontal-hop-pass-environment-from-stale-rows", vmc, "sweep",
+     "            rows = peps.sampled_network(cfg)\n            Tm, _ = P.compress(",
+     "            Tm, _ = P.compress(",
+     lambda mp: TV.test_sweep_ratios_equal_exact_amplitude_ratios(4, 4, 2, True, mp)),
+    ("vertical-hop-pass-environment-from-stale-rows", vmc, "sweep",
+     "            rows = peps.sampled_network(cfg)\n            Bm, _ = P.compress(P.absorb(Bm, rows[r]), chi)",
+     "            Bm, _ = P.compress(P.absorb(Bm, rows[r]), chi)",
+     lambda mp: TV.test_sweep_ratios_equal_exact_amplitude_ratios(4, 4, 2, True, mp)),
+    ("hop-pass-row-value-on-wrong-row", vmc, "sweep",
+     "_row_value(peps, c2, r, Bm, Tm), _row_value(peps, cfg, r, Bm, Tm)",
+     "_row_value(peps, c2, r, Bm, Tm), _row_value(peps, c2, r, Bm, Tm)",
+     lambda mp: TV.test_sweep_ratios_equal_exact_amplitude_ratios(3, 4, 3, True, mp)),
+    # SR / tVMC (Eqs. S3, S6-S8)
+    ("sr-matrix-missing-conjugate", vmc, "sr_matrices", "(O.conj().T * w) @ O", "(O.T * w) @ O",
+     lambda mp: TV.test_cg_equals_dense_solve_and_residual()),
+    ("cg-direction-update", vmc, "cg_solve", "(rs_new / rs) * p", "(rs / rs_new) * p",
+     lambda mp: TV.test_cg_equals_dense_solve_and_residual()),
+    ("tdvp-time-direction", vmc, "tdvp_velocity", "-1j * sr_solve", "1j * sr_solve",
+     lambda mp: TV.test_tvmc_two_stage_follows_exact_evolution()),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_planted_mistake_fails_a_pin(case, monkeypatch):
+    _, owner, name, old, new, pin = case
+    plant(monkeypatch, owner, name, old, new)
+    with pytest.raises(AssertionError):
+        pin(monkeypatch)

@@ -6,7 +6,9 @@
   entries 1, g = 0) E_loc is the same for every configuration.
 * O = d ln psi / d A~ equals central finite differences, both of the row value
   with fixed environments and of the full exact amplitude.
-* The Metropolis sweep samples |psi|^2 (histogram on 3x3), and conserves the
+* The Metropolis sweep samples |psi|^2 (histograms on 3x3 and 3x4 Z2 and 3x2
+  Z3); at exact chi every ratio it forms from its carried environments equals
+  the exact amplitude ratio (plaquette and both hop passes); it conserves the
   Gauss law and the boson number.
 * SR: CG equals the dense solve; an SR step lowers the exact energy.
 * tVMC: the two-stage update with alpha_dot = -i (S+lambda)^{-1} F follows
@@ -134,8 +136,13 @@ def test_log_grad_fixed_environment_finite_difference_truncated():
         assert abs(blk[idx] - d) <= 1e-7 * max(1.0, abs(d))
 
 
-def test_sampler_histogram_matches_born_weights():
-    pe = make_peps(3, 3, 2, 2, seed=41)
+@pytest.mark.parametrize("Lx,Ly,N,tv_max", [(3, 3, 2, 0.05), (3, 2, 3, 0.05), (3, 4, 2, 0.1)])
+def test_sampler_histogram_matches_born_weights(Lx, Ly, N, tv_max):
+    # Z3 also fixes the proposal: P^t with t uniform in [1, N-1] is symmetric
+    # (P^t and its inverse P^(N-t) equally likely), P alone is not.  Four rows
+    # (three row pairs, 64 states, hence the wider bound) fix the bottom
+    # environment that the sweep carries from one row pair to the next.
+    pe = make_peps(Lx, Ly, N, 2, seed=41)
     lat = pe.lat
     basis = lat.physical_basis()
     psi = exact_psi(pe, basis)
@@ -151,7 +158,48 @@ def test_sampler_histogram_matches_born_weights():
                 counts[index[tuple(cfg)]] += 1
     freq = counts / counts.sum()
     tv = 0.5 * np.abs(freq - target).sum()
-    assert tv < 0.05, (tv, freq, target)
+    assert tv < tv_max, (tv, freq, target)
+
+
+@pytest.mark.parametrize("Lx,Ly,N,matter", [(4, 4, 3, False), (4, 4, 2, True), (3, 4, 3, True)])
+def test_sweep_ratios_equal_exact_amplitude_ratios(Lx, Ly, N, matter, monkeypatch):
+    """At exact chi every Metropolis ratio the sweep forms from its carried
+    environments (plaquette pass, horizontal and vertical hop passes) equals
+    psi(s') / psi(s) of the exactly contracted network.  The proposed s' is
+    recorded from the move functions, the ratio from the acceptance rule."""
+    pe = make_peps(Lx, Ly, N, 2, seed=45, matter=matter)
+    lat = pe.lat
+    nb = (4 if N == 2 else 3) if matter else 0  # the open lattice holds sum(p) = 0 mod N
+    cfg = random_physical(lat, 7, n_bosons=nb)
+    last, checked = {}, []
+    plaquette, hop, accept = Lattice.plaquette, Lattice.hop, vmc._accept
+
+    def rec_plaquette(self, c, x, y, t=1):
+        out = plaquette(self, c, x, y, t)
+        last["move"] = (np.array(c), out)
+        return out
+
+    def rec_hop(self, c, x, y, a):
+        out = hop(self, c, x, y, a)
+        last["move"] = (np.array(c), out)
+        return out
+
+    def rec_accept(u, num, den):
+        s0, s1 = last.pop("move")
+        ref = P.contract_exact(pe.sampled_network(s1)) / P.contract_exact(pe.sampled_network(s0))
+        checked.append(abs(num / den - ref) / max(1.0, abs(ref)))
+        return accept(u, num, den)
+
+    monkeypatch.setattr(Lattice, "plaquette", rec_plaquette)
+    monkeypatch.setattr(Lattice, "hop", rec_hop)
+    monkeypatch.setattr(vmc, "_accept", rec_accept)
+    chi = 2 ** (Lx // 2)
+    n_acc = 0
+    for w in range(2):
+        cfg, acc, prop = vmc.sweep(pe, cfg, chi, seed=5, chain=0, w=w)
+        n_acc += acc
+    assert len(checked) >= 2 * lat.n_plaquettes and n_acc > 0
+    assert max(checked) < 1e-9, max(checked)
 
 
 def test_matter_sweep_conserves_gauss_and_boson_number():
