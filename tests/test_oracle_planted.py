@@ -51,6 +51,8 @@ CASES = [
      "c[li] = (c[li] - 1) % self.N", lambda mp: TM.test_moves_preserve_gauss_law(3)),
     ("block-selection-leg-signs", P, "block_id", "tot = p + sum(", "tot = p - sum(",
      lambda mp: TP.test_gi_peps_vanishes_off_gauss_and_matches_sampled_network(3, 1, True, 2, 2)),
+    ("leg-values-up-down-swapped", L.Lattice, "leg_values", "return nl, nr, nd, nu", "return nl, nr, nu, nd",
+     lambda mp: TM.test_physical_basis_equals_brute_force(3, 2, 3, False)),
     # counter-based generator
     ("splitmix-shift", rng, "mix64", "z ^ (z >> 30)", "z ^ (z >> 31)", lambda mp: TM.test_splitmix64_reference_vector()),
     # boundary MPS (Sec. S-2)
@@ -63,12 +65,18 @@ CASES = [
      lambda mp: TP.test_two_site_compression_is_eckart_young()),
     ("strip-rows-swapped", P, "contract_strip", '"aijb,adA,iIdm,jJmu,buB->AIJB"', '"aijb,adA,iIdm,jJmu,buB->AJIB"',
      lambda mp: TV.test_local_energy_equals_H_psi_over_psi(4, 4, 2, 2, False, 24)),
+    ("compress-log-norm-halved", P, "compress", "return mps, float(np.log(nrm))", "return mps, float(np.log(nrm)) / 2",
+     lambda mp: TP.test_boundary_mps_exact_when_chi_reaches_bound(6, 5, 2, 2, False)),
+    ("amplitude-drops-environment-scale", vmc, "amplitude", "return s + float(np.log(abs(val)))",
+     "return float(np.log(abs(val)))", lambda mp: TP.test_boundary_mps_exact_when_chi_reaches_bound(6, 5, 2, 2, False)),
     # E_loc, Eq. (S2)
     ("eloc-z2-factor", vmc, "local_energy", "amp = -2.0 * model.h if", "amp = -1.0 * model.h if",
      lambda mp: TV.test_local_energy_equals_H_psi_over_psi(4, 4, 2, 2, False, 24)),
     ("eloc-missing-plaquette-dagger", vmc, "local_energy", "powers = (1,) if lat.N == 2 else (1, lat.N - 1)",
      "powers = (1,)", lambda mp: TV.test_local_energy_equals_H_psi_over_psi(3, 3, 3, 2, True, 81)),
     ("eloc-hop-sign", vmc, "local_energy", "e += model.J * _strip_value", "e -= model.J * _strip_value",
+     lambda mp: TV.test_local_energy_with_matter_hops()),
+    ("eloc-horizontal-hop-sign", vmc, "local_energy", "e += model.J * _row_value", "e -= model.J * _row_value",
      lambda mp: TV.test_local_energy_with_matter_hops()),
     # O = d ln psi / d A (Eq. S3)
     ("log-grad-not-divided-by-psi", vmc, "log_grad", "P.row_site_environment(Bm, rows[r], Tm, x) / val",
@@ -106,6 +114,14 @@ CASES = [
      lambda mp: TV.test_cg_equals_dense_solve_and_residual()),
     ("cg-direction-update", vmc, "cg_solve", "(rs_new / rs) * p", "(rs / rs_new) * p",
      lambda mp: TV.test_cg_equals_dense_solve_and_residual()),
+    ("sr-force-without-mean-subtraction", vmc, "sr_matrices", " - Obar.conj() * Ebar", "",
+     lambda mp: TV.test_tvmc_two_stage_follows_exact_evolution()),
+    ("sr-update-ascends", vmc, "sr_update", "params - lr * x", "params + lr * x",
+     lambda mp: TV.test_sr_step_lowers_exact_energy()),
+    ("cg-step-length", vmc, "cg_solve", "alpha = rs / np.vdot(p, Ap).real", "alpha = rs / np.vdot(Ap, Ap).real",
+     lambda mp: TV.test_cg_equals_dense_solve_and_residual()),
+    ("born-weights-not-squared", vmc, "exact_weights", "np.exp(2.0 * (la - la.max()))", "np.exp(la - la.max())",
+     lambda mp: TV.test_expectation_value_and_variational_bound()),
     ("tdvp-time-direction", vmc, "tdvp_velocity", "-1j * sr_solve", "1j * sr_solve",
      lambda mp: TV.test_tvmc_two_stage_follows_exact_evolution()),
 ]
