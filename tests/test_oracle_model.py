@@ -50,10 +50,14 @@ def test_ed_pin_rejects_single_counted_z2_plaquette():
     assert abs(e0 - gd["energy_per_site"]) > 1e-2
 
 
-@pytest.mark.parametrize("Lx,Ly,N,matter", [(2, 2, 2, False), (3, 2, 3, False), (3, 3, 2, False),
-                                            (2, 2, 4, False), (3, 2, 2, True), (2, 2, 3, True)])
-def test_physical_basis_equals_brute_force(Lx, Ly, N, matter):
-    lat = Lattice(Lx, Ly, N, matter=matter)
+@pytest.mark.parametrize("Lx,Ly,N,matter,Q", [(2, 2, 2, False, None), (3, 2, 3, False, None),
+                                              (3, 3, 2, False, None), (2, 2, 4, False, None),
+                                              (3, 2, 2, True, None), (2, 2, 3, True, None),
+                                              (3, 2, 3, False, [[1, 0, 0], [0, 0, 2]]),
+                                              (3, 2, 2, True, [[0, 1, 0], [0, 0, 0]])])
+def test_physical_basis_equals_brute_force(Lx, Ly, N, matter, Q):
+    # the last two carry static background charges Q_x (Eq. 1)
+    lat = Lattice(Lx, Ly, N, matter=matter, Q=Q)
     a = lat.physical_basis()
     b = lat.brute_force_physical()
     assert len(a) == len(b)

@@ -44,7 +44,9 @@ CASES = [
      lambda mp: TM.test_ed_pin_z2_hardcore_bosons_3x3()),
     # Gauss law, Eq. (1), and the moves that preserve it
     ("gauss-law-signs", L.Lattice, "gauss_residual", "p + nl + nd - nr - nu", "p + nl - nd - nr + nu",
-     lambda mp: TM.test_physical_basis_equals_brute_force(3, 2, 3, False)),
+     lambda mp: TM.test_physical_basis_equals_brute_force(3, 2, 3, False, None)),
+    ("gauss-law-ignores-background-charge", L.Lattice, "gauss_residual", " - self.Q[y, x]) % self.N", ") % self.N",
+     lambda mp: TM.test_physical_basis_equals_brute_force(3, 2, 3, False, [[1, 0, 0], [0, 0, 2]])),
     ("plaquette-orientation", L.Lattice, "plaquette", "c[self.hi(x, y + 1)] - t", "c[self.hi(x, y + 1)] + t",
      lambda mp: TM.test_moves_preserve_gauss_law(3)),
     ("hop-lowers-instead-of-raising", L.Lattice, "hop", "c[li] = (c[li] + 1) % self.N",
@@ -52,7 +54,7 @@ CASES = [
     ("block-selection-leg-signs", P, "block_id", "tot = p + sum(", "tot = p - sum(",
      lambda mp: TP.test_gi_peps_vanishes_off_gauss_and_matches_sampled_network(3, 1, True, 2, 2)),
     ("leg-values-up-down-swapped", L.Lattice, "leg_values", "return nl, nr, nd, nu", "return nl, nr, nu, nd",
-     lambda mp: TM.test_physical_basis_equals_brute_force(3, 2, 3, False)),
+     lambda mp: TM.test_physical_basis_equals_brute_force(3, 2, 3, False, None)),
     # counter-based generator
     ("splitmix-shift", rng, "mix64", "z ^ (z >> 30)", "z ^ (z >> 31)", lambda mp: TM.test_splitmix64_reference_vector()),
     # boundary MPS (Sec. S-2)
