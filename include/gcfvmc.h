@@ -32,6 +32,14 @@
  * - Every entry point returns a gcf_status and never aborts; on failure the
  *   reason is available from gcf_last_error().  Calls on one context are not
  *   thread-safe.
+ * - A batch of zero configurations or chains is valid wherever a count may
+ *   be 0 (gcf_init_configs, gcf_amplitude, gcf_amplitude_noalloc,
+ *   gcf_local_energy, gcf_log_grad, gcf_log_grad_vjp, gcf_sample_batch,
+ *   gcf_sample_batch_async, contexts of gcf_sample_multi): the call returns
+ *   GCF_OK without launching a kernel, its configuration and per-sample
+ *   pointers may be NULL, and it writes nothing (gcf_log_grad_vjp writes a
+ *   zero gradient to grad, which must be valid).  An SR step
+ *   (gcf_sr_step, gcf_vmc_step_host) needs at least one sample.
  */
 #ifndef GCFVMC_H
 #define GCFVMC_H
