@@ -18,7 +18,6 @@ the slowest rank's time sets the whole-job rate.
 from __future__ import annotations
 
 import argparse
-import glob
 import hashlib
 import json
 import os
@@ -56,30 +55,39 @@ def load_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
+# the files the FP32 sampling kernel is compiled from (its translation unit and
+# every header it includes)
+KERNEL_SOURCES = ("vmc_f32.cu", "launch.h", "common.cuh", "envsteps.cuh", "linalg.cuh", "mma.cuh",
+                  "peps_dev.cuh", "vmc_kernel.cuh")
+
+
 def source_hash():
-    """sha256 (first 16 hex) of the CUDA sources, in sorted order: *.cu, *.cuh, *.h."""
+    """sha256 (first 16 hex) of the sampling kernel's sources, in sorted order."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2503_20566_gb300", "csrc")
-    for pat in ("*.cu", "*.cuh", "*.h"):
-        for f in sorted(glob.glob(os.path.join(d, pat))):
-            with open(f, "rb") as fh:
-                h.update(fh.read())
+    for name in sorted(KERNEL_SOURCES):
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 PROFILE = os.path.join(ROOT, "profiles", "vmc_kernel_grouped4_f32_z2_8x8_D4_chi16.md")
 
 
-def profiled_traffic(samples_per_launch):
+def profiled_traffic(samples_per_launch, kernel, smem_level):
     """DRAM bytes per launch scaled from the committed ncu capture, or None if
-    the kernel sources changed since the counters were taken."""
+    the kernel's sources changed since the counters were taken or the launch
+    runs another kernel form (kernel and shared-memory level)."""
     try:
         txt = open(PROFILE).read()
     except OSError:
         return None
     m1 = re.search(r"source_sha256: ([0-9a-f]+)", txt)
     m2 = re.search(r"traffic_bytes_per_sample: ([0-9.eE+]+)", txt)
-    if not (m1 and m2) or m1.group(1) != source_hash():
+    m3 = re.search(r"kernel_form: (\S+) level (\d+)", txt)
+    if not (m1 and m2 and m3) or m1.group(1) != source_hash():
+        return None
+    if m3.group(1) != kernel or int(m3.group(2)) != smem_level:
         return None
     return float(m2.group(1)) * samples_per_launch
 
@@ -345,7 +353,7 @@ def main():
             "kernel_ms": float(np.mean(t_kernel)),
             "sr_ms": float(np.mean([a - b for a, b in zip(t_steps, t_kernel)])),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(samples_per_step),
+                         "frac": achieved / peak, "traffic": profiled_traffic(samples_per_step, kernel_name, ctx.smem_level),
                          "kernel": kernel_name,
                          "algorithmic_flop_per_launch": fl,
                          "peak_source": "FP32 FMA units x max SM clock (152 x 128 x 2 x 2070 MHz)",

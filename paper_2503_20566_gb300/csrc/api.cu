@@ -707,7 +707,10 @@ gcf_status ensure_sr(gcf_ctx* c, long long Ns, int n_chains) {
     cdouble** vecs[7] = {&c->sr.obar, &c->sr.F, &c->sr.x, &c->sr.r, &c->sr.p, &c->sr.Ap, &c->sr.z};
     for (auto v : vecs)
       if (cudaMalloc(v, sizeof(cdouble) * Np) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR vectors");
-    if (cudaMalloc(&c->sr.dinv, sizeof(double) * Np) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR vectors");
+    if (cudaMalloc(&c->sr.dinv, sizeof(double) * Np) != cudaSuccess ||
+        cudaMalloc(&c->sr.xf, sizeof(float) * Np) != cudaSuccess ||
+        cudaMalloc(&c->sr.part, sizeof(cdouble) * kSumParts) != cudaSuccess)
+      return fail(c, GCF_ENOMEM, "SR vectors");
     if (cudaMalloc(&c->sr.tbar, sizeof(cdouble)) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR");
     if (cudaMalloc(&c->sr.scal, 32 * sizeof(double)) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR");
   }
@@ -742,11 +745,14 @@ gcf_status ensure_sr(gcf_ctx* c, long long Ns, int n_chains) {
     if (c->sr.coef) cudaFree(c->sr.coef);
     if (c->sr.perm) cudaFree(c->sr.perm);
     if (c->sr.osort) cudaFree(c->sr.osort);
+    if (c->sr.coef_f) cudaFree(c->sr.coef_f);
     c->sr.t = c->sr.coef = nullptr;
     c->sr.perm = nullptr;
     c->sr.osort = nullptr;
+    c->sr.coef_f = nullptr;
     if (cudaMalloc(&c->sr.t, sizeof(cdouble) * Ns) != cudaSuccess ||
         cudaMalloc(&c->sr.coef, sizeof(cdouble) * Ns) != cudaSuccess ||
+        cudaMalloc(&c->sr.coef_f, sizeof(float) * Ns) != cudaSuccess ||
         cudaMalloc(&c->sr.perm, sizeof(int) * Ns * c->n_s) != cudaSuccess ||
         cudaMalloc(&c->sr.osort, c->sbytes * (size_t)Ns * c->sr_sum_bs) != cudaSuccess)
       return fail(c, GCF_ENOMEM, "SR sample vectors");
@@ -849,7 +855,7 @@ void gcf_destroy(gcf_ctx* c) {
   void* ptrs[] = {c->d_params, c->d_Q, c->d_voff, c->d_vbs, c->d_vnb, c->d_tables, c->d_status,
                   c->d_scratch, c->sr.obar, c->sr.F, c->sr.x, c->sr.r, c->sr.p, c->sr.Ap, c->sr.z, c->sr.dinv,
                   c->sr.t, c->sr.coef, c->sr.chain_mean, c->sr.tbar, c->sr.scal, c->sr.perm, c->sr.seg,
-                  c->sr.pbs, c->sr.osort,
+                  c->sr.pbs, c->sr.osort, c->sr.xf, c->sr.coef_f, c->sr.part,
                   c->sr.seg_v, c->sr.seg_b, c->d_cfg, c->d_e,
                   c->d_la, c->d_ph, c->d_bid, c->d_O, c->d_acc, c->vjp_bid, c->vjp_O, c->vjp_coef,
                   c->vjp_acc, c->multi_arena, c->multi_tab};

@@ -133,6 +133,28 @@ __global__ void k_sum_c(const cdouble* v, long long n, cdouble* out, double scal
   if (threadIdx.x == 0) *out = {r * scale_, i * scale_};
 }
 
+// First stage of a deterministic sum over many blocks: block b writes the sum
+// of its grid-stride share to part[b]; k_sum_c over part[] finishes it.
+__global__ void k_sum_c_part(const cdouble* v, long long n, cdouble* part) {
+  __shared__ double red[64];
+  double r = 0.0, i = 0.0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    r += v[k].x;
+    i += v[k].y;
+  }
+  block_sum2(r, i, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = {r, i};
+}
+
+// FP32 copy of the real parts of a vector.  The FP32-storage kernels form
+// their products in FP32 from exactly these values, so reading the copy
+// instead of the FP64 vector changes no result.
+__global__ void k_real_to_f32(const cdouble* v, long long n, float* out) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) out[k] = (float)v[k].x;
+}
+
 // dot products <a, b> = sum conj(a) b (single block, grid-stride)
 __global__ void k_dot(const cdouble* a, const cdouble* b, long long n, double* out) {
   __shared__ double red[64];
@@ -309,6 +331,36 @@ __global__ void k_gather_vec(SrGeom g, const int* bids, const T* O, const cdoubl
   if (lane == 0) t[s] = {ar, CPLX ? ai : 0.0};
 }
 
+// k_gather_vec for real FP32 storage whose block sizes (hence vertex offsets)
+// are multiples of 4, with D4 = 2^d4_shift: the direction x comes as its FP32
+// copy xf and is read in 16-byte quads like O.  Same products, same order.
+__global__ void k_gather_f4(SrGeom g, const int* bids, const float* O, const float* xf, int d4_shift,
+                            cdouble* t) {
+  const int lane = threadIdx.x & 31;
+  const long long s = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (s >= g.Ns) return;
+  const int nvec = (g.n_s * g.D4) >> 2;
+  const float4* row = reinterpret_cast<const float4*>(O + s * g.n_s * (long long)g.D4);
+  const int* brow = bids + s * g.n_s;
+  double ar = 0.0;
+#pragma unroll 2
+  for (int j = lane; j < nvec; j += 32) {
+    const int el = j << 2, v = el >> d4_shift, e0 = el - (v << d4_shift);
+    const int bs = g.vbs[v];
+    if (e0 >= bs) continue;
+    const float4 o = row[j];
+    const float4 xq = *reinterpret_cast<const float4*>(xf + g.voff[v] + (long long)brow[v] * bs + e0);
+    float pr = 0.f;
+    pr += o.x * xq.x;
+    pr += o.y * xq.y;
+    pr += o.z * xq.z;
+    pr += o.w * xq.w;
+    ar += (double)pr;
+  }
+  ar = warp_sum(ar);
+  if (lane == 0) t[s] = {ar, 0.0};
+}
+
 // O in segment order: osort[Ns * pbs[v] + q * bs_v + e] = O[perm_v[q]][v][e].
 // Grid (row chunks, vertices); consecutive threads write consecutive entries.
 template <class T>
@@ -396,10 +448,12 @@ __global__ void k_scatter_sorted(SrGeom g, const int* perm, const int* seg, int 
 }
 
 // Real FP32 storage with bs a multiple of 4: each thread takes a 16-byte
-// quad (4 entries) of a row; otherwise as k_scatter_sorted.
+// quad (4 entries) of a row, and the coefficients come as the FP32 copy of
+// their real parts (the values the products use); otherwise as
+// k_scatter_sorted.
 template <bool SQ>
 __global__ void k_scatter_sorted_f4(SrGeom g, const int* perm, const int* seg, int maxnb, int split,
-                                    const float* osort, const long long* pbs, const cdouble* coef, cdouble* out,
+                                    const float* osort, const long long* pbs, const float* coef, cdouble* out,
                                     const int* seg_v, const int* seg_b) {
   __shared__ double red[256 * 4];
   const int sid = blockIdx.x / split, part = blockIdx.x - (blockIdx.x / split) * split;
@@ -421,7 +475,7 @@ __global__ void k_scatter_sorted_f4(SrGeom g, const int* perm, const int* seg, i
 #pragma unroll 2
     for (int q = s_begin + rr; q < s_end; q += rps) {
       const float4 o = *reinterpret_cast<const float4*>(rows + (long long)q * bs + 4 * qi);
-      const float c = (float)coef[pv[q]].x;
+      const float c = coef[pv[q]];
       if (SQ) {
         part4[0] += c * o.x * o.x; part4[1] += c * o.y * o.y;
         part4[2] += c * o.z * o.z; part4[3] += c * o.w * o.w;
@@ -496,13 +550,14 @@ static cudaError_t scatter(const SrGeom& g, const SrWork& w, const T* O, const c
   (void)O;
   if constexpr (std::is_same<T, float>::value) {
     if (w.all_bs4) {
+      k_real_to_f32<<<nblk(g.Ns, 256), 256, 0, st>>>(coef, g.Ns, w.coef_f);
       if (sq)
-        k_scatter_sorted_f4<true><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, os, w.pbs, coef, out,
-                                                         w.seg_v, w.seg_b);
+        k_scatter_sorted_f4<true><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, os, w.pbs, w.coef_f,
+                                                         out, w.seg_v, w.seg_b);
       else
-        k_scatter_sorted_f4<false><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, os, w.pbs, coef, out,
-                                                          w.seg_v, w.seg_b);
-      ++*launches;
+        k_scatter_sorted_f4<false><<<grid, 256, 0, st>>>(g, w.perm, w.seg, w.maxnb, split, os, w.pbs, w.coef_f,
+                                                          out, w.seg_v, w.seg_b);
+      *launches += 2;
       return cudaGetLastError();
     }
   }
@@ -539,6 +594,10 @@ cudaError_t sr_solve_update(const SrGeom& g, SrWork& w, const double* e_loc, con
   const long long Np = g.Np, Ns = g.Ns;
   // 16-byte vector reads of O need a 16-byte aligned base and whole vectors per vertex
   const bool vec_ok = (reinterpret_cast<uintptr_t>(Ov) % 16 == 0) && (g.D4 % (16 / (int)sizeof(T)) == 0);
+  // log2(D4) when D4 is a power of two (D_k = 2: 16), else -1
+  int d4_shift = -1;
+  for (int sh = 0; sh < 31; ++sh)
+    if ((1 << sh) == g.D4) d4_shift = sh;
   cudaError_t err;
 #define CK(x)                                   \
   do {                                          \
@@ -611,13 +670,25 @@ cudaError_t sr_solve_update(const SrGeom& g, SrWork& w, const double* e_loc, con
   bool converged = !(fnorm > 0.0);
   while (!converged && it < max_iter) {
     // Ap = S p + shift p
-    if (vec_ok)
-      k_gather_vec<T, Traits<T>::cplx><<<nblk(Ns * 32, 256), 256, 0, st>>>(g, bids, O, w.p, w.t);
-    else
-      k_gather2<T, Traits<T>::cplx><<<nblk(Ns * 32, 256), 256, 0, st>>>(g, bids, O, w.p, w.t);
-    ++*launches;
-    k_sum_c<<<1, 1024, 0, st>>>(w.t, Ns, w.tbar, 1.0 / (double)Ns);
-    ++*launches;
+    bool quad = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (vec_ok && w.all_bs4 && d4_shift >= 2) {
+        k_real_to_f32<<<nblk(Np, 256), 256, 0, st>>>(w.p, Np, w.xf);
+        k_gather_f4<<<nblk(Ns * 32, 256), 256, 0, st>>>(g, bids, O, w.xf, d4_shift, w.t);
+        *launches += 2;
+        quad = true;
+      }
+    }
+    if (!quad) {
+      if (vec_ok)
+        k_gather_vec<T, Traits<T>::cplx><<<nblk(Ns * 32, 256), 256, 0, st>>>(g, bids, O, w.p, w.t);
+      else
+        k_gather2<T, Traits<T>::cplx><<<nblk(Ns * 32, 256), 256, 0, st>>>(g, bids, O, w.p, w.t);
+      ++*launches;
+    }
+    k_sum_c_part<<<kSumParts, 256, 0, st>>>(w.t, Ns, w.part);
+    k_sum_c<<<1, 1024, 0, st>>>(w.part, kSumParts, w.tbar, 1.0 / (double)Ns);
+    *launches += 2;
     k_center<<<nblk(Ns, 256), 256, 0, st>>>(w.t, Ns, w.tbar);
     ++*launches;
     CK(cudaMemsetAsync(w.Ap, 0, sizeof(cdouble) * Np, st));

@@ -18,6 +18,9 @@ struct SrGeom {
   int max_nb_bs;          // max_v nb*bs
 };
 
+// blocks of the first stage of a sample sum (two per SM of a 152-SM GPU)
+constexpr int kSumParts = 304;
+
 struct SrWork {
   cdouble *obar, *F, *x, *r, *p, *Ap;  // [Np]
   cdouble* z;                          // [Np] preconditioned residual
@@ -37,6 +40,10 @@ struct SrWork {
   long long* pbs;  // [n_s] prefix sums of the block sizes
   void* osort;     // [Ns * sum_v bs_v] storage scalars
   int all_bs4;     // every block size is a multiple of 4
+  // FP32 copies for the real FP32 storage kernels
+  float* xf;       // [Np] CG direction
+  float* coef_f;   // [Ns] scatter coefficients
+  cdouble* part;   // [kSumParts] first-stage partial sums
 };
 
 // Computes <E>, F, solves (S + shift) x = F by CG, then params += (cr + i ci) x.

@@ -252,3 +252,37 @@ def test_sr_step_parity_fp64_full_rank_preconditioned():
     ref = -0.1 * x.real
     dp = p1 - p0
     assert np.linalg.norm(dp - ref) <= 1e-7 * np.linalg.norm(ref), (np.linalg.norm(dp - ref), np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("case", [(4, 3, 4, 4, 24, 1e-2), (3, 3, 4, 2, None, 10.0)], ids=["plain-cg", "jacobi"])
+def test_sr_step_parity_fp32(case):
+    """The FP32 storage path of the SR step (O in FP32, FP32 partial products,
+    FP64 sums and CG; the path the benchmark runs) against the oracle's dense
+    FP64 solve on the same rounded tensors, Eqs. S3 and S7.  The first case has
+    fewer samples than parameters (plain CG), the second twice as many
+    (Jacobi-preconditioned; the larger shift keeps its condition number where
+    CG converges).  Bound: 2e-3 relative, about a hundred times the change of
+    the dense solution under 1e-5 relative noise on O and E_loc."""
+    Lx, Ly, D, chi, n, shift = case
+    lat, pe, ctx = setup(Lx, Ly, 2, D, chi, seed=15, precision="fp32", h=1.0, g=0.3)
+    if n is None:
+        n = 2 * ctx.n_params
+    cfgs, _, _ = configs_for(lat, n, seed=25)
+    dev = torch.from_numpy(cfgs).cuda()
+    e = ctx.local_energy(dev)
+    bid, O = ctx.log_grad(dev)
+    samples = {"e_loc": torch.view_as_real(e).reshape(-1).contiguous(), "block_ids": bid, "O": O}
+    p0 = ctx.get_tensors()
+    stats = ctx.sr_step(samples, n_chains=n, diag_shift=shift, lr=0.1, max_iter=2000, tol=1e-10)
+    p1 = ctx.get_tensors()
+    assert stats[7] == (1.0 if n >= ctx.n_params else 0.0)
+    model = vmc.Model(h=1.0, g=0.3)
+    Ed = np.array([vmc.local_energy(pe, model, c, chi) for c in cfgs])
+    Od = np.array([vmc.log_grad_dense(pe, c, chi) for c in cfgs])
+    S, F, eb = vmc.sr_matrices(Od, Ed, np.full(len(cfgs), 1.0 / len(cfgs)))
+    ref = -0.1 * vmc.sr_solve(S, F, shift).real
+    assert abs(stats[0] - eb.real) < 1e-4 * max(1, abs(eb))
+    dp = p1 - p0
+    print("fp32 SR", n, "samples", ctx.n_params, "params: rel dev %.2e" % (np.linalg.norm(dp - ref) / np.linalg.norm(ref)),
+          "iters", stats[3])
+    assert np.linalg.norm(dp - ref) <= 2e-3 * np.linalg.norm(ref)
