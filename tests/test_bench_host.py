@@ -1,0 +1,44 @@
+"""Host logic of bench.py that needs no GPU.
+
+* The source hash that keys the committed ncu capture covers exactly the files
+  the FP32 sampling kernel is compiled from: its translation unit and the
+  closure of its quoted includes.
+* The DRAM traffic from the capture is reported only for the captured kernel
+  form (kernel and shared-memory level), scaled by the samples per launch.
+"""
+
+import os
+import re
+
+import pytest
+
+import bench
+
+CSRC = os.path.join(os.path.dirname(bench.__file__), "paper_2503_20566_gb300", "csrc")
+
+
+def _include_closure(name, seen=None):
+    seen = set() if seen is None else seen
+    if name in seen:
+        return seen
+    seen.add(name)
+    with open(os.path.join(CSRC, name)) as f:
+        for inc in re.findall(r'^\s*#include\s+"([^"]+)"', f.read(), flags=re.M):
+            _include_closure(inc, seen)
+    return seen
+
+
+def test_kernel_sources_are_the_include_closure_of_the_fp32_kernel():
+    assert _include_closure("vmc_f32.cu") == set(bench.KERNEL_SOURCES)
+    assert len(bench.source_hash()) == 16
+
+
+def test_traffic_only_for_the_captured_form():
+    txt = open(bench.PROFILE).read()
+    kernel, level = re.search(r"kernel_form: (\S+) level (\d+)", txt).groups()
+    per_sample = float(re.search(r"traffic_bytes_per_sample: ([0-9.eE+]+)", txt).group(1))
+    if re.search(r"source_sha256: ([0-9a-f]+)", txt).group(1) != bench.source_hash():
+        pytest.skip("kernel sources changed since the capture (traffic is then null by design)")
+    assert bench.profiled_traffic(1000, kernel, int(level)) == pytest.approx(1000 * per_sample)
+    assert bench.profiled_traffic(1000, kernel, int(level) + 1) is None
+    assert bench.profiled_traffic(1000, "gcf::vmc_kernel<float>", int(level)) is None
