@@ -701,20 +701,39 @@ gcf_status upload_params(gcf_ctx* c, const double* vals /* n_params or 2*n_param
   return GCF_OK;
 }
 
+// Each group of SR buffers is (re)allocated as a whole: a group is marked
+// ready (its last pointer set, or its capacity raised) only after every
+// allocation in it succeeded, so a call after an allocation failure retries
+// instead of running on missing buffers.
 gcf_status ensure_sr(gcf_ctx* c, long long Ns, int n_chains) {
-  if (!c->sr.obar) {
+  if (!c->sr.part) {
+    void** grp[12] = {(void**)&c->sr.obar, (void**)&c->sr.F, (void**)&c->sr.x, (void**)&c->sr.r,
+                      (void**)&c->sr.p, (void**)&c->sr.Ap, (void**)&c->sr.z, (void**)&c->sr.dinv,
+                      (void**)&c->sr.xf, (void**)&c->sr.tbar, (void**)&c->sr.scal, (void**)&c->sr.part};
+    for (auto q : grp) {
+      if (*q) cudaFree(*q);
+      *q = nullptr;
+    }
     const long long Np = c->n_params;
     cdouble** vecs[7] = {&c->sr.obar, &c->sr.F, &c->sr.x, &c->sr.r, &c->sr.p, &c->sr.Ap, &c->sr.z};
     for (auto v : vecs)
       if (cudaMalloc(v, sizeof(cdouble) * Np) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR vectors");
     if (cudaMalloc(&c->sr.dinv, sizeof(double) * Np) != cudaSuccess ||
         cudaMalloc(&c->sr.xf, sizeof(float) * Np) != cudaSuccess ||
-        cudaMalloc(&c->sr.part, sizeof(cdouble) * kSumParts) != cudaSuccess)
+        cudaMalloc(&c->sr.tbar, sizeof(cdouble)) != cudaSuccess ||
+        cudaMalloc(&c->sr.scal, 32 * sizeof(double)) != cudaSuccess)
       return fail(c, GCF_ENOMEM, "SR vectors");
-    if (cudaMalloc(&c->sr.tbar, sizeof(cdouble)) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR");
-    if (cudaMalloc(&c->sr.scal, 32 * sizeof(double)) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR");
+    if (cudaMalloc(&c->sr.part, sizeof(cdouble) * kSumParts) != cudaSuccess) {
+      c->sr.part = nullptr;
+      return fail(c, GCF_ENOMEM, "SR vectors");
+    }
   }
-  if (!c->sr.seg) {
+  if (!c->sr.pbs) {
+    void** grp[4] = {(void**)&c->sr.seg, (void**)&c->sr.seg_v, (void**)&c->sr.seg_b, (void**)&c->sr.pbs};
+    for (auto q : grp) {
+      if (*q) cudaFree(*q);
+      *q = nullptr;
+    }
     int maxnb = 1;
     for (int v = 0; v < c->n_s; ++v) maxnb = std::max(maxnb, c->vnb[v]);
     std::vector<int> sv, sb;
@@ -736,9 +755,14 @@ gcf_status ensure_sr(gcf_ctx* c, long long Ns, int n_chains) {
     c->sr.all_bs4 = 1;
     for (int v = 0; v < c->n_s; ++v)
       if (c->vbs[v] % 4) c->sr.all_bs4 = 0;
-    if (cudaMalloc(&c->sr.pbs, sizeof(long long) * c->n_s) != cudaSuccess ||
-        cudaMemcpy(c->sr.pbs, pbs.data(), sizeof(long long) * c->n_s, cudaMemcpyHostToDevice) != cudaSuccess)
+    long long* d_pbs = nullptr;
+    if (cudaMalloc(&d_pbs, sizeof(long long) * c->n_s) != cudaSuccess)
       return fail(c, GCF_ENOMEM, "SR segment tables");
+    if (cudaMemcpy(d_pbs, pbs.data(), sizeof(long long) * c->n_s, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(d_pbs);
+      return fail(c, GCF_ECUDA, "SR segment tables");
+    }
+    c->sr.pbs = d_pbs;
   }
   if (Ns > c->sr_ns_cap) {
     if (c->sr.t) cudaFree(c->sr.t);
@@ -750,6 +774,7 @@ gcf_status ensure_sr(gcf_ctx* c, long long Ns, int n_chains) {
     c->sr.perm = nullptr;
     c->sr.osort = nullptr;
     c->sr.coef_f = nullptr;
+    c->sr_ns_cap = 0;
     if (cudaMalloc(&c->sr.t, sizeof(cdouble) * Ns) != cudaSuccess ||
         cudaMalloc(&c->sr.coef, sizeof(cdouble) * Ns) != cudaSuccess ||
         cudaMalloc(&c->sr.coef_f, sizeof(float) * Ns) != cudaSuccess ||
@@ -760,6 +785,8 @@ gcf_status ensure_sr(gcf_ctx* c, long long Ns, int n_chains) {
   }
   if (n_chains > c->sr_chain_cap) {
     if (c->sr.chain_mean) cudaFree(c->sr.chain_mean);
+    c->sr.chain_mean = nullptr;
+    c->sr_chain_cap = 0;
     if (cudaMalloc(&c->sr.chain_mean, sizeof(cdouble) * n_chains) != cudaSuccess)
       return fail(c, GCF_ENOMEM, "SR chain means");
     c->sr_chain_cap = n_chains;
@@ -1210,6 +1237,8 @@ gcf_status gcf_vmc_step_host(gcf_ctx* c, int n_chains, int n_sweeps, uint64_t se
       if (p) cudaFree(p);
     c->d_cfg = nullptr; c->d_e = c->d_la = c->d_ph = nullptr; c->d_bid = c->d_acc = nullptr;
     c->d_O = nullptr;
+    c->e2e_cap = 0;
+    c->e2e_chains = 0;
     bool ok = cudaMalloc(&c->d_cfg, (size_t)n_chains * c->cfg_len) == cudaSuccess &&
               cudaMalloc(&c->d_e, sizeof(double) * 2 * ns) == cudaSuccess &&
               cudaMalloc(&c->d_la, sizeof(double) * ns) == cudaSuccess &&
