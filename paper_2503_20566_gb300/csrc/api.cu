@@ -545,6 +545,15 @@ int grid_for(gcf_ctx* c, int n_chains) {
   return (int)balanced_slots(n_chains, (long long)c->sms * std::max(1, per_sm));
 }
 
+// cudaMalloc that leaves the pointer null when it fails (retry paths free
+// whatever a group holds)
+template <class P>
+bool dalloc(P** p, size_t bytes) {
+  if (cudaMalloc((void**)p, bytes) == cudaSuccess) return true;
+  *p = nullptr;
+  return false;
+}
+
 gcf_status ensure_scratch(gcf_ctx* c, long long ctas) {
   if (ctas <= c->scratch_ctas) return GCF_OK;
   if (c->d_scratch) cudaFree(c->d_scratch);
@@ -717,16 +726,13 @@ gcf_status ensure_sr(gcf_ctx* c, long long Ns, int n_chains) {
     const long long Np = c->n_params;
     cdouble** vecs[7] = {&c->sr.obar, &c->sr.F, &c->sr.x, &c->sr.r, &c->sr.p, &c->sr.Ap, &c->sr.z};
     for (auto v : vecs)
-      if (cudaMalloc(v, sizeof(cdouble) * Np) != cudaSuccess) return fail(c, GCF_ENOMEM, "SR vectors");
-    if (cudaMalloc(&c->sr.dinv, sizeof(double) * Np) != cudaSuccess ||
-        cudaMalloc(&c->sr.xf, sizeof(float) * Np) != cudaSuccess ||
-        cudaMalloc(&c->sr.tbar, sizeof(cdouble)) != cudaSuccess ||
-        cudaMalloc(&c->sr.scal, 32 * sizeof(double)) != cudaSuccess)
+      if (!dalloc(v, sizeof(cdouble) * Np)) return fail(c, GCF_ENOMEM, "SR vectors");
+    if (!dalloc(&c->sr.dinv, sizeof(double) * Np) ||
+        !dalloc(&c->sr.xf, sizeof(float) * Np) ||
+        !dalloc(&c->sr.tbar, sizeof(cdouble)) ||
+        !dalloc(&c->sr.scal, 32 * sizeof(double)) ||
+        !dalloc(&c->sr.part, sizeof(cdouble) * kSumParts))
       return fail(c, GCF_ENOMEM, "SR vectors");
-    if (cudaMalloc(&c->sr.part, sizeof(cdouble) * kSumParts) != cudaSuccess) {
-      c->sr.part = nullptr;
-      return fail(c, GCF_ENOMEM, "SR vectors");
-    }
   }
   if (!c->sr.pbs) {
     void** grp[4] = {(void**)&c->sr.seg, (void**)&c->sr.seg_v, (void**)&c->sr.seg_b, (void**)&c->sr.pbs};
@@ -741,9 +747,9 @@ gcf_status ensure_sr(gcf_ctx* c, long long Ns, int n_chains) {
       for (int b = 0; b < c->vnb[v]; ++b) { sv.push_back(v); sb.push_back(b); }
     c->sr.maxnb = maxnb;
     c->sr.n_seg = (int)sv.size();
-    if (cudaMalloc(&c->sr.seg, sizeof(int) * ((size_t)c->n_s * (maxnb + 1) + 1)) != cudaSuccess ||
-        cudaMalloc(&c->sr.seg_v, sizeof(int) * sv.size()) != cudaSuccess ||
-        cudaMalloc(&c->sr.seg_b, sizeof(int) * sb.size()) != cudaSuccess)
+    if (!dalloc(&c->sr.seg, sizeof(int) * ((size_t)c->n_s * (maxnb + 1) + 1)) ||
+        !dalloc(&c->sr.seg_v, sizeof(int) * sv.size()) ||
+        !dalloc(&c->sr.seg_b, sizeof(int) * sb.size()))
       return fail(c, GCF_ENOMEM, "SR segment tables");
     if (cudaMemcpy(c->sr.seg_v, sv.data(), sizeof(int) * sv.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->sr.seg_b, sb.data(), sizeof(int) * sb.size(), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -756,7 +762,7 @@ gcf_status ensure_sr(gcf_ctx* c, long long Ns, int n_chains) {
     for (int v = 0; v < c->n_s; ++v)
       if (c->vbs[v] % 4) c->sr.all_bs4 = 0;
     long long* d_pbs = nullptr;
-    if (cudaMalloc(&d_pbs, sizeof(long long) * c->n_s) != cudaSuccess)
+    if (!dalloc(&d_pbs, sizeof(long long) * c->n_s))
       return fail(c, GCF_ENOMEM, "SR segment tables");
     if (cudaMemcpy(d_pbs, pbs.data(), sizeof(long long) * c->n_s, cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaFree(d_pbs);
@@ -775,11 +781,11 @@ gcf_status ensure_sr(gcf_ctx* c, long long Ns, int n_chains) {
     c->sr.osort = nullptr;
     c->sr.coef_f = nullptr;
     c->sr_ns_cap = 0;
-    if (cudaMalloc(&c->sr.t, sizeof(cdouble) * Ns) != cudaSuccess ||
-        cudaMalloc(&c->sr.coef, sizeof(cdouble) * Ns) != cudaSuccess ||
-        cudaMalloc(&c->sr.coef_f, sizeof(float) * Ns) != cudaSuccess ||
-        cudaMalloc(&c->sr.perm, sizeof(int) * Ns * c->n_s) != cudaSuccess ||
-        cudaMalloc(&c->sr.osort, c->sbytes * (size_t)Ns * c->sr_sum_bs) != cudaSuccess)
+    if (!dalloc(&c->sr.t, sizeof(cdouble) * Ns) ||
+        !dalloc(&c->sr.coef, sizeof(cdouble) * Ns) ||
+        !dalloc(&c->sr.coef_f, sizeof(float) * Ns) ||
+        !dalloc(&c->sr.perm, sizeof(int) * Ns * c->n_s) ||
+        !dalloc(&c->sr.osort, c->sbytes * (size_t)Ns * c->sr_sum_bs))
       return fail(c, GCF_ENOMEM, "SR sample vectors");
     c->sr_ns_cap = Ns;
   }
@@ -787,7 +793,7 @@ gcf_status ensure_sr(gcf_ctx* c, long long Ns, int n_chains) {
     if (c->sr.chain_mean) cudaFree(c->sr.chain_mean);
     c->sr.chain_mean = nullptr;
     c->sr_chain_cap = 0;
-    if (cudaMalloc(&c->sr.chain_mean, sizeof(cdouble) * n_chains) != cudaSuccess)
+    if (!dalloc(&c->sr.chain_mean, sizeof(cdouble) * n_chains))
       return fail(c, GCF_ENOMEM, "SR chain means");
     c->sr_chain_cap = n_chains;
   }
@@ -991,7 +997,7 @@ gcf_status gcf_log_grad_vjp(gcf_ctx* c, int n, const int8_t* configs, const doub
       return fail(c, GCF_ENOMEM, "log_grad_vjp buffers");
     c->vjp_cap = n;
   }
-  if (!c->vjp_acc && cudaMalloc(&c->vjp_acc, sizeof(cdouble) * c->n_params) != cudaSuccess)
+  if (!c->vjp_acc && !dalloc(&c->vjp_acc, sizeof(cdouble) * c->n_params))
     return fail(c, GCF_ENOMEM, "log_grad_vjp buffers");
   gcf_samples out{};
   out.block_ids = c->vjp_bid;
