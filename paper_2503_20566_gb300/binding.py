@@ -117,9 +117,12 @@ class Context:
         self.precision = precision
         self.n_s = Lx * Ly
         self.n_plaq = (Lx - 1) * (Ly - 1)
+        self.h, self.g, self.J, self.m = float(h), float(g), float(J), float(m)
+        self.Q = None
         q = None
         if Q is not None:
             self._Q = np.ascontiguousarray(np.asarray(Q, dtype=np.int32).reshape(-1))
+            self.Q = self._Q.copy()
             q = self._Q.ctypes.data_as(C.POINTER(C.c_int32))
         mdl = _Model(N, Lx, Ly, D, chi, int(matter), q, h, g, J, m, COMPLEX if complex_ else REAL,
                      PRECISIONS[precision])
