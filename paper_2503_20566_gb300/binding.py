@@ -101,6 +101,48 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _need(cond, msg):
+    if not cond:
+        raise ValueError(msg)
+
+
+def _check_device_buffers(bufs):
+    """Buffers the library reads or writes through raw device pointers, as
+    (tensor, dtype, min_numel, name): each must be a contiguous torch tensor of
+    `dtype` with at least `min_numel` entries, on the GPU.  The C ABI cannot
+    see a buffer's size or placement, so these are checked here, before any
+    pointer is passed: first every shape and dtype, then the placement."""
+    for t, dtype, min_numel, what in bufs:
+        _need(hasattr(t, "data_ptr") and hasattr(t, "is_cuda"), f"{what} must be a torch tensor")
+        _need(t.dtype == dtype, f"{what} must be {dtype}, got {t.dtype}")
+        _need(t.numel() >= min_numel, f"{what} holds {t.numel()} entries, the call uses {min_numel}")
+        _need(t.is_contiguous(), f"{what} must be contiguous")
+    for t, _, _, what in bufs:
+        _need(t.is_cuda, f"{what} must be on the GPU")
+
+
+def _check_configs(t, cfg_len, what):
+    """In/out configurations: an int8 (n_chains, cfg_len) contiguous CUDA tensor."""
+    import torch
+
+    _need(hasattr(t, "dim") and t.dim() == 2 and t.shape[1] == cfg_len,
+          f"{what}: configs must be (n_chains, {cfg_len}), got {tuple(getattr(t, 'shape', ()))}")
+    _check_device_buffers([(t, torch.int8, t.shape[0] * cfg_len, f"{what}: configs")])
+
+
+def _check_samples(out, n_chains, n_sweeps, n_s, D4, o_dtype, what):
+    """Output buffers of a sampling call: every buffer present holds at least
+    the entries the call writes, in the documented dtype."""
+    import torch
+
+    ns = n_chains * max(0, n_sweeps)
+    need = {"log_abs": (torch.float64, ns), "phase": (torch.float64, ns), "e_loc": (torch.float64, 2 * ns),
+            "block_ids": (torch.int32, ns * n_s), "O": (o_dtype, ns * n_s * D4),
+            "accepted": (torch.int32, n_chains), "proposed": (torch.int32, n_chains)}
+    _check_device_buffers([(out[key], dt, cnt, f"{what}: out[{key!r}]") for key, (dt, cnt) in need.items()
+                           if out.get(key) is not None])
+
+
 class Context:
     """One GCF-PEPS ansatz on one lattice (a ``gcf_ctx``)."""
 
@@ -206,8 +248,14 @@ class Context:
     def init_configs(self, n_chains, occupations=None, powers=None):
         torch = self._torch
         dev = torch.device("cuda")
-        occ = None if occupations is None else torch.as_tensor(occupations, dtype=torch.int8).to(dev).contiguous()
-        pw = None if powers is None else torch.as_tensor(powers, dtype=torch.int8).to(dev).contiguous()
+        occ = None if occupations is None else torch.as_tensor(occupations, dtype=torch.int8)
+        pw = None if powers is None else torch.as_tensor(powers, dtype=torch.int8)
+        _need(occ is None or occ.numel() == n_chains * self.n_s,
+              f"init_configs: occupations must hold n_chains x {self.n_s} values")
+        _need(pw is None or pw.numel() == n_chains * self.n_plaq,
+              f"init_configs: powers must hold n_chains x {self.n_plaq} values")
+        occ = None if occ is None else occ.to(dev).contiguous()
+        pw = None if pw is None else pw.to(dev).contiguous()
         cfg = torch.empty((n_chains, self.cfg_len), dtype=torch.int8, device=dev)
         self._check(self.lib.gcf_init_configs(self.ctx, n_chains, _ptr(occ), _ptr(pw), _ptr(cfg)), "init_configs")
         return cfg
@@ -217,6 +265,8 @@ class Context:
         c = torch.as_tensor(configs, dtype=torch.int8)
         if c.dim() == 1:
             c = c.unsqueeze(0)
+        _need(c.dim() == 2 and c.shape[1] == self.cfg_len,
+              f"configs must be (n, {self.cfg_len}), got {tuple(c.shape)}")
         return c.to("cuda").contiguous()
 
     # ---- fixed-configuration evaluations ---------------------------------------
@@ -282,9 +332,11 @@ class Context:
 
     def sample_batch(self, configs, n_sweeps, seed, out=None, grad=True):
         """configs: device int8 tensor (n_chains, cfg_len), updated in place."""
+        _check_configs(configs, self.cfg_len, "sample_batch")
         n = configs.shape[0]
         if out is None:
             out = self.alloc_samples(n, n_sweeps, grad)
+        _check_samples(out, n, n_sweeps, self.n_s, self.Dk ** 4, self.o_dtype, "sample_batch")
         s = _Samples(*[C.c_void_p(out[k].data_ptr()) if k in out else None
                        for k in ("log_abs", "phase", "e_loc", "block_ids", "O", "accepted", "proposed")])
         self._check(self.lib.gcf_sample_batch(self.ctx, n, n_sweeps, C.c_uint64(seed), _ptr(configs),
@@ -296,7 +348,9 @@ class Context:
         context's) without synchronising or allocating: the launch can be
         recorded in a CUDA graph.  Call sample_batch with at least as many
         chains once before (it sizes the scratch)."""
+        _check_configs(configs, self.cfg_len, "sample_batch_async")
         n = configs.shape[0]
+        _check_samples(out, n, n_sweeps, self.n_s, self.Dk ** 4, self.o_dtype, "sample_batch_async")
         h = None if stream is None else C.c_void_p(stream.cuda_stream)
         s = _samples_struct(out)
         self._check(self.lib.gcf_sample_batch_async(self.ctx, n, n_sweeps, C.c_uint64(seed), _ptr(configs),
@@ -305,7 +359,11 @@ class Context:
 
     def sr_step(self, samples, n_chains, diag_shift=1e-4, lr=0.01, mode=SR, dt=0.0, max_iter=100,
                 tol=1e-10):
+        torch = self._torch
         ns = samples["e_loc"].shape[0] // 2
+        _check_device_buffers([(samples["e_loc"], torch.float64, 2 * ns, "sr_step: samples['e_loc']"),
+                               (samples["block_ids"], torch.int32, ns * self.n_s, "sr_step: samples['block_ids']"),
+                               (samples["O"], self.o_dtype, ns * self.n_s * self.Dk ** 4, "sr_step: samples['O']")])
         stats = (C.c_double * 8)()
         st = self.lib.gcf_sr_step(self.ctx, ns, n_chains, _ptr(samples["e_loc"]), _ptr(samples["block_ids"]),
                                   _ptr(samples["O"]), diag_shift, lr, mode, dt, max_iter, tol, stats)
@@ -315,7 +373,11 @@ class Context:
     def vmc_step_host(self, host_configs, n_sweeps, seed, diag_shift=1e-4, lr=0.01, mode=SR, dt=0.0,
                       max_iter=100, tol=1e-10):
         """One VMC iteration from host memory (configs: numpy int8, in/out)."""
-        assert host_configs.dtype == np.int8 and host_configs.flags["C_CONTIGUOUS"]
+        _need(isinstance(host_configs, np.ndarray) and host_configs.dtype == np.int8 and
+              host_configs.flags["C_CONTIGUOUS"] and host_configs.flags["WRITEABLE"],
+              "vmc_step_host: configs must be a writeable, contiguous numpy int8 array")
+        _need(host_configs.ndim == 2 and host_configs.shape[1] == self.cfg_len,
+              f"vmc_step_host: configs must be (n_chains, {self.cfg_len}), got {host_configs.shape}")
         n = host_configs.shape[0]
         stats = (C.c_double * 8)()
         st = self.lib.gcf_vmc_step_host(self.ctx, n, n_sweeps, C.c_uint64(seed),
@@ -338,8 +400,13 @@ def sample_multi(contexts, configs, n_sweeps, seeds, outs=None, grad=True):
     n = len(contexts)
     if not (len(configs) == len(seeds) == n) or n == 0:
         raise ValueError("one configs tensor and one seed per context")
+    for i, (ctx, c) in enumerate(zip(contexts, configs)):
+        _check_configs(c, ctx.cfg_len, f"sample_multi[{i}]")
     if outs is None:
         outs = [ctx.alloc_samples(c.shape[0], n_sweeps, grad) for ctx, c in zip(contexts, configs)]
+    _need(len(outs) == n, "one output dict per context")
+    for i, (ctx, c, o) in enumerate(zip(contexts, configs, outs)):
+        _check_samples(o, c.shape[0], n_sweeps, ctx.n_s, ctx.Dk ** 4, ctx.o_dtype, f"sample_multi[{i}]")
     lib = contexts[0].lib
     ctxs = (C.c_void_p * n)(*[ctx.ctx for ctx in contexts])
     nch = (C.c_int * n)(*[int(c.shape[0]) for c in configs])
