@@ -150,6 +150,7 @@ class Context:
                  complex_=False, precision="fp32", seed=0, stream=None):
         import torch
 
+        _need(Q is None or np.asarray(Q).size == Lx * Ly, f"Q must hold Lx x Ly = {Lx * Ly} background charges")
         self._torch = torch
         self.lib = load_library()
         self.N, self.Lx, self.Ly, self.D, self.chi = N, Lx, Ly, D, chi

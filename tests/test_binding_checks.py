@@ -76,3 +76,8 @@ def test_host_and_fixed_configuration_calls_refuse_bad_shapes():
         ctx.init_configs(4, powers=torch.zeros((4, 5), dtype=torch.int8))
     with pytest.raises(ValueError, match="occupations"):
         ctx.init_configs(4, occupations=torch.zeros((4, 11), dtype=torch.int8))
+
+
+def test_background_charges_must_cover_the_lattice():
+    with pytest.raises(ValueError, match="12 background charges"):
+        B.Context(2, 4, 3, 4, 4, Q=[1, 0, 0, 1])
