@@ -132,6 +132,32 @@ def cpu_oracle_rate(n_procs, chains_per_proc=1, sweeps=1):
 
 
 # ---------------------------------------------------------------------------
+def err_vs_fp64(ctx, configs, w, n_check=64):
+    """Error of the benchmarked precision against the library's FP64 form on
+    the same tensors (the FP64 form matches the FP64 oracle to ~1e-10 in the
+    parity tests), on the first n_check final configurations: amplitude error
+    |exp(d log|psi| + i d phase) - 1| and E_loc error |dE| / max(1, |E|)."""
+    import torch
+
+    import paper_2503_20566_gb300 as G
+
+    sub = configs[:n_check].contiguous()
+    ref = G.Context(w["N"], w["Lx"], w["Ly"], w["D"], w["chi"], h=w["h_p"], g=w["g"], precision="fp64", seed=0)
+    try:
+        ref.set_tensors(ctx.get_tensors())
+        la, ph = ctx.amplitude(sub)
+        la64, ph64 = ref.amplitude(sub)
+        e, e64 = ctx.local_energy(sub), ref.local_energy(sub)
+    finally:
+        ref.close()
+    amp = (torch.exp(torch.complex(la - la64, ph - ph64)) - 1).abs().cpu().numpy()
+    ee = ((e - e64).abs() / torch.clamp(e64.abs(), min=1.0)).cpu().numpy()
+    return {"configs": int(sub.shape[0]), "reference": "FP64 form of the library on the same tensors",
+            "amp_max": float(amp.max()), "amp_median": float(np.median(amp)),
+            "eloc_max": float(ee.max()), "eloc_median": float(np.median(ee))}
+
+
+# ---------------------------------------------------------------------------
 def clocks_sampler_start(path):
     q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -333,6 +359,10 @@ def main():
                "h2d_bytes_per_step": cfg_bytes, "d2h_bytes_per_step": cfg_bytes + 8 * 8}
 
     if rank == 0:
+        try:
+            err = err_vs_fp64(ctx, configs, w)
+        except Exception as exc:  # the JSON line is printed whatever happens here
+            err = {"error": f"{type(exc).__name__}: {exc}"[:300]}
         peaks, src = load_peaks()
         kern_s = float(np.mean(t_kernel)) / 1000.0
         fl = flops_per_sample(w["Lx"], w["Ly"], w["D"] // w["N"], w["chi"]) * samples_per_step
@@ -360,6 +390,7 @@ def main():
                          "tensor_peak_tf32_of_" + src: peaks.get("bf16_tflops", 0) / 2.0},
             "clocks": clocks,
             "sr_stats": {"e_mean": stats[0], "e_err": stats[2], "cg_iters": stats[3], "residual": stats[4]},
+            "err_vs_fp64": err,
         }
         if e2e:
             line["e2e"] = e2e
