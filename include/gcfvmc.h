@@ -205,6 +205,8 @@ gcf_status gcf_log_grad_vjp(gcf_ctx* ctx, int n, const int8_t* configs, const do
  * j = y*(Lx-1)+x; with matter, slot 2*Np + j for horizontal link j and
  * 2*Np + n_h + j for vertical link j; n_slots = 2*Np (+ n_h + n_v).
  * configs: device n_chains*cfg_len, in/out (must be physical).
+ * Deterministic: the same tensors, configurations, seed and kernel form give
+ * bit-identical configurations and outputs.
  * GCF_EGAUSS if a starting configuration is unphysical. */
 gcf_status gcf_sample_batch(gcf_ctx* ctx, int n_chains, int n_sweeps, uint64_t seed,
                             int8_t* configs, const gcf_samples* out);
@@ -235,7 +237,9 @@ gcf_status gcf_sample_batch_async(gcf_ctx* ctx, int n_chains, int n_sweeps, uint
  * |F|, 1 if CG reached tol, 1 if the diagonal preconditioner was used};
  * n_chains is the number of chains the samples came from
  * (chain-major order).  GCF_ETIMEOUT if CG hits max_iter before tol (the
- * update is still applied). */
+ * update is still applied).  Sums over samples and dot products combine
+ * per-block partial sums with FP64 atomics, so repeated calls on the same
+ * samples agree to rounding, not bit for bit. */
 gcf_status gcf_sr_step(gcf_ctx* ctx, int n_samples, int n_chains, const double* e_loc,
                        const int32_t* block_ids, const void* O, double diag_shift, double lr,
                        int mode, double dt, int max_iter, double tol, double* stats);
