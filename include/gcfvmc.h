@@ -5,7 +5,8 @@
  * network simulations for Abelian lattice gauge theory in (2+1)D".
  *
  * Library: libgcfvmc.so (hand-written CUDA for sm_103a).  No torch types
- * appear here; the Python binding passes raw pointers.
+ * appear here; the Python binding passes raw pointers, after checking each
+ * buffer's shape, dtype, size and placement (the library cannot).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
