@@ -34,6 +34,9 @@ left-canonicalised by QR (left to right), then swept right to left with an SVD
 on every bond keeping the chi largest singular values, and normalised with the
 norm accumulated in a log-scale.  Top environments are built the same way
 from the top row downward.
+`compress_variational` gives the other option the paper names: the
+bond-chi MPS closest to the input, fitted by one-site alternating least
+squares from the SVD truncation.
 """
 
 from __future__ import annotations
@@ -294,6 +297,77 @@ def compress(mps, chi):
         return mps, -np.inf
     mps[0] = mps[0] / nrm
     return mps, float(np.log(nrm))
+
+
+def compress_variational(mps, chi, sweeps=4, history=None):
+    """Variational compression (Sec. S-2, the alternative to SVD truncation):
+    the MPS phi of bond dimension <= chi that minimises ||psi - phi||, by
+    alternating least squares on one site at a time.
+
+    phi starts as the SVD truncation (`compress`), which is right-canonical
+    with its centre at site 0.  With every other site of phi orthonormal
+    towards the centre i, the best site tensor is the projection of psi,
+    B_i[b, d, b'] = sum L_i[b, a] A_i[a, d, a'] R_{i+1}[b', a'], where L and R
+    are the overlaps <phi|psi> of the sites left and right of i.  A sweep
+    updates left to right (QR moves the centre right) and back (LQ moves it
+    left).  Then ||psi - phi||^2 = ||psi||^2 - ||B_centre||^2, which never
+    grows from one update to the next; `history`, if a list, receives it
+    after the initial truncation and after every sweep.  Returns
+    (mps, log_norm) as `compress` does.
+    """
+    A = [np.asarray(m) for m in mps]
+    L = len(A)
+    B, _ = compress(A, chi)
+    B = [b.astype(np.result_type(b, *A)) for b in B]
+    psi2 = None
+    if history is not None:
+        # ||psi||^2 by the exact overlap <psi|psi>
+        E = np.ones((1, 1))
+        for a in A:
+            E = np.einsum("xy,xdb,yde->be", E, a.conj(), a)
+        psi2 = float(np.real(E.reshape(-1)[0]))
+
+    def right_env(i, env_next):
+        # R_i[b, a] = sum conj(B_i[b, d, b']) A_i[a, d, a'] R_{i+1}[b', a']
+        return np.einsum("bdc,ade,ce->ba", B[i].conj(), A[i], env_next)
+
+    def left_env(i, env_prev):
+        # L_{i+1}[b', a'] = sum L_i[b, a] conj(B_i[b, d, b']) A_i[a, d, a']
+        return np.einsum("ba,bdc,ade->ce", env_prev, B[i].conj(), A[i])
+
+    def optimal(i, Lenv, Renv):
+        return np.einsum("ba,ade,ce->bdc", Lenv, A[i], Renv)
+
+    R = [None] * (L + 1)
+    R[L] = np.ones((1, 1))
+    for i in range(L - 1, 0, -1):
+        R[i] = right_env(i, R[i + 1])
+    if history is not None:
+        c = optimal(0, np.ones((1, 1)), R[1])
+        history.append(max(psi2 - float(np.sum(np.abs(c) ** 2)), 0.0))
+    Lenv = [None] * (L + 1)
+    Lenv[0] = np.ones((1, 1))
+    for _ in range(sweeps):
+        for i in range(L - 1):                      # left to right
+            X = optimal(i, Lenv[i], R[i + 1])
+            b, d, c = X.shape
+            Q, _r = np.linalg.qr(X.reshape(b * d, c))
+            B[i] = Q.reshape(b, d, Q.shape[1])
+            Lenv[i + 1] = left_env(i, Lenv[i])
+        for i in range(L - 1, 0, -1):               # right to left
+            X = optimal(i, Lenv[i], R[i + 1])
+            b, d, c = X.shape
+            Q, _r = np.linalg.qr(X.reshape(b, d * c).T)   # X^T = Q r, so X = r^T Q^T (LQ)
+            B[i] = Q.T.reshape(Q.shape[1], d, c)
+            R[i] = right_env(i, R[i + 1])
+        B[0] = optimal(0, Lenv[0], R[1])
+        if history is not None:
+            history.append(max(psi2 - float(np.sum(np.abs(B[0]) ** 2)), 0.0))
+    nrm = np.linalg.norm(B[0])
+    if nrm == 0.0:
+        return B, -np.inf
+    B[0] = B[0] / nrm
+    return B, float(np.log(nrm))
 
 
 def bottom_envs(rows, chi):

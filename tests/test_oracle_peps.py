@@ -217,3 +217,56 @@ def test_compress_without_truncation_preserves_state():
     out, ls = P.compress(mps, chi=1000)
     assert np.allclose(dense(out) * np.exp(ls), dense(mps), atol=1e-10)
     assert abs(np.linalg.norm(dense(out)) - 1.0) < 1e-12
+
+
+def _random_mps(seed, L, d, D, cplx=False):
+    g = np.random.default_rng(seed)
+    dims = [1] + [D] * (L - 1) + [1]
+    out = []
+    for i in range(L):
+        t = g.standard_normal((dims[i], d, dims[i + 1]))
+        out.append(t + 1j * g.standard_normal(t.shape) if cplx else t)
+    return out
+
+
+def _dense(mps, log_norm=0.0):
+    v = np.ones((1, 1))
+    for s in mps:
+        v = np.einsum("xa,adb->xdb", v, s).reshape(-1, s.shape[2])
+    return v.reshape(-1) * np.exp(log_norm)
+
+
+def test_variational_compression_of_one_bond_is_the_eckart_young_optimum():
+    """Two sites: the best rank-chi approximation is the SVD truncation, and
+    its error is the root of the discarded squared singular values."""
+    for chi, cplx in [(1, False), (2, True), (3, False)]:
+        A = _random_mps(3, 2, 4, 5, cplx)
+        v = _dense(A)
+        out, ls = P.compress_variational(A, chi, sweeps=3)
+        s = np.linalg.svd(v.reshape(4, 4), compute_uv=False)
+        err = np.linalg.norm(v - _dense(out, ls))
+        assert abs(err - np.sqrt(np.sum(s[chi:] ** 2))) <= 1e-10 * np.linalg.norm(v)
+
+
+def test_variational_compression_is_exact_without_truncation():
+    A = _random_mps(4, 6, 2, 8, True)
+    v = _dense(A)
+    out, ls = P.compress_variational(A, chi=16, sweeps=2)
+    assert np.linalg.norm(v - _dense(out, ls)) <= 1e-10 * np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("L,d,D,chi,cplx", [(6, 2, 8, 3, True), (5, 3, 9, 4, False), (7, 2, 6, 2, False)])
+def test_variational_compression_improves_on_svd_and_never_gets_worse(L, d, D, chi, cplx):
+    """With several truncated bonds the SVD sweep is not the optimum: the fit
+    must end below it, and no sweep may raise the error."""
+    A = _random_mps(10 + L, L, d, D, cplx)
+    v = _dense(A)
+    s, ls = P.compress(A, chi)
+    e_svd = np.linalg.norm(v - _dense(s, ls))
+    hist = []
+    out, lv = P.compress_variational(A, chi, sweeps=5, history=hist)
+    e_var = np.linalg.norm(v - _dense(out, lv))
+    assert e_var < e_svd * (1 - 1e-4)
+    assert abs(hist[-1] - e_var ** 2) <= 1e-8 * np.linalg.norm(v) ** 2
+    assert all(b <= a + 1e-9 * hist[0] for a, b in zip(hist, hist[1:]))
+    assert max(m.shape[2] for m in out[:-1]) <= chi

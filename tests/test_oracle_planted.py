@@ -71,6 +71,12 @@ CASES = [
      lambda mp: TP.test_boundary_mps_exact_when_chi_reaches_bound(6, 5, 2, 2, False)),
     ("amplitude-drops-environment-scale", vmc, "amplitude", "return s + float(np.log(abs(val)))",
      "return float(np.log(abs(val)))", lambda mp: TP.test_boundary_mps_exact_when_chi_reaches_bound(6, 5, 2, 2, False)),
+    ("variational-right-env-without-conjugate", P, "compress_variational",
+     'np.einsum("bdc,ade,ce->ba", B[i].conj(), A[i], env_next)', 'np.einsum("bdc,ade,ce->ba", B[i], A[i], env_next)',
+     lambda mp: TP.test_variational_compression_improves_on_svd_and_never_gets_worse(6, 2, 8, 3, True)),
+    ("variational-lq-factor-untransposed", P, "compress_variational",
+     "B[i] = Q.T.reshape(Q.shape[1], d, c)", "B[i] = Q.reshape(Q.shape[1], d, c)",
+     lambda mp: TP.test_variational_compression_is_exact_without_truncation()),
     # E_loc, Eq. (S2)
     ("eloc-z2-factor", vmc, "local_energy", "amp = -2.0 * model.h if", "amp = -1.0 * model.h if",
      lambda mp: TV.test_local_energy_equals_H_psi_over_psi(4, 4, 2, 2, False, 24)),
