@@ -152,6 +152,38 @@ def log_grad_dense(peps: P.GIPEPS, cfg, chi):
     return vec if np.iscomplexobj(peps.params) else vec.real
 
 
+def log_grad_through_truncation(peps: P.GIPEPS, cfg, chi, eps=1e-6):
+    """d ln psi_chi(s) / d theta for the selected blocks, where psi_chi is the
+    boundary-MPS amplitude with its chi truncations: the environments move
+    with the parameters too (the adjoint *through* the truncation).  The
+    definition written out: central differences of ln psi_chi in every
+    selected parameter (real and imaginary parts for complex tensors),
+    ln psi = log|psi| + i arg psi.  Dense over all parameters, zeros
+    elsewhere.  Slow: two amplitudes per parameter; small lattices only."""
+    base = log_grad_dense(peps, cfg, chi)
+    sel = np.nonzero(base)[0]
+    cplx = np.iscomplexobj(peps.params)
+    out = np.zeros(peps.n_params, dtype=np.complex128)
+
+    def lnpsi(params):
+        la, ph = amplitude(P.GIPEPS(peps.lat, peps.Dk, params), cfg, chi)
+        return la + 1j * ph
+
+    for k in sel:
+        d = []
+        for step in ((eps, 1j * eps) if cplx else (eps,)):
+            pp, pm = peps.params.copy(), peps.params.copy()
+            pp[k] += step
+            pm[k] -= step
+            diff = lnpsi(pp) - lnpsi(pm)
+            diff = diff.real + 1j * np.angle(np.exp(1j * diff.imag))  # phase difference modulo 2 pi
+            d.append(diff / (2 * eps))
+        # holomorphic derivative: d/dtheta = (d/dRe) for a real step; for complex
+        # tensors the imaginary step gives i d/dtheta, so average the two
+        out[k] = d[0] if not cplx else 0.5 * (d[0] - 1j * d[1])
+    return out if cplx else out.real
+
+
 # ---------------------------------------------------------------------------
 # Sequential Metropolis sweep (Sec. S-1 acceptance rule, Sec. S-2 moves/order)
 # ---------------------------------------------------------------------------

@@ -281,3 +281,26 @@ def test_tvmc_two_stage_follows_exact_evolution():
     f_bwd = abs(np.vdot(bwd, psi_t))
     assert f_fwd > 1 - 1e-5, f_fwd
     assert f_bwd < f_fwd - 1e-3
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_gradient_through_truncation_equals_o_at_exact_chi(complex_):
+    """With chi at the exact bound nothing is truncated: the derivative with
+    moving environments is the fixed-environment O."""
+    pe = make_peps(4, 3, 2, 2, seed=35, complex_=complex_)
+    cfg = random_physical(pe.lat, 6)
+    full = vmc.log_grad_through_truncation(pe, cfg, chi=4)
+    fixed = vmc.log_grad_dense(pe, cfg, chi=4)
+    assert np.linalg.norm(full - fixed) <= 1e-6 * np.linalg.norm(fixed)
+
+
+def test_gradient_through_truncation_differs_below_exact_chi():
+    """Below the exact bound the environments depend on the parameters through
+    the truncation, so the full derivative is not O; it is stable in the step."""
+    pe = make_peps(6, 4, 2, 2, seed=37)
+    cfg = random_physical(pe.lat, 7)
+    full = vmc.log_grad_through_truncation(pe, cfg, chi=2, eps=1e-6)
+    full2 = vmc.log_grad_through_truncation(pe, cfg, chi=2, eps=1e-5)
+    fixed = vmc.log_grad_dense(pe, cfg, chi=2)
+    assert np.linalg.norm(full - full2) <= 1e-5 * np.linalg.norm(full)
+    assert np.linalg.norm(full - fixed) >= 1e-3 * np.linalg.norm(fixed)
