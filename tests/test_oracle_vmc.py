@@ -304,3 +304,22 @@ def test_gradient_through_truncation_differs_below_exact_chi():
     fixed = vmc.log_grad_dense(pe, cfg, chi=2)
     assert np.linalg.norm(full - full2) <= 1e-5 * np.linalg.norm(full)
     assert np.linalg.norm(full - fixed) >= 1e-3 * np.linalg.norm(fixed)
+
+
+def test_odd_z2_theory():
+    """The odd-Z2 gauge theory (Q_x = 1 on every vertex; an even number of
+    vertices on the open lattice): its physical basis is the brute-force
+    filter, and E_loc equals (H psi)(s) / psi(s) there."""
+    Lx, Ly = 4, 2
+    lat = Lattice(Lx, Ly, 2, Q=np.ones((Ly, Lx), dtype=int))
+    basis = lat.physical_basis()
+    assert set(map(tuple, basis)) == set(map(tuple, lat.brute_force_physical()))
+    assert len(basis) == 2 ** lat.n_plaquettes
+    _, n = P.layout(lat, 2)
+    pe = P.GIPEPS(lat, 2, synth.tensor_entries(47, n, False))
+    model = vmc.Model(h=1.0, g=0.6)
+    psi = exact_psi(pe, basis)
+    Hpsi = lat.hamiltonian_matrix(basis, model.h, model.g) @ psi
+    for i in range(len(basis)):
+        e = vmc.local_energy(pe, model, basis[i], chi=4)
+        assert abs(e - Hpsi[i] / psi[i]) <= 1e-9 * max(1.0, abs(Hpsi[i] / psi[i]))
