@@ -17,14 +17,17 @@ lattice  Z_N lattice gauge theory: Gauss law (Eq. 1), Hamiltonian
          diagonalisation.
 peps     Gauge-invariant PEPS (Eqs. 6-7), gauge canonical form (Eq. 9), the
          sampled single-layer network (Sec. S-2, Eq. S5), exact contraction and
-         the boundary-MPS contraction with SVD truncation to chi.
+         the boundary-MPS contraction with SVD truncation to chi; variational
+         compression (Sec. S-2) as the alternative.
 vmc      VMC estimators (Sec. S-1, Eqs. S1-S3), sequential Metropolis sweep
          (Sec. S-2), stochastic reconfiguration and the two-stage tVMC update
-         (Sec. S-3, Eqs. S6-S8).
+         (Sec. S-3, Eqs. S6-S8); the gradient of the truncated amplitude
+         through the truncation (finite differences, small lattices).
 rng      The counter-based SplitMix64 generator used for the Metropolis draws
          (the oracle's own implementation of the published definition).
 
 Parity pins: every function is pinned by tests in ``tests/test_oracle_*.py``
-against closed forms, brute force or numbers printed in the paper; functions
-without such a pin say "parity unpinned" in their docstring.
+against closed forms, brute force or numbers printed in the paper, and
+``tests/test_oracle_planted.py`` checks that planted mistakes fail them;
+functions without such a pin say "parity unpinned" in their docstring.
 """
