@@ -23,6 +23,8 @@ vmc      VMC estimators (Sec. S-1, Eqs. S1-S3), sequential Metropolis sweep
          (Sec. S-2), stochastic reconfiguration and the two-stage tVMC update
          (Sec. S-3, Eqs. S6-S8); the gradient of the truncated amplitude
          through the truncation (finite differences, small lattices).
+dynamics Exact real-time evolution exp(-iHt) on small complete bases, plaquette
+         and clock-operator matrices, the vison state (reference for tVMC).
 rng      The counter-based SplitMix64 generator used for the Metropolis draws
          (the oracle's own implementation of the published definition).
 

@@ -14,11 +14,13 @@ import textwrap
 
 import pytest
 
+from oracle import dynamics as DY
 from oracle import lattice as L
 from oracle import peps as P
 from oracle import rng
 from oracle import vmc
 
+import test_oracle_dynamics as TD
 import test_oracle_model as TM
 import test_oracle_peps as TP
 import test_oracle_vmc as TV
@@ -77,6 +79,8 @@ CASES = [
     ("variational-lq-factor-untransposed", P, "compress_variational",
      "B[i] = Q.T.reshape(Q.shape[1], d, c)", "B[i] = Q.reshape(Q.shape[1], d, c)",
      lambda mp: TP.test_variational_compression_is_exact_without_truncation()),
+    ("exact-evolution-time-reversed", DY, "evolve", "np.exp(-1j * evals * t)", "np.exp(1j * evals * t)",
+     lambda mp: TD.test_evolution_matches_the_matrix_exponential_and_conserves()),
     # E_loc, Eq. (S2)
     ("eloc-z2-factor", vmc, "local_energy", "amp = -2.0 * model.h if", "amp = -1.0 * model.h if",
      lambda mp: TV.test_local_energy_equals_H_psi_over_psi(4, 4, 2, 2, False, 24)),
