@@ -92,3 +92,17 @@ def test_tvmc_driver_follows_exact_vison_dynamics():
     assert f_fwd > 0.99999 and f_fwd > f_bwd + 0.1, (f_fwd, f_bwd)
     exact = [dyn.expectation(p, plaq).real for p in dyn.evolve(H, psi0, dt * np.arange(1, n_steps + 1))]
     assert np.allclose(seen, exact, atol=1e-3), (seen, exact)
+
+
+def test_sr_driver_lowers_the_exact_energy_towards_the_ground_state():
+    """SR steps with exact statistics: the energy falls step by step and stays
+    above the exact ground-state energy (variational bound)."""
+    lat, Dk, h, g, chi = Lattice(3, 3, 2), 2, 1.0, 0.3, 2
+    _, n = P.layout(lat, Dk)
+    ctx = ExactContext(lat, Dk, synth.tensor_entries(73, n, False), h, g, chi)
+    e0, _ = dyn.ground_state(lat.hamiltonian_matrix(ctx.basis, h, g))
+    _, recs = drivers.sr_optimize(ctx, torch.zeros((2, lat.cfg_len), dtype=torch.int8), n_steps=15, n_sweeps=1,
+                                  lr=0.05, diag_shift=1e-3)
+    energies = [r["e_mean"] for r in recs]
+    assert all(b < a for a, b in zip(energies, energies[1:])), energies
+    assert energies[-1] >= e0 - 1e-9 and energies[-1] < energies[0] - 0.1 * (energies[0] - e0)
