@@ -25,6 +25,9 @@ vmc      VMC estimators (Sec. S-1, Eqs. S1-S3), sequential Metropolis sweep
          through the truncation (finite differences, small lattices).
 dynamics Exact real-time evolution exp(-iHt) on small complete bases, plaquette
          and clock-operator matrices, the vison state (reference for tVMC).
+schwinger (1+1)D Schwinger model (End Matter): exact diagonalisation and the GCF
+         time evolution on a U(1)-symmetric MPS whose bond charges are the
+         electric fields.
 rng      The counter-based SplitMix64 generator used for the Metropolis draws
          (the oracle's own implementation of the published definition).
 

@@ -18,11 +18,13 @@ from oracle import dynamics as DY
 from oracle import lattice as L
 from oracle import peps as P
 from oracle import rng
+from oracle import schwinger as SW
 from oracle import vmc
 
 import test_oracle_dynamics as TD
 import test_oracle_model as TM
 import test_oracle_peps as TP
+import test_oracle_schwinger as TS
 import test_oracle_vmc as TV
 
 
@@ -34,6 +36,12 @@ def plant(monkeypatch, owner, name, old, new):
     ns = dict(vars(inspect.getmodule(fn)))
     exec(compile(src.replace(old, new), f"<{name} with a planted mistake>", "exec"), ns)
     monkeypatch.setattr(owner, name, ns[name])
+
+
+def _schwinger_chain():
+    L, m, J, g = 8, 0.2, 1.0, 0.5
+    H, B = SW.hamiltonian(L, m, J, g, 4)
+    return L, m, J, g, H, B, tuple(SW.charges(L))
 
 
 # (case id, owner, function, original text, planted text, pin that must fail;
@@ -81,6 +89,13 @@ CASES = [
      lambda mp: TP.test_variational_compression_is_exact_without_truncation()),
     ("exact-evolution-time-reversed", DY, "evolve", "np.exp(-1j * evals * t)", "np.exp(1j * evals * t)",
      lambda mp: TD.test_evolution_matches_the_matrix_exponential_and_conserves()),
+    # (1+1)D Schwinger model (End Matter)
+    ("schwinger-electric-term-not-squared", SW, "hamiltonian", "g * np.sum(fields(s, Q) ** 2)",
+     "g * np.sum(fields(s, Q))", lambda mp: TS.test_static_limit_is_the_brute_force_minimum()),
+    ("schwinger-step-not-halved", SW, "evolve", "half = tau / 2.0", "half = tau",
+     lambda mp: TS.test_real_time_follows_the_exact_evolution(_schwinger_chain())),
+    ("schwinger-last-mass-dropped", SW, "_bond_gate", "(mx[x + 1] * n2 if x + 1 == L - 1 else 0.0)", "0.0",
+     lambda mp: TS.test_imaginary_time_reaches_the_ground_energy(_schwinger_chain())),
     # E_loc, Eq. (S2)
     ("eloc-z2-factor", vmc, "local_energy", "amp = -2.0 * model.h if", "amp = -1.0 * model.h if",
      lambda mp: TV.test_local_energy_equals_H_psi_over_psi(4, 4, 2, 2, False, 24)),
