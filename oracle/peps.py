@@ -53,15 +53,48 @@ LEG_SIGN = (+1, -1, +1, -1)  # l, r, d, u in Eq. (1)
 @dataclass
 class VertexLayout:
     legs: tuple          # indices into (l, r, d, u) of the existing legs
-    dims: tuple          # (Dl, Dr, Dd, Du) with 1 for missing legs
+    dims: tuple          # (Dl, Dr, Dd, Du) with 1 for missing legs (uniform sectors; else None)
     n_blocks: int
-    block_size: int
+    block_size: int      # D_k^k (uniform sectors; else None)
     offset: int
+    block_offsets: tuple = ()   # start of every block in the parameter vector
+    block_dims: tuple = ()      # (Dl, Dr, Dd, Du) of every block
 
 
-def layout(lat: Lattice, Dk: int):
-    """Per-vertex block layout and the total parameter count."""
+def sector_dims(N, Dk):
+    """Degeneracy of every charge sector: D_k for all N charges (an int), or
+    one entry per charge (uneven sectors)."""
+    if np.ndim(Dk) == 0:
+        return (int(Dk),) * N
+    dq = tuple(int(d) for d in Dk)
+    if len(dq) != N or min(dq) < 1:
+        raise ValueError("one degeneracy >= 1 per charge sector")
+    return dq
+
+
+def _block_leg_charges(lat: Lattice, legs, x, y, bid):
+    """Leg charges (n_l, n_r, n_d, n_u) of block bid: the mixed-radix digits
+    of the first k-1 existing legs, the last leg's charge from Eq. (1)."""
+    N, k = lat.N, len(legs)
+    ch = [0, 0, 0, 0]
+    b = bid
+    for i in reversed(legs[:-1]):
+        ch[i] = b % N
+        b //= N
+    p = b
+    rest = (int(lat.Q[y, x]) - p - sum(LEG_SIGN[i] * ch[i] for i in legs[:-1])) % N
+    ch[legs[-1]] = (LEG_SIGN[legs[-1]] * rest) % N
+    return p, tuple(ch)
+
+
+def layout(lat: Lattice, Dk):
+    """Per-vertex block layout and the total parameter count.  Dk: the
+    degeneracy of every charge sector (an int), or one per charge; a block's
+    leg has the degeneracy of the charge it carries, so with uneven sectors
+    the blocks of a vertex differ in size."""
     P = 2 if lat.matter else 1
+    dq = sector_dims(lat.N, Dk)
+    uniform = len(set(dq)) == 1
     verts = []
     off = 0
     for y in range(lat.Ly):
@@ -69,11 +102,18 @@ def layout(lat: Lattice, Dk: int):
             has = lat.has_legs(x, y)
             legs = tuple(i for i in range(4) if has[i])
             k = len(legs)
-            dims = tuple(Dk if has[i] else 1 for i in range(4))
             nb = P * lat.N ** (k - 1)
-            bs = Dk ** k
-            verts.append(VertexLayout(legs, dims, nb, bs, off))
-            off += nb * bs
+            offs, bdims = [], []
+            start = off
+            for bid in range(nb):
+                _, ch = _block_leg_charges(lat, legs, x, y, bid)
+                d = tuple(dq[ch[i]] if has[i] else 1 for i in range(4))
+                offs.append(off)
+                bdims.append(d)
+                off += int(np.prod(d))
+            dims = tuple(dq[0] if has[i] else 1 for i in range(4)) if uniform else None
+            bs = dq[0] ** k if uniform else None
+            verts.append(VertexLayout(legs, dims, nb, bs, start, tuple(offs), tuple(bdims)))
     return verts, off
 
 
@@ -112,8 +152,8 @@ class GIPEPS:
 
     def block(self, x, y, bid):
         vl = self.vertex(x, y)
-        a = vl.offset + bid * vl.block_size
-        return self.params[a:a + vl.block_size].reshape(vl.dims)
+        a, d = vl.block_offsets[bid], vl.block_dims[bid]
+        return self.params[a:a + int(np.prod(d))].reshape(d)
 
     def selected_block(self, cfg, x, y):
         """(block id, tensor A~_x) selected by configuration cfg (Eq. S5).
@@ -145,12 +185,16 @@ class GIPEPS:
 
     # ---- dense (non-sampled) tensors for definition-level checks --------
     def dense_A(self, x, y):
-        """Full A^p_{lrdu}: shape (P, Dl', Dr', Dd', Du') with D' = N*D_k on
-        existing legs (index j has charge j // D_k) and 1 on missing legs."""
-        lat, Dk = self.lat, self.Dk
+        """Full A^p_{lrdu}: shape (P, Dl', Dr', Dd', Du') with D' = sum of the
+        sector degeneracies on existing legs (charge q occupies indices
+        start(q) .. start(q) + D_q - 1, sectors in charge order) and 1 on
+        missing legs."""
+        lat = self.lat
+        dq = sector_dims(lat.N, self.Dk)
+        start = np.concatenate([[0], np.cumsum(dq)])
         vl = self.vertex(x, y)
         P = 2 if lat.matter else 1
-        full = tuple(lat.N * Dk if i in vl.legs else 1 for i in range(4))
+        full = tuple(int(start[-1]) if i in vl.legs else 1 for i in range(4))
         A = np.zeros((P,) + full, dtype=self.params.dtype)
         ranges = [range(lat.N) if i in vl.legs else range(1) for i in range(4)]
         for p in range(P):
@@ -158,7 +202,7 @@ class GIPEPS:
                 bid = block_id(lat, vl, x, y, p, ch)
                 if bid < 0:
                     continue
-                sl = tuple(slice(ch[i] * Dk, (ch[i] + 1) * Dk) if i in vl.legs else slice(0, 1)
+                sl = tuple(slice(int(start[ch[i]]), int(start[ch[i] + 1])) if i in vl.legs else slice(0, 1)
                            for i in range(4))
                 A[(p,) + sl] = self.block(x, y, bid)
         return A
@@ -170,22 +214,27 @@ class GIPEPS:
 # ---------------------------------------------------------------------------
 
 def gcf_link_tensor(N, Dk):
-    """B^n_{lr} in gauge canonical form, Eq. (9): shape (N, N*Dk, N*Dk)."""
-    D = N * Dk
-    B = np.zeros((N, D, D))
+    """B^n_{lr} in gauge canonical form, Eq. (9): shape (N, D, D), D the sum
+    of the sector degeneracies; the identity on sector n."""
+    dq = sector_dims(N, Dk)
+    start = np.concatenate([[0], np.cumsum(dq)])
+    B = np.zeros((N, int(start[-1]), int(start[-1])))
     for n in range(N):
-        for i in range(Dk):
-            B[n, n * Dk + i, n * Dk + i] = 1.0
+        for i in range(int(start[n]), int(start[n + 1])):
+            B[n, i, i] = 1.0
     return B
 
 
 def general_link_tensor(blocks, N, Dk):
     """B^n_{lr} = calB^n_{lr} delta_{n,q(l)} delta_{n,q(r)}, Eq. (7), from
-    blocks[n] of shape (Dk, Dk)."""
-    D = N * Dk
+    blocks[n] of shape (D_n, D_n)."""
+    dq = sector_dims(N, Dk)
+    start = np.concatenate([[0], np.cumsum(dq)])
+    D = int(start[-1])
     B = np.zeros((N, D, D), dtype=np.result_type(*blocks))
     for n in range(N):
-        B[n, n * Dk:(n + 1) * Dk, n * Dk:(n + 1) * Dk] = blocks[n]
+        a, b = int(start[n]), int(start[n + 1])
+        B[n, a:b, a:b] = blocks[n]
     return B
 
 

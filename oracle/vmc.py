@@ -146,9 +146,8 @@ def log_grad_dense(peps: P.GIPEPS, cfg, chi):
     """O(s) as a dense vector over all parameters (zeros off the selected blocks)."""
     vec = np.zeros(peps.n_params, dtype=np.complex128)
     for v, (bid, blk) in enumerate(log_grad(peps, cfg, chi)):
-        vl = peps.verts[v]
-        a = vl.offset + bid * vl.block_size
-        vec[a:a + vl.block_size] = blk.reshape(-1)
+        a = peps.verts[v].block_offsets[bid]
+        vec[a:a + blk.size] = blk.reshape(-1)
     return vec if np.iscomplexobj(peps.params) else vec.real
 
 

@@ -64,7 +64,8 @@ def test_parameter_count_matches_block_counting():
 
 
 @pytest.mark.parametrize("N,Dk,matter,Lx,Ly", [(2, 2, False, 3, 3), (3, 1, False, 3, 2), (2, 1, True, 3, 2),
-                                                (3, 1, True, 2, 2)])
+                                                (3, 1, True, 2, 2), (3, (2, 1, 1), False, 3, 2),
+                                                (2, (2, 1), True, 2, 2)])
 def test_gi_peps_vanishes_off_gauss_and_matches_sampled_network(N, Dk, matter, Lx, Ly):
     # Z3 with matter fixes the sign of the matter charge against the leg sum
     # (for Z2 both signs agree, and without matter the sum's overall sign is free).
@@ -270,3 +271,72 @@ def test_variational_compression_improves_on_svd_and_never_gets_worse(L, d, D, c
     assert abs(hist[-1] - e_var ** 2) <= 1e-8 * np.linalg.norm(v) ** 2
     assert all(b <= a + 1e-9 * hist[0] for a, b in zip(hist, hist[1:]))
     assert max(m.shape[2] for m in out[:-1]) <= chi
+
+
+
+# ---- uneven charge sectors (a different degeneracy per charge) -------------
+
+def test_uneven_sector_parameter_count():
+    """Every block's size is the product of its legs' sector degeneracies:
+    count them by enumerating the Gauss-allowed charges of every vertex."""
+    lat = Lattice(3, 3, 3, matter=True)
+    dq = (2, 1, 3)
+    total = 0
+    for y in range(lat.Ly):
+        for x in range(lat.Lx):
+            has = lat.has_legs(x, y)
+            for p in (0, 1):
+                for ch in itertools.product(*[range(3) if has[i] else (0,) for i in range(4)]):
+                    tot = p + ch[0] - ch[1] + ch[2] - ch[3]
+                    if tot % 3 == 0:
+                        total += int(np.prod([dq[ch[i]] for i in range(4) if has[i]]))
+    assert P.layout(lat, dq)[1] == total
+
+
+def test_uneven_sector_gauge_transformation_leaves_amplitudes_unchanged():
+    N, dq, Lx, Ly = 3, (2, 1, 1), 3, 2
+    pe = make_peps(Lx, Ly, N, dq, seed=13)
+    lat = pe.lat
+    g = np.random.default_rng(4)
+    start = np.concatenate([[0], np.cumsum(dq)])
+    A = [[pe.dense_A(x, y) for x in range(Lx)] for y in range(Ly)]
+    A2 = [[a.copy() for a in row] for row in A]
+
+    def xblocks():
+        return [g.normal(size=(d, d)) + 2 * np.eye(d) for d in dq]
+
+    def bd(blocks):
+        X = np.zeros((start[-1], start[-1]))
+        for n, b in enumerate(blocks):
+            X[start[n]:start[n + 1], start[n]:start[n + 1]] = b
+        return X
+
+    Bh, Bv = [], []
+    for y in range(Ly):
+        row = []
+        for x in range(Lx - 1):
+            b = xblocks()
+            row.append(P.general_link_tensor(b, N, dq))
+            A2[y][x] = np.einsum("plrdu,rs->plsdu", A2[y][x], bd(b))
+        Bh.append(row)
+    for y in range(Ly - 1):
+        row = []
+        for x in range(Lx):
+            b = xblocks()
+            row.append(P.general_link_tensor(b, N, dq))
+            A2[y][x] = np.einsum("plrdu,us->plrds", A2[y][x], bd(b))
+        Bv.append(row)
+    Bg = P.gcf_link_tensor(N, dq)
+    for cfg in lat.physical_basis():
+        a = P.full_amplitude(lat, A, Bh, Bv, cfg)
+        b = P.full_amplitude(lat, A2, [[Bg] * (Lx - 1)] * Ly, [[Bg] * Lx] * (Ly - 1), cfg)
+        assert abs(a - b) <= 1e-10 * max(1.0, abs(a))
+
+
+def test_uneven_sector_boundary_mps_is_exact_at_the_bound():
+    pe = make_peps(5, 4, 3, (2, 1, 1), seed=15, complex_=True)
+    for seed in range(3):
+        cfg = random_physical(pe.lat, 20 + seed)
+        ex = P.contract_exact(pe.sampled_network(cfg))
+        la, ph = vmc.amplitude(pe, cfg, chi=4)   # max degeneracy 2, floor(5/2) = 2 cuts deep
+        assert abs(np.exp(la + 1j * ph) - ex) <= 1e-10 * abs(ex)

@@ -65,6 +65,8 @@ CASES = [
      lambda mp: TP.test_gi_peps_vanishes_off_gauss_and_matches_sampled_network(3, 1, True, 2, 2)),
     ("leg-values-up-down-swapped", L.Lattice, "leg_values", "return nl, nr, nd, nu", "return nl, nr, nu, nd",
      lambda mp: TM.test_physical_basis_equals_brute_force(3, 2, 3, False, None)),
+    ("uneven-sectors-sized-by-one-degeneracy", P, "layout", "d = tuple(dq[ch[i]] if has[i] else 1 for i in range(4))",
+     "d = tuple(dq[0] if has[i] else 1 for i in range(4))", lambda mp: TP.test_uneven_sector_parameter_count()),
     # counter-based generator
     ("splitmix-shift", rng, "mix64", "z ^ (z >> 30)", "z ^ (z >> 31)", lambda mp: TM.test_splitmix64_reference_vector()),
     # boundary MPS (Sec. S-2)

@@ -323,3 +323,30 @@ def test_odd_z2_theory():
     for i in range(len(basis)):
         e = vmc.local_energy(pe, model, basis[i], chi=4)
         assert abs(e - Hpsi[i] / psi[i]) <= 1e-9 * max(1.0, abs(Hpsi[i] / psi[i]))
+
+
+
+def test_uneven_sectors_local_energy_and_log_grad():
+    """Uneven charge sectors (degeneracies 2, 1, 1 for Z3): E_loc equals
+    (H psi)(s) / psi(s), and O equals central differences of the amplitude."""
+    pe = make_peps(3, 3, 3, (2, 1, 1), seed=17, complex_=True)
+    lat = pe.lat
+    model = vmc.Model(h=1.0, g=0.45)
+    basis = lat.physical_basis()
+    psi = exact_psi(pe, basis)
+    Hpsi = lat.hamiltonian_matrix(basis, model.h, model.g) @ psi
+    for i in range(0, len(basis), 5):
+        e = vmc.local_energy(pe, model, basis[i], chi=2)
+        assert abs(e - Hpsi[i] / psi[i]) <= 1e-9 * max(1.0, abs(Hpsi[i] / psi[i]))
+    cfg = basis[7]
+    O = vmc.log_grad_dense(pe, cfg, 2)
+    la0, ph0 = vmc.amplitude(pe, cfg, 2)
+    psi0 = np.exp(la0 + 1j * ph0)
+    for k in np.nonzero(O)[0][::3]:
+        pp, pm = pe.params.copy(), pe.params.copy()
+        pp[k] += 1e-6
+        pm[k] -= 1e-6
+        ap = vmc.amplitude(P.GIPEPS(lat, pe.Dk, pp), cfg, 2)
+        am = vmc.amplitude(P.GIPEPS(lat, pe.Dk, pm), cfg, 2)
+        d = (np.exp(ap[0] + 1j * ap[1]) - np.exp(am[0] + 1j * am[1])) / 2e-6 / psi0
+        assert abs(O[k] - d) <= 1e-6 * max(1.0, abs(d))
