@@ -6,7 +6,9 @@ Ansatz (main text, "Gauge-invariant TNS", Eqs. 6-7): every vertex carries a
 matter tensor A^p_{l r d u}; virtual index j on a leg has charge q(j) in Z_N,
 and A is non-zero only where p + q(l) + q(d) - q(r) - q(u) = Q_x (mod N).
 Gauge tensors B^n_{l r} on the links are non-zero only for n = q(l) = q(r).
-Bond dimension D = sum_k D_k; here every sector has the same degeneracy D_k.
+Bond dimension D = sum_q D_q over the charge sectors; `Dk` is either one
+degeneracy for every sector (the layout shared with the CUDA library) or one
+per charge (uneven sectors: block sizes then differ within a vertex).
 
 Gauge canonical form (Eqs. 8-9): after A -> A X, B -> X^{-1} B with
 X = (+)_k B^[k], every B becomes delta_{lr} delta_{n,q(l)} delta_{n,q(r)}; only
@@ -23,8 +25,9 @@ here).  Vertices in row-major order v = y*Lx + x.  At a vertex the existing
 legs, in the order (l, r, d, u), are legs[0..k-1].  The block index is the
 mixed-radix number (p, n_legs[0], ..., n_legs[k-2]) with p most significant
 and radix N for charges (P = 2 for matter, 1 without); the last existing leg's
-charge is fixed by Eq. (1).  A block holds D_k^k entries ordered
-[i_l][i_r][i_d][i_u] over existing legs (row-major).  Blocks of a vertex are
+charge is fixed by Eq. (1).  A block holds prod_legs D_(charge of the leg)
+entries (D_k^k for uniform sectors) ordered [i_l][i_r][i_d][i_u] over existing
+legs (row-major).  Blocks of a vertex are
 contiguous; vertices follow one another.
 
 Boundary-MPS contraction (Sec. S-2: "SVD or variational compression"; main
