@@ -28,6 +28,8 @@ dynamics Exact real-time evolution exp(-iHt) on small complete bases, plaquette
 schwinger (1+1)D Schwinger model (End Matter): exact diagonalisation and the GCF
          time evolution on a U(1)-symmetric MPS whose bond charges are the
          electric fields.
+campaign SR optimisation with exact statistics on enumerable lattices (the
+         ground-state workflow of Sec. S-3 free of sampling noise).
 rng      The counter-based SplitMix64 generator used for the Metropolis draws
          (the oracle's own implementation of the published definition).
 
