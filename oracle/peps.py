@@ -211,6 +211,27 @@ class GIPEPS:
         return A
 
 
+def link_clock_params(pe: "GIPEPS", x, y, axis, power=1):
+    """Parameters of Z^power psi for the clock operator Z |n> = omega^n |n>
+    (sigma_z for N = 2) on link (x, y, axis): in the GCF the charge on a leg
+    is the electric value of its link, so every block of vertex (x, y) is
+    multiplied by omega^(power * charge on its r leg (axis 1) or u leg
+    (axis 2)).  Real parameters stay real for N = 2."""
+    lat = pe.lat
+    leg = 1 if axis == 1 else 3
+    vl = pe.vertex(x, y)
+    if leg not in vl.legs:
+        raise ValueError("no such link")
+    real = lat.N == 2 and not np.iscomplexobj(pe.params)
+    out = pe.params.astype(np.float64 if real else np.complex128)
+    for bid in range(vl.n_blocks):
+        _, ch = _block_leg_charges(lat, vl.legs, x, y, bid)
+        n = (power * ch[leg]) % lat.N
+        a, d = vl.block_offsets[bid], vl.block_dims[bid]
+        out[a:a + int(np.prod(d))] *= (-1.0) ** n if real else np.exp(2j * np.pi * n / lat.N)
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Full (double-index) network with explicit B tensors: the definition of the
 # amplitude <s|Psi> before the GCF / sampling simplifications.

@@ -340,3 +340,19 @@ def test_uneven_sector_boundary_mps_is_exact_at_the_bound():
         ex = P.contract_exact(pe.sampled_network(cfg))
         la, ph = vmc.amplitude(pe, cfg, chi=4)   # max degeneracy 2, floor(5/2) = 2 cuts deep
         assert abs(np.exp(la + 1j * ph) - ex) <= 1e-10 * abs(ex)
+
+
+
+@pytest.mark.parametrize("N,Dk,cplx,link", [(2, 2, False, (0, 0, 2)), (3, (2, 1, 1), True, (1, 0, 1)),
+                                            (3, 1, True, (1, 1, 2))])
+def test_link_clock_multiplies_every_amplitude(N, Dk, cplx, link):
+    """Z on one link: psi'(s) = omega^(n_link(s)) psi(s) on every physical s."""
+    pe = make_peps(3, 3, N, Dk, seed=19, complex_=cplx)
+    lat = pe.lat
+    x, y, axis = link
+    pe2 = P.GIPEPS(lat, Dk, P.link_clock_params(pe, x, y, axis))
+    li = lat.hi(x, y) if axis == 1 else lat.vi(x, y)
+    for s in lat.physical_basis():
+        a = P.contract_exact(pe.sampled_network(s))
+        b = P.contract_exact(pe2.sampled_network(s))
+        assert abs(b - np.exp(2j * np.pi * s[li] / N) * a) <= 1e-12 * max(1.0, abs(a))
