@@ -14,6 +14,9 @@ configuration moves are index shifts on the host.
 * VBS order parameter D_alpha = (1 / n_alpha) sum_x (-1)^{x_alpha} Ebar^alpha_x
   with Ebar = 2 - 2 cos(2 pi n / N) on the alpha-links and n_alpha their number
   (L(L-1) on an L x L lattice).
+* With matter: the boson density n_x, and the gauge-dressed hop
+  c^dag_x U c_{x'} + h.c. on every link (Eq. 3), local value psi(s') / psi(s)
+  for the configuration s' the hop reaches.
 * Wilson loop W around a w x h block of plaquettes (U on its bottom and right
   edges, U^dag on its top and left edges): W is the product of the block's
   plaquette operators, so W s shifts only the boundary links; local value
@@ -118,6 +121,53 @@ def wilson_loop(ctx, configs, Lx, Ly, N, w, h=None, origin=None, la=None, ph=Non
         origin = ((Lx - 1 - w) // 2, (Ly - 1 - h) // 2)
     la, ph = _amps(ctx, configs, la, ph)
     return _ratio(ctx, shift_block(configs, Lx, Ly, N, origin[0], origin[1], w, h, N - 1), la, ph)
+
+
+def boson_density(configs, Lx, Ly):
+    """Per-sample occupations n_x: (n, Ly, Lx) (hard-core bosons)."""
+    c = _np(configs).astype(np.int64)
+    n_l = Ly * (Lx - 1) + (Ly - 1) * Lx
+    return c[:, n_l:n_l + Lx * Ly].reshape(-1, Ly, Lx).astype(np.float64)
+
+
+def hop_configs(configs, Lx, Ly, N, x, y, axis):
+    """The configurations reached by the gauge-dressed hop on link (x, y,
+    axis) (Eq. 3): a boson moves from the far end to (x, y) raising the link,
+    or from (x, y) to the far end lowering it.  Rows where neither applies
+    (hard-core) come back unchanged with mask False.  Returns (moved int8
+    configurations, mask)."""
+    c = _np(configs).astype(np.int64).copy()
+    n_h = Ly * (Lx - 1)
+    n_l = n_h + (Ly - 1) * Lx
+    x2, y2 = (x + 1, y) if axis == 1 else (x, y + 1)
+    li = y * (Lx - 1) + x if axis == 1 else n_h + y * Lx + x
+    s1, s2 = n_l + y * Lx + x, n_l + y2 * Lx + x2
+    fwd = (c[:, s1] == 0) & (c[:, s2] == 1)
+    bwd = (c[:, s1] == 1) & (c[:, s2] == 0)
+    c[fwd, s1], c[fwd, s2] = 1, 0
+    c[fwd, li] = (c[fwd, li] + 1) % N
+    c[bwd, s1], c[bwd, s2] = 0, 1
+    c[bwd, li] = (c[bwd, li] - 1) % N
+    return c.astype(np.int8), fwd | bwd
+
+
+def hop_map(ctx, configs, Lx, Ly, N, la=None, ph=None):
+    """Per-sample local values of c^dag_x U c_{x'} + h.c. on every link:
+    (horizontal (n, Ly, Lx-1), vertical (n, Ly-1, Lx)), psi(s')/psi(s) where
+    the hop applies and 0 elsewhere."""
+    la, ph = _amps(ctx, configs, la, ph)
+    n = la.shape[0]
+    hh = np.zeros((n, Ly, Lx - 1), dtype=np.complex128)
+    hv = np.zeros((n, Ly - 1, Lx), dtype=np.complex128)
+    for axis, out, ny, nx in ((1, hh, Ly, Lx - 1), (2, hv, Ly - 1, Lx)):
+        for y in range(ny):
+            for x in range(nx):
+                moved, mask = hop_configs(configs, Lx, Ly, N, x, y, axis)
+                if mask.any():
+                    r = np.zeros(n, dtype=np.complex128)
+                    r[mask] = _ratio(ctx, moved[mask], la[mask], ph[mask])
+                    out[:, y, x] = r
+    return hh, hv
 
 
 def mean_and_error(values, n_chains):

@@ -6,8 +6,9 @@ must equal psi^H M psi / psi^H psi, where M is the operator's matrix on that
 basis built from the oracle's own moves (plaquette operators composed for the
 Wilson loop).  Complex Z3 tensors make W and W^dag differ, so a reversed loop
 or a wrong local-estimator direction fails.  The configuration moves are also
-checked against the oracle's plaquette move, and the diagonal estimators
-against the oracle's electric term and an explicit staggered sum.
+checked against the oracle's plaquette and hop moves, and the diagonal
+estimators against the oracle's electric term, an explicit staggered sum and
+the occupations.
 """
 
 import numpy as np
@@ -117,3 +118,29 @@ def test_mean_and_error_over_chains():
     m, err = obs.mean_and_error(v, 3)
     means = v.reshape(3, 4).mean(axis=1)
     assert m == pytest.approx(means.mean()) and err == pytest.approx(means.std(ddof=1) / np.sqrt(3))
+
+
+def test_matter_observables_are_exact_expectations():
+    pe = make_peps(3, 2, 2, 2, seed=93, matter=True, complex_=True)
+    lat = pe.lat
+    basis = np.concatenate([lat.physical_basis(n_bosons=k) for k in (0, 2, 4, 6)])
+    psi = np.array([P.contract_exact(pe.sampled_network(b)) for b in basis])
+    w = np.abs(psi) ** 2 / np.sum(np.abs(psi) ** 2)
+    index = {tuple(b): i for i, b in enumerate(basis)}
+    cfgs = basis.astype(np.int8)
+    dens = obs.boson_density(cfgs, lat.Lx, lat.Ly)
+    assert np.allclose(dens.reshape(len(basis), -1), basis[:, lat.n_h + lat.n_v:])
+    hh, hv = obs.hop_map(OracleAmplitudes(pe, 2), cfgs, lat.Lx, lat.Ly, lat.N)
+    for axis, est, ny, nx in ((1, hh, lat.Ly, lat.Lx - 1), (2, hv, lat.Ly - 1, lat.Lx)):
+        for y in range(ny):
+            for x in range(nx):
+                M = np.zeros((len(basis), len(basis)))
+                for j, b in enumerate(basis):
+                    c2 = lat.hop(b, x, y, axis)
+                    if c2 is not None:
+                        M[index[tuple(c2)], j] = 1.0
+                exact = (psi.conj() @ M @ psi) / (psi.conj() @ psi)
+                assert abs(w @ est[:, y, x] - exact) < 1e-10 * max(1.0, abs(exact))
+                moved, mask = obs.hop_configs(cfgs, lat.Lx, lat.Ly, lat.N, x, y, axis)
+                for k in np.nonzero(mask)[0]:
+                    assert np.array_equal(moved[k], lat.hop(basis[k], x, y, axis))
