@@ -107,3 +107,16 @@ def test_link_phase_refuses_missing_links():
         states.link_phase(np.zeros(10), 2, 3, 3, 2, 2, 0, 1)
     with pytest.raises(ValueError):
         states.link_phase(np.zeros(10), 2, 3, 3, 2, 0, 2, 2)
+
+
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+def test_product_and_oracle_link_operators_agree(case):
+    """The product's transform and the oracle's own (written separately)
+    give the same parameters on every link."""
+    Lx, Ly, N, Dk, matter, cplx, Q = case
+    lat, pe = _peps(*case)
+    for x, y, axis in [(0, 0, 2), (1, 0, 1), (Lx - 2, Ly - 1, 1), (Lx - 1, Ly - 2, 2)]:
+        for power in (1, N - 1):
+            a = states.link_phase(pe.params, N, Lx, Ly, Dk, x, y, axis, power, matter, Q)
+            b = P.link_clock_params(pe, x, y, axis, power)
+            assert np.allclose(a, b, atol=0, rtol=1e-15)
