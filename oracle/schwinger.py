@@ -55,21 +55,31 @@ def fields(occ, Q):
     return np.cumsum(np.asarray(occ) - Q)[:-1]
 
 
-def hamiltonian(L, m, J, g, n_f):
-    """Dense H on the n_f-fermion sector, in `basis` order."""
+def hamiltonian(L, m, J, g, n_f, sparse=False):
+    """H on the n_f-fermion sector, in `basis` order: dense, or a scipy
+    sparse matrix when `sparse` (for 16 sites and beyond)."""
     B = basis(L, n_f)
     index = {s: i for i, s in enumerate(B)}
     Q, mx = charges(L), masses(L, m)
-    H = np.zeros((len(B), len(B)), dtype=np.complex128)
+    rows, cols, vals = [], [], []
     for i, s in enumerate(B):
-        H[i, i] = mx @ np.asarray(s) + g * np.sum(fields(s, Q) ** 2)
+        rows.append(i)
+        cols.append(i)
+        vals.append(mx @ np.asarray(s) + g * np.sum(fields(s, Q) ** 2))
         for x in range(L - 1):
             if s[x] == 0 and s[x + 1] == 1:          # c^dag_x U_x c_{x+1}: fermion x+1 -> x
                 t = list(s)
                 t[x], t[x + 1] = 1, 0
                 j = index[tuple(t)]
-                H[j, i] += J
-                H[i, j] += np.conj(J)
+                rows += [j, i]
+                cols += [i, j]
+                vals += [J, np.conj(J)]
+    if sparse:
+        import scipy.sparse as sp
+
+        return sp.csr_matrix((np.array(vals, dtype=np.complex128), (rows, cols)), shape=(len(B), len(B))), B
+    H = np.zeros((len(B), len(B)), dtype=np.complex128)
+    np.add.at(H, (rows, cols), vals)
     return H, B
 
 

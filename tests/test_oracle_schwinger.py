@@ -96,3 +96,9 @@ def test_real_time_follows_the_exact_evolution(chain):
     bwd = U @ (np.exp(+1j * w * dt * n) * (U.conj().T @ p0))
     f, b = abs(np.vdot(fwd, v)) / np.linalg.norm(v), abs(np.vdot(bwd, v)) / np.linalg.norm(v)
     assert f > 0.99999 and b < 0.9, (f, b)
+
+
+def test_sparse_and_dense_hamiltonians_agree():
+    Hd, B = S.hamiltonian(8, 0.2, -5j, 0.05, 4)
+    Hs, B2 = S.hamiltonian(8, 0.2, -5j, 0.05, 4, sparse=True)
+    assert B == B2 and np.allclose(Hs.toarray(), Hd) and np.allclose(Hd, Hd.conj().T)
