@@ -340,7 +340,7 @@ def flip_row(row):
     return [np.transpose(W, (0, 1, 3, 2)) for W in row]
 
 
-def compress(mps, chi):
+def compress(mps, chi, spectra=None):
     """SVD compression of an MPS to bond dimension <= chi, normalised.
 
     1. QR left to right (left-canonical sites 0..L-2);
@@ -350,6 +350,11 @@ def compress(mps, chi):
     3. divide the first site by the state norm.
     Returns (mps, log_norm); the input state equals exp(log_norm) * output
     (up to the discarded weight).
+    `spectra`, if a list, receives (bond i, all singular values of that
+    bond) for every bond the sweep cuts (more than chi values); it is a
+    diagnostic and changes nothing in the result.  The kept subspace at a cut
+    is well defined only when sigma_chi > sigma_chi+1, and a small gap there
+    makes the truncated state sensitive to rounding in its input.
     """
     mps = [m.copy() for m in mps]
     L = len(mps)
@@ -363,6 +368,8 @@ def compress(mps, chi):
         a, d, b = mps[i].shape
         U, S, Vh = np.linalg.svd(mps[i].reshape(a, d * b), full_matrices=False)
         k = min(chi, len(S))
+        if spectra is not None and len(S) > chi:
+            spectra.append((i, S.copy()))
         mps[i] = Vh[:k].reshape(k, d, b)
         mps[i - 1] = np.tensordot(mps[i - 1], U[:, :k] * S[:k], axes=(2, 0))
     nrm = np.linalg.norm(mps[0])
@@ -443,32 +450,57 @@ def compress_variational(mps, chi, sweeps=4, history=None):
     return B, float(np.log(nrm))
 
 
-def bottom_envs(rows, chi):
+def bottom_envs(rows, chi, spectra=None):
     """B[r] (r = -1 .. Ly-1) as (mps, log_scale): rows 0..r absorbed bottom-up.
 
     Returned as a dict keyed by r; B[-1] is the trivial MPS with log-scale 0.
+    `spectra`, if a list, receives (r, bond, singular values) of every cut
+    (see `compress`).
     """
     Lx = len(rows[0])
     dt = np.result_type(*[w.dtype for w in rows[0]])
     env = {-1: (trivial_mps(Lx, dt), 0.0)}
     for r in range(len(rows)):
         m, s = env[r - 1]
-        m2, ds = compress(absorb(m, rows[r]), chi)
+        cuts = [] if spectra is not None else None
+        m2, ds = compress(absorb(m, rows[r]), chi, cuts)
+        if spectra is not None:
+            spectra.extend((r, i, S) for i, S in cuts)
         env[r] = (m2, s + ds)
     return env
 
 
-def top_envs(rows, chi):
+def top_envs(rows, chi, spectra=None):
     """T[r] (r = Ly .. 0): rows r..Ly-1 absorbed top-down; physical legs are
-    the down legs of row r.  T[Ly] is trivial."""
+    the down legs of row r.  T[Ly] is trivial.  `spectra` as in
+    `bottom_envs`."""
     Ly, Lx = len(rows), len(rows[0])
     dt = np.result_type(*[w.dtype for w in rows[0]])
     env = {Ly: (trivial_mps(Lx, dt), 0.0)}
     for r in range(Ly - 1, -1, -1):
         m, s = env[r + 1]
-        m2, ds = compress(absorb(m, flip_row(rows[r])), chi)
+        cuts = [] if spectra is not None else None
+        m2, ds = compress(absorb(m, flip_row(rows[r])), chi, cuts)
+        if spectra is not None:
+            spectra.extend((r, i, S) for i, S in cuts)
         env[r] = (m2, s + ds)
     return env
+
+
+def _chain(spec, *ops):
+    """np.einsum(spec, *ops) evaluated as a left-to-right chain of two-operand
+    contractions: each step sums the indices that no later operand and not the
+    output carries.  The same sum as the single einsum, reached through
+    pairwise products (BLAS) instead of one loop over every index at once."""
+    ins, out = spec.split("->")
+    ins = ins.split(",")
+    cur, cur_idx = ops[0], ins[0]
+    for k in range(1, len(ops)):
+        rest = "".join(ins[k + 1:]) + out
+        keep = "".join(ch for ch in dict.fromkeys(cur_idx + ins[k]) if ch in rest)
+        cur = np.einsum(f"{cur_idx},{ins[k]}->{keep}", cur, ops[k], optimize=True)
+        cur_idx = keep
+    return np.einsum(f"{cur_idx}->{out}", cur)
 
 
 def contract_row(Bm, row, Tm):
@@ -476,7 +508,7 @@ def contract_row(Bm, row, Tm):
     E = np.ones((1, 1, 1))
     for Bs, W, Ts in zip(Bm, row, Tm):
         # E[a, l, b] Bs[a, d, a'] W[l, r, d, u] Ts[b, u, b']
-        E = np.einsum("alb,adA,lrdu,buB->ArB", E, Bs, W, Ts)
+        E = _chain("alb,adA,lrdu,buB->ArB", E, Bs, W, Ts)
     return E.reshape(-1)[0]
 
 
@@ -485,7 +517,7 @@ def contract_strip(Bm, row1, row2, Tm):
     E = np.ones((1, 1, 1, 1))
     for Bs, W1, W2, Ts in zip(Bm, row1, row2, Tm):
         # E[a,i,j,b] Bs[a,d,A] W1[i,I,d,m] W2[j,J,m,u] Ts[b,u,B] -> E[A,I,J,B]
-        E = np.einsum("aijb,adA,iIdm,jJmu,buB->AIJB", E, Bs, W1, W2, Ts)
+        E = _chain("aijb,adA,iIdm,jJmu,buB->AIJB", E, Bs, W1, W2, Ts)
     return E.reshape(-1)[0]
 
 
@@ -493,11 +525,11 @@ def row_site_environment(Bm, row, Tm, x):
     """d<B|row|T>/dW_x: the open tensor of shape W_x.shape (Dl, Dr, Dd, Du)."""
     L = np.ones((1, 1, 1))
     for c in range(x):
-        L = np.einsum("alb,adA,lrdu,buB->ArB", L, Bm[c], row[c], Tm[c])
+        L = _chain("alb,adA,lrdu,buB->ArB", L, Bm[c], row[c], Tm[c])
     R = np.ones((1, 1, 1))
     for c in range(len(row) - 1, x, -1):
-        R = np.einsum("adA,lrdu,buB,ArB->alb", Bm[c], row[c], Tm[c], R)
-    return np.einsum("alb,adA,buB,ArB->lrdu", L, Bm[x], Tm[x], R)
+        R = _chain("ArB,buB,lrdu,adA->alb", R, Tm[c], row[c], Bm[c])
+    return _chain("alb,adA,ArB,buB->lrdu", L, Bm[x], R, Tm[x])
 
 
 def mps_bond_dims(mps):

@@ -67,14 +67,16 @@ def environments(peps: P.GIPEPS, cfg, chi):
     return rows, P.bottom_envs(rows, chi), P.top_envs(rows, chi)
 
 
-def amplitude(peps: P.GIPEPS, cfg, chi):
+def amplitude(peps: P.GIPEPS, cfg, chi, spectra=None):
     """(log|psi|, arg psi) of the boundary-MPS amplitude; (-inf, 0) if s is
-    unphysical (its amplitude is exactly zero, Sec. S-2)."""
+    unphysical (its amplitude is exactly zero, Sec. S-2).  `spectra`, if a
+    list, receives the singular values of every cut the bottom environments
+    make (diagnostic, see `peps.compress`)."""
     rows = peps.sampled_network(cfg)
     if rows is None:
         return -np.inf, 0.0
     Ly = len(rows)
-    Benv = P.bottom_envs(rows[:-1], chi)
+    Benv = P.bottom_envs(rows[:-1], chi, spectra)
     Bm, s = Benv[Ly - 2]
     val = _close(P.absorb(Bm, rows[Ly - 1]))
     if val == 0:

@@ -356,3 +356,43 @@ def test_link_clock_multiplies_every_amplitude(N, Dk, cplx, link):
         a = P.contract_exact(pe.sampled_network(s))
         b = P.contract_exact(pe2.sampled_network(s))
         assert abs(b - np.exp(2j * np.pi * s[li] / N) * a) <= 1e-12 * max(1.0, abs(a))
+
+
+def test_pairwise_chain_equals_one_einsum():
+    """The exact contractions sum over the same indices as one np.einsum of
+    all operands; the chain of pairwise contractions only changes the order
+    of evaluation (strip, row and open-row specs, complex operands)."""
+    rng = np.random.default_rng(5)
+
+    def rnd(*shape):
+        return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+    E, Bs, W1, W2, Ts = rnd(3, 2, 2, 4), rnd(3, 2, 5), rnd(2, 3, 2, 2), rnd(2, 3, 2, 2), rnd(4, 2, 6)
+    for spec, ops in [("aijb,adA,iIdm,jJmu,buB->AIJB", (E, Bs, W1, W2, Ts)),
+                      ("alb,adA,lrdu,buB->ArB", (E[:, :, 0, :], Bs, W1, Ts)),
+                      ("ArB,buB,lrdu,adA->alb", (rnd(5, 3, 6), Ts, W1, Bs)),
+                      ("alb,adA,ArB,buB->lrdu", (E[:, :, 0, :], Bs, rnd(5, 3, 6), Ts))]:
+        ref = np.einsum(spec, *ops)
+        np.testing.assert_allclose(P._chain(spec, *ops), ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+def test_compress_reports_the_spectrum_of_every_cut():
+    """The diagnostic `spectra` of `compress` records, for each bond the sweep
+    cuts, the singular values of that bond; on a two-site MPS the one bond's
+    values are those of the contracted two-site matrix (Eckart-Young setting),
+    and recording them changes nothing in the result."""
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((1, 6, 5))
+    B = rng.standard_normal((5, 7, 1))
+    chi = 3
+    sp = []
+    m1, s1 = P.compress([A, B], chi, sp)
+    m0, s0 = P.compress([A, B], chi)
+    assert len(sp) == 1 and sp[0][0] == 1
+    ref = np.linalg.svd((A.reshape(6, 5) @ B.reshape(5, 7)), compute_uv=False)
+    np.testing.assert_allclose(sp[0][1], ref[:len(sp[0][1])], rtol=1e-12)
+    assert s0 == s1 and all(np.array_equal(x, y) for x, y in zip(m0, m1))
+    # no cut is recorded when chi covers every bond
+    sp2 = []
+    P.compress([A, B], 5, sp2)
+    assert sp2 == []
