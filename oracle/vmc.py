@@ -67,14 +67,19 @@ def environments(peps: P.GIPEPS, cfg, chi):
     return rows, P.bottom_envs(rows, chi), P.top_envs(rows, chi)
 
 
-def amplitude(peps: P.GIPEPS, cfg, chi, spectra=None):
+def amplitude(peps: P.GIPEPS, cfg, chi, spectra=None, dtype=None):
     """(log|psi|, arg psi) of the boundary-MPS amplitude; (-inf, 0) if s is
     unphysical (its amplitude is exactly zero, Sec. S-2).  `spectra`, if a
     list, receives the singular values of every cut the bottom environments
-    make (diagnostic, see `peps.compress`)."""
+    make (diagnostic, see `peps.compress`).  `dtype` (e.g. np.float32 or
+    np.complex64), if given, runs the same steps in that type, with NumPy's
+    LAPACK routines of that precision: its distance from the FP64 result
+    measures how sensitive this amplitude is to rounding at that precision."""
     rows = peps.sampled_network(cfg)
     if rows is None:
         return -np.inf, 0.0
+    if dtype is not None:
+        rows = [[w.astype(dtype) for w in row] for row in rows]
     Ly = len(rows)
     Benv = P.bottom_envs(rows[:-1], chi, spectra)
     Bm, s = Benv[Ly - 2]

@@ -350,3 +350,27 @@ def test_uneven_sectors_local_energy_and_log_grad():
         am = vmc.amplitude(P.GIPEPS(lat, pe.Dk, pm), cfg, 2)
         d = (np.exp(ap[0] + 1j * ap[1]) - np.exp(am[0] + 1j * am[1])) / 2e-6 / psi0
         assert abs(O[k] - d) <= 1e-6 * max(1.0, abs(d))
+
+
+def test_amplitude_in_single_precision_follows_the_same_steps():
+    """`amplitude(..., dtype=float32)` runs the oracle's steps in single
+    precision: at exact chi it agrees with the FP64 amplitude to single
+    precision rounding (and not to double), and the singular spectra it
+    reports are those of the FP64 run to the same accuracy."""
+    import synth
+
+    lat = Lattice(4, 4, 2)
+    _, n = P.layout(lat, 2)
+    pe = P.GIPEPS(lat, 2, synth.round_to(synth.tensor_entries(17, n, False), "f32"))
+    cfg = lat.config_from_powers(np.zeros((4, 4)), synth.plaquette_powers(18, 1, lat.n_plaquettes, 2)[0])
+    la64, ph64 = vmc.amplitude(pe, cfg, 4)
+    la32, ph32 = vmc.amplitude(pe, cfg, 4, dtype=np.float32)
+    d = abs(np.exp((la32 - la64) + 1j * (ph32 - ph64)) - 1)
+    assert 1e-12 < d < 1e-5
+    sp64, sp32 = [], []
+    vmc.amplitude(pe, cfg, 2, spectra=sp64)
+    vmc.amplitude(pe, cfg, 2, spectra=sp32, dtype=np.float32)
+    assert len(sp64) == len(sp32) > 0
+    for (r, b, s64), (r2, b2, s32) in zip(sp64, sp32):
+        assert (r, b) == (r2, b2) and s32.dtype == np.float32
+        np.testing.assert_allclose(s32, s64, rtol=1e-4, atol=1e-5 * s64[0])
