@@ -1,15 +1,26 @@
 """VMC throughput benchmark of the GB300 GCF-PEPS library.
 
-Workload: pure Z2 gauge theory, 8x8 open lattice, GCF PEPS with D = 4
-(D_k = 2) and i.i.d. N(0,1) Z2-symmetric tensors, boundary cutoff chi = 16,
-coupling h = 0.5 (electric; paper form h_p = 1, g = 0.5), 4096 Markov chains
-x 64 sweeps per step in one persistent launch, FP32 contraction.  One step =
-one VMC iteration: sample_batch (sweeps + amplitude, E_loc and d ln psi/dA
-measured after every sweep) followed by the FP64 SR step (reductions + CG
-solve + parameter update).  Metric: VMC samples/s (one sample = one measured
-configuration).
+One step = one VMC iteration over one batch of chains: the sampling launch
+(sweeps, then amplitude, E_loc and d ln psi/dA measured on every sample)
+followed by the FP64 reductions, CG solve and parameter update of each
+context (SR; for the tVMC workload the two TDVP stages, each with its own
+sampling launch).  Metric: VMC samples/s (one sample = one measured
+configuration).  Workloads (--config):
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  z2b_32x32_mixed (default): Z2 gauge + hard-core bosons at half filling,
+      D = 4 (D_k = 2), chi = 24, (h, g, J) = (1, 0.33, 0.5), 16384 chains over
+      three lattices 16x16 / 24x24 / 32x32 (5462 / 5461 / 5461 chains) in one
+      persistent launch (gcf_sample_multi), one sweep per step, SR on each;
+  z3_16x16 / z4_16x16: pure Z3 D = 6 / Z4 D = 8 on 16x16, chi = 32, complex64
+      tensors, g = 0.375 / 0.33, 8192 chains x 1 sweep, full SR step
+      (FP64 CG, diagonal shift 1e-4);
+  z2_10x10_tvmc: pure Z2 10x10, D = 6 (D_k = 3), chi = 36, complex64,
+      g = 0.2, two-stage tVMC step with dt = 0.01, 8192 samples per stage;
+  z2_8x8: pure Z2 8x8, D = 4, chi = 16 (exact), h = 0.5, 4096 chains x 64
+      sweeps, SR.
+
+Usage: python bench.py [--config C] [--gpus N] [--steps K] [--warmup W]
+                       [--impl reference] [--precision fp32|tf32|bf16]
 Under torchrun (N > 1) every rank runs the workload on its own chains with
 the same tensors (chains are independent; no collective on the data path);
 the slowest rank's time sets the whole-job rate.
@@ -32,9 +43,30 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(workload="z2_8x8_D4_chi16_4096chains_x64sweeps", N=2, Lx=8, Ly=8, D=4, chi=16, h_p=1.0,
-                g=0.5, chains=4096, sweeps=64)
 METRIC = "VMC samples/sec (amp+E_loc+grad) per GB300 at D,chi"
+
+
+def _lattice(N, L, D, chi, chains, g, h=1.0, J=0.0, matter=False, cplx=False):
+    return dict(N=N, Lx=L, Ly=L, D=D, chi=chi, h_p=h, g=g, J=J, matter=matter, cplx=cplx, chains=chains)
+
+
+WORKLOADS = {
+    "z2b_32x32_mixed": dict(
+        workload="z2_hardcore_bosons_16x16+24x24+32x32_D4_chi24_16384chains_half_filling",
+        lattices=[_lattice(2, 16, 4, 24, 5462, 0.33, J=0.5, matter=True),
+                  _lattice(2, 24, 4, 24, 5461, 0.33, J=0.5, matter=True),
+                  _lattice(2, 32, 4, 24, 5461, 0.33, J=0.5, matter=True)],
+        sweeps=1, mode="sr", dt=0.0),
+    "z3_16x16": dict(workload="z3_16x16_D6_chi32_c64_8192chains", lattices=[_lattice(3, 16, 6, 32, 8192, 0.375, cplx=True)],
+                     sweeps=1, mode="sr", dt=0.0),
+    "z4_16x16": dict(workload="z4_16x16_D8_chi32_c64_8192chains", lattices=[_lattice(4, 16, 8, 32, 8192, 0.33, cplx=True)],
+                     sweeps=1, mode="sr", dt=0.0),
+    "z2_10x10_tvmc": dict(workload="z2_10x10_D6_chi36_c64_tvmc_dt0.01_8192samples", lattices=[_lattice(2, 10, 6, 36, 8192, 0.2, cplx=True)],
+                          sweeps=1, mode="tvmc", dt=0.01),
+    "z2_8x8": dict(workload="z2_8x8_D4_chi16_4096chains_x64sweeps", lattices=[_lattice(2, 8, 4, 16, 4096, 0.5)],
+                   sweeps=64, mode="sr", dt=0.0),
+}
+DEFAULT_CONFIG = "z2b_32x32_mixed"
 SR_ARGS = dict(diag_shift=1e-4, lr=0.01, max_iter=100, tol=1e-6)
 
 
@@ -58,7 +90,7 @@ def load_peaks():
 # the files the FP32 sampling kernel is compiled from (its translation unit and
 # every header it includes)
 KERNEL_SOURCES = ("vmc_f32.cu", "launch.h", "common.cuh", "envsteps.cuh", "linalg.cuh", "mma.cuh",
-                  "peps_dev.cuh", "vmc_kernel.cuh")
+                  "peps_dev.cuh", "tcgen05.cuh", "vmc_kernel.cuh")
 
 
 def source_hash():
@@ -71,28 +103,30 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-PROFILE = os.path.join(ROOT, "profiles", "vmc_kernel_grouped4_f32_z2_8x8_D4_chi16.md")
+def profiled_traffic(samples_per_launch, kernel, smem_level, workload, pdir=None):
+    """DRAM bytes per launch scaled from a committed ncu capture of this
+    workload (profiles/*.md carrying `workload: <name>`), or None if there is
+    none, the kernel's sources changed since the counters were taken, or the
+    launch runs another kernel form (kernel and shared-memory level)."""
+    pdir = pdir or os.path.join(ROOT, "profiles")
+    for name in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
+        try:
+            txt = open(os.path.join(pdir, name)).read()
+        except OSError:
+            continue
+        m0 = re.search(r"workload: (\S+)", txt)
+        m1 = re.search(r"source_sha256: ([0-9a-f]+)", txt)
+        m2 = re.search(r"traffic_bytes_per_sample: ([0-9.eE+]+)", txt)
+        m3 = re.search(r"kernel_form: (\S+) level (\d+)", txt)
+        if not (m0 and m1 and m2 and m3) or m0.group(1) != workload:
+            continue
+        if m1.group(1) != source_hash() or m3.group(1) != kernel or int(m3.group(2)) != smem_level:
+            return None
+        return float(m2.group(1)) * samples_per_launch
+    return None
 
 
-def profiled_traffic(samples_per_launch, kernel, smem_level):
-    """DRAM bytes per launch scaled from the committed ncu capture, or None if
-    the kernel's sources changed since the counters were taken or the launch
-    runs another kernel form (kernel and shared-memory level)."""
-    try:
-        txt = open(PROFILE).read()
-    except OSError:
-        return None
-    m1 = re.search(r"source_sha256: ([0-9a-f]+)", txt)
-    m2 = re.search(r"traffic_bytes_per_sample: ([0-9.eE+]+)", txt)
-    m3 = re.search(r"kernel_form: (\S+) level (\d+)", txt)
-    if not (m1 and m2 and m3) or m1.group(1) != source_hash():
-        return None
-    if m3.group(1) != kernel or int(m3.group(2)) != smem_level:
-        return None
-    return float(m2.group(1)) * samples_per_launch
-
-
-def fp32_alu_peak_tflops(sm_count=152, sm_mhz=2070.0):
+def fp32_alu_peak_tflops(sm_count, sm_mhz=2070.0):
     """FP32 FMA peak from unit counts: SMs x 128 FP32 lanes x 2 flop x clock."""
     return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
 
@@ -101,58 +135,84 @@ def fp32_alu_peak_tflops(sm_count=152, sm_mhz=2070.0):
 # CPU oracle baseline (bounded sample)
 # ---------------------------------------------------------------------------
 def _oracle_chain(args):
-    seed, chain, n_sweeps = args
+    config, li, seed, chain, n_sweeps = args
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     import synth
     from oracle import peps as P
     from oracle import vmc
     from oracle.lattice import Lattice
 
-    w = WORKLOAD
-    lat = Lattice(w["Lx"], w["Ly"], w["N"])
+    w = WORKLOADS[config]["lattices"][li]
+    lat = Lattice(w["Lx"], w["Ly"], w["N"], matter=w["matter"])
     Dk = w["D"] // w["N"]
     _, n = P.layout(lat, Dk)
-    pe = P.GIPEPS(lat, Dk, synth.round_to(synth.tensor_entries(2, n, False), "f32"))
-    powers = synth.plaquette_powers(102, chain + 1, lat.n_plaquettes, w["N"])[chain]
-    cfg = lat.config_from_powers(np.zeros((lat.Ly, lat.Lx)), powers)
-    recs = vmc.run_chain(pe, vmc.Model(h=w["h_p"], g=w["g"]), cfg, w["chi"], seed, chain, n_sweeps)
+    pe = P.GIPEPS(lat, Dk, synth.round_to(synth.tensor_entries(2 + li, n, w["cplx"]), "c64" if w["cplx"] else "f32"))
+    powers = synth.plaquette_powers(102 + li, chain + 1, lat.n_plaquettes, w["N"])[chain]
+    occ = np.zeros((lat.Ly, lat.Lx))
+    if w["matter"]:
+        occ = synth.occupations(102 + li, chain + 1, lat.n_s, lat.n_s // 2)[chain].reshape(lat.Ly, lat.Lx)
+    cfg = lat.config_from_powers(occ, powers)
+    recs = vmc.run_chain(pe, vmc.Model(h=w["h_p"], g=w["g"], J=w["J"]), cfg, w["chi"], seed, chain, n_sweeps)
     return len(recs)
 
 
-def cpu_oracle_rate(n_procs, chains_per_proc=1, sweeps=1):
+def cpu_oracle_rate(config, n_procs, sweeps=1):
+    """The oracle on n_procs host processes, one chain each, the chains spread
+    over the workload's lattices in proportion to their chain counts."""
     import multiprocessing as mp
 
+    lats = WORKLOADS[config]["lattices"]
+    tot = sum(l["chains"] for l in lats)
+    jobs = []
+    for c in range(n_procs):
+        li = min(len(lats) - 1, int(c * tot / n_procs) * len(lats) // tot) if len(lats) > 1 else 0
+        jobs.append((config, li, 7, c, sweeps))
     ctx = mp.get_context("spawn")
-    jobs = [(7, c, sweeps) for c in range(n_procs * chains_per_proc)]
+    # one thread per process: the spawned workers inherit these before NumPy loads
+    keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    os.environ.update({k: "1" for k in keep})
     t0 = time.perf_counter()
-    with ctx.Pool(n_procs) as pool:
-        done = sum(pool.map(_oracle_chain, jobs))
+    try:
+        with ctx.Pool(n_procs) as pool:
+            done = sum(pool.map(_oracle_chain, jobs))
+    finally:
+        for k, v in keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     dt = time.perf_counter() - t0
-    return done / dt, done, dt
+    mix = "/".join(str(sum(1 for j in jobs if j[1] == i)) for i in range(len(lats)))
+    return done / dt, done, dt, mix
 
 
 # ---------------------------------------------------------------------------
-def err_vs_fp64(ctx, configs, w, n_check=64):
+def err_vs_fp64(ctxs, configs, lats, n_check=16):
     """Error of the benchmarked precision against the library's FP64 form on
     the same tensors (the FP64 form matches the FP64 oracle to ~1e-10 in the
-    parity tests), on the first n_check final configurations: amplitude error
-    |exp(d log|psi| + i d phase) - 1| and E_loc error |dE| / max(1, |E|)."""
+    parity tests), on the first n_check final configurations of each lattice:
+    amplitude error |exp(d log|psi| + i d phase) - 1| and E_loc error
+    |dE| / max(1, |E|)."""
     import torch
 
     import paper_2503_20566_gb300 as G
 
-    sub = configs[:n_check].contiguous()
-    ref = G.Context(w["N"], w["Lx"], w["Ly"], w["D"], w["chi"], h=w["h_p"], g=w["g"], precision="fp64", seed=0)
-    try:
-        ref.set_tensors(ctx.get_tensors())
-        la, ph = ctx.amplitude(sub)
-        la64, ph64 = ref.amplitude(sub)
-        e, e64 = ctx.local_energy(sub), ref.local_energy(sub)
-    finally:
-        ref.close()
-    amp = (torch.exp(torch.complex(la - la64, ph - ph64)) - 1).abs().cpu().numpy()
-    ee = ((e - e64).abs() / torch.clamp(e64.abs(), min=1.0)).cpu().numpy()
-    return {"configs": int(sub.shape[0]), "reference": "FP64 form of the library on the same tensors",
+    amp, ee = [], []
+    for ctx, cfg, w in zip(ctxs, configs, lats):
+        sub = cfg[:n_check].contiguous()
+        ref = G.Context(w["N"], w["Lx"], w["Ly"], w["D"], w["chi"], matter=w["matter"], h=w["h_p"], g=w["g"],
+                        J=w["J"], complex_=w["cplx"], precision="fp64", seed=0)
+        try:
+            ref.set_tensors(ctx.get_tensors())
+            la, ph = ctx.amplitude(sub)
+            la64, ph64 = ref.amplitude(sub)
+            e, e64 = ctx.local_energy(sub), ref.local_energy(sub)
+        finally:
+            ref.close()
+        amp.append((torch.exp(torch.complex(la - la64, ph - ph64)) - 1).abs().cpu().numpy())
+        ee.append(((e - e64).abs() / torch.clamp(e64.abs(), min=1.0)).cpu().numpy())
+    amp, ee = np.concatenate(amp), np.concatenate(ee)
+    return {"configs": int(amp.size), "reference": "FP64 form of the library on the same tensors",
             "amp_max": float(amp.max()), "amp_median": float(np.median(amp)),
             "eloc_max": float(ee.max()), "eloc_median": float(np.median(ee))}
 
@@ -199,40 +259,133 @@ def clocks_sampler_stop(p, f, path, gpu_index):
 
 
 # ---------------------------------------------------------------------------
+REFERENCE_BUDGET_S = 150.0
+
+
 def run_reference(args):
-    """Reference arm: the FP64 oracle on the host cores, bounded samples."""
+    """Reference arm: the FP64 oracle on the host cores.  A step is one
+    bounded sample of the workload: one chain per host core (one sweep,
+    measured), spread over the workload's lattices in proportion to their
+    chains.  The CPU needs no warm-up, and the run stops after the step that
+    passes REFERENCE_BUDGET_S (at least one step), so that the arm ends within
+    a few minutes whatever --steps asks; the line reports the steps run."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    wl = WORKLOADS[args.config]
     cores = max(1, min(os.cpu_count() or 1, 16))
-    for _ in range(max(0, args.warmup)):
-        cpu_oracle_rate(cores, 1, 1)
     t0 = time.perf_counter()
     done = 0
-    for _ in range(args.steps):
-        _, d, _ = cpu_oracle_rate(cores, 1, 1)
+    mix = ""
+    steps = 0
+    while steps < max(1, args.steps):
+        _, d, _, mix = cpu_oracle_rate(args.config, cores, 1)
         done += d
+        steps += 1
+        if time.perf_counter() - t0 > REFERENCE_BUDGET_S:
+            break
     dt = time.perf_counter() - t0
     v = done / dt
+    sample = (f"{cores} chains x 1 sweep per step (lattice mix {mix}), FP64 NumPy, one process per core; "
+              f"{steps} of {args.steps} steps run (time cap {REFERENCE_BUDGET_S:.0f} s), no warm-up")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / max(1, args.steps),
+            "steps": steps, "warmup": 0, "ms_per_step": 1000 * dt / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD["workload"], "sample_per_step":
-                                             f"{cores} chains x 1 sweep (of 4096 x 64)"},
-            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{cores} chains x 1 sweep per step, FP64 NumPy, one process per core"},
+            "data": "synthetic", "config": {"workload": wl["workload"], "sample_per_step": sample},
+            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+class Workload:
+    """The workload's contexts, chains and sample buffers on this rank."""
+
+    def __init__(self, config, precision, seeds, chains_scale=1.0):
+        import torch
+
+        import paper_2503_20566_gb300 as G
+        import synth
+
+        self.wl = WORKLOADS[config]
+        self.lats = [dict(l, chains=max(1, int(round(l["chains"] * chains_scale)))) for l in self.wl["lattices"]]
+        self.sweeps = self.wl["sweeps"]
+        self.mode = self.wl["mode"]
+        self.ctxs, self.configs, self.samples = [], [], []
+        for li, w in enumerate(self.lats):
+            ctx = G.Context(w["N"], w["Lx"], w["Ly"], w["D"], w["chi"], matter=w["matter"], h=w["h_p"], g=w["g"],
+                            J=w["J"], complex_=w["cplx"], precision=precision, seed=seeds["tensors"] + li)
+            n = w["chains"]
+            powers = torch.from_numpy(synth.plaquette_powers(seeds["chains"] + li, n, (w["Lx"] - 1) * (w["Ly"] - 1),
+                                                             w["N"]))
+            occ = None
+            if w["matter"]:
+                occ = torch.from_numpy(synth.occupations(seeds["chains"] + li, n, w["Lx"] * w["Ly"],
+                                                         (w["Lx"] * w["Ly"]) // 2))
+            self.configs.append(ctx.init_configs(n, occupations=occ, powers=powers))
+            self.samples.append(ctx.alloc_samples(n, self.sweeps, grad=True))
+            self.ctxs.append(ctx)
+        self.samples_per_launch = sum(w["chains"] for w in self.lats) * self.sweeps
+        self.launches_per_step = 2 if self.mode == "tvmc" else 1
+        self.samples_per_step = self.samples_per_launch * self.launches_per_step
+
+    @property
+    def stream(self):
+        return self.ctxs[0].stream
+
+    def sample(self, seed):
+        import paper_2503_20566_gb300 as G
+
+        if len(self.ctxs) == 1:
+            self.ctxs[0].sample_batch(self.configs[0], self.sweeps, seed=seed, out=self.samples[0])
+        else:
+            G.sample_multi(self.ctxs, self.configs, self.sweeps, [seed + 7919 * i for i in range(len(self.ctxs))],
+                           outs=self.samples)
+
+    def update(self, stage=0):
+        import paper_2503_20566_gb300 as G
+
+        stats = []
+        mode = G.SR if self.mode == "sr" else (G.TDVP_STAGE1 if stage == 0 else G.TDVP_STAGE2)
+        for ctx, smp, w in zip(self.ctxs, self.samples, self.lats):
+            stats.append(ctx.sr_step(smp, w["chains"], mode=mode, dt=self.wl["dt"], **SR_ARGS))
+        return stats
+
+    def step(self, seed, ev=None, stream=None):
+        """One VMC iteration; ev: (start, after-sampling, end) events of each
+        sampling launch and update, recorded on `stream`."""
+        stats = None
+        for stage in range(self.launches_per_step):
+            if ev:
+                ev[stage][0].record(stream)
+            self.sample(seed + 100 * stage)
+            if ev:
+                ev[stage][1].record(stream)
+            stats = self.update(stage)
+            if ev:
+                ev[stage][2].record(stream)
+        return stats
+
+    def flops_per_launch(self):
+        return sum(flops_per_sample(w["Lx"], w["Ly"], w["D"] // w["N"], w["chi"], w["cplx"]) * w["chains"] * self.sweeps
+                   for w in self.lats)
+
+    def kernel_name(self):
+        if len(self.ctxs) > 1:
+            return "gcf::vmc_kernel_multi"
+        return self.ctxs[0].kernel_name
+
+    def scalar(self):
+        return "<gcf::cfloat>" if self.lats[0]["cplx"] else "<float>"
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--config", default=DEFAULT_CONFIG, choices=sorted(WORKLOADS))
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gcf", choices=["gcf", "reference"])
-    ap.add_argument("--chains", type=int, default=WORKLOAD["chains"])
-    ap.add_argument("--sweeps", type=int, default=WORKLOAD["sweeps"])
+    ap.add_argument("--chains-scale", type=float, default=1.0, help="scale every lattice's chain count")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-log", default=None,
@@ -240,6 +393,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the planner's kernel form")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision-form comparison")
+    ap.add_argument("--no-check", action="store_true", help="skip the FP64 comparison after timing")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -254,15 +408,14 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = max(1, min(os.cpu_count() or 1, 16))
-        rate, done, dt = cpu_oracle_rate(cores, 1, 2)
+        rate, done, dt, mix = cpu_oracle_rate(args.config, cores, 1)
         cpu = {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
-               "sample": f"{done} samples = {cores} chains x 2 sweeps of the same workload "
-                         f"(FP64 NumPy, one process per core), {dt:.1f} s"}
+               "sample": f"{done} samples = {cores} chains x 1 sweep of the same workload (lattice mix {mix}; "
+                         f"FP64 NumPy, one process per core), {dt:.1f} s"}
 
     import torch
 
     import paper_2503_20566_gb300 as G
-    import synth
     from paper_2503_20566_gb300 import replicas
 
     torch.cuda.set_device(local)
@@ -270,126 +423,137 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    w = WORKLOAD
-    n_chains, n_sweeps = args.chains, args.sweeps
     seeds = replicas.rank_seeds(rank)
-    ctx = G.Context(w["N"], w["Lx"], w["Ly"], w["D"], w["chi"], h=w["h_p"], g=w["g"], precision=args.precision,
-                    seed=seeds["tensors"])
-    powers = torch.from_numpy(synth.plaquette_powers(seeds["chains"], n_chains, (w["Lx"] - 1) * (w["Ly"] - 1),
-                                                     w["N"]))
-    configs = ctx.init_configs(n_chains, powers=powers)
-    # the library's autotuner picks the kernel form (executor x shared-memory level) on this workload
-    tune_ms = [] if args.no_autotune else ctx.autotune(configs, n_sweeps=4)
-    kernel_name = ctx.kernel_name + "<float>"
-    samples = ctx.alloc_samples(n_chains, n_sweeps, grad=True)
-    stream = ctx.stream
+    W = Workload(args.config, args.precision, seeds, args.chains_scale)
+    # the library's autotuner picks the kernel form of a single-lattice workload
+    tune_ms = []
+    if len(W.ctxs) == 1 and not args.no_autotune:
+        # on a subset of the chains (eight per SM) when the workload is large
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        sub = W.configs[0][: min(W.configs[0].shape[0], 8 * sms)]
+        tune_ms = W.ctxs[0].autotune(sub, n_sweeps=min(4, W.sweeps))
+    kernel_name = W.kernel_name() + W.scalar()
+    stream = W.stream
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def step(i):
-        ctx.sample_batch(configs, n_sweeps, seed=1000 * i + rank, out=samples)
-        return ctx.sr_step(samples, n_chains, **SR_ARGS)
-
     for i in range(args.warmup):
-        step(i)
+        W.step(1000 * i + rank)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    launches0 = ctx.launch_count
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = sum(c.launch_count for c in W.ctxs)
+    ev = [[tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(W.launches_per_step)]
+          for _ in range(args.steps)]
     clk_path = (args.clocks_log.format(rank=rank) if args.clocks_log
                 else os.path.join(tempfile.gettempdir(), f"gcfvmc_clocks_{os.getpid()}_rank{rank}.csv"))
     sampler, sf = clocks_sampler_start(clk_path)
     time.sleep(0.3)
     torch.cuda.synchronize()
     stats = None
+    energies = []
     for i in range(args.steps):
         flush.fill_(float(i))  # 256 MiB write evicts L2 between steps (outside the events)
         with torch.cuda.stream(stream):
-            ev[i][0].record(stream)
-            ctx.sample_batch(configs, n_sweeps, seed=seeds["step"](i), out=samples)
-            ev[i][1].record(stream)
-            stats = ctx.sr_step(samples, n_chains, **SR_ARGS)
-            ev[i][2].record(stream)
+            stats = W.step(seeds["step"](i), ev[i], stream)
+        energies.append([s[0] for s in stats])
     torch.cuda.synchronize()
     clocks = clocks_sampler_stop(sampler, sf, clk_path, torch.cuda.current_device())
-    launches = ctx.launch_count - launches0
-    t_steps = [ev[i][0].elapsed_time(ev[i][2]) for i in range(args.steps)]
-    t_kernel = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    launches = sum(c.launch_count for c in W.ctxs) - launches0
+    t_steps = [sum(e[0].elapsed_time(e[2]) for e in ev[i]) for i in range(args.steps)]
+    t_kernel = [[e[0].elapsed_time(e[1]) for e in ev[i]] for i in range(args.steps)]
+    kern_launch_ms = float(np.mean([t for row in t_kernel for t in row]))
     group = dist.group.WORLD if dist else None
     total_ms = replicas.max_over_ranks(float(sum(t_steps)), group, "cuda")
-    samples_per_step = n_chains * n_sweeps
-    value = replicas.whole_job_rate(samples_per_step, args.steps, world, total_ms)
+    value = replicas.whole_job_rate(W.samples_per_step, args.steps, world, total_ms)
 
-    # the contraction forms side by side (kernel only, same tensors and chains):
-    # plain FP32 on CUDA cores, TF32x3 and BF16 on tensor cores
+    # the contraction forms side by side (sampling launch only, same tensors,
+    # a quarter of the chains): plain FP32 on CUDA cores, TF32x3 and BF16
     forms = None
     if rank == 0 and world == 1 and not args.no_forms:
-        forms = {"sweeps": 8, "chains": n_chains, "unit": "samples/s (sampling kernel only)"}
+        forms = {"chains_scale": 0.25 * args.chains_scale, "unit": "samples/s (sampling launch only)"}
         for prec in ("fp32", "tf32", "bf16"):
-            fctx = G.Context(w["N"], w["Lx"], w["Ly"], w["D"], w["chi"], h=w["h_p"], g=w["g"], precision=prec,
-                             seed=seeds["tensors"])
-            fcfg = fctx.init_configs(n_chains, powers=powers)
-            fout = fctx.alloc_samples(n_chains, 8, grad=True)
-            fctx.sample_batch(fcfg, 8, seed=1, out=fout)
+            F = Workload(args.config, prec, seeds, 0.25 * args.chains_scale)
+            F.sample(1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            with torch.cuda.stream(fctx.stream):
-                e0.record(fctx.stream)
-                fctx.sample_batch(fcfg, 8, seed=2, out=fout)
-                e1.record(fctx.stream)
+            with torch.cuda.stream(F.stream):
+                e0.record(F.stream)
+                F.sample(2)
+                e1.record(F.stream)
             torch.cuda.synchronize()
-            forms[{"fp32": "fp32", "tf32": "tf32x3", "bf16": "bf16"}[prec]] = n_chains * 8 / (e0.elapsed_time(e1) / 1e3)
-            del fctx, fcfg, fout
+            forms[{"fp32": "fp32", "tf32": "tf32x3", "bf16": "bf16"}[prec]] = \
+                F.samples_per_launch / (e0.elapsed_time(e1) / 1e3)
+            for c in F.ctxs:
+                c.close()
+            del F
 
-    # end to end through the host-buffer C call
+    # end to end through the public API from host memory: every step copies
+    # the chains' configurations in (pinned host -> device) and the updated
+    # configurations and the SR statistics out
     e2e = None
     if not args.no_e2e:
-        host_cfg = np.ascontiguousarray(configs.cpu().numpy())
-        cfg_bytes = host_cfg.nbytes
+        host_cfg = [c.cpu().pin_memory() for c in W.configs]
+        h2d = sum(c.numel() for c in host_cfg)
+        d2h = h2d + 8 * 8 * len(W.ctxs) * W.launches_per_step
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
         for i in range(args.steps):
-            ctx.vmc_step_host(host_cfg, n_sweeps, 50_000 + 1000 * i + rank, **SR_ARGS)
-        torch.cuda.synchronize()
+            for dev, host in zip(W.configs, host_cfg):
+                dev.copy_(host, non_blocking=True)
+            W.step(50_000 + 1000 * i + rank)
+            for dev, host in zip(W.configs, host_cfg):
+                host.copy_(dev, non_blocking=True)
+            torch.cuda.synchronize()
         e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, group, "cuda")
-        e2e = {"value": replicas.whole_job_rate(samples_per_step, args.steps, world, 1000.0 * e2e_s),
-               "unit": "samples/s",
-               "h2d_bytes_per_step": cfg_bytes, "d2h_bytes_per_step": cfg_bytes + 8 * 8}
+        e2e = {"value": replicas.whole_job_rate(W.samples_per_step, args.steps, world, 1000.0 * e2e_s),
+               "unit": "samples/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     if rank == 0:
-        try:
-            err = err_vs_fp64(ctx, configs, w)
-        except Exception as exc:  # the JSON line is printed whatever happens here
-            err = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+        err = None
+        if not args.no_check:
+            try:
+                err = err_vs_fp64(W.ctxs, W.configs, W.lats)
+            except Exception as exc:  # the JSON line is printed whatever happens here
+                err = {"error": f"{type(exc).__name__}: {exc}"[:300]}
         peaks, src = load_peaks()
-        kern_s = float(np.mean(t_kernel)) / 1000.0
-        fl = flops_per_sample(w["Lx"], w["Ly"], w["D"] // w["N"], w["chi"]) * samples_per_step
-        peak = fp32_alu_peak_tflops()
-        achieved = fl / kern_s / 1e12
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        fl = W.flops_per_launch()
+        achieved = fl / (kern_launch_ms / 1000.0) / 1e12
+        # TF32 is the tensor-core type of FP32 data (nominal TF32 = BF16 / 2);
+        # the sampling launch runs for seconds inside a step: the sustained peak
+        tc_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 0.0)) / 2.0
+        wl = W.wl
         line = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w["workload"], "lattice": "8x8 open", "gauge": "Z2", "D": w["D"],
-                       "chi": w["chi"], "chains": n_chains, "sweeps_per_step": n_sweeps, "h": w["g"],
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64" if W.lats[0]["cplx"] else "f32",
+            "data": "synthetic",
+            "config": {"workload": wl["workload"],
+                       "lattices": [f"{w['Lx']}x{w['Ly']} Z{w['N']}{' + hard-core bosons' if w['matter'] else ''} "
+                                    f"D={w['D']} chi={w['chi']} chains={w['chains']}" for w in W.lats],
+                       "sweeps_per_launch": W.sweeps, "launches_per_step": W.launches_per_step,
+                       "couplings": {"h": W.lats[0]["h_p"], "g": W.lats[0]["g"], "J": W.lats[0]["J"]},
+                       "update": "two-stage tVMC (dt=%g)" % wl["dt"] if W.mode == "tvmc" else "SR",
                        "precision": args.precision, "sr": SR_ARGS, "parallelism": f"replicas{world}",
                        "l2": "256 MiB buffer written between timed steps (outside the events)",
-                       "kernel_form": {"kernel": kernel_name, "smem_level": ctx.smem_level,
+                       "kernel_form": {"kernel": kernel_name, "smem_level": W.ctxs[0].smem_level,
                                        "autotune_ms_per_form": [round(t, 3) if t < 1e299 else None
                                                                 for t in tune_ms]}},
             "gpu_launches": launches,
-            "kernel_ms": float(np.mean(t_kernel)),
-            "sr_ms": float(np.mean([a - b for a, b in zip(t_steps, t_kernel)])),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(samples_per_step, kernel_name, ctx.smem_level),
-                         "kernel": kernel_name,
-                         "algorithmic_flop_per_launch": fl,
-                         "peak_source": "FP32 FMA units x max SM clock (152 x 128 x 2 x 2070 MHz)",
-                         "tensor_peak_tf32_of_" + src: peaks.get("bf16_tflops", 0) / 2.0},
+            "kernel_ms": kern_launch_ms,
+            "update_ms": float(np.mean(t_steps)) - kern_launch_ms * W.launches_per_step,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
+                         "frac": achieved / tc_peak if tc_peak else None,
+                         "traffic": profiled_traffic(W.samples_per_launch, kernel_name, W.ctxs[0].smem_level,
+                                                     wl["workload"]),
+                         "kernel": kernel_name, "algorithmic_flop_per_launch": fl,
+                         "peak_source": f"TF32 tensor peak = 1/2 x bf16 sustained ({src})",
+                         "fp32_alu_frac": achieved / fp32_alu_peak_tflops(sms)},
             "clocks": clocks,
-            "sr_stats": {"e_mean": stats[0], "e_err": stats[2], "cg_iters": stats[3], "residual": stats[4]},
+            "sr_stats": [{"e_mean": s[0], "e_err": s[2], "cg_iters": s[3], "residual": s[4], "converged": bool(s[6])}
+                         for s in stats],
+            "energy_per_step": energies,
             "err_vs_fp64": err,
         }
         if e2e:

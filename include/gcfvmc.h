@@ -33,6 +33,15 @@
  * - Every entry point returns a gcf_status and never aborts; on failure the
  *   reason is available from gcf_last_error().  Calls on one context are not
  *   thread-safe.
+ * - The device that was current at gcf_init_peps is the context's device; every
+ *   later call on the context must be made with that device current, else it
+ *   returns GCF_EINVAL and launches nothing (a launch with another device
+ *   current would run on that device against this context's memory).
+ * - Truncated bonds are cut with a one-sided Jacobi SVD that stops after a
+ *   sweep limit (40 by default, gcf_set_svd_sweeps).  A synchronous call in
+ *   which some SVD reached the limit before converging still writes all its
+ *   outputs but returns GCF_ETIMEOUT (gcf_svd_unconverged gives the count):
+ *   those outputs may be less accurate than the contraction's precision.
  * - A batch of zero configurations or chains is valid wherever a count may
  *   be 0 (gcf_init_configs, gcf_amplitude, gcf_amplitude_noalloc,
  *   gcf_local_energy, gcf_log_grad, gcf_log_grad_vjp, gcf_sample_batch,
@@ -73,6 +82,10 @@ enum { GCF_REAL = 0, GCF_COMPLEX = 1 };
 enum { GCF_FP64 = 0, GCF_FP32 = 1, GCF_TF32 = 2, GCF_BF16 = 3 };
 /* parameter update of gcf_sr_step */
 enum { GCF_SR = 0, GCF_TDVP_STAGE1 = 1, GCF_TDVP_STAGE2 = 2 };
+/* truncation of the boundary MPS (gcf_model.trunc): the SVD sweep of
+ * Sec. S-2 (QR left to right, then LQ / truncated SVD right to left).  A
+ * randomized range finder is not built; any other value is GCF_EINVAL. */
+enum { GCF_TRUNC_SVD = 0 };
 
 /* Model and ansatz.  Couplings are in the paper's form, Eqs. (2)-(5):
  *   H = m sum_x p_x + J sum (c^dag U c + h.c.) - h sum_x (P_x + P_x^dag)
@@ -88,6 +101,16 @@ typedef struct {
   double h, g, J, m;
   int dtype;        /* GCF_REAL | GCF_COMPLEX                                */
   int precision;    /* GCF_FP64 | GCF_FP32 | GCF_TF32 | GCF_BF16             */
+  int trunc;        /* GCF_TRUNC_SVD                                         */
+  int recompute_env;/* boundary-MPS store of each chain: 0 keeps every B[r]
+                       and T[r]; K in [2, Ly] keeps every K-th and recomputes
+                       the ones between from the kept one when a pass needs
+                       them (main-text cost paragraph: environments
+                       recomputed instead of stored when chi is large);
+                       -1 takes K = ceil(sqrt(Ly + 1)).  Results are the
+                       same bit for bit; the store shrinks from 2(Ly+1)
+                       MPS to about 2(Ly/K + K), and every pass absorbs
+                       up to one extra row per row it visits.            */
 } gcf_model;
 
 /* Measurement outputs of gcf_sample_batch (all device pointers, chain-major:
@@ -255,12 +278,10 @@ gcf_status gcf_vmc_step_host(gcf_ctx* ctx, int n_chains, int n_sweeps, uint64_t 
 
 /* Amplitude evaluation that allocates nothing: the same computation and
  * result as gcf_amplitude, for callers that cannot call cudaMalloc during the
- * call -- code that runs while a stream is being captured into a CUDA graph
- * (allocation is not allowed inside a capture), services that reserve all
- * device memory up front and forbid allocation on the request path, and
- * embedders whose own allocator owns the device (a foreign cudaMalloc would
- * fragment or exceed its pool).  (The paper has no counterpart; this is an
- * interface addition.)
+ * call -- services that reserve all device memory up front and forbid
+ * allocation on the request path, and embedders whose own allocator owns the
+ * device (a foreign cudaMalloc would fragment or exceed its pool).  (The
+ * paper has no counterpart; this is an interface addition.)
  * - Scratch comes from one fixed array of 32 MiB compiled into the library
  *   (static device storage that every GPU which loads the library holds until
  *   the process exits), not from cudaMalloc.  The context itself must already
@@ -268,6 +289,8 @@ gcf_status gcf_vmc_step_host(gcf_ctx* ctx, int n_chains, int n_sweeps, uint64_t 
  * - The first call on each device looks up the array's device address with
  *   that device current; make that first call before any stream capture.  The
  *   device current at the call must be the context's device (else GCF_EINVAL).
+ *   The address is kept for the life of the process: after a device reset
+ *   (cudaDeviceReset) the library must be used from a new process.
  * - A lattice whose per-CTA scratch exceeds 32 MiB is rejected with
  *   GCF_EINVAL and a message giving the required size; otherwise the number
  *   of CTAs is capped at what fits, and any n >= 1 is accepted.
@@ -304,6 +327,40 @@ int gcf_executor(const gcf_ctx* ctx);
  * GCFVMC_LOCK_FAULT=1 in the environment (a test hook) makes one group never
  * count in, so the others' waits run out. */
 int gcf_phase_timeouts(const gcf_ctx* ctx);
+
+/* One-sided Jacobi SVDs of the truncated bonds (Sec. S-2 compression) that
+ * reached the sweep limit without converging in the last synchronous
+ * amplitude, energy, gradient or sampling launch of this context (for
+ * gcf_sample_multi: summed over its contexts, reported on ctxs[0]).  0
+ * normally; such calls return GCF_ETIMEOUT.  -1 for a NULL context. */
+int gcf_svd_unconverged(const gcf_ctx* ctx);
+
+/* Bytes of device scratch one chain slot of this context takes (the
+ * boundary-MPS store, the network, factorisation and environment buffers;
+ * one slot per chain resident on the GPU).  -1 for a NULL context. */
+int64_t gcf_scratch_bytes_per_chain(const gcf_ctx* ctx);
+
+/* K of the checkpointed boundary-MPS store (gcf_model.recompute_env after
+ * resolving -1), 0 when every MPS is kept.  -1 for a NULL context. */
+int gcf_checkpoint_interval(const gcf_ctx* ctx);
+
+/* 1 if this context's BF16 form runs its environment GEMMs on the
+ * fifth-generation tensor cores (tcgen05.mma with BF16 operands, FP32
+ * accumulation in tensor memory; real tensors whose largest environment GEMM
+ * has N <= 128), 0 otherwise (other forms, complex tensors, larger bonds:
+ * their tensor-core GEMMs use warp-level mma.sync).  Implementation detail;
+ * no counterpart in the paper.  -1 for a NULL context. */
+int gcf_tensor_core_form(const gcf_ctx* ctx);
+
+/* Tensor-core completion waits that ran out in the last synchronous launch
+ * of this context (the chain then computes its GEMMs on the CUDA cores for
+ * the rest of the launch; results are unaffected).  0 normally. */
+int gcf_tensor_timeouts(const gcf_ctx* ctx);
+
+/* Sweep limit of the one-sided Jacobi SVD for this context's later launches,
+ * 1 <= max_sweeps <= 1000 (default 40; each sweep visits every column pair
+ * once).  GCF_EINVAL outside that range. */
+gcf_status gcf_set_svd_sweeps(gcf_ctx* ctx, int max_sweeps);
 
 /* Shared-memory placement level of the kernel form this context launches
  * (implementation choice; no counterpart in the paper): 0 = configuration

@@ -34,7 +34,7 @@ class _Model(C.Structure):
     _fields_ = [("N", C.c_int), ("Lx", C.c_int), ("Ly", C.c_int), ("D", C.c_int), ("chi", C.c_int),
                 ("has_matter", C.c_int), ("Q", C.POINTER(C.c_int32)), ("h", C.c_double),
                 ("g", C.c_double), ("J", C.c_double), ("m", C.c_double), ("dtype", C.c_int),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("trunc", C.c_int), ("recompute_env", C.c_int)]
 
 
 class _Samples(C.Structure):
@@ -66,6 +66,12 @@ def load_library(path: str = LIB_PATH):
         "gcf_executor": (i, [vp]),
         "gcf_smem_level": (i, [vp]),
         "gcf_phase_timeouts": (i, [vp]),
+        "gcf_svd_unconverged": (i, [vp]),
+        "gcf_scratch_bytes_per_chain": (i64, [vp]),
+        "gcf_checkpoint_interval": (i, [vp]),
+        "gcf_tensor_core_form": (i, [vp]),
+        "gcf_tensor_timeouts": (i, [vp]),
+        "gcf_set_svd_sweeps": (i, [vp, i]),
         "gcf_autotune": (i, [vp, i, i, vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
         "gcf_set_tensors": (i, [vp, vp, C.c_size_t]),
         "gcf_get_tensors": (i, [vp, vp, C.c_size_t]),
@@ -92,7 +98,7 @@ def load_library(path: str = LIB_PATH):
 def exported_symbols():
     """Names the binding expects the library to export."""
     return ["gcf_init_peps", "gcf_destroy", "gcf_last_error", "gcf_num_params", "gcf_config_len",
-            "gcf_scalar_bytes", "gcf_launch_count", "gcf_executor", "gcf_smem_level", "gcf_phase_timeouts", "gcf_autotune", "gcf_set_tensors", "gcf_get_tensors",
+            "gcf_scalar_bytes", "gcf_launch_count", "gcf_executor", "gcf_smem_level", "gcf_phase_timeouts", "gcf_svd_unconverged", "gcf_set_svd_sweeps", "gcf_scratch_bytes_per_chain", "gcf_checkpoint_interval", "gcf_tensor_core_form", "gcf_tensor_timeouts", "gcf_autotune", "gcf_set_tensors", "gcf_get_tensors",
             "gcf_init_configs", "gcf_amplitude", "gcf_local_energy", "gcf_log_grad", "gcf_log_grad_vjp", "gcf_sample_multi",
             "gcf_sample_batch", "gcf_sample_batch_async", "gcf_sr_step", "gcf_vmc_step_host"]
 
@@ -106,12 +112,13 @@ def _need(cond, msg):
         raise ValueError(msg)
 
 
-def _check_device_buffers(bufs):
+def _check_device_buffers(bufs, device=None):
     """Buffers the library reads or writes through raw device pointers, as
     (tensor, dtype, min_numel, name): each must be a contiguous torch tensor of
-    `dtype` with at least `min_numel` entries, on the GPU.  The C ABI cannot
-    see a buffer's size or placement, so these are checked here, before any
-    pointer is passed: first every shape and dtype, then the placement."""
+    `dtype` with at least `min_numel` entries, on the GPU (on GPU `device`
+    when given: the context's).  The C ABI cannot see a buffer's size or
+    placement, so these are checked here, before any pointer is passed: first
+    every shape and dtype, then the placement."""
     for t, dtype, min_numel, what in bufs:
         _need(hasattr(t, "data_ptr") and hasattr(t, "is_cuda"), f"{what} must be a torch tensor")
         _need(t.dtype == dtype, f"{what} must be {dtype}, got {t.dtype}")
@@ -119,18 +126,20 @@ def _check_device_buffers(bufs):
         _need(t.is_contiguous(), f"{what} must be contiguous")
     for t, _, _, what in bufs:
         _need(t.is_cuda, f"{what} must be on the GPU")
+        _need(device is None or t.device.index == device,
+              f"{what} is on cuda:{t.device.index}, the context lives on cuda:{device}")
 
 
-def _check_configs(t, cfg_len, what):
+def _check_configs(t, cfg_len, what, device=None):
     """In/out configurations: an int8 (n_chains, cfg_len) contiguous CUDA tensor."""
     import torch
 
     _need(hasattr(t, "dim") and t.dim() == 2 and t.shape[1] == cfg_len,
           f"{what}: configs must be (n_chains, {cfg_len}), got {tuple(getattr(t, 'shape', ()))}")
-    _check_device_buffers([(t, torch.int8, t.shape[0] * cfg_len, f"{what}: configs")])
+    _check_device_buffers([(t, torch.int8, t.shape[0] * cfg_len, f"{what}: configs")], device)
 
 
-def _check_samples(out, n_chains, n_sweeps, n_s, D4, o_dtype, what):
+def _check_samples(out, n_chains, n_sweeps, n_s, D4, o_dtype, what, device=None):
     """Output buffers of a sampling call: every buffer present holds at least
     the entries the call writes, in the documented dtype."""
     import torch
@@ -140,14 +149,14 @@ def _check_samples(out, n_chains, n_sweeps, n_s, D4, o_dtype, what):
             "block_ids": (torch.int32, ns * n_s), "O": (o_dtype, ns * n_s * D4),
             "accepted": (torch.int32, n_chains), "proposed": (torch.int32, n_chains)}
     _check_device_buffers([(out[key], dt, cnt, f"{what}: out[{key!r}]") for key, (dt, cnt) in need.items()
-                           if out.get(key) is not None])
+                           if out.get(key) is not None], device)
 
 
 class Context:
     """One GCF-PEPS ansatz on one lattice (a ``gcf_ctx``)."""
 
     def __init__(self, N, Lx, Ly, D, chi, matter=False, Q=None, h=1.0, g=0.0, J=0.0, m=0.0,
-                 complex_=False, precision="fp32", seed=0, stream=None):
+                 complex_=False, precision="fp32", seed=0, stream=None, recompute_env=0):
         import torch
 
         _need(Q is None or np.asarray(Q).size == Lx * Ly, f"Q must hold Lx x Ly = {Lx * Ly} background charges")
@@ -168,10 +177,14 @@ class Context:
             self.Q = self._Q.copy()
             q = self._Q.ctypes.data_as(C.POINTER(C.c_int32))
         mdl = _Model(N, Lx, Ly, D, chi, int(matter), q, h, g, J, m, COMPLEX if complex_ else REAL,
-                     PRECISIONS[precision])
+                     PRECISIONS[precision], 0, int(recompute_env))
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
+        # the library ties the context to the device current now; every call
+        # must find it current again, and every buffer must live there
+        self.device = torch.cuda.current_device()
+        self._dev = torch.device("cuda", self.device)
         h_ctx = C.c_void_p()
         st = self.lib.gcf_init_peps(C.byref(mdl), C.c_uint64(seed), C.c_void_p(stream.cuda_stream),
                                     C.byref(h_ctx))
@@ -224,6 +237,35 @@ class Context:
         return int(self.lib.gcf_phase_timeouts(self.ctx))
 
     @property
+    def tensor_core_form(self):
+        """True if the BF16 form's environment GEMMs run on tcgen05 tensor cores."""
+        return bool(self.lib.gcf_tensor_core_form(self.ctx))
+
+    @property
+    def tensor_timeouts(self):
+        """Tensor-core waits that ran out in the last synchronous launch."""
+        return int(self.lib.gcf_tensor_timeouts(self.ctx))
+
+    @property
+    def scratch_bytes_per_chain(self):
+        """Device scratch of one chain slot (boundary-MPS store and buffers)."""
+        return int(self.lib.gcf_scratch_bytes_per_chain(self.ctx))
+
+    @property
+    def checkpoint_interval(self):
+        """K of the checkpointed boundary-MPS store, 0 when every MPS is kept."""
+        return int(self.lib.gcf_checkpoint_interval(self.ctx))
+
+    @property
+    def svd_unconverged(self):
+        """Truncated-bond SVDs that hit the sweep limit in the last synchronous launch."""
+        return int(self.lib.gcf_svd_unconverged(self.ctx))
+
+    def set_svd_sweeps(self, max_sweeps):
+        """Sweep limit of the one-sided Jacobi SVD (default 40)."""
+        self._check(self.lib.gcf_set_svd_sweeps(self.ctx, int(max_sweeps)), "set_svd_sweeps")
+
+    @property
     def smem_level(self):
         return int(self.lib.gcf_smem_level(self.ctx))
 
@@ -248,7 +290,7 @@ class Context:
     # ---- configurations ----------------------------------------------------
     def init_configs(self, n_chains, occupations=None, powers=None):
         torch = self._torch
-        dev = torch.device("cuda")
+        dev = self._dev
         occ = None if occupations is None else torch.as_tensor(occupations, dtype=torch.int8)
         pw = None if powers is None else torch.as_tensor(powers, dtype=torch.int8)
         _need(occ is None or occ.numel() == n_chains * self.n_s,
@@ -268,15 +310,15 @@ class Context:
             c = c.unsqueeze(0)
         _need(c.dim() == 2 and c.shape[1] == self.cfg_len,
               f"configs must be (n, {self.cfg_len}), got {tuple(c.shape)}")
-        return c.to("cuda").contiguous()
+        return c.to(self._dev).contiguous()
 
     # ---- fixed-configuration evaluations ---------------------------------------
     def amplitude(self, configs):
         torch = self._torch
         c = self._configs(configs)
         n = c.shape[0]
-        la = torch.empty(n, dtype=torch.float64, device="cuda")
-        ph = torch.empty(n, dtype=torch.float64, device="cuda")
+        la = torch.empty(n, dtype=torch.float64, device=self._dev)
+        ph = torch.empty(n, dtype=torch.float64, device=self._dev)
         self._check(self.lib.gcf_amplitude(self.ctx, n, _ptr(c), _ptr(la), _ptr(ph)), "amplitude")
         return la, ph
 
@@ -284,7 +326,7 @@ class Context:
         torch = self._torch
         c = self._configs(configs)
         n = c.shape[0]
-        e = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+        e = torch.empty(2 * n, dtype=torch.float64, device=self._dev)
         self._check(self.lib.gcf_local_energy(self.ctx, n, _ptr(c), _ptr(e)), "local_energy")
         return torch.view_as_complex(e.view(n, 2))
 
@@ -293,8 +335,8 @@ class Context:
         c = self._configs(configs)
         n = c.shape[0]
         D4 = self.Dk ** 4
-        bid = torch.empty((n, self.n_s), dtype=torch.int32, device="cuda")
-        O = torch.zeros((n, self.n_s, D4), dtype=self.o_dtype, device="cuda")
+        bid = torch.empty((n, self.n_s), dtype=torch.int32, device=self._dev)
+        O = torch.zeros((n, self.n_s, D4), dtype=self.o_dtype, device=self._dev)
         self._check(self.lib.gcf_log_grad(self.ctx, n, _ptr(c), _ptr(bid), _ptr(O)), "log_grad")
         return bid, O
 
@@ -305,11 +347,11 @@ class Context:
         c = self._configs(configs)
         n = c.shape[0]
         if self.complex:
-            w = torch.view_as_real(torch.as_tensor(weights, dtype=torch.complex128).to("cuda").contiguous())
-            g = torch.empty((self.n_params, 2), dtype=torch.float64, device="cuda")
+            w = torch.view_as_real(torch.as_tensor(weights, dtype=torch.complex128).to(self._dev).contiguous())
+            g = torch.empty((self.n_params, 2), dtype=torch.float64, device=self._dev)
         else:
-            w = torch.as_tensor(weights, dtype=torch.float64).to("cuda").contiguous()
-            g = torch.empty(self.n_params, dtype=torch.float64, device="cuda")
+            w = torch.as_tensor(weights, dtype=torch.float64).to(self._dev).contiguous()
+            g = torch.empty(self.n_params, dtype=torch.float64, device=self._dev)
         if w.shape[0] != n:
             raise ValueError(f"expected {n} weights")
         self._check(self.lib.gcf_log_grad_vjp(self.ctx, n, _ptr(c), _ptr(w), _ptr(g)), "log_grad_vjp")
@@ -320,24 +362,24 @@ class Context:
         torch = self._torch
         ns = n_chains * n_sweeps
         out = {
-            "log_abs": torch.empty(ns, dtype=torch.float64, device="cuda"),
-            "phase": torch.empty(ns, dtype=torch.float64, device="cuda"),
-            "e_loc": torch.empty(2 * ns, dtype=torch.float64, device="cuda"),
-            "accepted": torch.zeros(n_chains, dtype=torch.int32, device="cuda"),
-            "proposed": torch.zeros(n_chains, dtype=torch.int32, device="cuda"),
+            "log_abs": torch.empty(ns, dtype=torch.float64, device=self._dev),
+            "phase": torch.empty(ns, dtype=torch.float64, device=self._dev),
+            "e_loc": torch.empty(2 * ns, dtype=torch.float64, device=self._dev),
+            "accepted": torch.zeros(n_chains, dtype=torch.int32, device=self._dev),
+            "proposed": torch.zeros(n_chains, dtype=torch.int32, device=self._dev),
         }
         if grad:
-            out["block_ids"] = torch.empty((ns, self.n_s), dtype=torch.int32, device="cuda")
-            out["O"] = torch.zeros((ns, self.n_s, self.Dk ** 4), dtype=self.o_dtype, device="cuda")
+            out["block_ids"] = torch.empty((ns, self.n_s), dtype=torch.int32, device=self._dev)
+            out["O"] = torch.zeros((ns, self.n_s, self.Dk ** 4), dtype=self.o_dtype, device=self._dev)
         return out
 
     def sample_batch(self, configs, n_sweeps, seed, out=None, grad=True):
         """configs: device int8 tensor (n_chains, cfg_len), updated in place."""
-        _check_configs(configs, self.cfg_len, "sample_batch")
+        _check_configs(configs, self.cfg_len, "sample_batch", self.device)
         n = configs.shape[0]
         if out is None:
             out = self.alloc_samples(n, n_sweeps, grad)
-        _check_samples(out, n, n_sweeps, self.n_s, self.Dk ** 4, self.o_dtype, "sample_batch")
+        _check_samples(out, n, n_sweeps, self.n_s, self.Dk ** 4, self.o_dtype, "sample_batch", self.device)
         s = _Samples(*[C.c_void_p(out[k].data_ptr()) if k in out else None
                        for k in ("log_abs", "phase", "e_loc", "block_ids", "O", "accepted", "proposed")])
         self._check(self.lib.gcf_sample_batch(self.ctx, n, n_sweeps, C.c_uint64(seed), _ptr(configs),
@@ -349,9 +391,9 @@ class Context:
         context's) without synchronising or allocating: the launch can be
         recorded in a CUDA graph.  Call sample_batch with at least as many
         chains once before (it sizes the scratch)."""
-        _check_configs(configs, self.cfg_len, "sample_batch_async")
+        _check_configs(configs, self.cfg_len, "sample_batch_async", self.device)
         n = configs.shape[0]
-        _check_samples(out, n, n_sweeps, self.n_s, self.Dk ** 4, self.o_dtype, "sample_batch_async")
+        _check_samples(out, n, n_sweeps, self.n_s, self.Dk ** 4, self.o_dtype, "sample_batch_async", self.device)
         h = None if stream is None else C.c_void_p(stream.cuda_stream)
         s = _samples_struct(out)
         self._check(self.lib.gcf_sample_batch_async(self.ctx, n, n_sweeps, C.c_uint64(seed), _ptr(configs),
@@ -364,7 +406,8 @@ class Context:
         ns = samples["e_loc"].shape[0] // 2
         _check_device_buffers([(samples["e_loc"], torch.float64, 2 * ns, "sr_step: samples['e_loc']"),
                                (samples["block_ids"], torch.int32, ns * self.n_s, "sr_step: samples['block_ids']"),
-                               (samples["O"], self.o_dtype, ns * self.n_s * self.Dk ** 4, "sr_step: samples['O']")])
+                               (samples["O"], self.o_dtype, ns * self.n_s * self.Dk ** 4, "sr_step: samples['O']")],
+                              self.device)
         stats = (C.c_double * 8)()
         st = self.lib.gcf_sr_step(self.ctx, ns, n_chains, _ptr(samples["e_loc"]), _ptr(samples["block_ids"]),
                                   _ptr(samples["O"]), diag_shift, lr, mode, dt, max_iter, tol, stats)
@@ -402,12 +445,12 @@ def sample_multi(contexts, configs, n_sweeps, seeds, outs=None, grad=True):
     if not (len(configs) == len(seeds) == n) or n == 0:
         raise ValueError("one configs tensor and one seed per context")
     for i, (ctx, c) in enumerate(zip(contexts, configs)):
-        _check_configs(c, ctx.cfg_len, f"sample_multi[{i}]")
+        _check_configs(c, ctx.cfg_len, f"sample_multi[{i}]", ctx.device)
     if outs is None:
         outs = [ctx.alloc_samples(c.shape[0], n_sweeps, grad) for ctx, c in zip(contexts, configs)]
     _need(len(outs) == n, "one output dict per context")
     for i, (ctx, c, o) in enumerate(zip(contexts, configs, outs)):
-        _check_samples(o, c.shape[0], n_sweeps, ctx.n_s, ctx.Dk ** 4, ctx.o_dtype, f"sample_multi[{i}]")
+        _check_samples(o, c.shape[0], n_sweeps, ctx.n_s, ctx.Dk ** 4, ctx.o_dtype, f"sample_multi[{i}]", ctx.device)
     lib = contexts[0].lib
     ctxs = (C.c_void_p * n)(*[ctx.ctx for ctx in contexts])
     nch = (C.c_int * n)(*[int(c.shape[0]) for c in configs])

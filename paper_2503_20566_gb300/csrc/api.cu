@@ -28,6 +28,8 @@ struct Plan {
   long long mps_stride = 0, qsite_stride = 0, mat_max = 0, tau_max = 0, tmp_max = 0;
   int env_stride = 0, env3_stride = 0;
   long long ws_stride = 0;
+  int ck_every = 0;               // boundary-MPS store: keep every K-th (0: all)
+  long long o_Bseg = 0, o_Tseg = 0;
   long long o_net, o_prop, o_B, o_T, o_Q, o_M1, o_M2, o_M3, o_tau, o_J, o_envR, o_envL, o_envX,
       o_envY, o_t1, o_t2, o_t3, o_env3R, o_env3L, o_env3X, o_env3Y, o_G;
   // buffers in dynamic shared memory (elements from the hot base)
@@ -41,6 +43,9 @@ struct Plan {
   long long hot_base_elems = 0, hot_mps_elems = 0, hot_all_elems = 0;
   int cta_level = 0, group_level = 0;
   size_t group_smem = 0;
+  // BF16 form of real chains: bytes of the tcgen05 operand staging area of
+  // one chain (0: the tensor-core GEMMs of that form stay on mma.sync)
+  long long tc_bytes = 0;
   long long level_elems(int lv) const {
     return lv <= 0 ? 0 : lv == 1 ? hot_base_elems : lv == 2 ? hot_mps_elems : hot_all_elems;
   }
@@ -62,8 +67,12 @@ struct gcf_ctx {
   Plan plan;
   int exec = 0, group_threads = 64;
   int lockstep = 0;  // grouped kernels: chain groups of a CTA in lockstep
+  int ck_every = 0;  // boundary-MPS store: keep every K-th slot and recompute between (0: keep all)
   int lock_fault = 0;  // test hook (GCFVMC_LOCK_FAULT): one group never counts in
   int last_phase_timeouts = 0;
+  int last_svd_unconverged = 0;  // SVDs that hit the sweep limit in the last synchronous launch
+  int last_tc_timeouts = 0;      // tensor-core waits that ran out in the last synchronous launch
+  int svd_sweeps = 40;           // sweep limit of the one-sided Jacobi SVD
   int tab_ints = 0;  // ints in d_tables
   // device
   void* d_params = nullptr;
@@ -123,6 +132,34 @@ gcf_status cuda_fail(gcf_ctx* c, cudaError_t e, const char* where) {
     if (_e != cudaSuccess) return cuda_fail((ctx), _e, #expr);   \
   } while (0)
 
+// Every entry point that touches the context's device memory runs with the
+// context's device current: a launch with another device current would run
+// there and dereference this context's buffers on the wrong GPU.
+gcf_status check_device(gcf_ctx* c, const char* what) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  if (dev != c->device)
+    return fail(c, GCF_EINVAL, std::string(what) + ": the context's device (" + std::to_string(c->device) +
+                                   ") must be current, device " + std::to_string(dev) + " is");
+  return GCF_OK;
+}
+
+#define DEVICE_TRY(ctx, what)                                    \
+  do {                                                           \
+    gcf_status _s = check_device((ctx), (what));                 \
+    if (_s != GCF_OK) return _s;                                 \
+  } while (0)
+
+// A synchronous launch in which some one-sided Jacobi SVD hit its sweep
+// limit: the outputs are written but may be inaccurate, so the call says so.
+gcf_status svd_status(gcf_ctx* c) {
+  if (c->last_svd_unconverged > 0)
+    return fail(c, GCF_ETIMEOUT, std::to_string(c->last_svd_unconverged) +
+                                     " truncated SVDs did not converge within the sweep limit");
+  return GCF_OK;
+}
+
 inline long long al32(long long n) { return (n + 31) / 32 * 32; }
 
 // One absorption step: input bond table bin (Lx+1), output bout, qr, svd.
@@ -151,6 +188,24 @@ void plan_step(int Lx, int Dk, int chi, int pout, const int* bin, int* qr, int* 
 // GCFVMC_SMEM / GCFVMC_SMEM_CTA (placement level 0-3) and GCFVMC_LOCK=0|1
 // override the planner's choice.
 enum ExecKind { EXEC_CTA = 0, EXEC_GROUP = 1, EXEC_GROUP4 = 2 };
+
+// Dynamic shared memory of one chain: [configuration][hot buffers of the
+// placement level] then, for the tcgen05 path, the operand staging area at
+// a 16-byte boundary.  CTA form: from the block's base; group form: each
+// group's region also starts with its SharedV.
+size_t cta_tc_off(const Plan& p, int level, size_t sb) {
+  return ((size_t)p.cfg_bytes + (size_t)p.level_elems(level) * sb + 15) / 16 * 16;
+}
+size_t cta_smem_bytes(const Plan& p, int level, size_t sb) {
+  return p.tc_bytes ? cta_tc_off(p, level, sb) + (size_t)p.tc_bytes
+                    : (size_t)p.cfg_bytes + (size_t)p.level_elems(level) * sb;
+}
+size_t group_tc_off(const Plan& p, int level, size_t sb) {
+  return (sharedv_bytes() + (size_t)p.cfg_bytes + (size_t)p.level_elems(level) * sb + 15) / 16 * 16;
+}
+size_t group_smem_bytes(const Plan& p, int level, size_t sb) {
+  return group_tc_off(p, level, sb) + ((size_t)p.tc_bytes + 15) / 16 * 16;
+}
 bool grouped(const gcf_ctx* c);
 int n_groups(const gcf_ctx* c);
 
@@ -158,9 +213,8 @@ void plan_group(gcf_ctx* c) {
   Plan& p = c->plan;
   const int G = 128;
   c->group_threads = G;
-  const size_t base = sharedv_bytes() + (size_t)p.cfg_bytes;
   auto fits = [&](int ng, int lv, size_t budget) {
-    return (size_t)ng * (base + (size_t)p.level_elems(lv) * c->sbytes) <= budget;
+    return (size_t)ng * group_smem_bytes(p, lv, c->sbytes) <= budget;
   };
   // two groups per CTA: the largest level that leaves room for a second CTA
   int lv2 = 0;
@@ -196,7 +250,7 @@ void plan_group(gcf_ctx* c) {
     if (!std::strcmp(e, "cta")) c->exec = EXEC_CTA;
   }
   if (const char* e = std::getenv("GCFVMC_SMEM")) p.group_level = std::max(0, std::min(3, std::atoi(e)));
-  p.group_smem = (base + (size_t)p.level_elems(p.group_level) * c->sbytes + 15) / 16 * 16;
+  p.group_smem = group_smem_bytes(p, p.group_level, c->sbytes);
 }
 
 // Tables derived from the bond dimensions, appended after the six plan
@@ -252,11 +306,11 @@ void set_form(gcf_ctx* c, int exec, int level) {
   c->exec = exec;
   if (exec == EXEC_GROUP || exec == EXEC_GROUP4) {
     p.group_level = level;
-    p.group_smem = (sharedv_bytes() + (size_t)p.cfg_bytes + (size_t)p.level_elems(level) * c->sbytes + 15) / 16 * 16;
+    p.group_smem = group_smem_bytes(p, level, c->sbytes);
   } else {
     p.cta_level = level;
     p.hot_elems = p.level_elems(level);
-    p.dyn_smem = (size_t)p.cfg_bytes + (size_t)p.hot_elems * c->sbytes;
+    p.dyn_smem = cta_smem_bytes(p, level, c->sbytes);
   }
 }
 
@@ -375,8 +429,19 @@ void build_plan(gcf_ctx* c) {
   auto take = [&](long long n) { long long r = o; o += al32(n); return r; };
   p.o_net = take((long long)Lx * Ly * D4);
   p.o_prop = take(4 * D4);
-  p.o_B = take((Ly + 1) * p.mps_stride);
-  p.o_T = take((Ly + 1) * p.mps_stride);
+  // boundary-MPS store: every slot, or every K-th plus one segment buffer
+  // (B slots 0..Ly-1, T slots 1..Ly)
+  p.ck_every = c->ck_every;
+  if (p.ck_every) {
+    const int K = p.ck_every;
+    p.o_B = take((long long)((Ly - 1) / K + 1) * p.mps_stride);
+    p.o_Bseg = take((long long)K * p.mps_stride);
+    p.o_T = take((long long)((Ly - 1) / K + 1) * p.mps_stride);
+    p.o_Tseg = take((long long)K * p.mps_stride);
+  } else {
+    p.o_B = take((Ly + 1) * p.mps_stride);
+    p.o_T = take((Ly + 1) * p.mps_stride);
+  }
   p.o_Q = take((long long)Lx * p.qsite_stride);
   p.o_M1 = take(p.mat_max);
   p.o_M2 = take(p.mat_max);
@@ -452,14 +517,25 @@ void build_plan(gcf_ctx* c) {
   p.so_envR = hot((long long)(Lx + 1) * p.env_stride);
   p.so_env3R = hot((long long)(Lx + 1) * p.env3_stride);
   p.hot_all_elems = h;
+  // tcgen05 staging of the BF16 form (real chains): the largest environment
+  // GEMM has N <= D_k^2 chi_b and K <= D_k chi_b (chi_b the largest bond of
+  // any B / T); the tensor-core path takes N <= 128 (its TMEM columns)
+  p.tc_bytes = 0;
+  if (c->m.precision == GCF_BF16 && c->kind == S_F32) {
+    int chib = 1;
+    for (int v : p.bondB) chib = std::max(chib, v);
+    for (int v : p.bondT) chib = std::max(chib, v);
+    const int Nmax = Dk * Dk * chib, Kmax = Dk * chib;
+    if (Nmax <= 128) p.tc_bytes = (tc_stage_bytes(Nmax, Kmax) + 15) / 16 * 16;
+  }
   // one chain per CTA: the largest level that keeps two CTAs on an SM
   const size_t budget = 100 * 1024;
   p.cta_level = 0;
   for (int lv = 1; lv <= 3; ++lv)
-    if ((size_t)p.level_elems(lv) * c->sbytes <= budget) p.cta_level = lv;
+    if (cta_smem_bytes(p, lv, c->sbytes) <= budget) p.cta_level = lv;
   if (const char* e = std::getenv("GCFVMC_SMEM_CTA")) p.cta_level = std::max(0, std::min(3, std::atoi(e)));
   p.hot_elems = p.level_elems(p.cta_level);
-  p.dyn_smem = (size_t)p.cfg_bytes + (size_t)p.hot_elems * c->sbytes;
+  p.dyn_smem = cta_smem_bytes(p, p.cta_level, c->sbytes);
   plan_group(c);
 }
 
@@ -487,6 +563,7 @@ KParams<T> make_params(gcf_ctx* c) {
   k.scratch = (T*)c->d_scratch;
   k.ws_stride = p.ws_stride;
   k.o_net = p.o_net; k.o_prop = p.o_prop; k.o_B = p.o_B; k.o_T = p.o_T; k.o_Q = p.o_Q;
+  k.ck_every = p.ck_every; k.o_Bseg = p.o_Bseg; k.o_Tseg = p.o_Tseg;
   k.o_M1 = p.o_M1; k.o_M2 = p.o_M2; k.o_M3 = p.o_M3; k.o_tau = p.o_tau; k.o_J = p.o_J;
   k.o_envR = p.o_envR; k.o_envL = p.o_envL; k.o_envX = p.o_envX; k.o_envY = p.o_envY;
   k.o_t1 = p.o_t1; k.o_t2 = p.o_t2; k.o_t3 = p.o_t3;
@@ -494,7 +571,7 @@ KParams<T> make_params(gcf_ctx* c) {
   k.o_G = p.o_G;
   k.mps_stride = p.mps_stride; k.qsite_stride = p.qsite_stride;
   k.env_stride = p.env_stride; k.env3_stride = p.env3_stride;
-  k.max_sweeps_svd = 40;
+  k.max_sweeps_svd = c->svd_sweeps;
   k.hot_in_smem = p.cta_level >= 1;
   k.mps_in_smem = p.cta_level >= 2;
   k.renv_in_smem = p.cta_level >= 3;
@@ -518,9 +595,19 @@ KParams<T> make_params(gcf_ctx* c) {
     if (c->m.precision == GCF_TF32) k.gemm_mode = GEMM_TF32X3;
     if (c->m.precision == GCF_BF16) k.gemm_mode = GEMM_BF16;
   }
-  // BF16 form: the row environments (amplitude, O, horizontal-hop ratios)
-  // run in the 3-pass TF32 form, which halves the BF16 error of O
+  // Tensor-core forms.  The boundary-MPS absorption keeps FP32 products in
+  // every form: its truncations amplify operand rounding (the 3-pass TF32
+  // split, about 21 bits with tensor-core accumulation, measured 1.4-1.8e-4
+  // amplitude error on the truncated 10x10 and 16x16 lattices against
+  // 3e-6-1.6e-5 in FP32).  BF16 form: BF16 operands only in the strip
+  // environments (plaquette and vertical-hop ratios: Metropolis decisions and
+  // E_loc); the row environments (amplitude, O, horizontal-hop ratios) run in
+  // the 3-pass TF32 form.
   k.row_gemm_mode = k.gemm_mode == GEMM_BF16 ? GEMM_TF32X3 : k.gemm_mode;
+  k.absorb_gemm_mode = GEMM_FFMA;
+  k.tc_bf16 = p.tc_bytes > 0 && k.gemm_mode == GEMM_BF16 ? 1 : 0;
+  k.tc_bytes = p.tc_bytes;
+  k.tc_off = (long long)cta_tc_off(p, p.cta_level, c->sbytes);
   k.status = c->d_status;
   return k;
 }
@@ -588,6 +675,7 @@ gcf_status run_vmc(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t
     k.hot_in_smem = c->plan.group_level >= 1;
     k.mps_in_smem = c->plan.group_level >= 2;
     k.renv_in_smem = c->plan.group_level >= 3;
+    k.tc_off = (long long)group_tc_off(c->plan, c->plan.group_level, c->sbytes);
   }
   k.n_chains = n; k.n_sweeps = n_sweeps; k.mode = mode; k.want = want; k.seed = seed;
   k.configs = configs;
@@ -608,6 +696,8 @@ gcf_status run_vmc(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (gauss_count) *gauss_count = h_status[ST_GAUSS];
   c->last_phase_timeouts = h_status[ST_PHASE_TIMEOUT];
+  c->last_svd_unconverged = h_status[ST_SVD];
+  c->last_tc_timeouts = h_status[ST_TC_TIMEOUT];
   return GCF_OK;
 }
 
@@ -617,7 +707,7 @@ gcf_status run_multi(gcf_ctx* const* cs, int n_ctx, const int* n_chains, int n_s
   gcf_ctx* c0 = cs[0];
   std::vector<KParams<T>> ks(n_ctx);
   std::vector<long long> start(n_ctx + 1, 0);
-  size_t smem = 0;
+  size_t smem = 0, tc_off = 0, tc_bytes = 0;
   long long ws = 0;
   for (int i = 0; i < n_ctx; ++i) {
     gcf_ctx* c = cs[i];
@@ -631,11 +721,23 @@ gcf_status run_multi(gcf_ctx* const* cs, int n_ctx, const int* n_chains, int n_s
     ks[i] = k;
     start[i + 1] = start[i] + n_chains[i];
     smem = std::max(smem, c->plan.dyn_smem);
+    tc_off = std::max(tc_off, cta_tc_off(c->plan, c->plan.cta_level, c->sbytes));
+    tc_bytes = std::max(tc_bytes, (size_t)c->plan.tc_bytes);
     ws = std::max(ws, c->plan.ws_stride);
     CUDA_TRY(c0, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), c0->stream));
   }
   const long long total = start[n_ctx];
   if (total == 0) return GCF_OK;
+  // one staging area after the largest context's configuration and hot
+  // buffers; the tensor-core path runs only if every context takes it
+  bool tc_all = true;
+  for (int i = 0; i < n_ctx; ++i) tc_all = tc_all && ks[i].tc_bf16;
+  if (tc_bytes > 0) smem = std::max(smem, tc_off + tc_bytes);
+  for (int i = 0; i < n_ctx; ++i) {
+    ks[i].tc_bf16 = tc_all ? 1 : 0;
+    ks[i].tc_off = (long long)tc_off;
+    ks[i].tc_bytes = (long long)tc_bytes;
+  }
   const int per_sm = occupancy_vmc_multi<T>(smem);
   if (per_sm < 1) return fail(c0, GCF_EINVAL, "gcf_sample_multi: the largest context does not fit an SM");
   const long long grid = balanced_slots(total, (long long)c0->sms * per_sm);
@@ -667,9 +769,17 @@ gcf_status run_multi(gcf_ctx* const* cs, int n_ctx, const int* n_chains, int n_s
   for (int i = 0; i < n_ctx; ++i)
     CUDA_TRY(c0, cudaMemcpyAsync(&h[4 * i], cs[i]->d_status, 4 * sizeof(int), cudaMemcpyDeviceToHost, c0->stream));
   CUDA_TRY(c0, cudaStreamSynchronize(c0->stream));
+  c0->last_svd_unconverged = 0;
+  c0->last_phase_timeouts = 0;
+  c0->last_tc_timeouts = 0;
+  for (int i = 0; i < n_ctx; ++i) {
+    c0->last_svd_unconverged += h[4 * i + ST_SVD];
+    c0->last_phase_timeouts += h[4 * i + ST_PHASE_TIMEOUT];
+    c0->last_tc_timeouts += h[4 * i + ST_TC_TIMEOUT];
+  }
   for (int i = 0; i < n_ctx; ++i)
     if (h[4 * i + ST_GAUSS]) return fail(c0, GCF_EGAUSS, "a starting configuration violates the Gauss law");
-  return GCF_OK;
+  return svd_status(c0);
 }
 
 gcf_status dispatch(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t seed, int8_t* cfg,
@@ -810,7 +920,8 @@ gcf_status gcf_init_peps(const gcf_model* model, uint64_t seed, void* cuda_strea
   const gcf_model& m = *model;
   if (m.N < 2 || m.N > 8 || m.Lx < 2 || m.Ly < 2 || m.Lx > MAX_L || m.Ly > MAX_L || m.D < m.N ||
       m.D % m.N != 0 || m.D / m.N > 3 || m.chi < 1 || (m.dtype != GCF_REAL && m.dtype != GCF_COMPLEX) ||
-      m.precision < GCF_FP64 || m.precision > GCF_BF16 || (m.has_matter != 0 && m.has_matter != 1))
+      m.precision < GCF_FP64 || m.precision > GCF_BF16 || (m.has_matter != 0 && m.has_matter != 1) ||
+      m.trunc != GCF_TRUNC_SVD || m.recompute_env < -1 || m.recompute_env == 1 || m.recompute_env > m.Ly)
     return GCF_EINVAL;
   gcf_ctx* c = new gcf_ctx();
   c->m = m;
@@ -824,6 +935,13 @@ gcf_status gcf_init_peps(const gcf_model* model, uint64_t seed, void* cuda_strea
   c->n_plaq = (m.Lx - 1) * (m.Ly - 1);
   c->n_slots = 2 * c->n_plaq + (m.has_matter ? c->n_h + c->n_v : 0);
   c->Q.assign(c->n_s, 0);
+  if (m.recompute_env == -1) {
+    int K = 2;
+    while (K * K < m.Ly + 1) ++K;
+    c->ck_every = K;
+  } else {
+    c->ck_every = m.recompute_env;
+  }
   if (m.Q)
     for (int i = 0; i < c->n_s; ++i) c->Q[i] = ((m.Q[i] % m.N) + m.N) % m.N;
   const bool cplx = m.dtype == GCF_COMPLEX;
@@ -907,6 +1025,7 @@ int gcf_executor(const gcf_ctx* ctx) { return ctx ? ctx->exec : -1; }
 
 gcf_status gcf_set_tensors(gcf_ctx* c, const void* host, size_t bytes) {
   if (!c || !host) return GCF_EINVAL;
+  DEVICE_TRY(c, "gcf_set_tensors");
   const bool cplx = c->m.dtype == GCF_COMPLEX;
   if (bytes != (size_t)c->n_params * (cplx ? 16 : 8))
     return fail(c, GCF_EINVAL, "gcf_set_tensors: byte count does not match the layout");
@@ -915,6 +1034,7 @@ gcf_status gcf_set_tensors(gcf_ctx* c, const void* host, size_t bytes) {
 
 gcf_status gcf_get_tensors(gcf_ctx* c, void* host, size_t bytes) {
   if (!c || !host) return GCF_EINVAL;
+  DEVICE_TRY(c, "gcf_get_tensors");
   const bool cplx = c->m.dtype == GCF_COMPLEX;
   const long long nv = cplx ? 2 * c->n_params : c->n_params;
   if (bytes != (size_t)nv * 8) return fail(c, GCF_EINVAL, "gcf_get_tensors: byte count mismatch");
@@ -935,6 +1055,7 @@ gcf_status gcf_init_configs(gcf_ctx* c, int n_chains, const int8_t* occ, const i
                             int8_t* configs) {
   if (!c || n_chains < 0 || (n_chains > 0 && !configs)) return GCF_EINVAL;
   if (n_chains == 0) return GCF_OK;
+  DEVICE_TRY(c, "gcf_init_configs");
   CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), c->stream));
   CUDA_TRY(c, launch_init_configs(c->m.N, c->m.Lx, c->m.Ly, c->m.has_matter, c->d_Q, n_chains, occ,
                                   powers, configs, c->d_status, c->stream));
@@ -949,27 +1070,32 @@ gcf_status gcf_init_configs(gcf_ctx* c, int n_chains, const int8_t* occ, const i
 gcf_status gcf_amplitude(gcf_ctx* c, int n, const int8_t* configs, double* log_abs, double* phase) {
   if (!c || n < 0 || (n > 0 && (!configs || !log_abs || !phase))) return GCF_EINVAL;
   if (n == 0) return GCF_OK;
+  DEVICE_TRY(c, "gcf_amplitude");
   gcf_samples out{};
   out.log_abs = log_abs;
   out.phase = phase;
-  return dispatch(c, 0, WANT_AMP, n, 1, 0, (int8_t*)configs, &out, nullptr);
+  gcf_status st = dispatch(c, 0, WANT_AMP, n, 1, 0, (int8_t*)configs, &out, nullptr);
+  if (st != GCF_OK) return st;
+  return svd_status(c);
 }
 
 gcf_status gcf_local_energy(gcf_ctx* c, int n, const int8_t* configs, double* e_loc) {
   if (!c || n < 0 || (n > 0 && (!configs || !e_loc))) return GCF_EINVAL;
   if (n == 0) return GCF_OK;
+  DEVICE_TRY(c, "gcf_local_energy");
   gcf_samples out{};
   out.e_loc = e_loc;
   int gauss = 0;
   gcf_status st = dispatch(c, 0, WANT_ELOC, n, 1, 0, (int8_t*)configs, &out, &gauss);
   if (st != GCF_OK) return st;
   if (gauss) return fail(c, GCF_EGAUSS, "configuration violates the Gauss law");
-  return GCF_OK;
+  return svd_status(c);
 }
 
 gcf_status gcf_log_grad(gcf_ctx* c, int n, const int8_t* configs, int32_t* block_ids, void* O) {
   if (!c || n < 0 || (n > 0 && (!configs || !block_ids || !O))) return GCF_EINVAL;
   if (n == 0) return GCF_OK;
+  DEVICE_TRY(c, "gcf_log_grad");
   gcf_samples out{};
   out.block_ids = block_ids;
   out.O = O;
@@ -977,11 +1103,12 @@ gcf_status gcf_log_grad(gcf_ctx* c, int n, const int8_t* configs, int32_t* block
   gcf_status st = dispatch(c, 0, WANT_GRAD, n, 1, 0, (int8_t*)configs, &out, &gauss);
   if (st != GCF_OK) return st;
   if (gauss) return fail(c, GCF_EGAUSS, "configuration violates the Gauss law");
-  return GCF_OK;
+  return svd_status(c);
 }
 
 gcf_status gcf_log_grad_vjp(gcf_ctx* c, int n, const int8_t* configs, const double* weights, double* grad) {
   if (!c || n < 0 || !grad || (n > 0 && (!configs || !weights))) return GCF_EINVAL;
+  DEVICE_TRY(c, "gcf_log_grad_vjp");
   const bool cplx = c->m.dtype == GCF_COMPLEX;
   if (n == 0) {
     CUDA_TRY(c, cudaMemsetAsync(grad, 0, sizeof(double) * (cplx ? 2 : 1) * c->n_params, c->stream));
@@ -1033,18 +1160,19 @@ gcf_status gcf_log_grad_vjp(gcf_ctx* c, int n, const int8_t* configs, const doub
   }
   CUDA_TRY(c, e);
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  return GCF_OK;
+  return svd_status(c);
 }
 
 gcf_status gcf_autotune(gcf_ctx* c, int n_chains, int n_sweeps, const int8_t* configs, double* ms, int* n_forms) {
   if (!c || n_chains < 1 || n_sweeps < 1 || !configs) return GCF_EINVAL;
+  DEVICE_TRY(c, "gcf_autotune");
   // candidate forms that fit an SM (227 KB of shared memory per block)
   const size_t limit = 227 * 1024 - 8 * 1024;
   std::vector<std::pair<int, int>> forms;
   for (int lv = 0; lv <= 3; ++lv) {
-    const size_t cta = (size_t)c->plan.cfg_bytes + (size_t)c->plan.level_elems(lv) * c->sbytes;
+    const size_t cta = cta_smem_bytes(c->plan, lv, c->sbytes);
     if (cta <= limit) forms.push_back({EXEC_CTA, lv});
-    const size_t grp = 2 * (sharedv_bytes() + (size_t)c->plan.cfg_bytes + (size_t)c->plan.level_elems(lv) * c->sbytes);
+    const size_t grp = 2 * group_smem_bytes(c->plan, lv, c->sbytes);
     if (lv >= 1 && grp <= limit) forms.push_back({EXEC_GROUP, lv});
     if (lv >= 1 && 2 * grp <= limit) forms.push_back({EXEC_GROUP4, lv});
   }
@@ -1106,6 +1234,24 @@ gcf_status gcf_autotune(gcf_ctx* c, int n_chains, int n_sweeps, const int8_t* co
 
 int gcf_phase_timeouts(const gcf_ctx* c) { return c ? c->last_phase_timeouts : -1; }
 
+int gcf_svd_unconverged(const gcf_ctx* c) { return c ? c->last_svd_unconverged : -1; }
+
+int64_t gcf_scratch_bytes_per_chain(const gcf_ctx* c) {
+  return c ? (int64_t)c->plan.ws_stride * (int64_t)c->sbytes : -1;
+}
+
+int gcf_checkpoint_interval(const gcf_ctx* c) { return c ? c->ck_every : -1; }
+
+int gcf_tensor_core_form(const gcf_ctx* c) { return c ? (c->plan.tc_bytes > 0 ? 1 : 0) : -1; }
+
+int gcf_tensor_timeouts(const gcf_ctx* c) { return c ? c->last_tc_timeouts : -1; }
+
+gcf_status gcf_set_svd_sweeps(gcf_ctx* c, int max_sweeps) {
+  if (!c || max_sweeps < 1 || max_sweeps > 1000) return GCF_EINVAL;
+  c->svd_sweeps = max_sweeps;
+  return GCF_OK;
+}
+
 int gcf_smem_level(const gcf_ctx* c) {
   if (!c) return -1;
   return grouped(c) ? c->plan.group_level : c->plan.cta_level;
@@ -1121,6 +1267,7 @@ gcf_status gcf_sample_multi(gcf_ctx* const* ctxs, int n_ctx, const int* n_chains
     if (ctxs[i]->kind != c0->kind) return fail(c0, GCF_EINVAL, "contexts differ in scalar type");
     if (ctxs[i]->device != c0->device) return fail(c0, GCF_EINVAL, "contexts on different devices");
   }
+  DEVICE_TRY(c0, "gcf_sample_multi");
   // the other contexts' work (parameter uploads) precedes this launch
   for (int i = 1; i < n_ctx; ++i)
     if (ctxs[i]->stream != c0->stream) CUDA_TRY(c0, cudaStreamSynchronize(ctxs[i]->stream));
@@ -1136,6 +1283,7 @@ gcf_status gcf_sample_batch_async(gcf_ctx* c, int n_chains, int n_sweeps, uint64
                                   const gcf_samples* out, void* stream) {
   if (!c || n_chains < 0 || n_sweeps < 1 || (n_chains > 0 && !configs)) return GCF_EINVAL;
   if (n_chains == 0) return GCF_OK;
+  DEVICE_TRY(c, "gcf_sample_batch_async");
   cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
   // scratch must already cover this launch: no allocation here
   {
@@ -1170,6 +1318,7 @@ gcf_status gcf_sample_batch(gcf_ctx* c, int n_chains, int n_sweeps, uint64_t see
                             const gcf_samples* out) {
   if (!c || n_chains < 0 || n_sweeps < 1 || (n_chains > 0 && !configs)) return GCF_EINVAL;
   if (n_chains == 0) return GCF_OK;
+  DEVICE_TRY(c, "gcf_sample_batch");
   gcf_samples o{};
   if (out) o = *out;
   int want = (o.log_abs || o.phase ? WANT_AMP : 0) | (o.e_loc ? WANT_ELOC : 0) |
@@ -1178,7 +1327,7 @@ gcf_status gcf_sample_batch(gcf_ctx* c, int n_chains, int n_sweeps, uint64_t see
   gcf_status st = dispatch(c, 1, want, n_chains, n_sweeps, seed, configs, &o, &gauss);
   if (st != GCF_OK) return st;
   if (gauss) return fail(c, GCF_EGAUSS, "starting configuration violates the Gauss law");
-  return GCF_OK;
+  return svd_status(c);
 }
 
 gcf_status gcf_sr_step(gcf_ctx* c, int n_samples, int n_chains, const double* e_loc,
@@ -1188,6 +1337,7 @@ gcf_status gcf_sr_step(gcf_ctx* c, int n_samples, int n_chains, const double* e_
       !O || !stats || max_iter < 0 || !(diag_shift >= 0.0))
     return GCF_EINVAL;
   if (mode != GCF_SR && mode != GCF_TDVP_STAGE1 && mode != GCF_TDVP_STAGE2) return GCF_EINVAL;
+  DEVICE_TRY(c, "gcf_sr_step");
   if (mode != GCF_SR && c->m.dtype != GCF_COMPLEX)
     return fail(c, GCF_EINVAL, "TDVP modes need complex tensors");
   gcf_status st = ensure_sr(c, n_samples, n_chains);
@@ -1235,6 +1385,7 @@ gcf_status gcf_vmc_step_host(gcf_ctx* c, int n_chains, int n_sweeps, uint64_t se
                              double diag_shift, double lr, int mode, double dt, int max_iter, double tol,
                              double* stats) {
   if (!c || n_chains < 1 || n_sweeps < 1 || !host_configs || !stats) return GCF_EINVAL;
+  DEVICE_TRY(c, "gcf_vmc_step_host");
   const long long ns = (long long)n_chains * n_sweeps;
   const int D4 = c->Dk * c->Dk * c->Dk * c->Dk;
   if (ns > c->e2e_cap || n_chains > c->e2e_chains) {

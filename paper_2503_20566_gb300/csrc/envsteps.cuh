@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "mma.cuh"
+#include "tcgen05.cuh"
 
 namespace gcf {
 
@@ -93,7 +94,19 @@ __device__ __noinline__ int cta_gemm_scaled(const X ex, int M, int N, int K, con
   const int MN = M * N;
   const int nt = ex.size();
   bool done = false;
-  if constexpr (MmaOk<T>::value) {
+  if constexpr (std::is_same<T, float>::value) {
+    // BF16 form of a real chain: the fifth-generation tensor cores when the
+    // launch set them up and the operands fit the chain's staging area
+    const int slot = ex.slot();
+    if (g_gemm_mode[slot] == GEMM_BF16 && g_tc_stage[slot] && N <= kTcCols &&
+        tc_stage_bytes(N, K) <= g_tc_cap && g_tc[slot].ok) {
+      mx = tc_gemm_bf16(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc, g_tc_stage[slot], g_tc_status);
+      done = mx >= 0.f;
+      if (!done) mx = 0.f;
+    }
+  }
+  if (done) {
+  } else if constexpr (MmaOk<T>::value) {
     const int mode = g_gemm_mode[ex.slot()];
     if (mode != GEMM_FFMA) {
       if (mode == GEMM_BF16)

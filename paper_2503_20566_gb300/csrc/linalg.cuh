@@ -18,10 +18,12 @@
 namespace gcf {
 
 // C(i,j) = [C(i,j) +] sum_k op(A)(i,k) op(B)(k,j); op = optional conjugation.
-template <class T, bool CA = false, bool CB = false, class X>
+// TC = false keeps the product in the scalar's own precision whatever the
+// chain's GEMM mode (the factorisations' own products).
+template <class T, bool CA = false, bool CB = false, bool TC = true, class X>
 __device__ __noinline__ void cta_gemm(const X ex, int M, int N, int K, const T* A, int sAm, int sAk, const T* B,
                          int sBk, int sBn, T* C, int sCm, int sCn, bool accumulate) {
-  if constexpr (!CA && !CB && MmaOk<T>::value) {
+  if constexpr (TC && !CA && !CB && MmaOk<T>::value) {
     const int mode = g_gemm_mode[ex.slot()];
     if (mode != GEMM_FFMA) {
       if (mode == GEMM_BF16)
@@ -71,14 +73,83 @@ __device__ inline void householder(T alpha, typename Traits<T>::R xn2, T& tau, T
   beta = make_scalar<T>(b, R(0));
 }
 
+// Sum of v over the L consecutive lanes (L a power of two <= 32, aligned)
+// that share a column pair; every lane of the warp must call it.
+template <class R>
+__device__ __forceinline__ R lanes_sum(R v, int L) {
+#pragma unroll 1
+  for (int o = L >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Lanes per column for `cols` independent column operations on the
+// executor: the largest power of two <= 32 whose groups of lanes cover every
+// column at once (1 if the columns outnumber the threads).
+template <class X>
+__device__ __forceinline__ int lanes_per_column(const X ex, int cols) {
+  int L = 32;
+  while (L > 1 && L * cols > ex.size()) L >>= 1;
+  return L;
+}
+
+template <class T>
+__device__ __forceinline__ T lanes_sum_scalar(T v, int L);
+template <>
+__device__ __forceinline__ float lanes_sum_scalar<float>(float v, int L) { return lanes_sum(v, L); }
+template <>
+__device__ __forceinline__ double lanes_sum_scalar<double>(double v, int L) { return lanes_sum(v, L); }
+template <>
+__device__ __forceinline__ cfloat lanes_sum_scalar<cfloat>(cfloat v, int L) {
+  return {lanes_sum(v.x, L), lanes_sum(v.y, L)};
+}
+template <>
+__device__ __forceinline__ cdouble lanes_sum_scalar<cdouble>(cdouble v, int L) {
+  return {lanes_sum(v.x, L), lanes_sum(v.y, L)};
+}
+
+// Apply the reflector H = I - f v v^H (v = (1; A[j+1.., j])) from the left
+// to columns c0 .. c1-1 of M (rows j..m-1): w_c = v^H M_c, M_c -= v (f w_c).
+// Each column is served by a group of L lanes that split its rows and sum
+// their parts by shuffles, so that all columns proceed at once.
+template <class T, class X>
+__device__ __forceinline__ void apply_reflector(const X ex, int m, int j, const T* A, int sm, int sn, T f,
+                                                T* Mt, int sMm, int sMn, int c0, int c1) {
+  const int nc = c1 - c0;
+  if (nc <= 0) return;
+  const int L = lanes_per_column(ex, nc);
+  const int slots = ex.size() / L;
+  const int sub = ex.tid() / L, li = ex.tid() - (ex.tid() / L) * L;
+#pragma unroll 1
+  for (int base = 0; base < nc; base += slots) {
+    const int c = c0 + base + sub;
+    const bool act = c < c1;
+    T w = zero<T>();
+    if (act) {
+#pragma unroll 1
+      for (int i = j + li; i < m; i += L) {
+        const T v = (i == j) ? one<T>() : A[i * sm + j * sn];
+        w = fmac(w, conjg(v), Mt[i * sMm + c * sMn]);
+      }
+    }
+    w = lanes_sum_scalar(w, L);
+    if (act) {
+      const T g = f * w;
+#pragma unroll 1
+      for (int i = j + li; i < m; i += L) {
+        const T v = (i == j) ? one<T>() : A[i * sm + j * sn];
+        Mt[i * sMm + c * sMn] -= v * g;
+      }
+    }
+  }
+}
+
 // In-place Householder QR of A (m x n): on return the upper triangle of the
 // leading k = min(m,n) rows holds R, the part below the diagonal holds the
-// reflector vectors, tau[0..k) their factors.  `red` is shared scratch (64 doubles).
+// reflector vectors, tau[0..k) their factors.
 template <class T, class X>
 __device__ __noinline__ void cta_qr(const X ex, int m, int n, T* A, int sm, int sn, T* tau) {
   using R = typename Traits<T>::R;
   const int k = min(m, n);
-  const int lane = ex.lane(), wid = ex.warp(), nw = ex.nwarps();
   for (int j = 0; j < k; ++j) {
     R part = R(0);
 #pragma unroll 1
@@ -92,20 +163,7 @@ __device__ __noinline__ void cta_qr(const X ex, int m, int n, T* A, int sm, int 
     for (int i = j + 1 + ex.tid(); i < m; i += ex.size()) A[i * sm + j * sn] = A[i * sm + j * sn] * sc;
     if (ex.tid() == 0) { A[j * sm + j * sn] = beta; tau[j] = t; }
     ex.sync();
-    const T ct = conjg(t);
-    for (int c = j + 1 + wid; c < n; c += nw) {
-      T w = zero<T>();
-      for (int i = j + lane; i < m; i += 32) {
-        const T v = (i == j) ? one<T>() : A[i * sm + j * sn];
-        w = fmac(w, conjg(v), A[i * sm + c * sn]);
-      }
-      w = warp_sum_scalar(w);
-      const T f = ct * w;
-      for (int i = j + lane; i < m; i += 32) {
-        const T v = (i == j) ? one<T>() : A[i * sm + j * sn];
-        A[i * sm + c * sn] -= v * f;
-      }
-    }
+    apply_reflector(ex, m, j, A, sm, sn, conjg(t), A, sm, sn, j + 1, n);
     ex.sync();
   }
 }
@@ -115,7 +173,6 @@ __device__ __noinline__ void cta_qr(const X ex, int m, int n, T* A, int sm, int 
 template <class T, class X>
 __device__ __noinline__ void cta_form_q(const X ex, int m, int k, const T* A, int sm, int sn, const T* tau, T* Q, int sQm,
                            int sQn) {
-  const int lane = ex.lane(), wid = ex.warp(), nw = ex.nwarps();
 #pragma unroll 1
   for (int idx = ex.tid(); idx < m * k; idx += ex.size()) {
     const int i = idx / k, c = idx - (idx / k) * k;
@@ -123,20 +180,7 @@ __device__ __noinline__ void cta_form_q(const X ex, int m, int k, const T* A, in
   }
   ex.sync();
   for (int j = k - 1; j >= 0; --j) {
-    const T t = tau[j];
-    for (int c = j + wid; c < k; c += nw) {
-      T w = zero<T>();
-      for (int i = j + lane; i < m; i += 32) {
-        const T v = (i == j) ? one<T>() : A[i * sm + j * sn];
-        w = fmac(w, conjg(v), Q[i * sQm + c * sQn]);
-      }
-      w = warp_sum_scalar(w);
-      const T f = t * w;
-      for (int i = j + lane; i < m; i += 32) {
-        const T v = (i == j) ? one<T>() : A[i * sm + j * sn];
-        Q[i * sQm + c * sQn] -= v * f;
-      }
-    }
+    apply_reflector(ex, m, j, A, sm, sn, tau[j], Q, sQm, sQn, j, k);
     ex.sync();
   }
 }
@@ -157,60 +201,102 @@ __device__ __noinline__ void cta_adjoint(const X ex, int rows, int cols, const T
 // to the identity here) so that on return W = W_in J has mutually orthogonal
 // columns.  Returns the number of sweeps used; *converged set to 0 if the
 // sweep limit was hit.  sflag: shared int scratch.
+// Each sweep visits every column pair once in the round-robin order (n - 1
+// rounds of n/2 disjoint pairs, n = q rounded up to even).  A pair is served
+// by L consecutive lanes (the largest power of two <= 32 with L x n/2 within
+// the executor), which split its rows and combine their partial sums by
+// shuffles, so that all pairs of a round proceed at once.
 template <class T, class X>
 __device__ __noinline__ int cta_jacobi_svd(const X ex, int p, int q, T* W, int sWm, int sWn, T* J, int sJm, int sJn,
                               int* sflag, int max_sweeps, int* converged) {
   using R = typename Traits<T>::R;
-  const int lane = ex.lane(), wid = ex.warp(), nw = ex.nwarps();
 #pragma unroll 1
   for (int idx = ex.tid(); idx < q * q; idx += ex.size()) {
     const int i = idx / q, c = idx - (idx / q) * q;
     J[i * sJm + c * sJn] = (i == c) ? one<T>() : zero<T>();
   }
   const int n = q + (q & 1);
-  const R tol = R(8) * Traits<T>::eps();
+  const int npair = n / 2;
+  int L = 32;
+  while (L > 1 && L * npair > ex.size()) L >>= 1;
+  const int slots = ex.size() / L;
+  const int sub = ex.tid() / L, li = ex.tid() - (ex.tid() / L) * L;
+  // convergence threshold on |w_a^H w_b| / (|w_a| |w_b|): the rounding of a
+  // length-p dot product is about sqrt(p) eps, below which rotations only
+  // stir noise (the threshold of LAPACK's one-sided Jacobi, xGESVJ, scaled
+  // by 4)
+  const R tol = R(4) * sqrt(R(p > 4 ? p : 4)) * Traits<T>::eps();
+  // a column whose norm is below eps ||W||_F (rotations keep ||W||_F) is
+  // rounding noise of the matrix: pairs with one are left as they are
+  R f2 = R(0);
+#pragma unroll 1
+  for (int idx = ex.tid(); idx < p * q; idx += ex.size()) {
+    const int i = idx / q, c = idx - (idx / q) * q;
+    f2 += abs2(W[i * sWm + c * sWn]);
+  }
+  f2 = ex.template sum<R>(f2);
+  const R negl = Traits<T>::eps() * Traits<T>::eps() * f2;
   int sweep = 0;
   if (converged) *converged = 1;
   for (; sweep < max_sweeps; ++sweep) {
     if (ex.tid() == 0) *sflag = 0;
     ex.sync();
+#pragma unroll 1
     for (int r = 0; r < n - 1; ++r) {
-      for (int kp = wid; kp < n / 2; kp += nw) {
-        int a, b;
+#pragma unroll 1
+      for (int base = 0; base < npair; base += slots) {
+        const int kp = base + sub;
+        int a = 0, b = 0;
         if (kp == 0) { a = r % (n - 1); b = n - 1; }
         else { a = (r + kp) % (n - 1); b = (r - kp + n - 1) % (n - 1); }
-        if (a >= q || b >= q) continue;
-        if (a > b) { int t = a; a = b; b = t; }
-        R al = R(0), be = R(0);
-        T g = zero<T>();
-        for (int i = lane; i < p; i += 32) {
-          const T wa = W[i * sWm + a * sWn], wb = W[i * sWm + b * sWn];
-          al += abs2(wa);
-          be += abs2(wb);
-          g = fmac(g, conjg(wa), wb);
+        if (a > b) { const int t = a; a = b; b = t; }
+        const bool act = kp < npair && b < q;
+        R al = R(0), be = R(0), gr = R(0), gi = R(0);
+        if (act) {
+          T g = zero<T>();
+#pragma unroll 1
+          for (int i = li; i < p; i += L) {
+            const T wa = W[i * sWm + a * sWn], wb = W[i * sWm + b * sWn];
+            al += abs2(wa);
+            be += abs2(wb);
+            g = fmac(g, conjg(wa), wb);
+          }
+          gr = re(g);
+          gi = im(g);
         }
-        al = warp_sum(al); be = warp_sum(be); g = warp_sum_scalar(g);
-        const R gr = re(g), gi = im(g);
+        al = lanes_sum(al, L);
+        be = lanes_sum(be, L);
+        gr = lanes_sum(gr, L);
+        gi = lanes_sum(gi, L);
         const R ga = sqrt(gr * gr + gi * gi);
-        if (ga == R(0) || !(ga > tol * sqrt(al * be))) continue;
+        // sqrt(al) sqrt(be), not sqrt(al be): the product of two small squared
+        // norms can underflow, and a zero threshold would rotate rounding
+        // noise forever
+        if (!act || ga == R(0) || !(al > negl) || !(be > negl) || !(ga > tol * (sqrt(al) * sqrt(be)))) continue;
         const R zeta = (be - al) / (R(2) * ga);
-        const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+        // tan of the rotation angle; for |zeta| beyond 1e15, zeta^2 would
+        // overflow in FP32, and t = 1 / (2 zeta) to rounding
+        const R az = fabs(zeta);
+        const R t = (zeta >= R(0) ? R(1) : R(-1)) / (az > R(1e15) ? R(2) * az : az + sqrt(R(1) + zeta * zeta));
+        if (t == R(0)) continue;  // a rotation below rounding leaves the pair as it is
         const R c = R(1) / sqrt(R(1) + t * t), s = c * t;
         // G = [[c, s e^{i phi}], [-s e^{-i phi}, c]], e^{i phi} = g / |g|
         const T eph = make_scalar<T>(gr / ga, gi / ga);
         const T s_e = scale(eph, (R)s);                 // s e^{i phi}
         const T s_ec = scale(conjg(eph), (R)s);         // s e^{-i phi}
-        for (int i = lane; i < p; i += 32) {
+#pragma unroll 1
+        for (int i = li; i < p; i += L) {
           const T wa = W[i * sWm + a * sWn], wb = W[i * sWm + b * sWn];
           W[i * sWm + a * sWn] = scale(wa, (R)c) - wb * s_ec;
           W[i * sWm + b * sWn] = wa * s_e + scale(wb, (R)c);
         }
-        for (int i = lane; i < q; i += 32) {
+#pragma unroll 1
+        for (int i = li; i < q; i += L) {
           const T ja = J[i * sJm + a * sJn], jb = J[i * sJm + b * sJn];
           J[i * sJm + a * sJn] = scale(ja, (R)c) - jb * s_ec;
           J[i * sJm + b * sJn] = ja * s_e + scale(jb, (R)c);
         }
-        if (lane == 0) *sflag = 1;
+        if (li == 0) *sflag = 1;
       }
       ex.sync();
     }

@@ -55,6 +55,16 @@ struct KParams {
   long long o_net, o_prop, o_B, o_T, o_Q, o_M1, o_M2, o_M3, o_tau, o_J, o_envR, o_envL,
       o_envX, o_envY, o_t1, o_t2, o_t3, o_env3R, o_env3L, o_env3X, o_env3Y, o_G;
   long long mps_stride, qsite_stride;
+  // Boundary-MPS store.  ck_every = 0: every B[r] / T[r] of the chain is kept
+  // (B slot j at o_B + j mps_stride, T slot r at o_T + r mps_stride).
+  // ck_every = K >= 2: only every K-th is kept (B slot j with j % K == 0 at
+  // o_B + (j / K) mps_stride; T slot r with (Ly - r) % K == 0 at
+  // o_T + ((Ly - r) / K) mps_stride) and the slots of one segment between
+  // two kept ones live in a segment buffer (o_Bseg / o_Tseg + position
+  // mps_stride), recomputed from the segment's kept slot when a pass needs
+  // them.
+  int ck_every;
+  long long o_Bseg, o_Tseg;
   int env_stride, env3_stride;
   int max_sweeps_svd;
   // hot buffers: in dynamic shared memory when hot_in_smem, else in scratch
@@ -68,6 +78,12 @@ struct KParams {
   int lock_fault;             // test hook: group 0 never counts in, so the others' waits run out
   int gemm_mode;              // GemmMode of the contraction GEMMs
   int row_gemm_mode;          // GemmMode of the row environments (O, amplitude, hops)
+  int absorb_gemm_mode;       // GemmMode of the boundary-MPS absorption (B[r], T[r])
+  // BF16 GEMMs of real chains on the fifth-generation tensor cores
+  // (tcgen05.cuh): 1 if used, the bytes of a chain's operand staging area and
+  // its byte offset from the start of the chain's dynamic shared memory
+  int tc_bf16;
+  long long tc_bytes, tc_off;
   // right environments and the staged B / T rows of the current pass
   int mps_in_smem, renv_in_smem;
   long long so_envR, so_env3R, so_sB, so_sT;
@@ -82,11 +98,11 @@ struct KParams {
   T* O;
   int* accepted;
   int* proposed;
-  int* status;       // [4] error flags (gauss, numeric, svd not converged)
+  int* status;       // [4] counters: Gauss violations, tensor-core waits run out, SVDs not converged, lockstep waits run out
 };
 
 enum { WANT_AMP = 1, WANT_ELOC = 2, WANT_GRAD = 4 };
-enum { ST_GAUSS = 0, ST_NUMERIC = 1, ST_SVD = 2, ST_PHASE_TIMEOUT = 3 };
+enum { ST_GAUSS = 0, ST_TC_TIMEOUT = 1, ST_SVD = 2, ST_PHASE_TIMEOUT = 3 };
 
 struct Shared {
   double red[64];
@@ -154,6 +170,23 @@ __device__ inline void gather_box(const X ex, const KParams<T>& k, int x, int y,
     const int il = t;
     box[((il * Dk + ir) * Dk + id) * Dk + iu] = src[e];
   }
+}
+
+// Address of B slot j (B[j-1]) and of T slot r (T[r]) in a chain's scratch.
+template <class T>
+__device__ inline T* bslot_ptr(const KParams<T>& k, T* ws, int j) {
+  const int K = k.ck_every;
+  if (!K) return ws + k.o_B + (long long)j * k.mps_stride;
+  if (j % K == 0) return ws + k.o_B + (long long)(j / K) * k.mps_stride;
+  return ws + k.o_Bseg + (long long)(j % K) * k.mps_stride;
+}
+template <class T>
+__device__ inline T* tslot_ptr(const KParams<T>& k, T* ws, int r) {
+  const int K = k.ck_every;
+  if (!K) return ws + k.o_T + (long long)r * k.mps_stride;
+  const int d = k.Ly - r;
+  if (d % K == 0) return ws + k.o_T + (long long)(d / K) * k.mps_stride;
+  return ws + k.o_Tseg + (long long)(d % K) * k.mps_stride;
 }
 
 template <class T>
@@ -448,9 +481,33 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
       if (!svd[c]) {
         cta_adjoint<T>(ex, k0, yc, Qp, k0, 1, site, yc, 1);
       } else {
+        // L J = W with orthogonal columns W (one-sided Jacobi).  J is a
+        // product of many rotations, and in FP32 it drifts from orthogonal by
+        // ~1e-5, which enters the kept subspace at every cut; one
+        // Newton-Schulz step J <- J (3 I - J^H J) / 2 restores orthogonality
+        // to rounding, and W = L J is recomputed so that both factors agree.
+        T* L0 = ws + k.o_M2;
+        T* Gm = ws + k.o_M1;
+        T* Jn = ws + k.o_M3;
+#pragma unroll 1
+        for (int idx = ex.tid(); idx < yr * k0; idx += ex.size()) L0[idx] = Lc[idx];
+        ex.sync();
         int conv = 1;
         cta_jacobi_svd<T>(ex, yr, k0, Lc, k0, 1, Jm, k0, 1, &sh.iflag[0], k.max_sweeps_svd, &conv);
         if (!conv && ex.tid() == 0) atomicAdd(&k.status[ST_SVD], 1);
+        cta_gemm<T, true, false, false>(ex, k0, k0, k0, Jm, 1, k0, Jm, k0, 1, Gm, k0, 1, false);
+        {
+          using RR = typename Traits<T>::R;
+#pragma unroll 1
+          for (int idx = ex.tid(); idx < k0 * k0; idx += ex.size()) {
+            const int i = idx / k0, j = idx - (idx / k0) * k0;
+            Gm[idx] = scale(Gm[idx], RR(-0.5));
+            if (i == j) Gm[idx] += make_scalar<T>(RR(1.5), RR(0));
+          }
+        }
+        ex.sync();
+        cta_gemm<T, false, false, false>(ex, k0, k0, k0, Jm, k0, 1, Gm, k0, 1, Jn, k0, 1, false);
+        cta_gemm<T, false, false, false>(ex, yr, k0, k0, L0, k0, 1, Jn, k0, 1, Lc, k0, 1, false);
         // squared column norms -> sigma, selected columns -> sel (scratch)
         using RR = typename Traits<T>::R;
         RR* sigma = (RR*)(ws + k.o_sigma);
@@ -479,7 +536,7 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
           const int n = idx / yc, x = idx - (idx / yc) * yc;
           const int jn = sel[n];
           T s = zero<T>();
-          for (int j = 0; j < k0; ++j) s = fmac(s, conjg(Jm[j * k0 + jn]), conjg(Qp[x * k0 + j]));
+          for (int j = 0; j < k0; ++j) s = fmac(s, conjg(Jn[j * k0 + jn]), conjg(Qp[x * k0 + j]));
           site[idx] = s;
         }
         // carry U S = W[:, sel] (yr x kk)

@@ -28,6 +28,7 @@ struct SharedV {
   double eacc[2];
   int flag, ok, bad;
   int lock, phase;   // lockstep with the CTA's other chain groups; phases passed
+  int segB, segT;    // segment of B / T slots the segment buffers hold (-1: none)
   float redf[32];
   int n_acc, n_prop;
 };
@@ -119,8 +120,28 @@ struct Chain {
     ex.sync();
   }
 
-  __device__ T* Bslot(int j) const { return ws + k.o_B + (long long)j * k.mps_stride; }
-  __device__ T* Tslot(int r) const { return ws + k.o_T + (long long)r * k.mps_stride; }
+  __device__ T* Bslot(int j) const { return bslot_ptr(k, ws, j); }
+  __device__ T* Tslot(int r) const { return tslot_ptr(k, ws, r); }
+
+  // Checkpointed store: make B slot j (T slot r) readable.  A kept slot
+  // always is; a slot of another segment than the buffer holds is rebuilt
+  // by absorbing the rows above the segment's kept slot, with the network
+  // as it stands (the rows a pass has not reached yet, so the same tensors
+  // the slot was first built from).  Both run on every thread of the chain.
+  __device__ void ensure_B(int j) {
+    const int K = k.ck_every;
+    if (!K || j % K == 0 || sv.segB == j / K) return;
+    const int s0 = (j / K) * K;
+    const int top = min(s0 + K - 1, k.Ly - 1);
+    for (int r = s0; r < top; ++r) absorb_B(r);
+  }
+  __device__ void ensure_T(int r) {
+    const int K = k.ck_every;
+    if (!K || (k.Ly - r) % K == 0 || sv.segT == (k.Ly - r) / K) return;
+    const int r0 = k.Ly - ((k.Ly - r) / K) * K;  // the segment's kept slot
+    const int bottom = max(r0 - K + 1, 1);
+    for (int rr = r0 - 1; rr >= bottom; --rr) absorb_T(rr);
+  }
   __device__ int tW() const { return k.Lx + 1; }
   __device__ int tR() const { return k.Ly + 1; }
   __device__ const int* bdB(int j) const { return tab + j * tW(); }
@@ -266,18 +287,30 @@ struct Chain {
 
   // ---- boundary MPS --------------------------------------------------------
   __device__ __noinline__ void absorb_B(int r) {  // B[r] = absorb(B[r-1], row r)
+    const bool own_mode = k.absorb_gemm_mode != k.gemm_mode;
+    if (own_mode) set_gemm_mode(k.absorb_gemm_mode);
     const int ls = absorb_compress(ex, k, ws, hot, sv.base, net, Bslot(r), bdB(r), physB(r), r, 0, Bslot(r + 1),
                                       bdB(r + 1), physB(r + 1), qrBt(r), svdBt(r), offBt(r), offBt(r + 1),
                                       denseB(r));
-    if (ex.tid() == 0) sv.logB[r + 1] = sv.logB[r] + ls;
+    if (ex.tid() == 0) {
+      sv.logB[r + 1] = sv.logB[r] + ls;
+      if (k.ck_every && (r + 1) % k.ck_every) sv.segB = (r + 1) / k.ck_every;
+    }
     ex.sync();
+    if (own_mode) set_gemm_mode(k.gemm_mode);
   }
   __device__ __noinline__ void absorb_T(int r) {  // T[r] = absorb(T[r+1], row r flipped)
+    const bool own_mode = k.absorb_gemm_mode != k.gemm_mode;
+    if (own_mode) set_gemm_mode(k.absorb_gemm_mode);
     const int ls = absorb_compress(ex, k, ws, hot, sv.base, net, Tslot(r + 1), bdT(r + 1), physT(r + 1), r, 1,
                                       Tslot(r), bdT(r), physT(r), qrTt(r), svdTt(r), offTt(r + 1), offTt(r),
                                       denseT(r));
-    if (ex.tid() == 0) sv.logT[r] = sv.logT[r + 1] + ls;
+    if (ex.tid() == 0) {
+      sv.logT[r] = sv.logT[r + 1] + ls;
+      if (k.ck_every && (k.Ly - r) % k.ck_every) sv.segT = (k.Ly - r) / k.ck_every;
+    }
     ex.sync();
+    if (own_mode) set_gemm_mode(k.gemm_mode);
   }
 
   // ---- strip (rows r, r+1) between B[r-1] (slot r) and T[r+2] -------------
@@ -300,15 +333,23 @@ struct Chain {
   // memory when available, else the scratch slots
   const T* curB;
   const T* curT;
+  // The staged rows are copied by the tensor memory accelerator (one bulk
+  // copy per row, rounded up to 16 bytes within the slot's padding), or by
+  // the threads if a bulk wait ran out.
   __device__ __noinline__ void stage(int jb, int jt, int physb, int physt) {
     const T* b = Bslot(jb);
     const T* t = Tslot(jt);
     if (sB) {
       const int nb = sv.offB[k.Lx], nt = sv.offT[k.Lx];
+      const unsigned bb = (unsigned)((nb * sizeof(T) + 15) / 16 * 16), bt = (unsigned)((nt * sizeof(T) + 15) / 16 * 16);
+      bool bulk = false;
+      if (bb + bt < (1u << 20)) bulk = bulk_copy2(ex, sB, b, bb, sT, t, bt, k.status + ST_TC_TIMEOUT);
+      if (!bulk) {
 #pragma unroll 1
-      for (int i = ex.tid(); i < nb; i += ex.size()) sB[i] = b[i];
+        for (int i = ex.tid(); i < nb; i += ex.size()) sB[i] = b[i];
 #pragma unroll 1
-      for (int i = ex.tid(); i < nt; i += ex.size()) sT[i] = t[i];
+        for (int i = ex.tid(); i < nt; i += ex.size()) sT[i] = t[i];
+      }
       ex.sync();
       curB = sB;
       curT = sT;
@@ -516,6 +557,7 @@ __device__ __noinline__ void plaquette_pass(Chain<T, X>& ch, int w) {
   T* X2 = ch.envY;
   for (int r = 0; r < Ly - 1; ++r) {
     ch.phase_sync();
+    ch.ensure_T(r + 2);
     R dr, di;
     int de;
     ch.strip_right_envs(r, dr, di, de);
@@ -574,6 +616,7 @@ __device__ __noinline__ void hhop_pass(Chain<T, X>& ch, int w) {
   T* X2 = ch.env3Y;
   for (int r = Ly - 1; r >= 0; --r) {
     ch.phase_sync();
+    ch.ensure_B(r);
     R dr, di;
     int de;
     ch.row_right_envs(r, dr, di, de);
@@ -635,6 +678,7 @@ __device__ __noinline__ void vhop_pass(Chain<T, X>& ch, int w) {
   T* Lnext = ch.envY;
   for (int r = 0; r < Ly - 1; ++r) {
     ch.phase_sync();
+    ch.ensure_T(r + 2);
     R dr, di;
     int de;
     ch.strip_right_envs(r, dr, di, de);
@@ -697,6 +741,7 @@ __device__ __noinline__ void measure_pass(Chain<T, X>& ch, long long s) {
   ex.sync();
   for (int r = Ly - 1; r >= 0; --r) {
     ch.phase_sync();
+    ch.ensure_B(r);
     // ---- row r: gradient, horizontal hops, amplitude
     const bool need_row = want_g || (r == Ly - 1 && want_a) || (want_e && k.matter && k.J != 0.0);
     if (need_row) {
@@ -806,8 +851,8 @@ template <class T, class X>
 __device__ void init_trivial_slots(const X ex, const KParams<T>& k, T* ws) {
 #pragma unroll 1
   for (int c = ex.tid(); c < k.Lx; c += ex.size()) {
-    (ws + k.o_B)[c] = one<T>();                                     // B[-1]
-    (ws + k.o_T + (long long)k.Ly * k.mps_stride)[c] = one<T>();    // T[Ly]
+    bslot_ptr(k, ws, 0)[c] = one<T>();      // B[-1]
+    tslot_ptr(k, ws, k.Ly)[c] = one<T>();   // T[Ly]
   }
   ex.sync();
 }
@@ -857,6 +902,7 @@ __device__ void run_chain(const X ex, const KParams<T>& k, T* ws, SharedV& sv, i
   if (ex.leader()) {
     sv.logB[0] = 0; sv.logT[k.Ly] = 0; sv.n_acc = 0; sv.n_prop = 0;
     sv.lock = 0; sv.phase = 0;
+    sv.segB = -1; sv.segT = -1;
   }
   ex.sync();
   Chain<T, X> ch(ex, k, ws, sv, cfg, chain, hot, tab);
@@ -905,6 +951,30 @@ __device__ void run_chain(const X ex, const KParams<T>& k, T* ws, SharedV& sv, i
   ex.sync();
 }
 
+// Tensor-core set-up of a launch (tcgen05.cuh): TMEM columns and a
+// completion barrier per chain group, and each group's operand staging area
+// at byte `tc_off` of the group's dynamic shared memory (group g's region
+// starts at g * group_bytes).  Every thread of the CTA calls it.
+template <class T>
+__device__ void tc_begin(const KParams<T>& k, int n_groups, int8_t* dyn_base, long long group_bytes) {
+  if (threadIdx.x < 4)
+    g_tc_stage[threadIdx.x] = (k.tc_bf16 && threadIdx.x < n_groups)
+                                  ? (unsigned char*)(dyn_base + threadIdx.x * group_bytes + k.tc_off)
+                                  : nullptr;
+  if (threadIdx.x == 0) {
+    g_tc_cap = k.tc_bytes;
+    g_tc_status = k.status + ST_TC_TIMEOUT;
+  }
+  if (k.tc_bf16) tc_setup(n_groups);
+  bulk_setup(n_groups);
+}
+template <class T>
+__device__ void tc_end(const KParams<T>& k, int n_groups) {
+  __syncthreads();
+  bulk_teardown(n_groups);
+  if (k.tc_bf16) tc_teardown(n_groups);
+}
+
 // One CTA per chain (any size; the general form).
 template <class T>
 __global__ void __launch_bounds__(256, 2) vmc_kernel(const __grid_constant__ KParams<T> k) {
@@ -915,10 +985,12 @@ __global__ void __launch_bounds__(256, 2) vmc_kernel(const __grid_constant__ KPa
   CtaExec ex;
   if (threadIdx.x < 4) g_gemm_mode[threadIdx.x] = k.gemm_mode;
   const int* tab = stage_tables(k);
+  tc_begin(k, 1, dyn_smem, 0);
   T* ws = k.scratch + (long long)blockIdx.x * k.ws_stride;
   init_trivial_slots(ex, k, ws);
   for (int chain = blockIdx.x; chain < k.n_chains; chain += gridDim.x)
     run_chain(ex, k, ws, sv, dyn_cfg, hot, tab, chain);
+  tc_end(k, 1);
 }
 
 // Several chains per CTA, one per group of G = 128 threads (GroupExec, a
@@ -930,6 +1002,7 @@ __device__ void grouped_body(const KParams<T>& k) {
   if (threadIdx.x < 4) g_gemm_mode[threadIdx.x] = k.gemm_mode;
   const int* tab = stage_tables(k);
   const int g = threadIdx.x / G, NG = blockDim.x / G;
+  tc_begin(k, NG, dyn_smem, k.group_smem_bytes);
   int8_t* base = dyn_smem + g * k.group_smem_bytes;
   SharedV& sv = *reinterpret_cast<SharedV*>(base);
   int8_t* cfg = base + sizeof_sharedv_aligned();
@@ -942,18 +1015,19 @@ __device__ void grouped_body(const KParams<T>& k) {
   if (!k.lockstep) {
     for (long long chain = slot; chain < k.n_chains; chain += stride)
       run_chain(ex, k, ws, sv, cfg, hot, tab, (int)chain);
-    return;
+  } else {
+    // lockstep: every group takes part in every round's exchange and barrier
+    const long long rounds = (k.n_chains + stride - 1) / stride;
+    for (long long rd = 0; rd < rounds; ++rd) {
+      const long long chain = slot + rd * stride;
+      if (chain < k.n_chains)
+        run_chain(ex, k, ws, sv, cfg, hot, tab, (int)chain, g, NG);
+      else
+        lock_exchange(ex, (SharedV*)nullptr, g, NG, false);
+      __syncthreads();
+    }
   }
-  // lockstep: every group takes part in every round's exchange and barrier
-  const long long rounds = (k.n_chains + stride - 1) / stride;
-  for (long long rd = 0; rd < rounds; ++rd) {
-    const long long chain = slot + rd * stride;
-    if (chain < k.n_chains)
-      run_chain(ex, k, ws, sv, cfg, hot, tab, (int)chain, g, NG);
-    else
-      lock_exchange(ex, (SharedV*)nullptr, g, NG, false);
-    __syncthreads();
-  }
+  tc_end(k, NG);
 }
 
 template <class T>
@@ -982,6 +1056,7 @@ __global__ void __launch_bounds__(256, 2)
   T* ws = arena + (long long)blockIdx.x * ws_stride;
   const int* tab = nullptr;
   int cur = -1;
+  tc_begin(ks[0], 1, dyn_smem, 0);
   for (long long gidx = blockIdx.x; gidx < total; gidx += gridDim.x) {
     int i = 0;
     while (i + 1 < n_ctx && gidx >= start[i + 1]) ++i;
@@ -995,6 +1070,7 @@ __global__ void __launch_bounds__(256, 2)
     }
     run_chain(ex, k, ws, sv, dyn_smem, (T*)(dyn_smem + k.smem_cfg_bytes), tab, (int)(gidx - start[i]));
   }
+  tc_end(ks[0], 1);
 }
 
 }  // namespace gcf

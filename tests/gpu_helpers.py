@@ -13,18 +13,25 @@ from oracle.lattice import Lattice
 TOL = {"fp32": 1e-4, "fp64": 1e-9}
 
 
-def setup(Lx, Ly, N, D, chi, seed, complex_=False, matter=False, precision="fp32", h=1.0, g=0.5, J=0.0,
-          Q=None):
-    """Oracle PEPS + GPU context on the same rounded tensors."""
-    import paper_2503_20566_gb300 as G
-
+def oracle_net(Lx, Ly, N, D, seed, complex_=False, matter=False, precision="fp32", Q=None):
+    """Lattice, oracle PEPS and the parameter vector, the tensors rounded to
+    the storage type of `precision` (no GPU needed)."""
     lat = Lattice(Lx, Ly, N, matter=matter, Q=Q)
     Dk = D // N
     _, n = P.layout(lat, Dk)
     raw = synth.tensor_entries(seed, n, complex_)
     store = ("c64" if complex_ else "f32") if precision != "fp64" else ("c128" if complex_ else "f64")
     vals = synth.round_to(raw, store)
-    pe = P.GIPEPS(lat, Dk, vals)
+    return lat, P.GIPEPS(lat, Dk, vals), vals
+
+
+def setup(Lx, Ly, N, D, chi, seed, complex_=False, matter=False, precision="fp32", h=1.0, g=0.5, J=0.0,
+          Q=None):
+    """Oracle PEPS + GPU context on the same rounded tensors."""
+    import paper_2503_20566_gb300 as G
+
+    lat, pe, vals = oracle_net(Lx, Ly, N, D, seed, complex_, matter, precision, Q)
+    n = pe.n_params
     ctx = G.Context(N, Lx, Ly, D, chi, matter=matter, Q=Q, h=h, g=g, J=J, complex_=complex_,
                     precision=precision, seed=seed)
     assert ctx.n_params == n

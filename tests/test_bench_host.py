@@ -33,15 +33,28 @@ def test_kernel_sources_are_the_include_closure_of_the_fp32_kernel():
     assert len(bench.source_hash()) == 16
 
 
-def test_traffic_only_for_the_captured_form():
-    txt = open(bench.PROFILE).read()
-    kernel, level = re.search(r"kernel_form: (\S+) level (\d+)", txt).groups()
-    per_sample = float(re.search(r"traffic_bytes_per_sample: ([0-9.eE+]+)", txt).group(1))
-    if re.search(r"source_sha256: ([0-9a-f]+)", txt).group(1) != bench.source_hash():
-        pytest.skip("kernel sources changed since the capture (traffic is then null by design)")
-    assert bench.profiled_traffic(1000, kernel, int(level)) == pytest.approx(1000 * per_sample)
-    assert bench.profiled_traffic(1000, kernel, int(level) + 1) is None
-    assert bench.profiled_traffic(1000, "gcf::vmc_kernel<float>", int(level)) is None
+def test_traffic_only_for_the_captured_form(tmp_path):
+    """A capture counts for its own workload, kernel form and sources only."""
+    kernel, level, wl = "gcf::vmc_kernel_multi<float>", 0, "some_workload"
+    (tmp_path / "k.md").write_text(f"workload: {wl}\nsource_sha256: {bench.source_hash()}\n"
+                                   f"kernel_form: {kernel} level {level}\ntraffic_bytes_per_sample: 2.5e4\n")
+    assert bench.profiled_traffic(1000, kernel, level, wl, str(tmp_path)) == pytest.approx(2.5e7)
+    assert bench.profiled_traffic(1000, kernel, level + 1, wl, str(tmp_path)) is None
+    assert bench.profiled_traffic(1000, "gcf::vmc_kernel<float>", level, wl, str(tmp_path)) is None
+    assert bench.profiled_traffic(1000, kernel, level, "other_workload", str(tmp_path)) is None
+    (tmp_path / "k.md").write_text(f"workload: {wl}\nsource_sha256: 0000000000000000\n"
+                                   f"kernel_form: {kernel} level {level}\ntraffic_bytes_per_sample: 2.5e4\n")
+    assert bench.profiled_traffic(1000, kernel, level, wl, str(tmp_path)) is None
+
+
+def test_workloads_follow_the_stated_configurations():
+    """The default workload is the mixed-size Z2 + bosons one: 16384 chains
+    over 16x16 / 24x24 / 32x32, D = 4, chi = 24, half filling."""
+    w = bench.WORKLOADS[bench.DEFAULT_CONFIG]
+    assert sum(l["chains"] for l in w["lattices"]) == 16384
+    assert [l["Lx"] for l in w["lattices"]] == [16, 24, 32]
+    assert all(l["D"] == 4 and l["chi"] == 24 and l["matter"] and l["N"] == 2 for l in w["lattices"])
+    assert bench.flops_per_sample(32, 32, 2, 24) == pytest.approx(1.1e9, rel=0.05)
 
 
 def test_err_vs_fp64_compares_the_two_forms(monkeypatch):
@@ -75,7 +88,8 @@ def test_err_vs_fp64_compares_the_two_forms(monkeypatch):
             self.closed = True
 
     monkeypatch.setattr(G, "Context", Form)
-    out = bench.err_vs_fp64(Form(), torch.zeros((100, 5), dtype=torch.int8), bench.WORKLOAD, n_check=64)
+    lat = bench.WORKLOADS["z2_8x8"]["lattices"][0]
+    out = bench.err_vs_fp64([Form()], [torch.zeros((100, 5), dtype=torch.int8)], [lat], n_check=64)
     assert out["configs"] == 64
     assert out["amp_max"] == pytest.approx(1e-5, rel=1e-3) and out["amp_median"] == pytest.approx(1e-5, rel=1e-3)
     assert out["eloc_max"] == pytest.approx(1e-4, rel=1e-3)

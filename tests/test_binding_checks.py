@@ -20,7 +20,39 @@ def fake_ctx():
     ctx.N, ctx.Lx, ctx.Ly, ctx.D, ctx.chi, ctx.Dk = 2, 4, 3, 4, 4, 2
     ctx.n_s, ctx.n_plaq, ctx.cfg_len = 12, 6, 29
     ctx.o_dtype, ctx.complex = torch.float32, False
+    ctx.device = 0
+    ctx._dev = torch.device("cuda", 0)
     return ctx
+
+
+class _OtherGpuTensor:
+    """Stands in for a CUDA tensor on another GPU (cuda:1): right dtype, size
+    and layout, wrong device."""
+
+    def __init__(self, dtype, n):
+        self.dtype, self._n = dtype, n
+        self.is_cuda = True
+        self.device = torch.device("cuda", 1)
+
+    def data_ptr(self):
+        return 0
+
+    def numel(self):
+        return self._n
+
+    def is_contiguous(self):
+        return True
+
+
+def test_buffers_on_another_gpu_are_refused():
+    """A buffer on another GPU than the context's would be dereferenced by a
+    kernel on the context's GPU: refused before any pointer is passed."""
+    buf = _OtherGpuTensor(torch.float64, 100)
+    with pytest.raises(ValueError, match="cuda:1, the context lives on cuda:0"):
+        B._check_device_buffers([(buf, torch.float64, 10, "out['log_abs']")], 0)
+    B._check_device_buffers([(buf, torch.float64, 10, "out['log_abs']")], 1)  # same device: accepted
+    with pytest.raises(ValueError, match="cuda:1"):
+        B._check_samples({"e_loc": buf}, 4, 2, 12, 16, torch.float32, "sample_batch", 0)
 
 
 def test_sample_batch_refuses_bad_configs():

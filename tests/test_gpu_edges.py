@@ -157,3 +157,32 @@ def test_rejected_calls():
     assert ei.value.status == GCF_EINVAL
     assert ctx.launch_count == n0
     assert np.array_equal(dev.cpu().numpy(), cfgs)
+
+
+def test_svd_sweep_limit_is_reported():
+    """A truncated-bond SVD that stops at its sweep limit is reported, not
+    silent: with one Jacobi sweep a truncating contraction cannot converge,
+    so gcf_amplitude returns GCF_ETIMEOUT and counts the SVDs; with the
+    default limit the same call converges, reports none and matches the
+    oracle."""
+    from paper_2503_20566_gb300.binding import GCF_ETIMEOUT, GcfError
+
+    Lx, Ly, N, D, chi = 6, 5, 2, 4, 3
+    lat, pe, ctx = setup(Lx, Ly, N, D, chi, seed=151)
+    cfgs, _, _ = configs_for(lat, 3, seed=152)
+    dev = torch.from_numpy(cfgs).cuda()
+    la, ph = (t.cpu().numpy() for t in ctx.amplitude(dev))
+    assert ctx.svd_unconverged == 0
+    for i, c in enumerate(cfgs):
+        assert amp_err(la[i], ph[i], *vmc.amplitude(pe, c, chi)) < TOL["fp32"]
+    ctx.set_svd_sweeps(1)
+    with pytest.raises(GcfError) as err:
+        ctx.amplitude(dev)
+    assert err.value.status == GCF_ETIMEOUT
+    assert ctx.svd_unconverged > 0
+    ctx.set_svd_sweeps(40)
+    ctx.amplitude(dev)
+    assert ctx.svd_unconverged == 0
+    with pytest.raises(GcfError) as err:
+        ctx.set_svd_sweeps(0)
+    assert err.value.status == GCF_EINVAL

@@ -2,9 +2,13 @@
 
 precision="tf32": the contraction GEMMs run on tensor cores with the 3-pass
 TF32 split (about 21 significant bits), held to the FP32 bound 1e-4.
-precision="bf16": boundary-MPS and strip GEMM operands rounded to BF16 with
-FP32 accumulation (row environments in the TF32 form); its measured error is
-printed and guarded.  Amplitudes are compared as |exp(d log|psi| + i d
+precision="bf16": the strip-environment GEMMs (plaquette and vertical-hop
+ratios: Metropolis decisions and E_loc) take BF16 operands with FP32
+accumulation, on the fifth-generation tensor cores (tcgen05) for real tensors
+and on mma.sync for complex ones; the boundary-MPS absorption and the row
+environments (amplitude, O) run in the TF32x3 form.  Held to the BF16 bound
+1e-2 on E_loc and to the FP32-class bound on amplitudes and O, whose GEMMs
+never see BF16.  Amplitudes are compared as |exp(d log|psi| + i d
 phase) - 1|, E_loc relative to its off-diagonal part, O relative to the
 largest entry of its block, as in the FP32 parity tests.
 """
@@ -20,12 +24,11 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-# TF32x3 is held to the FP32 bound.  Plain BF16 operand rounding does not
-# reach 1e-2 on these random-tensor networks (measured 0.6-5% amplitude
-# error, up to 18% on E_loc and 11% on O); the BF16 bounds below guard that
-# measured level against regressions.
+# TF32x3 is held to the FP32 bound; the BF16 form to the BF16 bound 1e-2 on
+# E_loc (the only output that passes through BF16 GEMMs) and to the TF32x3
+# bounds on amplitudes and O.
 TOL = {"tf32": {"amp": 1e-4, "eloc": 1e-3, "grad": 1e-3},
-       "bf16": {"amp": 0.1, "eloc": 0.5, "grad": 0.3}}
+       "bf16": {"amp": 1e-4, "eloc": 1e-2, "grad": 1e-3}}
 
 CASES = [
     (8, 8, 2, 4, 16, False, False),  # 8x8 Z2 D=4 chi=16 (exact)
@@ -70,7 +73,11 @@ def test_mixed_precision_amplitude_energy_gradient(case, prec):
             d = O[i, v, : r.size] - r
             worst["grad"] = max(worst["grad"], np.abs(d).max() / max(1.0, np.abs(r).max()))
             worst["grad_fro"] = max(worst["grad_fro"], np.linalg.norm(d) / max(1e-300, np.linalg.norm(r)))
-    print(prec, _ids(case), {k: float("%.3g" % v) for k, v in worst.items()})
+    print(prec, _ids(case), {k: float("%.3g" % v) for k, v in worst.items()},
+          "tcgen05" if ctx.tensor_core_form else "mma.sync")
+    if prec == "bf16" and not cplx:
+        assert ctx.tensor_core_form  # real chains of the BF16 form run on tcgen05
+    assert ctx.tensor_timeouts == 0
     for key in ("amp", "eloc", "grad"):
         assert worst[key] <= tol[key], (key, worst[key])
 
