@@ -56,15 +56,15 @@ WORKLOADS = {
         lattices=[_lattice(2, 16, 4, 24, 5462, 0.33, J=0.5, matter=True),
                   _lattice(2, 24, 4, 24, 5461, 0.33, J=0.5, matter=True),
                   _lattice(2, 32, 4, 24, 5461, 0.33, J=0.5, matter=True)],
-        sweeps=1, mode="sr", dt=0.0),
+        sweeps=1, batches=16, mode="sr", dt=0.0),
     "z3_16x16": dict(workload="z3_16x16_D6_chi32_c64_8192chains", lattices=[_lattice(3, 16, 6, 32, 8192, 0.375, cplx=True)],
-                     sweeps=1, mode="sr", dt=0.0),
+                     sweeps=1, batches=8, mode="sr", dt=0.0),
     "z4_16x16": dict(workload="z4_16x16_D8_chi32_c64_8192chains", lattices=[_lattice(4, 16, 8, 32, 8192, 0.33, cplx=True)],
-                     sweeps=1, mode="sr", dt=0.0),
+                     sweeps=1, batches=8, mode="sr", dt=0.0),
     "z2_10x10_tvmc": dict(workload="z2_10x10_D6_chi36_c64_tvmc_dt0.01_8192samples", lattices=[_lattice(2, 10, 6, 36, 8192, 0.2, cplx=True)],
-                          sweeps=1, mode="tvmc", dt=0.01),
+                          sweeps=1, batches=8, mode="tvmc", dt=0.01),
     "z2_8x8": dict(workload="z2_8x8_D4_chi16_4096chains_x64sweeps", lattices=[_lattice(2, 8, 4, 16, 4096, 0.5)],
-                   sweeps=64, mode="sr", dt=0.0),
+                   sweeps=64, batches=1, mode="sr", dt=0.0),
 }
 DEFAULT_CONFIG = "z2b_32x32_mixed"
 SR_ARGS = dict(diag_shift=1e-4, lr=0.01, max_iter=100, tol=1e-6)
@@ -298,7 +298,13 @@ def run_reference(args):
 
 
 class Workload:
-    """The workload's contexts, chains and sample buffers on this rank."""
+    """The workload's contexts, chains and sample buffers on this rank.
+
+    The chains of the truncated workloads are advanced in `batches` equal
+    shares, one share per step in turn (one persistent launch per step), so
+    that a step takes seconds; every chain of the workload is kept and
+    advances once every `batches` steps, and the SR / tVMC update of a step
+    uses that step's samples."""
 
     def __init__(self, config, precision, seeds, chains_scale=1.0):
         import torch
@@ -310,6 +316,9 @@ class Workload:
         self.lats = [dict(l, chains=max(1, int(round(l["chains"] * chains_scale)))) for l in self.wl["lattices"]]
         self.sweeps = self.wl["sweeps"]
         self.mode = self.wl["mode"]
+        self.batches = max(1, int(self.wl.get("batches", 1)))
+        self.batch = 0
+        self.per_batch = [-(-w["chains"] // self.batches) for w in self.lats]
         self.ctxs, self.configs, self.samples = [], [], []
         for li, w in enumerate(self.lats):
             ctx = G.Context(w["N"], w["Lx"], w["Ly"], w["D"], w["chi"], matter=w["matter"], h=w["h_p"], g=w["g"],
@@ -322,56 +331,90 @@ class Workload:
                 occ = torch.from_numpy(synth.occupations(seeds["chains"] + li, n, w["Lx"] * w["Ly"],
                                                          (w["Lx"] * w["Ly"]) // 2))
             self.configs.append(ctx.init_configs(n, occupations=occ, powers=powers))
-            self.samples.append(ctx.alloc_samples(n, self.sweeps, grad=True))
+            self.samples.append(ctx.alloc_samples(self.per_batch[li], self.sweeps, grad=True))
             self.ctxs.append(ctx)
-        self.samples_per_launch = sum(w["chains"] for w in self.lats) * self.sweeps
         self.launches_per_step = 2 if self.mode == "tvmc" else 1
-        self.samples_per_step = self.samples_per_launch * self.launches_per_step
+
+    def _slice(self, b):
+        """Per lattice: (configs of batch b, its chain count)."""
+        out = []
+        for li, w in enumerate(self.lats):
+            a = b * self.per_batch[li]
+            e = min(w["chains"], a + self.per_batch[li])
+            out.append((self.configs[li][a:e], max(0, e - a)))
+        return out
+
+    def _outs(self, counts):
+        """The sample buffers cut to n chains (e_loc holds two values per sample)."""
+        per = {"e_loc": 2}
+        out = []
+        for smp, n in zip(self.samples, counts):
+            d = {}
+            for k, v in smp.items():
+                d[k] = v[:n] if k in ("accepted", "proposed") else v[: n * self.sweeps * per.get(k, 1)]
+            out.append(d)
+        return out
+
+    def samples_in_batch(self, b):
+        return sum(n for _, n in self._slice(b)) * self.sweeps
+
+    @property
+    def samples_per_launch(self):
+        """Samples of one launch, averaged over the batches."""
+        return sum(self.samples_in_batch(b) for b in range(self.batches)) / self.batches
 
     @property
     def stream(self):
         return self.ctxs[0].stream
 
-    def sample(self, seed):
+    def sample(self, seed, b):
         import paper_2503_20566_gb300 as G
 
+        sl = self._slice(b)
+        outs = self._outs([n for _, n in sl])
         if len(self.ctxs) == 1:
-            self.ctxs[0].sample_batch(self.configs[0], self.sweeps, seed=seed, out=self.samples[0])
+            self.ctxs[0].sample_batch(sl[0][0], self.sweeps, seed=seed, out=outs[0])
         else:
-            G.sample_multi(self.ctxs, self.configs, self.sweeps, [seed + 7919 * i for i in range(len(self.ctxs))],
-                           outs=self.samples)
+            G.sample_multi(self.ctxs, [c for c, _ in sl], self.sweeps, [seed + 7919 * i for i in range(len(self.ctxs))],
+                           outs=outs)
+        return outs, [n for _, n in sl]
 
-    def update(self, stage=0):
+    def update(self, outs, counts, stage=0):
         import paper_2503_20566_gb300 as G
 
         stats = []
         mode = G.SR if self.mode == "sr" else (G.TDVP_STAGE1 if stage == 0 else G.TDVP_STAGE2)
-        for ctx, smp, w in zip(self.ctxs, self.samples, self.lats):
-            stats.append(ctx.sr_step(smp, w["chains"], mode=mode, dt=self.wl["dt"], **SR_ARGS))
+        for ctx, smp, n in zip(self.ctxs, outs, counts):
+            stats.append(ctx.sr_step(smp, n, mode=mode, dt=self.wl["dt"], **SR_ARGS))
         return stats
 
     def step(self, seed, ev=None, stream=None):
-        """One VMC iteration; ev: (start, after-sampling, end) events of each
-        sampling launch and update, recorded on `stream`."""
+        """One VMC iteration on the next batch of chains; ev: (start,
+        after-sampling, end) events of each sampling launch and update,
+        recorded on `stream`.  Returns (stats, samples of the step)."""
         stats = None
+        b = self.batch
+        self.batch = (self.batch + 1) % self.batches
         for stage in range(self.launches_per_step):
             if ev:
                 ev[stage][0].record(stream)
-            self.sample(seed + 100 * stage)
+            outs, counts = self.sample(seed + 100 * stage, b)
             if ev:
                 ev[stage][1].record(stream)
-            stats = self.update(stage)
+            stats = self.update(outs, counts, stage)
             if ev:
                 ev[stage][2].record(stream)
-        return stats
+        return stats, self.samples_in_batch(b) * self.launches_per_step
 
     def flops_per_launch(self):
+        """Algorithmic work of one launch, averaged over the batches."""
         return sum(flops_per_sample(w["Lx"], w["Ly"], w["D"] // w["N"], w["chi"], w["cplx"]) * w["chains"] * self.sweeps
-                   for w in self.lats)
+                   for w in self.lats) / self.batches
 
     def kernel_name(self):
+        """Name of the sampling kernel the last launch ran."""
         if len(self.ctxs) > 1:
-            return "gcf::vmc_kernel_multi"
+            return "gcf::vmc_kernel_multi4" if self.ctxs[0].multi_chains_per_cta == 4 else "gcf::vmc_kernel_multi"
         return self.ctxs[0].kernel_name
 
     def scalar(self):
@@ -432,7 +475,6 @@ def main():
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         sub = W.configs[0][: min(W.configs[0].shape[0], 8 * sms)]
         tune_ms = W.ctxs[0].autotune(sub, n_sweeps=min(4, W.sweeps))
-    kernel_name = W.kernel_name() + W.scalar()
     stream = W.stream
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -451,37 +493,45 @@ def main():
     torch.cuda.synchronize()
     stats = None
     energies = []
+    samples_done = 0
     for i in range(args.steps):
         flush.fill_(float(i))  # 256 MiB write evicts L2 between steps (outside the events)
         with torch.cuda.stream(stream):
-            stats = W.step(seeds["step"](i), ev[i], stream)
+            stats, n_smp = W.step(seeds["step"](i), ev[i], stream)
+        samples_done += n_smp
         energies.append([s[0] for s in stats])
     torch.cuda.synchronize()
     clocks = clocks_sampler_stop(sampler, sf, clk_path, torch.cuda.current_device())
+    kernel_name = W.kernel_name() + W.scalar()
+    # the four-chain multi-context kernel keeps its hot buffers in scratch
+    smem_level = 0 if "multi4" in kernel_name else W.ctxs[0].smem_level
     launches = sum(c.launch_count for c in W.ctxs) - launches0
     t_steps = [sum(e[0].elapsed_time(e[2]) for e in ev[i]) for i in range(args.steps)]
     t_kernel = [[e[0].elapsed_time(e[1]) for e in ev[i]] for i in range(args.steps)]
     kern_launch_ms = float(np.mean([t for row in t_kernel for t in row]))
     group = dist.group.WORLD if dist else None
     total_ms = replicas.max_over_ranks(float(sum(t_steps)), group, "cuda")
-    value = replicas.whole_job_rate(W.samples_per_step, args.steps, world, total_ms)
+    value = replicas.whole_job_rate(samples_done / args.steps, args.steps, world, total_ms)
 
     # the contraction forms side by side (sampling launch only, same tensors,
     # a quarter of the chains): plain FP32 on CUDA cores, TF32x3 and BF16
     forms = None
     if rank == 0 and world == 1 and not args.no_forms:
-        forms = {"chains_scale": 0.25 * args.chains_scale, "unit": "samples/s (sampling launch only)"}
+        forms = {"chains": "one batch of the workload (the first), second launch on it",
+                 "unit": "samples/s (sampling launch only)"}
         for prec in ("fp32", "tf32", "bf16"):
-            F = Workload(args.config, prec, seeds, 0.25 * args.chains_scale)
-            F.sample(1)
+            F = Workload(args.config, prec, seeds, args.chains_scale)
+            F.sample(1, 0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(F.stream):
                 e0.record(F.stream)
-                F.sample(2)
+                F.sample(2, 0)
                 e1.record(F.stream)
             torch.cuda.synchronize()
-            forms[{"fp32": "fp32", "tf32": "tf32x3", "bf16": "bf16"}[prec]] = \
-                F.samples_per_launch / (e0.elapsed_time(e1) / 1e3)
+            forms[{"fp32": "fp32", "tf32": "tf32x3", "bf16": "bf16x3"}[prec]] = \
+                F.samples_in_batch(0) / (e0.elapsed_time(e1) / 1e3)
+            if prec == "bf16":
+                forms["bf16x3_on_tcgen05"] = all(c.tensor_core_form for c in F.ctxs)
             for c in F.ctxs:
                 c.close()
             del F
@@ -492,22 +542,32 @@ def main():
     e2e = None
     if not args.no_e2e:
         host_cfg = [c.cpu().pin_memory() for c in W.configs]
-        h2d = sum(c.numel() for c in host_cfg)
-        d2h = h2d + 8 * 8 * len(W.ctxs) * W.launches_per_step
+        e2e_steps = min(args.steps, 3)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
-        for i in range(args.steps):
-            for dev, host in zip(W.configs, host_cfg):
-                dev.copy_(host, non_blocking=True)
-            W.step(50_000 + 1000 * i + rank)
-            for dev, host in zip(W.configs, host_cfg):
-                host.copy_(dev, non_blocking=True)
+        done, h2d, d2h = 0, 0, 0
+        for i in range(e2e_steps):
+            b = W.batch
+            for li, w in enumerate(W.lats):
+                a = b * W.per_batch[li]
+                e = min(w["chains"], a + W.per_batch[li])
+                W.configs[li][a:e].copy_(host_cfg[li][a:e], non_blocking=True)
+                h2d += host_cfg[li][a:e].numel()
+            _, n_smp = W.step(50_000 + 1000 * i + rank)
+            done += n_smp
+            for li, w in enumerate(W.lats):
+                a = b * W.per_batch[li]
+                e = min(w["chains"], a + W.per_batch[li])
+                host_cfg[li][a:e].copy_(W.configs[li][a:e], non_blocking=True)
+                d2h += host_cfg[li][a:e].numel()
+            d2h += 8 * 8 * len(W.ctxs) * W.launches_per_step  # the SR statistics
             torch.cuda.synchronize()
         e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, group, "cuda")
-        e2e = {"value": replicas.whole_job_rate(W.samples_per_step, args.steps, world, 1000.0 * e2e_s),
-               "unit": "samples/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        e2e = {"value": replicas.whole_job_rate(done / e2e_steps, e2e_steps, world, 1000.0 * e2e_s),
+               "unit": "samples/s", "h2d_bytes_per_step": int(h2d // e2e_steps),
+               "d2h_bytes_per_step": int(d2h // e2e_steps), "steps": e2e_steps}
 
     if rank == 0:
         err = None
@@ -532,12 +592,18 @@ def main():
             "config": {"workload": wl["workload"],
                        "lattices": [f"{w['Lx']}x{w['Ly']} Z{w['N']}{' + hard-core bosons' if w['matter'] else ''} "
                                     f"D={w['D']} chi={w['chi']} chains={w['chains']}" for w in W.lats],
+                       "chains_total": sum(w["chains"] for w in W.lats), "batches": W.batches,
+                       "chains_per_step": samples_done / args.steps / W.launches_per_step / W.sweeps,
+                       "batching": ("all chains every step" if W.batches == 1 else
+                                    f"the chains in {W.batches} equal shares, one share per step in turn "
+                                    "(one persistent launch per step; every chain kept and advanced once "
+                                    f"every {W.batches} steps; the update uses the step's samples)"),
                        "sweeps_per_launch": W.sweeps, "launches_per_step": W.launches_per_step,
                        "couplings": {"h": W.lats[0]["h_p"], "g": W.lats[0]["g"], "J": W.lats[0]["J"]},
                        "update": "two-stage tVMC (dt=%g)" % wl["dt"] if W.mode == "tvmc" else "SR",
                        "precision": args.precision, "sr": SR_ARGS, "parallelism": f"replicas{world}",
                        "l2": "256 MiB buffer written between timed steps (outside the events)",
-                       "kernel_form": {"kernel": kernel_name, "smem_level": W.ctxs[0].smem_level,
+                       "kernel_form": {"kernel": kernel_name, "smem_level": smem_level,
                                        "autotune_ms_per_form": [round(t, 3) if t < 1e299 else None
                                                                 for t in tune_ms]}},
             "gpu_launches": launches,
@@ -545,7 +611,7 @@ def main():
             "update_ms": float(np.mean(t_steps)) - kern_launch_ms * W.launches_per_step,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
                          "frac": achieved / tc_peak if tc_peak else None,
-                         "traffic": profiled_traffic(W.samples_per_launch, kernel_name, W.ctxs[0].smem_level,
+                         "traffic": profiled_traffic(W.samples_per_launch, kernel_name, smem_level,
                                                      wl["workload"]),
                          "kernel": kernel_name, "algorithmic_flop_per_launch": fl,
                          "peak_source": f"TF32 tensor peak = 1/2 x bf16 sustained ({src})",

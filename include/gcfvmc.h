@@ -357,6 +357,14 @@ int gcf_tensor_core_form(const gcf_ctx* ctx);
  * the rest of the launch; results are unaffected).  0 normally. */
 int gcf_tensor_timeouts(const gcf_ctx* ctx);
 
+/* Chains per CTA of the last gcf_sample_multi launch made with ctx as
+ * ctxs[0] (implementation detail, no counterpart in the paper): 1 for
+ * gcf::vmc_kernel_multi (one chain per CTA of 256 threads), 4 for
+ * gcf::vmc_kernel_multi4 (four chains per CTA of 512 threads, chosen when a
+ * context truncates; GCFVMC_MULTI=cta|group4 forces one), 0 before any
+ * launch, -1 for a NULL context. */
+int gcf_multi_chains_per_cta(const gcf_ctx* ctx);
+
 /* Sweep limit of the one-sided Jacobi SVD for this context's later launches,
  * 1 <= max_sweeps <= 1000 (default 40; each sweep visits every column pair
  * once).  GCF_EINVAL outside that range. */

@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH):
         "gcf_checkpoint_interval": (i, [vp]),
         "gcf_tensor_core_form": (i, [vp]),
         "gcf_tensor_timeouts": (i, [vp]),
+        "gcf_multi_chains_per_cta": (i, [vp]),
         "gcf_set_svd_sweeps": (i, [vp, i]),
         "gcf_autotune": (i, [vp, i, i, vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
         "gcf_set_tensors": (i, [vp, vp, C.c_size_t]),
@@ -98,7 +99,7 @@ def load_library(path: str = LIB_PATH):
 def exported_symbols():
     """Names the binding expects the library to export."""
     return ["gcf_init_peps", "gcf_destroy", "gcf_last_error", "gcf_num_params", "gcf_config_len",
-            "gcf_scalar_bytes", "gcf_launch_count", "gcf_executor", "gcf_smem_level", "gcf_phase_timeouts", "gcf_svd_unconverged", "gcf_set_svd_sweeps", "gcf_scratch_bytes_per_chain", "gcf_checkpoint_interval", "gcf_tensor_core_form", "gcf_tensor_timeouts", "gcf_autotune", "gcf_set_tensors", "gcf_get_tensors",
+            "gcf_scalar_bytes", "gcf_launch_count", "gcf_executor", "gcf_smem_level", "gcf_phase_timeouts", "gcf_svd_unconverged", "gcf_set_svd_sweeps", "gcf_scratch_bytes_per_chain", "gcf_checkpoint_interval", "gcf_tensor_core_form", "gcf_tensor_timeouts", "gcf_multi_chains_per_cta", "gcf_autotune", "gcf_set_tensors", "gcf_get_tensors",
             "gcf_init_configs", "gcf_amplitude", "gcf_local_energy", "gcf_log_grad", "gcf_log_grad_vjp", "gcf_sample_multi",
             "gcf_sample_batch", "gcf_sample_batch_async", "gcf_sr_step", "gcf_vmc_step_host"]
 
@@ -240,6 +241,11 @@ class Context:
     def tensor_core_form(self):
         """True if the BF16 form's environment GEMMs run on tcgen05 tensor cores."""
         return bool(self.lib.gcf_tensor_core_form(self.ctx))
+
+    @property
+    def multi_chains_per_cta(self):
+        """Chains per CTA of the last sample_multi launch with this context first."""
+        return int(self.lib.gcf_multi_chains_per_cta(self.ctx))
 
     @property
     def tensor_timeouts(self):

@@ -46,6 +46,8 @@ struct Plan {
   // BF16 form of real chains: bytes of the tcgen05 operand staging area of
   // one chain (0: the tensor-core GEMMs of that form stay on mma.sync)
   long long tc_bytes = 0;
+  // shared-memory factorisation workspace of one chain (scalars; 0: none)
+  long long fz_elems = 0;
   long long level_elems(int lv) const {
     return lv <= 0 ? 0 : lv == 1 ? hot_base_elems : lv == 2 ? hot_mps_elems : hot_all_elems;
   }
@@ -72,6 +74,7 @@ struct gcf_ctx {
   int last_phase_timeouts = 0;
   int last_svd_unconverged = 0;  // SVDs that hit the sweep limit in the last synchronous launch
   int last_tc_timeouts = 0;      // tensor-core waits that ran out in the last synchronous launch
+  int last_multi_block = 0;      // block size of the last gcf_sample_multi launch (256 or 512)
   int svd_sweeps = 40;           // sweep limit of the one-sided Jacobi SVD
   int tab_ints = 0;  // ints in d_tables
   // device
@@ -193,18 +196,22 @@ enum ExecKind { EXEC_CTA = 0, EXEC_GROUP = 1, EXEC_GROUP4 = 2 };
 // placement level] then, for the tcgen05 path, the operand staging area at
 // a 16-byte boundary.  CTA form: from the block's base; group form: each
 // group's region also starts with its SharedV.
+// Then the factorisation workspace (fz_elems scalars) at a 16-byte boundary.
+inline size_t r16(size_t b) { return (b + 15) / 16 * 16; }
 size_t cta_tc_off(const Plan& p, int level, size_t sb) {
-  return ((size_t)p.cfg_bytes + (size_t)p.level_elems(level) * sb + 15) / 16 * 16;
+  return r16((size_t)p.cfg_bytes + (size_t)p.level_elems(level) * sb);
 }
+size_t cta_fz_off(const Plan& p, int level, size_t sb) { return cta_tc_off(p, level, sb) + r16((size_t)p.tc_bytes); }
 size_t cta_smem_bytes(const Plan& p, int level, size_t sb) {
-  return p.tc_bytes ? cta_tc_off(p, level, sb) + (size_t)p.tc_bytes
-                    : (size_t)p.cfg_bytes + (size_t)p.level_elems(level) * sb;
+  if (!p.tc_bytes && !p.fz_elems) return (size_t)p.cfg_bytes + (size_t)p.level_elems(level) * sb;
+  return cta_fz_off(p, level, sb) + (size_t)p.fz_elems * sb;
 }
 size_t group_tc_off(const Plan& p, int level, size_t sb) {
-  return (sharedv_bytes() + (size_t)p.cfg_bytes + (size_t)p.level_elems(level) * sb + 15) / 16 * 16;
+  return r16(sharedv_bytes() + (size_t)p.cfg_bytes + (size_t)p.level_elems(level) * sb);
 }
+size_t group_fz_off(const Plan& p, int level, size_t sb) { return group_tc_off(p, level, sb) + r16((size_t)p.tc_bytes); }
 size_t group_smem_bytes(const Plan& p, int level, size_t sb) {
-  return group_tc_off(p, level, sb) + ((size_t)p.tc_bytes + 15) / 16 * 16;
+  return r16(group_fz_off(p, level, sb) + (size_t)p.fz_elems * sb);
 }
 bool grouped(const gcf_ctx* c);
 int n_groups(const gcf_ctx* c);
@@ -342,7 +349,8 @@ void build_plan(gcf_ctx* c) {
   }
   p.mps_stride = al32(ms);
   // QR-pass sites, matrices, taus
-  long long qs = 1, mat = 1, tau = 1;
+  long long qs = 1, mat = 1, tau = 1, fzq = 0, fzj = 0;
+  bool truncates = false;
   auto step_sizes = [&](const int* bin, const int* qr, const int* svd, const int* bout, int pin,
                         int pout) {
     std::vector<int> ab(Lx + 1);
@@ -351,6 +359,7 @@ void build_plan(gcf_ctx* c) {
     ab[Lx] = 1;
     for (int cc = 0; cc < Lx; ++cc) {
       const long long rows = (long long)qr[cc] * pout, cols = ab[cc + 1];
+      fzq = std::max(fzq, rows * cols + rows * std::min(rows, cols));
       qs = std::max(qs, rows * std::min(rows, cols));
       mat = std::max(mat, (long long)ab[cc] * pout * ab[cc + 1]);  // Z
       mat = std::max(mat, rows * cols);                             // X
@@ -361,18 +370,33 @@ void build_plan(gcf_ctx* c) {
     for (int cc = Lx - 1; cc >= 1; --cc) {
       const long long yr = qr[cc], yc = (long long)pout * bout[cc + 1];
       const long long k0 = std::min(yr, yc);
+      fzq = std::max(fzq, yc * yr + yc * k0);
+      if (svd[cc]) {
+        truncates = true;
+        fzj = std::max(fzj, yr * k0 + k0 * k0);
+      }
       mat = std::max(mat, std::max(yr, yc) * std::max(yr, yc));
       mat = std::max(mat, k0 * k0);
       mat = std::max(mat, (long long)qr[cc - 1] * pout * bout[cc]);
       tau = std::max(tau, std::max(yr, yc));
     }
     (void)pin;
-    (void)svd;
   };
   for (int r = 0; r <= Ly - 2; ++r)
     step_sizes(&p.bondB[r * W], &p.qrB[r * W], &p.svdB[r * W], &p.bondB[(r + 1) * W], r == 0 ? 1 : Dk, Dk);
   for (int r = Ly - 1; r >= 1; --r)
     step_sizes(&p.bondT[(r + 1) * W], &p.qrT[r * W], &p.svdT[r * W], &p.bondT[r * W], r == Ly - 1 ? 1 : Dk, Dk);
+  // shared-memory factorisation workspace: for plans that truncate (the
+  // QR, Q formation and Jacobi sweeps then dominate), the largest of the QR
+  // and Jacobi needs that fits 64 KB; the other runs in global scratch
+  {
+    const long long cap = (64 * 1024) / (long long)c->sbytes;
+    p.fz_elems = 0;
+    if (truncates) {
+      if (fzq <= cap) p.fz_elems = std::max(p.fz_elems, fzq);
+      if (fzj <= cap) p.fz_elems = std::max(p.fz_elems, fzj);
+    }
+  }
   p.qsite_stride = al32(qs);
   p.mat_max = al32(mat);
   p.tau_max = al32(tau);
@@ -608,6 +632,8 @@ KParams<T> make_params(gcf_ctx* c) {
   k.tc_bf16 = p.tc_bytes > 0 && k.gemm_mode == GEMM_BF16 ? 1 : 0;
   k.tc_bytes = p.tc_bytes;
   k.tc_off = (long long)cta_tc_off(p, p.cta_level, c->sbytes);
+  k.fz_elems = p.fz_elems;
+  k.fz_off = (long long)cta_fz_off(p, p.cta_level, c->sbytes);
   k.status = c->d_status;
   return k;
 }
@@ -676,6 +702,7 @@ gcf_status run_vmc(gcf_ctx* c, int mode, int want, int n, int n_sweeps, uint64_t
     k.mps_in_smem = c->plan.group_level >= 2;
     k.renv_in_smem = c->plan.group_level >= 3;
     k.tc_off = (long long)group_tc_off(c->plan, c->plan.group_level, c->sbytes);
+    k.fz_off = (long long)group_fz_off(c->plan, c->plan.group_level, c->sbytes);
   }
   k.n_chains = n; k.n_sweeps = n_sweeps; k.mode = mode; k.want = want; k.seed = seed;
   k.configs = configs;
@@ -731,17 +758,54 @@ gcf_status run_multi(gcf_ctx* const* cs, int n_ctx, const int* n_chains, int n_s
   // one staging area after the largest context's configuration and hot
   // buffers; the tensor-core path runs only if every context takes it
   bool tc_all = true;
-  for (int i = 0; i < n_ctx; ++i) tc_all = tc_all && ks[i].tc_bf16;
-  if (tc_bytes > 0) smem = std::max(smem, tc_off + tc_bytes);
+  long long fz = 0;
+  for (int i = 0; i < n_ctx; ++i) {
+    tc_all = tc_all && ks[i].tc_bf16;
+    fz = std::max(fz, ks[i].fz_elems);
+  }
+  const size_t fz_off = tc_off + (tc_bytes + 15) / 16 * 16;
+  if (tc_bytes > 0 || fz > 0) smem = std::max(smem, fz_off + (size_t)fz * c0->sbytes);
   for (int i = 0; i < n_ctx; ++i) {
     ks[i].tc_bf16 = tc_all ? 1 : 0;
     ks[i].tc_off = (long long)tc_off;
     ks[i].tc_bytes = (long long)tc_bytes;
+    ks[i].fz_elems = fz;
+    ks[i].fz_off = (long long)fz_off;
   }
-  const int per_sm = occupancy_vmc_multi<T>(smem);
+  // Four chains per CTA (vmc_kernel_multi4) when some context truncates: its
+  // sampling is bound by the latency of the factorisations, which more
+  // resident chains hide; hot buffers then stay in scratch (level 0).
+  // GCFVMC_MULTI=cta|group4 forces a form.
+  int block = 256;
+  long long group_bytes = 0;
+  {
+    size_t cfg_max = 0;
+    for (int i = 0; i < n_ctx; ++i) cfg_max = std::max(cfg_max, (size_t)cs[i]->plan.cfg_bytes);
+    const size_t g_tc = (sharedv_bytes() + cfg_max + 15) / 16 * 16;
+    const size_t g_fz = g_tc + (tc_bytes + 15) / 16 * 16;
+    const size_t gb = (g_fz + (size_t)fz * c0->sbytes + 15) / 16 * 16;
+    bool want4 = fz > 0;
+    if (const char* e = std::getenv("GCFVMC_MULTI")) want4 = !std::strcmp(e, "group4");
+    if (want4 && 4 * gb <= 216 * 1024 && occupancy_vmc_multi<T>(512, 4 * gb) >= 1) {
+      block = 512;
+      group_bytes = (long long)gb;
+      smem = 4 * gb;
+      for (int i = 0; i < n_ctx; ++i) {
+        ks[i].hot_in_smem = 0;
+        ks[i].mps_in_smem = 0;
+        ks[i].renv_in_smem = 0;
+        ks[i].tc_off = (long long)g_tc;
+        ks[i].fz_off = (long long)g_fz;
+        ks[i].group_smem_bytes = group_bytes;
+      }
+    }
+  }
+  const int per_sm = occupancy_vmc_multi<T>(block, smem);
   if (per_sm < 1) return fail(c0, GCF_EINVAL, "gcf_sample_multi: the largest context does not fit an SM");
-  const long long grid = balanced_slots(total, (long long)c0->sms * per_sm);
-  const size_t arena = (size_t)grid * ws * c0->sbytes;
+  const int per_cta = block == 512 ? 4 : 1;
+  const long long slots = balanced_slots(total, (long long)c0->sms * per_sm * per_cta);
+  const long long grid = (slots + per_cta - 1) / per_cta;
+  const size_t arena = (size_t)grid * per_cta * ws * c0->sbytes;
   if (arena > c0->multi_arena_bytes) {
     if (c0->multi_arena) cudaFree(c0->multi_arena);
     c0->multi_arena = nullptr;
@@ -762,8 +826,9 @@ gcf_status run_multi(gcf_ctx* const* cs, int n_ctx, const int* n_chains, int n_s
   CUDA_TRY(c0, cudaMemcpyAsync(d_ks, ks.data(), kb, cudaMemcpyHostToDevice, c0->stream));
   CUDA_TRY(c0, cudaMemcpyAsync(d_start, start.data(), sizeof(long long) * (n_ctx + 1), cudaMemcpyHostToDevice,
                                c0->stream));
-  CUDA_TRY(c0, launch_vmc_multi<T>(d_ks, n_ctx, d_start, total, (T*)c0->multi_arena, ws, (int)grid, smem,
-                                   c0->stream));
+  CUDA_TRY(c0, launch_vmc_multi<T>(d_ks, n_ctx, d_start, total, (T*)c0->multi_arena, ws, (int)grid, block,
+                                   group_bytes, smem, c0->stream));
+  c0->last_multi_block = block;
   c0->launches += 1;
   std::vector<int> h(4 * n_ctx);
   for (int i = 0; i < n_ctx; ++i)
@@ -1245,6 +1310,10 @@ int gcf_checkpoint_interval(const gcf_ctx* c) { return c ? c->ck_every : -1; }
 int gcf_tensor_core_form(const gcf_ctx* c) { return c ? (c->plan.tc_bytes > 0 ? 1 : 0) : -1; }
 
 int gcf_tensor_timeouts(const gcf_ctx* c) { return c ? c->last_tc_timeouts : -1; }
+
+int gcf_multi_chains_per_cta(const gcf_ctx* c) {
+  return c ? (c->last_multi_block == 512 ? 4 : c->last_multi_block == 256 ? 1 : 0) : -1;
+}
 
 gcf_status gcf_set_svd_sweeps(gcf_ctx* c, int max_sweeps) {
   if (!c || max_sweeps < 1 || max_sweeps > 1000) return GCF_EINVAL;

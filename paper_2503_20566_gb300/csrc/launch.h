@@ -20,11 +20,14 @@ cudaError_t launch_vmc_grouped(const KParams<T>& k, int grid, int block, size_t 
 template <class T>
 int occupancy_vmc_grouped(int block, size_t smem);
 // chains of several contexts in one launch (one chain per CTA of 256 threads)
+// block 256: one chain per CTA (vmc_kernel_multi); block 512: four chains per
+// CTA of group_bytes shared memory each (vmc_kernel_multi4)
 template <class T>
 cudaError_t launch_vmc_multi(const KParams<T>* ks, int n_ctx, const long long* start, long long total, T* arena,
-                             long long ws_stride, int grid, size_t smem, cudaStream_t st);
+                             long long ws_stride, int grid, int block, long long group_bytes, size_t smem,
+                             cudaStream_t st);
 template <class T>
-int occupancy_vmc_multi(size_t smem);
+int occupancy_vmc_multi(int block, size_t smem);
 // bytes of the per-chain shared state of the VMC kernels (16-byte aligned)
 size_t sharedv_bytes();
 cudaError_t launch_init_configs(int N, int Lx, int Ly, int matter, const int* Q, int n_chains,

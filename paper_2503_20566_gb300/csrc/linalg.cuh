@@ -82,6 +82,15 @@ __device__ __forceinline__ R lanes_sum(R v, int L) {
   return v;
 }
 
+// Reciprocal and reciprocal square root of the Jacobi rotation parameters:
+// the hardware approximations in FP32 (a rotation need only be orthogonal to
+// rounding, and the accumulated J is re-orthogonalised after the sweeps),
+// exact in FP64.
+__device__ __forceinline__ float jrcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double jrcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float jrsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double jrsqrt(double x) { return 1.0 / sqrt(x); }
+
 // Lanes per column for `cols` independent column operations on the
 // executor: the largest power of two <= 32 whose groups of lanes cover every
 // column at once (1 if the columns outnumber the threads).
@@ -119,25 +128,27 @@ __device__ __forceinline__ void apply_reflector(const X ex, int m, int j, const 
   const int L = lanes_per_column(ex, nc);
   const int slots = ex.size() / L;
   const int sub = ex.tid() / L, li = ex.tid() - (ex.tid() / L) * L;
+  const T* vcol = A + j * sn;  // v_i = A[i][j] below the diagonal, v_j = 1
 #pragma unroll 1
   for (int base = 0; base < nc; base += slots) {
     const int c = c0 + base + sub;
     const bool act = c < c1;
+    T* mc = Mt + c * sMn;
     T w = zero<T>();
     if (act) {
-#pragma unroll 1
+#pragma unroll 2
       for (int i = j + li; i < m; i += L) {
-        const T v = (i == j) ? one<T>() : A[i * sm + j * sn];
-        w = fmac(w, conjg(v), Mt[i * sMm + c * sMn]);
+        const T v = (i == j) ? one<T>() : vcol[i * sm];
+        w = fmac(w, conjg(v), mc[i * sMm]);
       }
     }
     w = lanes_sum_scalar(w, L);
     if (act) {
       const T g = f * w;
-#pragma unroll 1
+#pragma unroll 2
       for (int i = j + li; i < m; i += L) {
-        const T v = (i == j) ? one<T>() : A[i * sm + j * sn];
-        Mt[i * sMm + c * sMn] -= v * g;
+        const T v = (i == j) ? one<T>() : vcol[i * sm];
+        mc[i * sMm] -= v * g;
       }
     }
   }
@@ -182,6 +193,44 @@ __device__ __noinline__ void cta_form_q(const X ex, int m, int k, const T* A, in
   for (int j = k - 1; j >= 0; --j) {
     apply_reflector(ex, m, j, A, sm, sn, tau[j], Q, sQm, sQn, j, k);
     ex.sync();
+  }
+}
+
+// Shared-memory factorisation workspace of each chain group: the QR / Q
+// formation and the Jacobi sweeps run on shared-memory copies of their
+// matrices when they fit (every step of these factorisations depends on the
+// previous one, so each access would otherwise wait on L2).  Set at kernel
+// entry; null when the launch has none.
+__shared__ void* g_fz[4];
+__shared__ long long g_fz_elems;  // scalars of each workspace
+
+template <class T, class X>
+__device__ inline void cta_copy(const X ex, int rows, int cols, const T* src, int lds, T* dst, int ldd) {
+#pragma unroll 1
+  for (int idx = ex.tid(); idx < rows * cols; idx += ex.size()) {
+    const int i = idx / cols, j = idx - (idx / cols) * cols;
+    dst[i * ldd + j] = src[i * lds + j];
+  }
+  ex.sync();
+}
+
+// A (m x n, row stride lda) <- its Householder QR in place (cta_qr) and
+// Q (m x kq, row stride ldq) <- the first kq columns of the orthogonal factor
+// (cta_form_q), in the chain's shared-memory workspace when both fit.
+template <class T, class X>
+__device__ __noinline__ void qr_with_q(const X ex, int m, int n, T* A, int lda, T* tau, int kq, T* Q, int ldq) {
+  T* fz = (T*)g_fz[ex.slot()];
+  if (fz && (long long)m * n + (long long)m * kq <= g_fz_elems) {
+    T* a = fz;
+    T* q = fz + m * n;
+    cta_copy(ex, m, n, A, lda, a, n);
+    cta_qr<T>(ex, m, n, a, n, 1, tau);
+    cta_form_q<T>(ex, m, kq, a, n, 1, tau, q, kq, 1);
+    cta_copy(ex, m, n, a, n, A, lda);
+    cta_copy(ex, m, kq, q, kq, Q, ldq);
+  } else {
+    cta_qr<T>(ex, m, n, A, lda, 1, tau);
+    cta_form_q<T>(ex, m, kq, A, lda, 1, tau, Q, ldq, 1);
   }
 }
 
@@ -246,17 +295,26 @@ __device__ __noinline__ int cta_jacobi_svd(const X ex, int p, int q, T* W, int s
 #pragma unroll 1
       for (int base = 0; base < npair; base += slots) {
         const int kp = base + sub;
-        int a = 0, b = 0;
-        if (kp == 0) { a = r % (n - 1); b = n - 1; }
-        else { a = (r + kp) % (n - 1); b = (r - kp + n - 1) % (n - 1); }
+        // round-robin pair kp of round r: (r + kp, r - kp) mod (n - 1), and
+        // (r, n - 1) for kp = 0; kp < n/2 keeps each sum within one period
+        int a = r, b = n - 1;
+        if (kp > 0) {
+          a = r + kp;
+          if (a >= n - 1) a -= n - 1;
+          b = r - kp;
+          if (b < 0) b += n - 1;
+        }
         if (a > b) { const int t = a; a = b; b = t; }
         const bool act = kp < npair && b < q;
+        const int rstep = L * sWm;
+        T* pa = W + li * sWm + a * sWn;
+        T* pb = W + li * sWm + b * sWn;
         R al = R(0), be = R(0), gr = R(0), gi = R(0);
         if (act) {
           T g = zero<T>();
-#pragma unroll 1
-          for (int i = li; i < p; i += L) {
-            const T wa = W[i * sWm + a * sWn], wb = W[i * sWm + b * sWn];
+#pragma unroll 2
+          for (int i = li, o = 0; i < p; i += L, o += rstep) {
+            const T wa = pa[o], wb = pb[o];
             al += abs2(wa);
             be += abs2(wb);
             g = fmac(g, conjg(wa), wb);
@@ -273,28 +331,32 @@ __device__ __noinline__ int cta_jacobi_svd(const X ex, int p, int q, T* W, int s
         // norms can underflow, and a zero threshold would rotate rounding
         // noise forever
         if (!act || ga == R(0) || !(al > negl) || !(be > negl) || !(ga > tol * (sqrt(al) * sqrt(be)))) continue;
-        const R zeta = (be - al) / (R(2) * ga);
+        const R iga = jrcp(ga);
+        const R zeta = (be - al) * (R(0.5) * iga);
         // tan of the rotation angle; for |zeta| beyond 1e15, zeta^2 would
         // overflow in FP32, and t = 1 / (2 zeta) to rounding
         const R az = fabs(zeta);
-        const R t = (zeta >= R(0) ? R(1) : R(-1)) / (az > R(1e15) ? R(2) * az : az + sqrt(R(1) + zeta * zeta));
+        const R t = (zeta >= R(0) ? R(1) : R(-1)) * jrcp(az > R(1e15) ? R(2) * az : az + sqrt(R(1) + zeta * zeta));
         if (t == R(0)) continue;  // a rotation below rounding leaves the pair as it is
-        const R c = R(1) / sqrt(R(1) + t * t), s = c * t;
+        const R c = jrsqrt(R(1) + t * t), s = c * t;
         // G = [[c, s e^{i phi}], [-s e^{-i phi}, c]], e^{i phi} = g / |g|
-        const T eph = make_scalar<T>(gr / ga, gi / ga);
+        const T eph = make_scalar<T>(gr * iga, gi * iga);
         const T s_e = scale(eph, (R)s);                 // s e^{i phi}
         const T s_ec = scale(conjg(eph), (R)s);         // s e^{-i phi}
-#pragma unroll 1
-        for (int i = li; i < p; i += L) {
-          const T wa = W[i * sWm + a * sWn], wb = W[i * sWm + b * sWn];
-          W[i * sWm + a * sWn] = scale(wa, (R)c) - wb * s_ec;
-          W[i * sWm + b * sWn] = wa * s_e + scale(wb, (R)c);
+#pragma unroll 2
+        for (int i = li, o = 0; i < p; i += L, o += rstep) {
+          const T wa = pa[o], wb = pb[o];
+          pa[o] = scale(wa, (R)c) - wb * s_ec;
+          pb[o] = wa * s_e + scale(wb, (R)c);
         }
-#pragma unroll 1
-        for (int i = li; i < q; i += L) {
-          const T ja = J[i * sJm + a * sJn], jb = J[i * sJm + b * sJn];
-          J[i * sJm + a * sJn] = scale(ja, (R)c) - jb * s_ec;
-          J[i * sJm + b * sJn] = ja * s_e + scale(jb, (R)c);
+        T* ja_p = J + li * sJm + a * sJn;
+        T* jb_p = J + li * sJm + b * sJn;
+        const int jstep = L * sJm;
+#pragma unroll 2
+        for (int i = li, o = 0; i < q; i += L, o += jstep) {
+          const T ja = ja_p[o], jb = jb_p[o];
+          ja_p[o] = scale(ja, (R)c) - jb * s_ec;
+          jb_p[o] = ja * s_e + scale(jb, (R)c);
         }
         if (li == 0) *sflag = 1;
       }

@@ -84,6 +84,10 @@ struct KParams {
   // its byte offset from the start of the chain's dynamic shared memory
   int tc_bf16;
   long long tc_bytes, tc_off;
+  // shared-memory factorisation workspace of a chain (linalg.cuh): scalars
+  // (0: none) and byte offset from the start of the chain's dynamic shared
+  // memory
+  long long fz_elems, fz_off;
   // right environments and the staged B / T rows of the current pass
   int mps_in_smem, renv_in_smem;
   long long so_envR, so_env3R, so_sB, so_sT;
@@ -432,9 +436,8 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
     T* X = (c == cL) ? Xb : M1;
     cta_gemm<T>(ex, Rrows, pout * abr, abl, M3, abl, 1, Z + sh.zoff[c], pout * abr, 1, X, pout * abr, 1, false);
     if (c == cL) break;
-    cta_qr<T>(ex, rows, cols, M1, cols, 1, tau);
     const int kq = min(rows, cols);
-    cta_form_q<T>(ex, rows, kq, M1, cols, 1, tau, Qs + sh.qoff[c], kq, 1);
+    qr_with_q<T>(ex, rows, cols, M1, cols, tau, kq, Qs + sh.qoff[c], kq);
 #pragma unroll 1
     for (int idx = ex.tid(); idx < kq * cols; idx += ex.size()) {
       const int i = idx / cols, j = idx - (idx / cols) * cols;
@@ -468,9 +471,8 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
     if (c >= 1 && (svd[c] || bdo[c] < cur)) {
       const int kk = bdo[c];
       cta_adjoint<T>(ex, yc, yr, Yp, yc, 1, Yh, yr, 1);
-      cta_qr<T>(ex, yc, yr, Yh, yr, 1, tau);
       const int k0 = min(yr, yc);
-      cta_form_q<T>(ex, yc, k0, Yh, yr, 1, tau, Qp, k0, 1);
+      qr_with_q<T>(ex, yc, yr, Yh, yr, tau, k0, Qp, k0);
       // L = R'^H (yr x k0)
 #pragma unroll 1
       for (int idx = ex.tid(); idx < yr * k0; idx += ex.size()) {
@@ -493,7 +495,18 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
         for (int idx = ex.tid(); idx < yr * k0; idx += ex.size()) L0[idx] = Lc[idx];
         ex.sync();
         int conv = 1;
-        cta_jacobi_svd<T>(ex, yr, k0, Lc, k0, 1, Jm, k0, 1, &sh.iflag[0], k.max_sweeps_svd, &conv);
+        T* fz = (T*)g_fz[ex.slot()];
+        if (fz && (long long)yr * k0 + (long long)k0 * k0 <= g_fz_elems) {
+          // sweeps on shared-memory copies; only J is needed afterwards
+          // (W is recomputed as L J below)
+          T* w = fz;
+          T* jj = fz + yr * k0;
+          cta_copy(ex, yr, k0, Lc, k0, w, k0);
+          cta_jacobi_svd<T>(ex, yr, k0, w, k0, 1, jj, k0, 1, &sh.iflag[0], k.max_sweeps_svd, &conv);
+          cta_copy(ex, k0, k0, jj, k0, Jm, k0);
+        } else {
+          cta_jacobi_svd<T>(ex, yr, k0, Lc, k0, 1, Jm, k0, 1, &sh.iflag[0], k.max_sweeps_svd, &conv);
+        }
         if (!conv && ex.tid() == 0) atomicAdd(&k.status[ST_SVD], 1);
         cta_gemm<T, true, false, false>(ex, k0, k0, k0, Jm, 1, k0, Jm, k0, 1, Gm, k0, 1, false);
         {

@@ -42,20 +42,25 @@ int occupancy_vmc_grouped<float>(int block, size_t smem) {
 size_t sharedv_bytes() { return sizeof_sharedv_aligned(); }
 template <>
 cudaError_t launch_vmc_multi<float>(const KParams<float>* ks, int n_ctx, const long long* start, long long total,
-                                  float* arena, long long ws_stride, int grid, size_t smem, cudaStream_t st) {
-  {
-    cudaError_t e = cudaFuncSetAttribute(vmc_kernel_multi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                  float* arena, long long ws_stride, int grid, int block, long long group_bytes,
+                                  size_t smem, cudaStream_t st) {
+  if (block == 512) {
+    cudaError_t e = cudaFuncSetAttribute(vmc_kernel_multi4<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    vmc_kernel_multi4<float><<<grid, 512, smem, st>>>(ks, n_ctx, start, total, arena, ws_stride, group_bytes);
+    return cudaGetLastError();
   }
+  cudaError_t e = cudaFuncSetAttribute(vmc_kernel_multi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   vmc_kernel_multi<float><<<grid, 256, smem, st>>>(ks, n_ctx, start, total, arena, ws_stride);
   return cudaGetLastError();
 }
 template <>
-int occupancy_vmc_multi<float>(size_t smem) {
-  if (cudaFuncSetAttribute(vmc_kernel_multi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
+int occupancy_vmc_multi<float>(int block, size_t smem) {
+  const void* fn = block == 512 ? (const void*)vmc_kernel_multi4<float> : (const void*)vmc_kernel_multi<float>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, vmc_kernel_multi<float>, 256, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem) != cudaSuccess) return 0;
   return n;
 }
 }  // namespace gcf

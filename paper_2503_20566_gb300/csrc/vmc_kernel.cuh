@@ -961,9 +961,14 @@ __device__ void tc_begin(const KParams<T>& k, int n_groups, int8_t* dyn_base, lo
     g_tc_stage[threadIdx.x] = (k.tc_bf16 && threadIdx.x < n_groups)
                                   ? (unsigned char*)(dyn_base + threadIdx.x * group_bytes + k.tc_off)
                                   : nullptr;
+  if (threadIdx.x < 4)
+    g_fz[threadIdx.x] = (k.fz_elems > 0 && threadIdx.x < n_groups)
+                            ? (void*)(dyn_base + threadIdx.x * group_bytes + k.fz_off)
+                            : nullptr;
   if (threadIdx.x == 0) {
     g_tc_cap = k.tc_bytes;
     g_tc_status = k.status + ST_TC_TIMEOUT;
+    g_fz_elems = k.fz_elems;
   }
   if (k.tc_bf16) tc_setup(n_groups);
   bulk_setup(n_groups);
@@ -1071,6 +1076,42 @@ __global__ void __launch_bounds__(256, 2)
     run_chain(ex, k, ws, sv, dyn_smem, (T*)(dyn_smem + k.smem_cfg_bytes), tab, (int)(gidx - start[i]));
   }
   tc_end(ks[0], 1);
+}
+
+// The same with four chains per CTA of 512 threads (groups of 128, one CTA
+// per SM): chain slot s = 4 blockIdx + group owns scratch s of the arena.
+// The groups run chains of different contexts at once, so they read the
+// contexts' tables from global memory, keep their hot buffers in scratch
+// (placement level 0) and do not keep lockstep; dynamic shared memory per
+// group: [SharedV][configuration of the largest context][tcgen05 staging]
+// [factorisation workspace] (offsets in the KParams, common to all contexts).
+template <class T>
+__global__ void __launch_bounds__(512, 1)
+    vmc_kernel_multi4(const KParams<T>* __restrict__ ks, int n_ctx, const long long* __restrict__ start,
+                      long long total, T* arena, long long ws_stride, long long group_bytes) {
+  extern __shared__ __align__(16) int8_t dyn_smem[];
+  constexpr int G = 128;
+  const int g = threadIdx.x / G, NG = blockDim.x / G;
+  if (threadIdx.x < 4) g_gemm_mode[threadIdx.x] = ks[0].gemm_mode;
+  tc_begin(ks[0], NG, dyn_smem, group_bytes);
+  int8_t* base = dyn_smem + g * group_bytes;
+  SharedV& sv = *reinterpret_cast<SharedV*>(base);
+  int8_t* cfg = base + sizeof_sharedv_aligned();
+  GroupExec<G> ex;
+  const long long slot = (long long)blockIdx.x * NG + g;
+  T* ws = arena + slot * ws_stride;
+  int cur = -1;
+  for (long long gidx = slot; gidx < total; gidx += (long long)gridDim.x * NG) {
+    int i = 0;
+    while (i + 1 < n_ctx && gidx >= start[i + 1]) ++i;
+    const KParams<T>& k = ks[i];
+    if (i != cur) {
+      init_trivial_slots(ex, k, ws);
+      cur = i;
+    }
+    run_chain(ex, k, ws, sv, cfg, (T*)(cfg + k.smem_cfg_bytes), k.tab, (int)(gidx - start[i]));
+  }
+  tc_end(ks[0], NG);
 }
 
 }  // namespace gcf

@@ -30,17 +30,23 @@ def _contexts(matter):
     return out
 
 
+@pytest.mark.parametrize("form", ["cta", "group4"])
 @pytest.mark.parametrize("matter", [False, True], ids=["gauge", "matter"])
-def test_sample_multi_equals_per_context_sampling(matter, monkeypatch):
+def test_sample_multi_equals_per_context_sampling(matter, form, monkeypatch):
+    """Both forms of the launch (one chain per CTA; four chains per CTA, the
+    form taken when a context truncates) against per-context sampling in
+    the same executor."""
     import paper_2503_20566_gb300 as G
 
-    monkeypatch.setenv("GCFVMC_EXEC", "cta")
+    monkeypatch.setenv("GCFVMC_EXEC", form)
+    monkeypatch.setenv("GCFVMC_MULTI", form)
     items = _contexts(matter)
     seeds = [1001, 2002, 3003]
     n_sweeps = 2
     dev = [torch.from_numpy(c).cuda() for (_, _, _, c) in items]
     outs = G.sample_multi([it[2] for it in items], dev, n_sweeps, seeds)
     torch.cuda.synchronize()
+    assert items[0][2].multi_chains_per_cta == (4 if form == "group4" else 1)
     for (lat, pe, ctx, cfgs), d, o, sd in zip(items, dev, outs, seeds):
         ref_cfg = torch.from_numpy(cfgs).cuda()
         ref = ctx.sample_batch(ref_cfg, n_sweeps, seed=sd)
