@@ -736,7 +736,18 @@ gcf_status run_multi(gcf_ctx* const* cs, int n_ctx, const int* n_chains, int n_s
   std::vector<long long> start(n_ctx + 1, 0);
   size_t smem = 0, tc_off = 0, tc_bytes = 0;
   long long ws = 0;
-  for (int i = 0; i < n_ctx; ++i) {
+  // The chains form one queue that the kernel's chain slots draw from when
+  // free: contexts in decreasing order of the work of one chain (sites x
+  // chi^3, the factorisations' scaling), so the longest chains start first.
+  std::vector<int> order(n_ctx);
+  for (int i = 0; i < n_ctx; ++i) order[i] = i;
+  auto cost = [&](int i) {
+    const double chi = cs[i]->m.chi;
+    return (double)cs[i]->m.Lx * cs[i]->m.Ly * chi * chi * chi * cs[i]->Dk;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  for (int j = 0; j < n_ctx; ++j) {
+    const int i = order[j];
     gcf_ctx* c = cs[i];
     KParams<T> k = make_params<T>(c);
     gcf_samples o{};
@@ -745,8 +756,8 @@ gcf_status run_multi(gcf_ctx* const* cs, int n_ctx, const int* n_chains, int n_s
     k.want = (o.log_abs || o.phase ? WANT_AMP : 0) | (o.e_loc ? WANT_ELOC : 0) | (o.O || o.block_ids ? WANT_GRAD : 0);
     k.log_abs = o.log_abs; k.phase = o.phase; k.e_loc = o.e_loc; k.block_ids = o.block_ids; k.O = (T*)o.O;
     k.accepted = o.accepted; k.proposed = o.proposed;
-    ks[i] = k;
-    start[i + 1] = start[i] + n_chains[i];
+    ks[j] = k;
+    start[j + 1] = start[j] + n_chains[i];
     smem = std::max(smem, c->plan.dyn_smem);
     tc_off = std::max(tc_off, cta_tc_off(c->plan, c->plan.cta_level, c->sbytes));
     tc_bytes = std::max(tc_bytes, (size_t)c->plan.tc_bytes);
@@ -803,7 +814,9 @@ gcf_status run_multi(gcf_ctx* const* cs, int n_ctx, const int* n_chains, int n_s
   const int per_sm = occupancy_vmc_multi<T>(block, smem);
   if (per_sm < 1) return fail(c0, GCF_EINVAL, "gcf_sample_multi: the largest context does not fit an SM");
   const int per_cta = block == 512 ? 4 : 1;
-  const long long slots = balanced_slots(total, (long long)c0->sms * per_sm * per_cta);
+  // every resident slot draws from the queue: as many slots as fit, at most
+  // one per chain
+  const long long slots = std::min<long long>(total, (long long)c0->sms * per_sm * per_cta);
   const long long grid = (slots + per_cta - 1) / per_cta;
   const size_t arena = (size_t)grid * per_cta * ws * c0->sbytes;
   if (arena > c0->multi_arena_bytes) {
@@ -813,7 +826,8 @@ gcf_status run_multi(gcf_ctx* const* cs, int n_ctx, const int* n_chains, int n_s
     if (cudaMalloc(&c0->multi_arena, arena) != cudaSuccess) return fail(c0, GCF_ENOMEM, "multi-context scratch");
     c0->multi_arena_bytes = arena;
   }
-  const size_t kb = sizeof(KParams<T>) * n_ctx, tb = (kb + 15) / 16 * 16 + sizeof(long long) * (n_ctx + 1);
+  const size_t kb = sizeof(KParams<T>) * n_ctx,
+               tb = (kb + 15) / 16 * 16 + sizeof(long long) * (n_ctx + 1) + 16;
   if (tb > c0->multi_tab_bytes) {
     if (c0->multi_tab) cudaFree(c0->multi_tab);
     c0->multi_tab = nullptr;
@@ -826,8 +840,10 @@ gcf_status run_multi(gcf_ctx* const* cs, int n_ctx, const int* n_chains, int n_s
   CUDA_TRY(c0, cudaMemcpyAsync(d_ks, ks.data(), kb, cudaMemcpyHostToDevice, c0->stream));
   CUDA_TRY(c0, cudaMemcpyAsync(d_start, start.data(), sizeof(long long) * (n_ctx + 1), cudaMemcpyHostToDevice,
                                c0->stream));
+  unsigned long long* d_queue = (unsigned long long*)(d_start + n_ctx + 1);
+  CUDA_TRY(c0, cudaMemsetAsync(d_queue, 0, sizeof(unsigned long long), c0->stream));
   CUDA_TRY(c0, launch_vmc_multi<T>(d_ks, n_ctx, d_start, total, (T*)c0->multi_arena, ws, (int)grid, block,
-                                   group_bytes, smem, c0->stream));
+                                   group_bytes, d_queue, smem, c0->stream));
   c0->last_multi_block = block;
   c0->launches += 1;
   std::vector<int> h(4 * n_ctx);

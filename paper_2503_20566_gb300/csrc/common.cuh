@@ -323,6 +323,14 @@ struct GroupExec {
 };
 
 
+// Streaming store of an output the kernel never reads back (evict-first in
+// L2, so that the chains' scratch stays resident instead).
+__device__ __forceinline__ void store_stream(float* p, float v) { __stcs(p, v); }
+__device__ __forceinline__ void store_stream(double* p, double v) { __stcs(p, v); }
+__device__ __forceinline__ void store_stream(cfloat* p, cfloat v) { __stcs((float2*)p, make_float2(v.x, v.y)); }
+__device__ __forceinline__ void store_stream(cdouble* p, cdouble v) { __stcs((double2*)p, make_double2(v.x, v.y)); }
+__device__ __forceinline__ void store_stream(int* p, int v) { __stcs(p, v); }
+
 // Power-of-two scaling: the exponent e with m = f 2^e, f in [0.5, 1).
 // Scaling by 2^-e is exact, so log-scales are integers (units of ln 2).
 __device__ inline int exp2_of(float m) {

@@ -24,8 +24,8 @@ int occupancy_vmc_grouped(int block, size_t smem);
 // CTA of group_bytes shared memory each (vmc_kernel_multi4)
 template <class T>
 cudaError_t launch_vmc_multi(const KParams<T>* ks, int n_ctx, const long long* start, long long total, T* arena,
-                             long long ws_stride, int grid, int block, long long group_bytes, size_t smem,
-                             cudaStream_t st);
+                             long long ws_stride, int grid, int block, long long group_bytes,
+                             unsigned long long* queue, size_t smem, cudaStream_t st);
 template <class T>
 int occupancy_vmc_multi(int block, size_t smem);
 // bytes of the per-chain shared state of the VMC kernels (16-byte aligned)

@@ -42,16 +42,16 @@ int occupancy_vmc_grouped<double>(int block, size_t smem) {
 template <>
 cudaError_t launch_vmc_multi<double>(const KParams<double>* ks, int n_ctx, const long long* start, long long total,
                                   double* arena, long long ws_stride, int grid, int block, long long group_bytes,
-                                  size_t smem, cudaStream_t st) {
+                                  unsigned long long* queue, size_t smem, cudaStream_t st) {
   if (block == 512) {
     cudaError_t e = cudaFuncSetAttribute(vmc_kernel_multi4<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    vmc_kernel_multi4<double><<<grid, 512, smem, st>>>(ks, n_ctx, start, total, arena, ws_stride, group_bytes);
+    vmc_kernel_multi4<double><<<grid, 512, smem, st>>>(ks, n_ctx, start, total, arena, ws_stride, group_bytes, queue);
     return cudaGetLastError();
   }
   cudaError_t e = cudaFuncSetAttribute(vmc_kernel_multi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  vmc_kernel_multi<double><<<grid, 256, smem, st>>>(ks, n_ctx, start, total, arena, ws_stride);
+  vmc_kernel_multi<double><<<grid, 256, smem, st>>>(ks, n_ctx, start, total, arena, ws_stride, queue);
   return cudaGetLastError();
 }
 template <>

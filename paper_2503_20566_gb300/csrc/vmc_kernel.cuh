@@ -31,6 +31,7 @@ struct SharedV {
   int segB, segT;    // segment of B / T slots the segment buffers hold (-1: none)
   float redf[32];
   int n_acc, n_prop;
+  long long next;    // multi-context launches: the chain this group takes next
 };
 
 // Lockstep of the chain groups of one CTA: before each row of a pass every
@@ -777,9 +778,9 @@ __device__ __noinline__ void measure_pass(Chain<T, X>& ch, long long s) {
           if (k.O) {
             T* dst = k.O + (s * k.n_s + v) * (long long)D4;
 #pragma unroll 1
-            for (int i = ex.tid(); i < n; i += ex.size()) dst[i] = G[i] * fac;
+            for (int i = ex.tid(); i < n; i += ex.size()) store_stream(dst + i, G[i] * fac);
           }
-          if (k.block_ids && ex.tid() == 0) k.block_ids[s * k.n_s + v] = block_of(k, ch.cfg, c, r);
+          if (k.block_ids && ex.tid() == 0) store_stream(k.block_ids + s * k.n_s + v, block_of(k, ch.cfg, c, r));
         }
         if (want_e && k.matter && k.J != 0.0 && c < Lx - 1) ch.hhop_ratio(r, c, Lc, X1, X2, eL, dr, di, de);
         if (c < Lx - 1) {
@@ -1054,7 +1055,7 @@ __global__ void __launch_bounds__(512, 1) vmc_kernel_grouped4(const __grid_const
 template <class T>
 __global__ void __launch_bounds__(256, 2)
     vmc_kernel_multi(const KParams<T>* __restrict__ ks, int n_ctx, const long long* __restrict__ start,
-                     long long total, T* arena, long long ws_stride) {
+                     long long total, T* arena, long long ws_stride, unsigned long long* queue) {
   extern __shared__ __align__(16) int8_t dyn_smem[];
   __shared__ SharedV sv;
   CtaExec ex;
@@ -1062,7 +1063,14 @@ __global__ void __launch_bounds__(256, 2)
   const int* tab = nullptr;
   int cur = -1;
   tc_begin(ks[0], 1, dyn_smem, 0);
-  for (long long gidx = blockIdx.x; gidx < total; gidx += gridDim.x) {
+  for (;;) {
+    // the next chain of the launch's queue (contexts in the host's order,
+    // the costliest first), taken when this CTA is free
+    if (threadIdx.x == 0) sv.next = (long long)atomicAdd(queue, 1ull);
+    __syncthreads();
+    const long long gidx = sv.next;
+    __syncthreads();
+    if (gidx >= total) break;
     int i = 0;
     while (i + 1 < n_ctx && gidx >= start[i + 1]) ++i;
     const KParams<T>& k = ks[i];
@@ -1079,7 +1087,8 @@ __global__ void __launch_bounds__(256, 2)
 }
 
 // The same with four chains per CTA of 512 threads (groups of 128, one CTA
-// per SM): chain slot s = 4 blockIdx + group owns scratch s of the arena.
+// per SM): chain slot s = 4 blockIdx + group owns scratch s of the arena and
+// takes the queue's next chain whenever it is free.
 // The groups run chains of different contexts at once, so they read the
 // contexts' tables from global memory, keep their hot buffers in scratch
 // (placement level 0) and do not keep lockstep; dynamic shared memory per
@@ -1088,7 +1097,8 @@ __global__ void __launch_bounds__(256, 2)
 template <class T>
 __global__ void __launch_bounds__(512, 1)
     vmc_kernel_multi4(const KParams<T>* __restrict__ ks, int n_ctx, const long long* __restrict__ start,
-                      long long total, T* arena, long long ws_stride, long long group_bytes) {
+                      long long total, T* arena, long long ws_stride, long long group_bytes,
+                      unsigned long long* queue) {
   extern __shared__ __align__(16) int8_t dyn_smem[];
   constexpr int G = 128;
   const int g = threadIdx.x / G, NG = blockDim.x / G;
@@ -1101,7 +1111,12 @@ __global__ void __launch_bounds__(512, 1)
   const long long slot = (long long)blockIdx.x * NG + g;
   T* ws = arena + slot * ws_stride;
   int cur = -1;
-  for (long long gidx = slot; gidx < total; gidx += (long long)gridDim.x * NG) {
+  for (;;) {
+    if (ex.leader()) sv.next = (long long)atomicAdd(queue, 1ull);
+    ex.sync();
+    const long long gidx = sv.next;
+    ex.sync();
+    if (gidx >= total) break;
     int i = 0;
     while (i + 1 < n_ctx && gidx >= start[i + 1]) ++i;
     const KParams<T>& k = ks[i];
