@@ -114,7 +114,7 @@ def profiled_traffic(samples_per_launch, kernel, smem_level, workload, pdir=None
             txt = open(os.path.join(pdir, name)).read()
         except OSError:
             continue
-        m0 = re.search(r"workload: (\S+)", txt)
+        m0 = re.search(r"workload: ([^\s`]+)", txt)
         m1 = re.search(r"source_sha256: ([0-9a-f]+)", txt)
         m2 = re.search(r"traffic_bytes_per_sample: ([0-9.eE+]+)", txt)
         m3 = re.search(r"kernel_form: (\S+) level (\d+)", txt)

@@ -196,22 +196,25 @@ enum ExecKind { EXEC_CTA = 0, EXEC_GROUP = 1, EXEC_GROUP4 = 2 };
 // placement level] then, for the tcgen05 path, the operand staging area at
 // a 16-byte boundary.  CTA form: from the block's base; group form: each
 // group's region also starts with its SharedV.
-// Then the factorisation workspace (fz_elems scalars) at a 16-byte boundary.
+// The factorisation workspace (fz_elems scalars) shares that area: the
+// staging area is live only inside an environment GEMM, the workspace only
+// inside a factorisation of the absorption, and neither calls the other.
 inline size_t r16(size_t b) { return (b + 15) / 16 * 16; }
+size_t scratch_area(const Plan& p, size_t sb) { return std::max(r16((size_t)p.tc_bytes), (size_t)p.fz_elems * sb); }
 size_t cta_tc_off(const Plan& p, int level, size_t sb) {
   return r16((size_t)p.cfg_bytes + (size_t)p.level_elems(level) * sb);
 }
-size_t cta_fz_off(const Plan& p, int level, size_t sb) { return cta_tc_off(p, level, sb) + r16((size_t)p.tc_bytes); }
+size_t cta_fz_off(const Plan& p, int level, size_t sb) { return cta_tc_off(p, level, sb); }
 size_t cta_smem_bytes(const Plan& p, int level, size_t sb) {
   if (!p.tc_bytes && !p.fz_elems) return (size_t)p.cfg_bytes + (size_t)p.level_elems(level) * sb;
-  return cta_fz_off(p, level, sb) + (size_t)p.fz_elems * sb;
+  return cta_tc_off(p, level, sb) + scratch_area(p, sb);
 }
 size_t group_tc_off(const Plan& p, int level, size_t sb) {
   return r16(sharedv_bytes() + (size_t)p.cfg_bytes + (size_t)p.level_elems(level) * sb);
 }
-size_t group_fz_off(const Plan& p, int level, size_t sb) { return group_tc_off(p, level, sb) + r16((size_t)p.tc_bytes); }
+size_t group_fz_off(const Plan& p, int level, size_t sb) { return group_tc_off(p, level, sb); }
 size_t group_smem_bytes(const Plan& p, int level, size_t sb) {
-  return r16(group_fz_off(p, level, sb) + (size_t)p.fz_elems * sb);
+  return r16(group_tc_off(p, level, sb) + scratch_area(p, sb));
 }
 bool grouped(const gcf_ctx* c);
 int n_groups(const gcf_ctx* c);
@@ -774,8 +777,9 @@ gcf_status run_multi(gcf_ctx* const* cs, int n_ctx, const int* n_chains, int n_s
     tc_all = tc_all && ks[i].tc_bf16;
     fz = std::max(fz, ks[i].fz_elems);
   }
-  const size_t fz_off = tc_off + (tc_bytes + 15) / 16 * 16;
-  if (tc_bytes > 0 || fz > 0) smem = std::max(smem, fz_off + (size_t)fz * c0->sbytes);
+  const size_t fz_off = tc_off;  // the two share one area (see cta_tc_off)
+  const size_t area = std::max((tc_bytes + 15) / 16 * 16, (size_t)fz * c0->sbytes);
+  if (tc_bytes > 0 || fz > 0) smem = std::max(smem, tc_off + area);
   for (int i = 0; i < n_ctx; ++i) {
     ks[i].tc_bf16 = tc_all ? 1 : 0;
     ks[i].tc_off = (long long)tc_off;
@@ -793,8 +797,8 @@ gcf_status run_multi(gcf_ctx* const* cs, int n_ctx, const int* n_chains, int n_s
     size_t cfg_max = 0;
     for (int i = 0; i < n_ctx; ++i) cfg_max = std::max(cfg_max, (size_t)cs[i]->plan.cfg_bytes);
     const size_t g_tc = (sharedv_bytes() + cfg_max + 15) / 16 * 16;
-    const size_t g_fz = g_tc + (tc_bytes + 15) / 16 * 16;
-    const size_t gb = (g_fz + (size_t)fz * c0->sbytes + 15) / 16 * 16;
+    const size_t g_fz = g_tc;
+    const size_t gb = (g_tc + area + 15) / 16 * 16;
     bool want4 = fz > 0;
     if (const char* e = std::getenv("GCFVMC_MULTI")) want4 = !std::strcmp(e, "group4");
     if (want4 && 4 * gb <= 216 * 1024 && occupancy_vmc_multi<T>(512, 4 * gb) >= 1) {
