@@ -362,7 +362,8 @@ void build_plan(gcf_ctx* c) {
     ab[Lx] = 1;
     for (int cc = 0; cc < Lx; ++cc) {
       const long long rows = (long long)qr[cc] * pout, cols = ab[cc + 1];
-      fzq = std::max(fzq, rows * cols + rows * std::min(rows, cols));
+      // columns padded to whole 4-row chunks (the FP32 column-major form)
+      fzq = std::max(fzq, ((rows + 3) & ~3LL) * (cols + std::min(rows, cols)));
       qs = std::max(qs, rows * std::min(rows, cols));
       mat = std::max(mat, (long long)ab[cc] * pout * ab[cc + 1]);  // Z
       mat = std::max(mat, rows * cols);                             // X
@@ -373,10 +374,11 @@ void build_plan(gcf_ctx* c) {
     for (int cc = Lx - 1; cc >= 1; --cc) {
       const long long yr = qr[cc], yc = (long long)pout * bout[cc + 1];
       const long long k0 = std::min(yr, yc);
-      fzq = std::max(fzq, yc * yr + yc * k0);
+      fzq = std::max(fzq, ((yc + 3) & ~3LL) * (yr + k0));
       if (svd[cc]) {
         truncates = true;
-        fzj = std::max(fzj, yr * k0 + k0 * k0);
+        // columns padded to whole 4-row chunks (the FP32 column-major form)
+        fzj = std::max(fzj, ((yr + 3) & ~3LL) * k0 + ((k0 + 3) & ~3LL) * k0);
       }
       mat = std::max(mat, std::max(yr, yc) * std::max(yr, yc));
       mat = std::max(mat, k0 * k0);

@@ -6,6 +6,8 @@
 #include <stdint.h>
 #include <math.h>
 
+#include <type_traits>
+
 namespace gcf {
 
 struct cfloat { float x, y; };

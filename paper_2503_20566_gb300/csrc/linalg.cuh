@@ -196,6 +196,173 @@ __device__ __noinline__ void cta_form_q(const X ex, int m, int k, const T* A, in
   }
 }
 
+// Column length of the column-major FP32 workspaces below: rows rounded up
+// to whole 16-byte chunks of four floats.
+__host__ __device__ inline int jac_ld(int rows) { return (rows + 3) & ~3; }
+
+// Chunk kk (rows 4kk .. 4kk+3) of the reflector v of column j of a
+// column-major A: 0 above row j, 1 at row j, sc A[i][j] below (the stored
+// column before its scaling).
+__device__ __forceinline__ float4 reflector_chunk(const float4* aj, int kk, int j, float sc) {
+  float4 x = aj[kk];
+  if (kk == (j >> 2)) {
+    const int r0 = kk << 2;
+    x.x = (r0 < j) ? 0.f : (r0 == j ? 1.f : sc * x.x);
+    x.y = (r0 + 1 < j) ? 0.f : (r0 + 1 == j ? 1.f : sc * x.y);
+    x.z = (r0 + 2 < j) ? 0.f : (r0 + 2 == j ? 1.f : sc * x.z);
+    x.w = (r0 + 3 < j) ? 0.f : (r0 + 3 == j ? 1.f : sc * x.w);
+  } else {
+    x.x *= sc; x.y *= sc; x.z *= sc; x.w *= sc;
+  }
+  return x;
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
+}
+
+// cta_qr for real FP32 on a column-major shared-memory A (m x n, column c at
+// A + c lda, lda = jac_ld(m), 16-byte aligned, padding rows zero): the same
+// Householder reflectors (householder()), stored the same way (R on and
+// above the diagonal, the scaled v below it, tau[0..min(m,n))).  Per
+// column one barrier: the lanes that apply H_j to column j+1 also reduce
+// that column's next norm and diagonal entry and publish them, and the
+// scaling of column j's v is done in the next step, when nothing reads it.
+template <class X>
+__device__ __noinline__ void qr_cm(const X ex, int m, int n, float* A, int lda, float* tau) {
+  const int k = min(m, n);
+  const int cw = lda >> 2;
+  // two (alpha, |x|^2) slots, alternating between steps
+  float* pub = reinterpret_cast<float*>(g_exec_red[ex.slot()]) + 120;
+  float part = 0.f;
+#pragma unroll 1
+  for (int i = 1 + ex.tid(); i < m; i += ex.size()) part = fmaf(A[i], A[i], part);
+  float xn2 = ex.template sum<float>(part);
+  float alpha = A[0];
+  float sc_p = 0.f, t_p = 0.f, beta_p = 0.f;
+  for (int j = 0; j < k; ++j) {
+    if (j > 0) {
+      alpha = pub[2 * (j & 1)];
+      xn2 = pub[2 * (j & 1) + 1];
+    }
+    float t, sc, beta;
+    householder(alpha, xn2, t, sc, beta);
+    if (j > 0) {
+      // column j-1: scaled v below the diagonal, beta on it
+      float* ap = A + (j - 1) * lda;
+#pragma unroll 1
+      for (int i = j + ex.tid(); i < m; i += ex.size()) ap[i] *= sc_p;
+      if (ex.tid() == 0) { ap[j - 1] = beta_p; tau[j - 1] = t_p; }
+    }
+    const int c0 = j + 1, nc = n - c0;
+    if (nc > 0) {
+      const int L = lanes_per_column(ex, nc);
+      const int slots = ex.size() / L;
+      const int sub = ex.tid() / L, li = ex.tid() - (ex.tid() / L) * L;
+      const float4* aj = reinterpret_cast<const float4*>(A + j * lda);
+      const int kb = j >> 2;
+#pragma unroll 1
+      for (int base = 0; base < nc; base += slots) {
+        const int c = c0 + base + sub;
+        const bool act = c < n;
+        float4* mc = reinterpret_cast<float4*>(A + c * lda);
+        float w = 0.f;
+        if (act) {
+#pragma unroll 2
+          for (int kk = kb + li; kk < cw; kk += L) w = dot4(reflector_chunk(aj, kk, j, sc), mc[kk], w);
+        }
+        w = lanes_sum(w, L);
+        const bool next = act && c == j + 1 && c < k;
+        float nn = 0.f, al = 0.f;
+        if (act) {
+          const float g = t * w;
+#pragma unroll 2
+          for (int kk = kb + li; kk < cw; kk += L) {
+            const float4 x = reflector_chunk(aj, kk, j, sc);
+            float4 y = mc[kk];
+            y.x = fmaf(-g, x.x, y.x); y.y = fmaf(-g, x.y, y.y); y.z = fmaf(-g, x.z, y.z); y.w = fmaf(-g, x.w, y.w);
+            mc[kk] = y;
+            if (next) {
+              const int r0 = kk << 2;
+              const float e[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                if (r0 + q > c) nn = fmaf(e[q], e[q], nn);
+                if (r0 + q == c) al = e[q];
+              }
+            }
+          }
+        }
+        // every lane of the warp joins the shuffles; only the pivot's lanes
+        // hold non-zero parts
+        nn = lanes_sum(nn, L);
+        al = lanes_sum(al, L);
+        if (next && li == 0) {
+          pub[2 * ((j + 1) & 1)] = al;
+          pub[2 * ((j + 1) & 1) + 1] = nn;
+        }
+      }
+    }
+    sc_p = sc; t_p = t; beta_p = beta;
+    ex.sync();
+  }
+  if (k > 0) {
+    float* ap = A + (k - 1) * lda;
+#pragma unroll 1
+    for (int i = k + ex.tid(); i < m; i += ex.size()) ap[i] *= sc_p;
+    if (ex.tid() == 0) { ap[k - 1] = beta_p; tau[k - 1] = t_p; }
+  }
+  ex.sync();
+}
+
+// cta_form_q for the column-major A of qr_cm: Q (m x kq, column c at
+// Q + c ldq, ldq = jac_ld(m), 16-byte aligned) = H_0 ... H_{kq-1} applied to
+// the first kq columns of the identity, the reflectors applied last to
+// first.
+template <class X>
+__device__ __noinline__ void form_q_cm(const X ex, int m, int kq, const float* A, int lda, const float* tau, float* Q,
+                                       int ldq) {
+#pragma unroll 1
+  for (int idx = ex.tid(); idx < kq * ldq; idx += ex.size()) {
+    const int c = idx / ldq, i = idx - (idx / ldq) * ldq;
+    Q[idx] = (i == c) ? 1.f : 0.f;
+  }
+  ex.sync();
+  const int cw = ldq >> 2;
+  for (int j = kq - 1; j >= 0; --j) {
+    const float t = tau[j];
+    const int nc = kq - j;
+    const int L = lanes_per_column(ex, nc);
+    const int slots = ex.size() / L;
+    const int sub = ex.tid() / L, li = ex.tid() - (ex.tid() / L) * L;
+    const float4* aj = reinterpret_cast<const float4*>(A + j * lda);
+    const int kb = j >> 2;
+#pragma unroll 1
+    for (int base = 0; base < nc; base += slots) {
+      const int c = j + base + sub;
+      const bool act = c < kq;
+      float4* qc = reinterpret_cast<float4*>(Q + c * ldq);
+      float w = 0.f;
+      if (act) {
+#pragma unroll 2
+        for (int kk = kb + li; kk < cw; kk += L) w = dot4(reflector_chunk(aj, kk, j, 1.f), qc[kk], w);
+      }
+      w = lanes_sum(w, L);
+      if (act) {
+        const float g = t * w;
+#pragma unroll 2
+        for (int kk = kb + li; kk < cw; kk += L) {
+          const float4 x = reflector_chunk(aj, kk, j, 1.f);
+          float4 y = qc[kk];
+          y.x = fmaf(-g, x.x, y.x); y.y = fmaf(-g, x.y, y.y); y.z = fmaf(-g, x.z, y.z); y.w = fmaf(-g, x.w, y.w);
+          qc[kk] = y;
+        }
+      }
+    }
+    ex.sync();
+  }
+}
+
 // Shared-memory factorisation workspace of each chain group: the QR / Q
 // formation and the Jacobi sweeps run on shared-memory copies of their
 // matrices when they fit (every step of these factorisations depends on the
@@ -220,6 +387,34 @@ __device__ inline void cta_copy(const X ex, int rows, int cols, const T* src, in
 template <class T, class X>
 __device__ __noinline__ void qr_with_q(const X ex, int m, int n, T* A, int lda, T* tau, int kq, T* Q, int ldq) {
   T* fz = (T*)g_fz[ex.slot()];
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32: column-major copies in 16-byte chunks (qr_cm, form_q_cm)
+    const int ld = jac_ld(m);
+    if (fz && (long long)ld * (n + kq) <= g_fz_elems) {
+      float* a = fz;
+      float* q = fz + ld * n;
+#pragma unroll 1
+      for (int idx = ex.tid(); idx < n * ld; idx += ex.size()) {
+        const int c = idx / ld, i = idx - (idx / ld) * ld;
+        a[idx] = (i < m) ? A[i * lda + c] : 0.f;
+      }
+      ex.sync();
+      qr_cm(ex, m, n, a, ld, tau);
+      form_q_cm(ex, m, kq, a, ld, tau, q, ld);
+#pragma unroll 1
+      for (int idx = ex.tid(); idx < n * m; idx += ex.size()) {
+        const int c = idx / m, i = idx - (idx / m) * m;
+        A[i * lda + c] = a[c * ld + i];
+      }
+#pragma unroll 1
+      for (int idx = ex.tid(); idx < kq * m; idx += ex.size()) {
+        const int c = idx / m, i = idx - (idx / m) * m;
+        Q[i * ldq + c] = q[c * ld + i];
+      }
+      ex.sync();
+      return;
+    }
+  }
   if (fz && (long long)m * n + (long long)m * kq <= g_fz_elems) {
     T* a = fz;
     T* q = fz + m * n;
@@ -357,6 +552,109 @@ __device__ __noinline__ int cta_jacobi_svd(const X ex, int p, int q, T* W, int s
           const T ja = ja_p[o], jb = jb_p[o];
           ja_p[o] = scale(ja, (R)c) - jb * s_ec;
           jb_p[o] = ja * s_e + scale(jb, (R)c);
+        }
+        if (li == 0) *sflag = 1;
+      }
+      ex.sync();
+    }
+    const int any = *sflag;
+    ex.sync();
+    if (!any) break;
+  }
+  if (sweep >= max_sweeps && converged) *converged = 0;
+  ex.sync();
+  return sweep;
+}
+
+// cta_jacobi_svd for real FP32 on a column-major shared-memory workspace:
+// W (p x q, column c at W + c ldw) and J (q x q, column c at J + c ldj), with
+// ldw = jac_ld(p), ldj = jac_ld(q), 16-byte aligned, the padding rows of W
+// zero (rotations keep them zero).  The same rotations in the same round-
+// robin order; a pair's L lanes split its columns into chunks of four rows
+// (chunk k to lane k mod L) and move each chunk with one 16-byte access, so a
+// round costs a quarter of the shared-memory instructions and address
+// arithmetic of the strided form.
+template <class X>
+__device__ __noinline__ int jacobi_svd_cm(const X ex, int p, int q, float* W, int ldw, float* J, int ldj, int* sflag,
+                                          int max_sweeps, int* converged) {
+#pragma unroll 1
+  for (int idx = ex.tid(); idx < q * ldj; idx += ex.size()) {
+    const int c = idx / ldj, i = idx - (idx / ldj) * ldj;
+    J[idx] = (i == c) ? 1.f : 0.f;
+  }
+  const int n = q + (q & 1);
+  const int npair = n / 2;
+  int L = 32;
+  while (L > 1 && L * npair > ex.size()) L >>= 1;
+  const int slots = ex.size() / L;
+  const int sub = ex.tid() / L, li = ex.tid() - (ex.tid() / L) * L;
+  const int cw = ldw >> 2, cj = ldj >> 2;  // chunks per column
+  const float tol = 4.f * sqrtf((float)(p > 4 ? p : 4)) * Traits<float>::eps();
+  float f2 = 0.f;
+#pragma unroll 1
+  for (int idx = ex.tid(); idx < q * ldw; idx += ex.size()) f2 += W[idx] * W[idx];
+  f2 = ex.template sum<float>(f2);
+  const float negl = Traits<float>::eps() * Traits<float>::eps() * f2;
+  int sweep = 0;
+  if (converged) *converged = 1;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (ex.tid() == 0) *sflag = 0;
+    ex.sync();
+#pragma unroll 1
+    for (int r = 0; r < n - 1; ++r) {
+#pragma unroll 1
+      for (int base = 0; base < npair; base += slots) {
+        const int kp = base + sub;
+        int a = r, b = n - 1;
+        if (kp > 0) {
+          a = r + kp;
+          if (a >= n - 1) a -= n - 1;
+          b = r - kp;
+          if (b < 0) b += n - 1;
+        }
+        if (a > b) { const int t = a; a = b; b = t; }
+        const bool act = kp < npair && b < q;
+        float4* pa = reinterpret_cast<float4*>(W + a * ldw);
+        float4* pb = reinterpret_cast<float4*>(W + b * ldw);
+        float al = 0.f, be = 0.f, g = 0.f;
+        if (act) {
+#pragma unroll 3
+          for (int k = li; k < cw; k += L) {
+            const float4 x = pa[k], y = pb[k];
+            al = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, al))));
+            be = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, be))));
+            g = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, g))));
+          }
+        }
+        al = lanes_sum(al, L);
+        be = lanes_sum(be, L);
+        g = lanes_sum(g, L);
+        const float ga = fabsf(g);
+        if (!act || ga == 0.f || !(al > negl) || !(be > negl) || !(ga > tol * (sqrtf(al) * sqrtf(be)))) continue;
+        const float iga = jrcp(ga);
+        const float zeta = (be - al) * (0.5f * iga);
+        const float az = fabsf(zeta);
+        const float t = (zeta >= 0.f ? 1.f : -1.f) * jrcp(az > 1e15f ? 2.f * az : az + sqrtf(1.f + zeta * zeta));
+        if (t == 0.f) continue;
+        const float c = jrsqrt(1.f + t * t);
+        const float s = (g >= 0.f ? c : -c) * t;  // s e^{i phi}, e^{i phi} = sign(g)
+#pragma unroll 3
+        for (int k = li; k < cw; k += L) {
+          const float4 x = pa[k], y = pb[k];
+          pa[k] = make_float4(fmaf(c, x.x, -s * y.x), fmaf(c, x.y, -s * y.y), fmaf(c, x.z, -s * y.z),
+                              fmaf(c, x.w, -s * y.w));
+          pb[k] = make_float4(fmaf(s, x.x, c * y.x), fmaf(s, x.y, c * y.y), fmaf(s, x.z, c * y.z),
+                              fmaf(s, x.w, c * y.w));
+        }
+        float4* ja = reinterpret_cast<float4*>(J + a * ldj);
+        float4* jb = reinterpret_cast<float4*>(J + b * ldj);
+#pragma unroll 3
+        for (int k = li; k < cj; k += L) {
+          const float4 x = ja[k], y = jb[k];
+          ja[k] = make_float4(fmaf(c, x.x, -s * y.x), fmaf(c, x.y, -s * y.y), fmaf(c, x.z, -s * y.z),
+                              fmaf(c, x.w, -s * y.w));
+          jb[k] = make_float4(fmaf(s, x.x, c * y.x), fmaf(s, x.y, c * y.y), fmaf(s, x.z, c * y.z),
+                              fmaf(s, x.w, c * y.w));
         }
         if (li == 0) *sflag = 1;
       }

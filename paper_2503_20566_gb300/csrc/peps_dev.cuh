@@ -496,16 +496,41 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
         ex.sync();
         int conv = 1;
         T* fz = (T*)g_fz[ex.slot()];
-        if (fz && (long long)yr * k0 + (long long)k0 * k0 <= g_fz_elems) {
-          // sweeps on shared-memory copies; only J is needed afterwards
-          // (W is recomputed as L J below)
-          T* w = fz;
-          T* jj = fz + yr * k0;
-          cta_copy(ex, yr, k0, Lc, k0, w, k0);
-          cta_jacobi_svd<T>(ex, yr, k0, w, k0, 1, jj, k0, 1, &sh.iflag[0], k.max_sweeps_svd, &conv);
-          cta_copy(ex, k0, k0, jj, k0, Jm, k0);
-        } else {
-          cta_jacobi_svd<T>(ex, yr, k0, Lc, k0, 1, Jm, k0, 1, &sh.iflag[0], k.max_sweeps_svd, &conv);
+        bool done = false;
+        if constexpr (std::is_same<T, float>::value) {
+          // FP32: column-major copies in 16-byte chunks (jacobi_svd_cm)
+          const int ldw = jac_ld(yr), ldj = jac_ld(k0);
+          if (fz && (long long)ldw * k0 + (long long)ldj * k0 <= g_fz_elems) {
+            float* w = fz;
+            float* jj = w + ldw * k0;
+#pragma unroll 1
+            for (int idx = ex.tid(); idx < k0 * ldw; idx += ex.size()) {
+              const int c = idx / ldw, i = idx - (idx / ldw) * ldw;
+              w[idx] = (i < yr) ? Lc[i * k0 + c] : 0.f;
+            }
+            ex.sync();
+            jacobi_svd_cm(ex, yr, k0, w, ldw, jj, ldj, &sh.iflag[0], k.max_sweeps_svd, &conv);
+#pragma unroll 1
+            for (int idx = ex.tid(); idx < k0 * k0; idx += ex.size()) {
+              const int i = idx / k0, c = idx - (idx / k0) * k0;
+              Jm[idx] = jj[c * ldj + i];
+            }
+            ex.sync();
+            done = true;
+          }
+        }
+        if (!done) {
+          if (fz && (long long)yr * k0 + (long long)k0 * k0 <= g_fz_elems) {
+            // sweeps on shared-memory copies; only J is needed afterwards
+            // (W is recomputed as L J below)
+            T* w = fz;
+            T* jj = fz + yr * k0;
+            cta_copy(ex, yr, k0, Lc, k0, w, k0);
+            cta_jacobi_svd<T>(ex, yr, k0, w, k0, 1, jj, k0, 1, &sh.iflag[0], k.max_sweeps_svd, &conv);
+            cta_copy(ex, k0, k0, jj, k0, Jm, k0);
+          } else {
+            cta_jacobi_svd<T>(ex, yr, k0, Lc, k0, 1, Jm, k0, 1, &sh.iflag[0], k.max_sweeps_svd, &conv);
+          }
         }
         if (!conv && ex.tid() == 0) atomicAdd(&k.status[ST_SVD], 1);
         cta_gemm<T, true, false, false>(ex, k0, k0, k0, Jm, 1, k0, Jm, k0, 1, Gm, k0, 1, false);
