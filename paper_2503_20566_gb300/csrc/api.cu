@@ -377,8 +377,11 @@ void build_plan(gcf_ctx* c) {
       fzq = std::max(fzq, ((yc + 3) & ~3LL) * (yr + k0));
       if (svd[cc]) {
         truncates = true;
-        // columns padded to whole 4-row chunks (the FP32 column-major form)
-        fzj = std::max(fzj, ((yr + 3) & ~3LL) * k0 + ((k0 + 3) & ~3LL) * k0);
+        // FP32 column-major form: W and J with columns padded to whole 4-row
+        // chunks, the kept columns of J before and after re-orthogonalisation
+        // and their Gram matrix
+        const long long kk = bout[cc], ldj = (k0 + 3) & ~3LL;
+        fzj = std::max(fzj, ((yr + 3) & ~3LL) * k0 + ldj * k0 + 2 * ldj * kk + kk * kk);
       }
       mat = std::max(mat, std::max(yr, yc) * std::max(yr, yc));
       mat = std::max(mat, k0 * k0);

@@ -334,6 +334,80 @@ __device__ __noinline__ int dense_absorb(const X ex, const KParams<T>& k, Shared
   return e;
 }
 
+// sel[0..kk) <- the indices of the kk largest of sigma[0..k0), largest first
+// (ties: lower index first).
+template <class R, class X>
+__device__ inline void select_largest(const X ex, int k0, int kk, const R* sigma, int* sel) {
+#pragma unroll 1
+  for (int j = ex.tid(); j < k0; j += ex.size()) {
+    int rank = 0;
+    const R sj = sigma[j];
+    for (int i = 0; i < k0; ++i) {
+      const R si = sigma[i];
+      rank += (si > sj) || (si == sj && i < j);
+    }
+    if (rank < kk) sel[rank] = j;
+  }
+  ex.sync();
+}
+
+// Truncated SVD step of a bond in FP32, in the chain's shared-memory
+// workspace: L (yr x k0, row-major) = W J^T by one-sided Jacobi
+// (jacobi_svd_cm), the kk columns of W with the largest norms kept, one
+// Newton-Schulz step on the kept columns of J only,
+//   Jn = J_s (3 I - J_s^T J_s) / 2,
+// then carry = L Jn (yr x kk, row-major) and site = Jn^T Q'^T (kk x yc,
+// row-major), Q' = Qp (yc x k0, row-major).  The squared column norms of W
+// go to sigma.  Returns false, having done nothing, when the workspace is
+// too small.
+template <class X>
+__device__ __noinline__ bool truncate_f32_smem(const X ex, int yr, int yc, int k0, int kk, const float* L,
+                                               const float* Qp, float* carry, float* site, float* sigma, int* sel,
+                                               int* sflag, int max_sweeps, int* conv) {
+  float* fz = (float*)g_fz[ex.slot()];
+  const int ldw = jac_ld(yr), ldj = jac_ld(k0);
+  if (!fz || (long long)(ldw + ldj) * k0 + 2LL * ldj * kk + (long long)kk * kk > g_fz_elems) return false;
+  float* w = fz;                // W, column-major (ldw)
+  float* jj = w + ldw * k0;     // J, column-major (ldj)
+  float* js = jj + ldj * k0;    // kept columns of J
+  float* jn = js + ldj * kk;    // after the Newton-Schulz step
+  float* gg = jn + ldj * kk;    // kk x kk, row-major
+#pragma unroll 1
+  for (int idx = ex.tid(); idx < k0 * ldw; idx += ex.size()) {
+    const int c = idx / ldw, i = idx - (idx / ldw) * ldw;
+    w[idx] = (i < yr) ? L[i * k0 + c] : 0.f;
+  }
+  ex.sync();
+  jacobi_svd_cm(ex, yr, k0, w, ldw, jj, ldj, sflag, max_sweeps, conv);
+#pragma unroll 1
+  for (int j = ex.tid(); j < k0; j += ex.size()) {
+    const float4* col = reinterpret_cast<const float4*>(w + j * ldw);
+    float s2 = 0.f;
+    for (int q = 0; q < (ldw >> 2); ++q) s2 = dot4(col[q], col[q], s2);
+    sigma[j] = s2;
+  }
+  ex.sync();
+  select_largest(ex, k0, kk, sigma, sel);
+#pragma unroll 1
+  for (int idx = ex.tid(); idx < kk * ldj; idx += ex.size()) {
+    const int n = idx / ldj, i = idx - (idx / ldj) * ldj;
+    js[idx] = jj[sel[n] * ldj + i];
+  }
+  ex.sync();
+  // gg = J_s^T J_s, then (3 I - gg) / 2
+  tile_gemm_f32(ex, kk, kk, k0, js, ldj, 1, js, 1, ldj, gg, kk, 1);
+#pragma unroll 1
+  for (int idx = ex.tid(); idx < kk * kk; idx += ex.size()) {
+    const int i = idx / kk, j = idx - (idx / kk) * kk;
+    gg[idx] = fmaf(-0.5f, gg[idx], i == j ? 1.5f : 0.f);
+  }
+  ex.sync();
+  tile_gemm_f32(ex, k0, kk, kk, js, 1, ldj, gg, kk, 1, jn, 1, ldj);
+  tile_gemm_f32(ex, yr, kk, k0, L, k0, 1, jn, 1, ldj, carry, kk, 1);
+  tile_gemm_f32(ex, kk, yc, k0, jn, ldj, 1, Qp, 1, k0, site, yc, 1);
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // Row absorption + compression.
 //   in : MPS `mps_in` (bond table bdi, physical dim pin) and row `row` whose
@@ -487,39 +561,24 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
         // product of many rotations, and in FP32 it drifts from orthogonal by
         // ~1e-5, which enters the kept subspace at every cut; one
         // Newton-Schulz step J <- J (3 I - J^H J) / 2 restores orthogonality
-        // to rounding, and W = L J is recomputed so that both factors agree.
-        T* L0 = ws + k.o_M2;
-        T* Gm = ws + k.o_M1;
-        T* Jn = ws + k.o_M3;
-#pragma unroll 1
-        for (int idx = ex.tid(); idx < yr * k0; idx += ex.size()) L0[idx] = Lc[idx];
-        ex.sync();
+        // to rounding, and the kept W = L J is recomputed so that both
+        // factors agree.
+        using RR = typename Traits<T>::R;
+        RR* sigma = (RR*)(ws + k.o_sigma);
+        int* sel = (int*)(ws + k.o_sel);
         int conv = 1;
-        T* fz = (T*)g_fz[ex.slot()];
         bool done = false;
-        if constexpr (std::is_same<T, float>::value) {
-          // FP32: column-major copies in 16-byte chunks (jacobi_svd_cm)
-          const int ldw = jac_ld(yr), ldj = jac_ld(k0);
-          if (fz && (long long)ldw * k0 + (long long)ldj * k0 <= g_fz_elems) {
-            float* w = fz;
-            float* jj = w + ldw * k0;
-#pragma unroll 1
-            for (int idx = ex.tid(); idx < k0 * ldw; idx += ex.size()) {
-              const int c = idx / ldw, i = idx - (idx / ldw) * ldw;
-              w[idx] = (i < yr) ? Lc[i * k0 + c] : 0.f;
-            }
-            ex.sync();
-            jacobi_svd_cm(ex, yr, k0, w, ldw, jj, ldj, &sh.iflag[0], k.max_sweeps_svd, &conv);
-#pragma unroll 1
-            for (int idx = ex.tid(); idx < k0 * k0; idx += ex.size()) {
-              const int i = idx / k0, c = idx - (idx / k0) * k0;
-              Jm[idx] = jj[c * ldj + i];
-            }
-            ex.sync();
-            done = true;
-          }
-        }
+        if constexpr (std::is_same<T, float>::value)
+          done = truncate_f32_smem(ex, yr, yc, k0, kk, Lc, Qp, Yh, site, sigma, sel, &sh.iflag[0],
+                                   k.max_sweeps_svd, &conv);
         if (!done) {
+          T* L0 = ws + k.o_M2;
+          T* Gm = ws + k.o_M1;
+          T* Jn = ws + k.o_M3;
+#pragma unroll 1
+          for (int idx = ex.tid(); idx < yr * k0; idx += ex.size()) L0[idx] = Lc[idx];
+          ex.sync();
+          T* fz = (T*)g_fz[ex.slot()];
           if (fz && (long long)yr * k0 + (long long)k0 * k0 <= g_fz_elems) {
             // sweeps on shared-memory copies; only J is needed afterwards
             // (W is recomputed as L J below)
@@ -531,59 +590,43 @@ __device__ __noinline__ int absorb_compress(const X ex, const KParams<T>& k, T* 
           } else {
             cta_jacobi_svd<T>(ex, yr, k0, Lc, k0, 1, Jm, k0, 1, &sh.iflag[0], k.max_sweeps_svd, &conv);
           }
-        }
-        if (!conv && ex.tid() == 0) atomicAdd(&k.status[ST_SVD], 1);
-        cta_gemm<T, true, false, false>(ex, k0, k0, k0, Jm, 1, k0, Jm, k0, 1, Gm, k0, 1, false);
-        {
-          using RR = typename Traits<T>::R;
+          cta_gemm<T, true, false, false>(ex, k0, k0, k0, Jm, 1, k0, Jm, k0, 1, Gm, k0, 1, false);
 #pragma unroll 1
           for (int idx = ex.tid(); idx < k0 * k0; idx += ex.size()) {
             const int i = idx / k0, j = idx - (idx / k0) * k0;
             Gm[idx] = scale(Gm[idx], RR(-0.5));
             if (i == j) Gm[idx] += make_scalar<T>(RR(1.5), RR(0));
           }
-        }
-        ex.sync();
-        cta_gemm<T, false, false, false>(ex, k0, k0, k0, Jm, k0, 1, Gm, k0, 1, Jn, k0, 1, false);
-        cta_gemm<T, false, false, false>(ex, yr, k0, k0, L0, k0, 1, Jn, k0, 1, Lc, k0, 1, false);
-        // squared column norms -> sigma, selected columns -> sel (scratch)
-        using RR = typename Traits<T>::R;
-        RR* sigma = (RR*)(ws + k.o_sigma);
-        int* sel = (int*)(ws + k.o_sel);
+          ex.sync();
+          cta_gemm<T, false, false, false>(ex, k0, k0, k0, Jm, k0, 1, Gm, k0, 1, Jn, k0, 1, false);
+          cta_gemm<T, false, false, false>(ex, yr, k0, k0, L0, k0, 1, Jn, k0, 1, Lc, k0, 1, false);
+          // squared column norms -> sigma, selected columns -> sel (scratch)
 #pragma unroll 1
-        for (int j = ex.tid(); j < k0; j += ex.size()) {
-          RR s2 = RR(0);
-          for (int i = 0; i < yr; ++i) s2 += abs2(Lc[i * k0 + j]);
-          sigma[j] = s2;
-        }
-        ex.sync();
-#pragma unroll 1
-        for (int j = ex.tid(); j < k0; j += ex.size()) {
-          int rank = 0;
-          const RR sj = sigma[j];
-          for (int i = 0; i < k0; ++i) {
-            const RR si = sigma[i];
-            rank += (si > sj) || (si == sj && i < j);
+          for (int j = ex.tid(); j < k0; j += ex.size()) {
+            RR s2 = RR(0);
+            for (int i = 0; i < yr; ++i) s2 += abs2(Lc[i * k0 + j]);
+            sigma[j] = s2;
           }
-          if (rank < kk) sel[rank] = j;
-        }
-        ex.sync();
-        // site[n][x] = sum_j conj(J[j][sel n]) Q'^H[j][x]
+          ex.sync();
+          select_largest(ex, k0, kk, sigma, sel);
+          // site[n][x] = sum_j conj(J[j][sel n]) Q'^H[j][x]
 #pragma unroll 1
-        for (int idx = ex.tid(); idx < kk * yc; idx += ex.size()) {
-          const int n = idx / yc, x = idx - (idx / yc) * yc;
-          const int jn = sel[n];
-          T s = zero<T>();
-          for (int j = 0; j < k0; ++j) s = fmac(s, conjg(Jn[j * k0 + jn]), conjg(Qp[x * k0 + j]));
-          site[idx] = s;
-        }
-        // carry U S = W[:, sel] (yr x kk)
+          for (int idx = ex.tid(); idx < kk * yc; idx += ex.size()) {
+            const int n = idx / yc, x = idx - (idx / yc) * yc;
+            const int jn = sel[n];
+            T s = zero<T>();
+            for (int j = 0; j < k0; ++j) s = fmac(s, conjg(Jn[j * k0 + jn]), conjg(Qp[x * k0 + j]));
+            site[idx] = s;
+          }
+          // carry U S = W[:, sel] (yr x kk)
 #pragma unroll 1
-        for (int idx = ex.tid(); idx < yr * kk; idx += ex.size()) {
-          const int i = idx / kk, n = idx - (idx / kk) * kk;
-          Yh[idx] = Lc[i * k0 + sel[n]];
+          for (int idx = ex.tid(); idx < yr * kk; idx += ex.size()) {
+            const int i = idx / kk, n = idx - (idx / kk) * kk;
+            Yh[idx] = Lc[i * k0 + sel[n]];
+          }
+          ex.sync();
         }
-        ex.sync();
+        if (!conv && ex.tid() == 0) atomicAdd(&k.status[ST_SVD], 1);
 #pragma unroll 1
         for (int idx = ex.tid(); idx < yr * kk; idx += ex.size()) Lc[idx] = Yh[idx];
         ex.sync();
