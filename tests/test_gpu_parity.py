@@ -40,6 +40,8 @@ AMP_CASES = [
     (4, 4, 4, 8, 4, True, False, "fp32"),    # Z4 complex
     (5, 5, 2, 6, 5, False, False, "fp32"),   # D_k = 3 truncated
     (4, 3, 2, 4, 4, False, True, "fp32"),    # Z2 + hard-core bosons
+    (3, 3, 2, 6, 3, False, True, "fp64"),    # Z2 + bosons, D_k = 3 (the 3x3 ED check's lattice)
+    (3, 3, 2, 6, 3, False, True, "fp32"),
 ]
 
 
@@ -77,7 +79,8 @@ def test_local_energy_parity(case):
         assert abs(e[i] - ref) <= TOL[prec] * scale_ * 10, (i, e[i], ref)
 
 
-@pytest.mark.parametrize("case", [AMP_CASES[0], AMP_CASES[1], AMP_CASES[2], AMP_CASES[4], AMP_CASES[8]],
+@pytest.mark.parametrize("case", [AMP_CASES[0], AMP_CASES[1], AMP_CASES[2], AMP_CASES[4], AMP_CASES[8],
+                                  AMP_CASES[9], AMP_CASES[10]],
                          ids=_ids)
 def test_log_grad_parity(case):
     Lx, Ly, N, D, chi, cplx, matter, prec = case
@@ -145,6 +148,8 @@ def _replay_chain(pe, model, cfg0, chi, seed, chain, n_sweeps):
     (4, 3, 3, 6, 4, True, False, "fp64", 4, 3),
     (4, 3, 2, 4, 4, False, True, "fp64", 4, 2),
     (5, 4, 2, 4, 4, False, False, "fp32", 4, 2),
+    (3, 3, 2, 6, 3, False, True, "fp64", 6, 4),
+    (3, 3, 2, 6, 3, False, True, "fp32", 6, 4),
 ], ids=lambda c: "{}x{}-Z{}-{}{}-{}".format(c[0], c[1], c[2], "c" if c[5] else "r", "-m" if c[6] else "", c[7]))
 def test_sample_batch_replays_oracle_chain(case):
     """Same starting configurations, seed and SplitMix64 counters: the GPU

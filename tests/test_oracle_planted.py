@@ -139,6 +139,12 @@ CASES = [
      "_row_value(peps, c2, r, Bm, Tm), _row_value(peps, c2, r, Bm, Tm)",
      lambda mp: TV.test_sweep_ratios_equal_exact_amplitude_ratios(3, 4, 3, True, mp)),
     # SR / tVMC (Eqs. S3, S6-S8)
+    ("horizontal-hop-ratio-inverted", vmc, "sweep",
+     "_accept(u, _row_value(peps, c2, r, Bm, Tm), _row_value(peps, cfg, r, Bm, Tm))",
+     "_accept(u, _row_value(peps, cfg, r, Bm, Tm), _row_value(peps, c2, r, Bm, Tm))",
+     lambda mp: TV.test_sampler_histogram_matches_born_weights_with_matter(3, 2)),
+    ("vertical-hops-never-proposed", vmc, "sweep", "c2 = lat.hop(cfg, x, r, 2)", "c2 = None",
+     lambda mp: TV.test_sampler_histogram_matches_born_weights_with_matter(2, 3)),
     ("sr-matrix-missing-conjugate", vmc, "sr_matrices", "(O.conj().T * w) @ O", "(O.T * w) @ O",
      lambda mp: TV.test_cg_equals_dense_solve_and_residual()),
     ("cg-direction-update", vmc, "cg_solve", "(rs_new / rs) * p", "(rs / rs_new) * p",

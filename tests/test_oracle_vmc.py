@@ -7,7 +7,8 @@
 * O = d ln psi / d A~ equals central finite differences, both of the row value
   with fixed environments and of the full exact amplitude.
 * The Metropolis sweep samples |psi|^2 (histograms on 3x3 and 3x4 Z2 and 3x2
-  Z3); at exact chi every ratio it forms from its carried environments equals
+  Z3, and with two hard-core bosons on 3x2 and 2x3 Z2, where the horizontal
+  and the vertical hops move them); at exact chi every ratio it forms from its carried environments equals
   the exact amplitude ratio (plaquette and both hop passes); it conserves the
   Gauss law and the boson number.
 * SR: CG equals the dense solve; an SR step lowers the exact energy.
@@ -161,6 +162,33 @@ def test_sampler_histogram_matches_born_weights(Lx, Ly, N, tv_max):
     freq = counts / counts.sum()
     tv = 0.5 * np.abs(freq - target).sum()
     assert tv < tv_max, (tv, freq, target)
+
+
+@pytest.mark.parametrize("Lx,Ly", [(3, 2), (2, 3)])
+def test_sampler_histogram_matches_born_weights_with_matter(Lx, Ly):
+    # Two bosons in the 2-boson sector (60 physical states).  On 3x2 a boson
+    # crosses between columns only by the horizontal hops (row values), on
+    # 2x3 between rows only by the vertical hops (strip values); a hop
+    # proposed in one direction only, or accepted with the wrong ratio,
+    # leaves the histogram far from |psi|^2.  The bound is about twice the
+    # total variation that 2240 independent draws from 60 states reach.
+    pe = make_peps(Lx, Ly, 2, 2, seed=41, matter=True)
+    lat = pe.lat
+    basis = lat.physical_basis(n_bosons=2)
+    psi = exact_psi(pe, basis)
+    target = np.abs(psi) ** 2 / np.sum(np.abs(psi) ** 2)
+    index = {tuple(b): i for i, b in enumerate(basis)}
+    counts = np.zeros(len(basis))
+    n_chains, n_sweeps = 16, 150
+    for c in range(n_chains):
+        cfg = random_physical(lat, 100 + c, n_bosons=2)
+        for w in range(n_sweeps):
+            cfg, _, _ = vmc.sweep(pe, cfg, 4, seed=77, chain=c, w=w)
+            if w >= 10:
+                counts[index[tuple(cfg)]] += 1
+    freq = counts / counts.sum()
+    tv = 0.5 * np.abs(freq - target).sum()
+    assert tv < 0.08, (tv, freq, target)
 
 
 @pytest.mark.parametrize("Lx,Ly,N,matter", [(4, 4, 3, False), (4, 4, 2, True), (3, 4, 3, True)])
