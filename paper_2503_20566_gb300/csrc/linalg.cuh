@@ -17,6 +17,50 @@
 
 namespace gcf {
 
+// C (M x N) = A (M x K) B (K x N) in FP32, strided operands in shared or
+// global memory: each thread accumulates 4 x 4 tiles of C in registers, so a
+// multiply-add costs half a load instead of two.  C must not overlap A or B.
+template <class X>
+__device__ __noinline__ void tile_gemm_f32(const X ex, int M, int N, int K, const float* A, int sAm, int sAk,
+                                           const float* B, int sBk, int sBn, float* C, int sCm, int sCn) {
+  const int tm = (M + 3) >> 2, tn = (N + 3) >> 2;
+#pragma unroll 1
+  for (int t = ex.tid(); t < tm * tn; t += ex.size()) {
+    const int i0 = (t / tn) << 2, j0 = (t - (t / tn) * tn) << 2;
+    const float* ap[4];
+    const float* bp[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ap[q] = A + min(i0 + q, M - 1) * sAm;  // rows / columns past the edge repeat the last one
+      bp[q] = B + min(j0 + q, N - 1) * sBn;
+    }
+    float acc[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[q][r] = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < K; ++k) {
+      float a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = ap[q][k * sAk];
+        b[q] = bp[q][k * sBk];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[q][r] = fmaf(a[q], b[r], acc[q][r]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (i0 + q < M && j0 + r < N) C[(i0 + q) * sCm + (j0 + r) * sCn] = acc[q][r];
+  }
+  ex.sync();
+}
+
 // C(i,j) = [C(i,j) +] sum_k op(A)(i,k) op(B)(k,j); op = optional conjugation.
 // TC = false keeps the product in the scalar's own precision whatever the
 // chain's GEMM mode (the factorisations' own products).
@@ -31,6 +75,13 @@ __device__ __noinline__ void cta_gemm(const X ex, int M, int N, int K, const T* 
       else
         mma_gemm<T, GEMM_TF32X3>(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, sCm, sCn, accumulate);
       ex.sync();
+      return;
+    }
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    // the same sum over k in the same order, from register tiles
+    if (!accumulate) {
+      tile_gemm_f32(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, sCm, sCn);
       return;
     }
   }
@@ -194,50 +245,6 @@ __device__ __noinline__ void cta_form_q(const X ex, int m, int k, const T* A, in
     apply_reflector(ex, m, j, A, sm, sn, tau[j], Q, sQm, sQn, j, k);
     ex.sync();
   }
-}
-
-// C (M x N) = A (M x K) B (K x N) in FP32, strided operands in shared or
-// global memory: each thread accumulates 4 x 4 tiles of C in registers, so a
-// multiply-add costs half a load instead of two.  C must not overlap A or B.
-template <class X>
-__device__ __noinline__ void tile_gemm_f32(const X ex, int M, int N, int K, const float* A, int sAm, int sAk,
-                                           const float* B, int sBk, int sBn, float* C, int sCm, int sCn) {
-  const int tm = (M + 3) >> 2, tn = (N + 3) >> 2;
-#pragma unroll 1
-  for (int t = ex.tid(); t < tm * tn; t += ex.size()) {
-    const int i0 = (t / tn) << 2, j0 = (t - (t / tn) * tn) << 2;
-    const float* ap[4];
-    const float* bp[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      ap[q] = A + min(i0 + q, M - 1) * sAm;  // rows / columns past the edge repeat the last one
-      bp[q] = B + min(j0 + q, N - 1) * sBn;
-    }
-    float acc[4][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[q][r] = 0.f;
-#pragma unroll 2
-    for (int k = 0; k < K; ++k) {
-      float a[4], b[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = ap[q][k * sAk];
-        b[q] = bp[q][k * sBk];
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) acc[q][r] = fmaf(a[q], b[r], acc[q][r]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-        if (i0 + q < M && j0 + r < N) C[(i0 + q) * sCm + (j0 + r) * sCn] = acc[q][r];
-  }
-  ex.sync();
 }
 
 // Column length of the column-major FP32 workspaces below: rows rounded up
