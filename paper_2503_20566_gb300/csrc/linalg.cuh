@@ -79,8 +79,9 @@ __device__ __noinline__ void cta_gemm(const X ex, int M, int N, int K, const T* 
     }
   }
   if constexpr (std::is_same<T, float>::value) {
-    // the same sum over k in the same order, from register tiles
-    if (!accumulate) {
+    // the same sum over k in the same order, from register tiles, when the
+    // product has a 4 x 4 tile for every thread
+    if (!accumulate && M >= 4 && (long long)M * N >= 16LL * ex.size()) {
       tile_gemm_f32(ex, M, N, K, A, sAm, sAk, B, sBk, sBn, C, sCm, sCn);
       return;
     }
@@ -346,8 +347,11 @@ __device__ __noinline__ void qr_cm(const X ex, int m, int n, float* A, int lda, 
         }
         // every lane of the warp joins the shuffles; only the pivot's lanes
         // hold non-zero parts
-        nn = lanes_sum(nn, L);
-        al = lanes_sum(al, L);
+#pragma unroll 1
+        for (int o = L >> 1; o > 0; o >>= 1) {
+          nn += __shfl_xor_sync(0xffffffffu, nn, o);
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+        }
         if (next && li == 0) {
           pub[2 * ((j + 1) & 1)] = al;
           pub[2 * ((j + 1) & 1) + 1] = nn;
@@ -677,9 +681,13 @@ __device__ __noinline__ int jacobi_svd_cm(const X ex, int p, int q, float* W, in
             g = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, g))));
           }
         }
-        al = lanes_sum(al, L);
-        be = lanes_sum(be, L);
-        g = lanes_sum(g, L);
+        // the three sums together, offsets L/2 .. 1 as in lanes_sum
+#pragma unroll 1
+        for (int o = L >> 1; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
         const float ga = fabsf(g);
         if (!act || ga == 0.f || !(al > negl) || !(be > negl) || !(ga > tol * (sqrtf(al) * sqrtf(be)))) continue;
         const float iga = jrcp(ga);
