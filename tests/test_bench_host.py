@@ -47,6 +47,34 @@ def test_traffic_only_for_the_captured_form(tmp_path):
     assert bench.profiled_traffic(1000, kernel, level, wl, str(tmp_path)) is None
 
 
+def test_traffic_fields_in_markdown_code_spans(tmp_path):
+    """The profiles write their fields as Markdown code spans: the closing
+    backtick is not part of the workload name."""
+    kernel, level, wl = "gcf::vmc_kernel_multi4<float>", 0, "z2_a+b_D4"
+    (tmp_path / "k.md").write_text(f"`workload: {wl}`\n`source_sha256: {bench.source_hash()}`\n"
+                                   f"`kernel_form: {kernel} level {level}`\n`traffic_bytes_per_sample: 1.5e8`\n")
+    assert bench.profiled_traffic(10, kernel, level, wl, str(tmp_path)) == pytest.approx(1.5e9)
+
+
+def test_committed_profiles_name_bench_workloads():
+    """Every committed profile with a workload line names a bench workload
+    and carries the other three fields."""
+    pdir = os.path.join(os.path.dirname(CSRC), "..", "profiles")
+    names = {w["workload"] for w in bench.WORKLOADS.values()}
+    seen = 0
+    for name in sorted(os.listdir(pdir)):
+        txt = open(os.path.join(pdir, name)).read()
+        m = re.search(r"workload: ([^\s`]+)", txt)
+        if not m:
+            continue
+        seen += 1
+        assert m.group(1) in names, (name, m.group(1))
+        for field in (r"source_sha256: [0-9a-f]{16}", r"kernel_form: \S+ level \d+",
+                      r"traffic_bytes_per_sample: [0-9.eE+]+"):
+            assert re.search(field, txt), (name, field)
+    assert seen >= 1
+
+
 def test_workloads_follow_the_stated_configurations():
     """The default workload is the mixed-size Z2 + bosons one: 16384 chains
     over 16x16 / 24x24 / 32x32, D = 4, chi = 24, half filling."""
