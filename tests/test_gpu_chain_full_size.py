@@ -2,9 +2,10 @@
 
 Z2 gauge field + hard-core bosons at half filling, D = 4 (D_k = 2), chi = 24
 (every boundary-MPS bond truncated from 48), (h, g, J) = (1, 0.33, 0.5): the
-largest lattices of the benchmark workload, 16x16 and 32x32.  The library's
-FP64 form samples the chains with gcf_sample_batch (plaquette pass, both hop
-passes, then the measurement) and the oracle replays them from the same
+largest lattices of the benchmark workload, 16x16 and 32x32; and pure Z3 on
+16x16, D = 6, chi = 32, complex tensors, g = 0.375 (the Z3 workload).  The
+library's FP64 form samples the chains with gcf_sample_batch (plaquette pass,
+both hop passes with matter, then the measurement) and the oracle replays them from the same
 starting configurations with the same SplitMix64 counters (Sec. S-1 sweep,
 Eq. S2 E_loc).  In FP64 every Metropolis ratio agrees to ~1e-12, far from any
 acceptance threshold, so the configurations after every sweep and the
@@ -23,18 +24,21 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-CASES = [(16, 2, 2), (32, 1, 1)]  # (L, chains, sweeps)
+# (L, N, D, chi, matter, complex, g, chains, sweeps)
+CASES = [(16, 2, 4, 24, True, False, 0.33, 2, 2), (32, 2, 4, 24, True, False, 0.33, 1, 1),
+         (16, 3, 6, 32, False, True, 0.375, 1, 1)]
 
 
-@pytest.mark.parametrize("L,n_chains,n_sweeps", CASES, ids=["16x16", "32x32"])
-def test_full_size_chains_replay_the_oracle(L, n_chains, n_sweeps):
+@pytest.mark.parametrize("L,N,D,chi,matter,cplx,g,n_chains,n_sweeps", CASES,
+                         ids=["16x16-Z2-bosons", "32x32-Z2-bosons", "16x16-Z3-complex"])
+def test_full_size_chains_replay_the_oracle(L, N, D, chi, matter, cplx, g, n_chains, n_sweeps):
     import paper_2503_20566_gb300 as G
 
-    h, g, J, chi = 1.0, 0.33, 0.5, 24
-    lat, pe, vals = oracle_net(L, L, 2, 4, 5, matter=True, precision="fp64")
-    ctx = G.Context(2, L, L, 4, chi, matter=True, h=h, g=g, J=J, precision="fp64", seed=5)
+    h, J = 1.0, (0.5 if matter else 0.0)
+    lat, pe, vals = oracle_net(L, L, N, D, 5, complex_=cplx, matter=matter, precision="fp64")
+    ctx = G.Context(N, L, L, D, chi, matter=matter, h=h, g=g, J=J, complex_=cplx, precision="fp64", seed=5)
     ctx.set_tensors(vals)
-    cfgs, _, _ = configs_for(lat, n_chains, seed=6, n_bosons=L * L // 2)
+    cfgs, _, _ = configs_for(lat, n_chains, seed=6, n_bosons=L * L // 2 if matter else 0)
     dev = torch.from_numpy(cfgs).cuda()
     out = ctx.sample_batch(dev, n_sweeps, seed=77)
     torch.cuda.synchronize()
@@ -56,6 +60,6 @@ def test_full_size_chains_replay_the_oracle(L, n_chains, n_sweeps):
             s = c * n_sweeps + w
             worst_amp = max(worst_amp, amp_err(la[s], ph[s], rec["log_abs"], rec["phase"]))
             worst_e = max(worst_e, abs(e[s] - rec["e_loc"]) / max(1.0, abs(rec["e_loc"])))
-    print(f"{L}x{L}: {n_chains} chains x {n_sweeps} sweeps, {int(prop.sum())} moves proposed, "
+    print(f"{L}x{L} Z{N}: {n_chains} chains x {n_sweeps} sweeps, {int(prop.sum())} moves proposed, "
           f"{int(acc.sum())} accepted; amplitude error max {worst_amp:.1e}, E_loc {worst_e:.1e}")
     assert worst_amp < 1e-7 and worst_e < 1e-7, (worst_amp, worst_e)
