@@ -21,9 +21,10 @@ variational energy of the optimised state, free of sampling error:
 * the last step's sampled <E> is within 1e-4 per site of that exact energy.
 
 The precision reached is printed beside the paper's.  The sampled
-optimisation does not always reach it: in five runs (FP64 and FP32, 4 or 8
-sweeps per step, several seeds) three came within 1e-9 per site of the ED
-energy, and two stopped 2.7e-4 and 3.7e-4 above it.  The two that stopped
+optimisation does not always reach it: in nine runs (FP64 and FP32, 4 or 8
+sweeps per step, several seeds) five came within 1e-9 per site of the ED
+energy, one 7.8e-7 above it, and three stopped 2.0e-4 to 3.7e-4 above it.
+The three that stopped
 show the signature of a sign structure the samples cannot move (the
 fixed-node situation of real-valued VMC): the sampled <E> lies about 8e-6 per
 site below the state's exact energy with an error bar near 1e-7, because the
