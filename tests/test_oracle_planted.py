@@ -142,9 +142,9 @@ CASES = [
     ("horizontal-hop-ratio-inverted", vmc, "sweep",
      "_accept(u, _row_value(peps, c2, r, Bm, Tm), _row_value(peps, cfg, r, Bm, Tm))",
      "_accept(u, _row_value(peps, cfg, r, Bm, Tm), _row_value(peps, c2, r, Bm, Tm))",
-     lambda mp: TV.test_sampler_histogram_matches_born_weights_with_matter(3, 2)),
+     lambda mp: TV.test_sampler_histogram_matches_born_weights_with_matter(3, 2, n_sweeps=60)),
     ("vertical-hops-never-proposed", vmc, "sweep", "c2 = lat.hop(cfg, x, r, 2)", "c2 = None",
-     lambda mp: TV.test_sampler_histogram_matches_born_weights_with_matter(2, 3)),
+     lambda mp: TV.test_sampler_histogram_matches_born_weights_with_matter(2, 3, n_sweeps=60)),
     ("sr-matrix-missing-conjugate", vmc, "sr_matrices", "(O.conj().T * w) @ O", "(O.T * w) @ O",
      lambda mp: TV.test_cg_equals_dense_solve_and_residual()),
     ("cg-direction-update", vmc, "cg_solve", "(rs_new / rs) * p", "(rs / rs_new) * p",

@@ -165,13 +165,15 @@ def test_sampler_histogram_matches_born_weights(Lx, Ly, N, tv_max):
 
 
 @pytest.mark.parametrize("Lx,Ly", [(3, 2), (2, 3)])
-def test_sampler_histogram_matches_born_weights_with_matter(Lx, Ly):
+def test_sampler_histogram_matches_born_weights_with_matter(Lx, Ly, n_sweeps=150):
     # Two bosons in the 2-boson sector (60 physical states).  On 3x2 a boson
     # crosses between columns only by the horizontal hops (row values), on
     # 2x3 between rows only by the vertical hops (strip values); a hop
     # proposed in one direction only, or accepted with the wrong ratio,
     # leaves the histogram far from |psi|^2.  The bound is about twice the
-    # total variation that 2240 independent draws from 60 states reach.
+    # total variation that 2240 independent draws from 60 states reach (the
+    # planted-mistake test runs the pin with fewer sweeps: the mistakes miss
+    # it by far more).
     pe = make_peps(Lx, Ly, 2, 2, seed=41, matter=True)
     lat = pe.lat
     basis = lat.physical_basis(n_bosons=2)
@@ -179,7 +181,7 @@ def test_sampler_histogram_matches_born_weights_with_matter(Lx, Ly):
     target = np.abs(psi) ** 2 / np.sum(np.abs(psi) ** 2)
     index = {tuple(b): i for i, b in enumerate(basis)}
     counts = np.zeros(len(basis))
-    n_chains, n_sweeps = 16, 150
+    n_chains = 16
     for c in range(n_chains):
         cfg = random_physical(lat, 100 + c, n_bosons=2)
         for w in range(n_sweeps):
